@@ -1,0 +1,558 @@
+"""Plain FP64 CPU oracle for the Newton power-flow iteration.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or
+link this module: only the test suite, the smoke check and the CPU-baseline leg
+of the benchmark use it.  It shares no code with the CUDA library; the only
+common input is the seeded case description drawn by the case generators.
+
+What it computes, in the paper's notation (arXiv 1711.10579):
+
+* ``ybus_single``        nodal admittance matrix, Eq. 2-3, pi-model branches.
+* ``power_polar``        P_i, Q_i in polar form, Eq. 6-7 (term by term).
+* ``mismatch_polar``     Delta P, Delta Q, Eq. 8-9 (with ZIP loads, Eq. 14-15).
+* ``jacobian_polar``     [J1 J2; J3 J4] of Eq. 10, first derivatives of Eq. 6-7.
+* ``newton_polar``       single-phase Newton-Raphson (Sec. II.A algorithm box).
+* ``ybus_three_phase``   3x3 complex block admittance matrix, Eq. 11.
+* ``cim_mismatch``       current mismatch Delta I, Eq. 12-19.
+* ``cim_jacobian``       6x6 real blocks of Eq. 21-23.
+* ``newton_cim``         three-phase current-injection Newton (Sec. II.B box).
+* ``ilu0`` / ``gmres``   ILU(0) and restarted, right-preconditioned GMRES used
+                         by the Newton-Krylov variant (Sec. III.B).
+
+Readings of points the paper leaves open (the same list is kept with the
+design notes):
+
+* line charging: pi model, total charging b split b/2 to each end (Eq. 2 sums
+  over j = 0, the ground);
+* theta_ij is the angle of Y_ij and delta_i the angle of bus i (the only way
+  Eq. 6-7 are consistent);
+* unknowns: angles of PV and PQ buses, magnitudes of PQ buses; the slack is
+  fixed (Eq. 10);
+* stop test: infinity norm of the power mismatch <= tol (default 1e-8 pu),
+  checked before each solve, in place of the unnamed step thresholds;
+* ZIP coefficients are the load at |V| = 1 pu split by fractions
+  (constant power, constant current, constant impedance), Eq. 14-15;
+* three-phase: every node has three phase slots; absent phases and the
+  source node carry no unknowns; the source is an ideal balanced source;
+  loads are wye-connected; no PV buses (Sec. II.B);
+* the diagonal adjustments a, b, c, d of Eq. 23 are the derivatives of the
+  specified current (Eq. 17) with respect to the real and imaginary voltage,
+  so that J is the exact Jacobian of Y V - I_sp in the ordering of Eq. 19-20;
+* flat start: |V| = set point or 1 pu, angle 0 (three-phase: balanced
+  1 pu at 0, -120, +120 degrees).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+SLACK, PV, PQ = 0, 1, 2
+
+
+# =============================================================================
+# single phase, polar form (Sec. II.A)
+# =============================================================================
+
+def ybus_single(case) -> sp.csr_matrix:
+    """Eq. 2-3: Y_ii = sum of admittances at bus i (incl. ground), Y_ij = -y_ij.
+
+    Each branch is a pi model: series admittance y = 1/(r + jx) and half of
+    the total line charging j b/2 to ground at each end.
+    """
+    n = case.n_bus
+    rows, cols, vals = [], [], []
+    for f, t, r, x, b in zip(case.br_from, case.br_to, case.br_r, case.br_x,
+                             case.br_b):
+        y = 1.0 / complex(r, x)
+        sh = complex(0.0, b / 2.0)
+        rows += [f, t, f, t]
+        cols += [f, t, t, f]
+        vals += [y + sh, y + sh, -y, -y]
+    Y = sp.coo_matrix((np.asarray(vals, dtype=np.complex128),
+                       (np.asarray(rows), np.asarray(cols))), shape=(n, n))
+    return Y.tocsr()  # duplicates are summed
+
+
+def specified_power(case, vm):
+    """Eq. 12-15: specified injection = generation - ZIP load at |V|."""
+    zp, zi, zz = case.zip[:, 0], case.zip[:, 1], case.zip[:, 2]
+    shape = zp + zi * vm + zz * vm * vm
+    return case.p_gen - case.p_load * shape, case.q_gen - case.q_load * shape
+
+
+def specified_power_dvm(case, vm):
+    """Derivative of the specified power (Eq. 12-15) with respect to |V_i|."""
+    zi, zz = case.zip[:, 1], case.zip[:, 2]
+    dshape = zi + 2.0 * zz * vm
+    return -case.p_load * dshape, -case.q_load * dshape
+
+
+def power_polar(Y, vm, va):
+    """Eq. 6-7: P_i and Q_i summed over the nonzeros of row i of Y."""
+    Yc = Y.tocoo()
+    i, j = Yc.row, Yc.col
+    mag = np.abs(Yc.data)
+    th = np.angle(Yc.data)
+    ang = th - va[i] + va[j]
+    n = vm.size
+    P = np.bincount(i, weights=vm[i] * vm[j] * mag * np.cos(ang), minlength=n)
+    Q = -np.bincount(i, weights=vm[i] * vm[j] * mag * np.sin(ang), minlength=n)
+    return P, Q
+
+
+def unknowns_polar(case):
+    """Rows/columns of Eq. 10: angle of every PV and PQ bus, |V| of every PQ."""
+    pvpq = np.flatnonzero(case.bus_type != SLACK)
+    pq = np.flatnonzero(case.bus_type == PQ)
+    return pvpq, pq
+
+
+def mismatch_polar(case, Y, vm, va):
+    """Eq. 8-9 stacked as [Delta P (PV, PQ); Delta Q (PQ)]."""
+    pvpq, pq = unknowns_polar(case)
+    P, Q = power_polar(Y, vm, va)
+    Psp, Qsp = specified_power(case, vm)
+    return np.concatenate([(Psp - P)[pvpq], (Qsp - Q)[pq]])
+
+
+def jacobian_polar(case, Y, vm, va) -> sp.csr_matrix:
+    """Eq. 10: derivatives of P_calc - P_sp and Q_calc - Q_sp (Eq. 6-9).
+
+    Off-diagonal entries (j != i), with a = theta_ij - delta_i + delta_j:
+        dP_i/d delta_j = -|V_i||V_j||Y_ij| sin a
+        dQ_i/d delta_j = -|V_i||V_j||Y_ij| cos a
+        dP_i/d |V_j|  =  |V_i||Y_ij| cos a
+        dQ_i/d |V_j|  = -|V_i||Y_ij| sin a
+    Diagonal entries collect the j != i terms of the same derivatives taken
+    with respect to bus i plus the j = i term of Eq. 6-7, and subtract the
+    derivative of the ZIP load (Eq. 14-15).
+    """
+    n = case.n_bus
+    Yc = Y.tocoo()
+    i, j = Yc.row, Yc.col
+    mag = np.abs(Yc.data)
+    th = np.angle(Yc.data)
+    ang = th - va[i] + va[j]
+    off = i != j
+    io, jo, mo, ao = i[off], j[off], mag[off], ang[off]
+
+    # off-diagonal derivatives
+    dP_dd = -vm[io] * vm[jo] * mo * np.sin(ao)
+    dQ_dd = -vm[io] * vm[jo] * mo * np.cos(ao)
+    dP_dv = vm[io] * mo * np.cos(ao)
+    dQ_dv = -vm[io] * mo * np.sin(ao)
+
+    # diagonal derivatives
+    d = ~off
+    yii = np.zeros(n)
+    th_ii = np.zeros(n)
+    yii[i[d]] = mag[d]
+    th_ii[i[d]] = th[d]
+    dPi_ddi = np.bincount(io, weights=vm[io] * vm[jo] * mo * np.sin(ao), minlength=n)
+    dQi_ddi = np.bincount(io, weights=vm[io] * vm[jo] * mo * np.cos(ao), minlength=n)
+    dPi_dvi = (np.bincount(io, weights=vm[jo] * mo * np.cos(ao), minlength=n)
+               + 2.0 * vm * yii * np.cos(th_ii))
+    dQi_dvi = (-np.bincount(io, weights=vm[jo] * mo * np.sin(ao), minlength=n)
+               - 2.0 * vm * yii * np.sin(th_ii))
+    dPsp, dQsp = specified_power_dvm(case, vm)
+    dPi_dvi = dPi_dvi - dPsp
+    dQi_dvi = dQi_dvi - dQsp
+
+    # full 2n x 2n matrix in (delta, |V|) x (P, Q) order, then select Eq. 10
+    rows = np.concatenate([io, io, n + io, n + io,
+                           np.arange(n), np.arange(n), n + np.arange(n), n + np.arange(n)])
+    cols = np.concatenate([jo, n + jo, jo, n + jo,
+                           np.arange(n), n + np.arange(n), np.arange(n), n + np.arange(n)])
+    vals = np.concatenate([dP_dd, dP_dv, dQ_dd, dQ_dv,
+                           dPi_ddi, dPi_dvi, dQi_ddi, dQi_dvi])
+    J = sp.coo_matrix((vals, (rows, cols)), shape=(2 * n, 2 * n)).tocsr()
+    pvpq, pq = unknowns_polar(case)
+    sel = np.concatenate([pvpq, n + pq])
+    return J[sel][:, sel].tocsr()
+
+
+def flat_start_polar(case):
+    """Initial guess: set-point magnitudes (1 pu for PQ), zero angles."""
+    vm = np.where(case.bus_type == PQ, 1.0, case.v_set).astype(np.float64)
+    return vm, np.zeros(case.n_bus)
+
+
+def newton_polar(case, tol=1e-8, max_iter=30, linear="splu", vm0=None,
+                 va0=None, gmres_restart=30, gmres_tol=1e-10, Y=None):
+    """Single-phase Newton-Raphson, Sec. II.A algorithm box.
+
+    Each iteration evaluates the mismatch (Eq. 8-9), stops when its infinity
+    norm is <= ``tol``, otherwise builds the Jacobian (Eq. 10), solves for
+    (Delta delta, Delta |V|) and updates the angles of PV/PQ buses and the
+    magnitudes of PQ buses.  ``linear`` picks the solve of Eq. 10:
+    ``"splu"`` SuperLU with COLAMD ordering (Sec. III.A, the paper's solver),
+    ``"dense"`` LAPACK partial-pivoting LU, ``"gmres"`` restarted GMRES with an
+    ILU(0) preconditioner on a bandwidth-reducing ordering (Sec. III.B).
+
+    Returns dict(vm, va, iterations, mismatch, history, steps, converged).
+    """
+    if Y is None:
+        Y = ybus_single(case)
+    vm, va = flat_start_polar(case)
+    if vm0 is not None:
+        vm = np.array(vm0, dtype=np.float64)
+    if va0 is not None:
+        va = np.array(va0, dtype=np.float64)
+    pvpq, pq = unknowns_polar(case)
+    npvpq = pvpq.size
+    history, steps = [], []
+    k = 0
+    converged = False
+    while True:
+        F = mismatch_polar(case, Y, vm, va)
+        norm = float(np.max(np.abs(F))) if F.size else 0.0
+        history.append(norm)
+        if not np.isfinite(norm):
+            break
+        if norm <= tol:
+            converged = True
+            break
+        if k >= max_iter:
+            break
+        k += 1
+        J = jacobian_polar(case, Y, vm, va)
+        dx = solve_linear(J, F, linear, gmres_restart, gmres_tol)
+        va[pvpq] += dx[:npvpq]
+        vm[pq] += dx[npvpq:]
+        steps.append(float(np.max(np.abs(dx))) if dx.size else 0.0)
+    return dict(vm=vm, va=va, iterations=k, mismatch=history[-1],
+                history=history, steps=steps, converged=converged)
+
+
+def solve_linear(J, F, linear="splu", restart=30, tol=1e-10):
+    """Solve J dx = F with the chosen method (see ``newton_polar``)."""
+    if F.size == 0:
+        return F.copy()
+    if linear == "dense":
+        return np.linalg.solve(J.toarray(), F)
+    if linear == "splu":
+        return spla.splu(J.tocsc(), permc_spec="COLAMD").solve(F)
+    if linear == "gmres":
+        from scipy.sparse.csgraph import reverse_cuthill_mckee
+        p = reverse_cuthill_mckee(J.tocsr(), symmetric_mode=False)
+        Jp = J.tocsr()[p][:, p].tocsr()
+        L, U = ilu0(Jp)
+        y, _ = gmres(Jp, F[p], L, U, restart=restart, tol=tol,
+                     max_restarts=200)
+        dx = np.empty_like(y)
+        dx[p] = y
+        return dx
+    raise ValueError(linear)
+
+
+# =============================================================================
+# Krylov pieces for the Newton-Krylov variant (Sec. III.B)
+# =============================================================================
+
+def ilu0(A):
+    """ILU(0): unit-lower L and upper U restricted to the pattern of A.
+
+    Row-by-row elimination where an update a_ij -= l_ik u_kj is kept only if
+    (i, j) is already a nonzero of A, so that (L U)_ij = A_ij on the pattern.
+    Plain Python loops over the sparse rows: for small and medium matrices.
+    """
+    A = A.tocsr().astype(np.float64)
+    A.sort_indices()
+    n = A.shape[0]
+    indptr, indices = A.indptr, A.indices
+    vals = A.data.copy()
+    pos = [dict(zip(indices[indptr[i]:indptr[i + 1]].tolist(),
+                    range(indptr[i], indptr[i + 1]))) for i in range(n)]
+    diag = np.array([pos[i][i] for i in range(n)])
+    for i in range(n):
+        row = pos[i]
+        for p in range(indptr[i], indptr[i + 1]):
+            k = indices[p]
+            if k >= i:
+                break
+            vals[p] /= vals[diag[k]]
+            lik = vals[p]
+            for q in range(diag[k] + 1, indptr[k + 1]):
+                j = indices[q]
+                t = row.get(j)
+                if t is not None:
+                    vals[t] -= lik * vals[q]
+    LU = sp.csr_matrix((vals, indices.copy(), indptr.copy()), shape=A.shape)
+    L = sp.tril(LU, k=-1, format="csr") + sp.eye(n, format="csr")
+    U = sp.triu(LU, k=0, format="csr")
+    return L.tocsr(), U.tocsr()
+
+
+def gmres(A, b, L=None, U=None, restart=30, tol=1e-10, max_restarts=100,
+          x0=None):
+    """Restarted GMRES(m) with right preconditioning M = L U.
+
+    Arnoldi with modified Gram-Schmidt, Givens rotations on the Hessenberg
+    matrix, stop when the residual norm <= tol * ||b||.  Returns (x, iters).
+    """
+    from scipy.sparse.linalg import spsolve_triangular
+
+    def apply_minv(v):
+        if L is None:
+            return v
+        y = spsolve_triangular(L, v, lower=True, unit_diagonal=True)
+        return spsolve_triangular(U, y, lower=False)
+
+    n = b.size
+    x = np.zeros(n) if x0 is None else x0.astype(np.float64).copy()
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros(n), 0
+    total = 0
+    for _ in range(max_restarts):
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        if beta <= tol * bnorm:
+            break
+        m = restart
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k_used = 0
+        for k in range(m):
+            w = A @ apply_minv(V[k])
+            for i in range(k + 1):
+                H[i, k] = V[i] @ w
+                w = w - H[i, k] * V[i]
+            H[k + 1, k] = np.linalg.norm(w)
+            if H[k + 1, k] != 0.0:
+                V[k + 1] = w / H[k + 1, k]
+            for i in range(k):
+                t = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
+                H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]
+                H[i, k] = t
+            den = math.hypot(H[k, k], H[k + 1, k])
+            cs[k] = H[k, k] / den
+            sn[k] = H[k + 1, k] / den
+            H[k, k] = den
+            H[k + 1, k] = 0.0
+            g[k + 1] = -sn[k] * g[k]
+            g[k] = cs[k] * g[k]
+            k_used = k + 1
+            total += 1
+            if abs(g[k + 1]) <= tol * bnorm:
+                break
+        y = np.zeros(k_used)
+        for i in range(k_used - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k_used] @ y[i + 1:]) / H[i, i]
+        x = x + apply_minv(V[:k_used].T @ y)
+    return x, total
+
+
+# =============================================================================
+# three phase, current injection method (Sec. II.B)
+# =============================================================================
+
+def _phase_list(mask):
+    return [s for s in range(3) if (int(mask) >> s) & 1]
+
+
+def ybus_three_phase(case) -> sp.csr_matrix:
+    """Eq. 11: 3x3 complex blocks; phase s of node i sits at row 3 i + s.
+
+    A branch's admittance is the inverse of the submatrix of its series
+    impedance over the phases present on that branch.
+    """
+    n = case.n_node
+    rows, cols, vals = [], [], []
+    for e in range(case.n_branch):
+        f, t = int(case.br_from[e]), int(case.br_to[e])
+        ph = _phase_list(case.br_phases[e])
+        Zs = case.br_z[e][np.ix_(ph, ph)]
+        Yb = np.linalg.inv(Zs)
+        for a, pa in enumerate(ph):
+            for c, pc in enumerate(ph):
+                y = Yb[a, c]
+                rows += [3 * f + pa, 3 * t + pa, 3 * f + pa, 3 * t + pa]
+                cols += [3 * f + pc, 3 * t + pc, 3 * t + pc, 3 * f + pc]
+                vals += [y, y, -y, -y]
+    Y = sp.coo_matrix((np.asarray(vals, dtype=np.complex128),
+                       (np.asarray(rows), np.asarray(cols))), shape=(3 * n, 3 * n))
+    return Y.tocsr()
+
+
+def cim_free_slots(case):
+    """Phase slots that carry unknowns: present phases of non-source nodes."""
+    mask = np.zeros(3 * case.n_node, dtype=bool)
+    for i in range(case.n_node):
+        if i == case.source:
+            continue
+        for s in _phase_list(case.phases[i]):
+            mask[3 * i + s] = True
+    return mask
+
+
+def cim_flat_start(case):
+    """Balanced v_source at 0, -120, +120 degrees on every present phase."""
+    rot = np.exp(-2j * np.pi / 3 * np.arange(3))
+    V = np.zeros(3 * case.n_node, dtype=np.complex128)
+    for i in range(case.n_node):
+        for s in _phase_list(case.phases[i]):
+            V[3 * i + s] = case.v_source * rot[s]
+    return V
+
+
+def cim_specified_power(case, V):
+    """Eq. 12-15 per phase slot: S_sp = -(ZIP load at |V|); no generators."""
+    vm = np.abs(V)
+    zp = np.repeat(case.zip[:, 0], 3)
+    zi = np.repeat(case.zip[:, 1], 3)
+    zz = np.repeat(case.zip[:, 2], 3)
+    shape = zp + zi * vm + zz * vm * vm
+    return -(case.p_load.reshape(-1) * shape) - 1j * (case.q_load.reshape(-1) * shape)
+
+
+def cim_specified_current(case, V):
+    """Eq. 17: I_sp = conj(S_sp / V) on free slots, 0 elsewhere."""
+    free = cim_free_slots(case)
+    S = cim_specified_power(case, V)
+    I = np.zeros_like(V)
+    I[free] = np.conj(S[free] / V[free])
+    return I
+
+
+def cim_mismatch(case, Y, V):
+    """Eq. 16, 18, 19: Delta I = I_sp - Y V, per node as [Im a,b,c, Re a,b,c].
+
+    Returns the full 6 n vector; entries of absent phases and of the source
+    are zero.
+    """
+    free = cim_free_slots(case)
+    dI = cim_specified_current(case, V) - Y @ V
+    dI = np.where(free, dI, 0.0)
+    n = case.n_node
+    out = np.empty((n, 6))
+    d3 = dI.reshape(n, 3)
+    out[:, :3] = d3.imag
+    out[:, 3:] = d3.real
+    return out.reshape(-1)
+
+
+def cim_power_mismatch(case, Y, V):
+    """Delta S = V conj(Delta I) = S_sp - V conj(Y V) on free slots."""
+    free = cim_free_slots(case)
+    dS = cim_specified_power(case, V) - V * np.conj(Y @ V)
+    return np.where(free, dS, 0.0)
+
+
+def cim_load_derivatives(case, V):
+    """a, b, c, d of Eq. 23 per phase slot.
+
+    With S_sp = P + jQ a function of m = |V| (Eq. 14-15) and
+    I_sp = conj(S_sp) V / m^2 (Eq. 17):
+        Re I_sp = (P Vr + Q Vi) / m^2,  Im I_sp = (P Vi - Q Vr) / m^2.
+    a = d Im/d Vr, b = d Im/d Vi, c = d Re/d Vr, d = d Re/d Vi by the product
+    rule, using dm/dVr = Vr/m, dm/dVi = Vi/m.
+    """
+    Vr, Vi = V.real, V.imag
+    m = np.abs(V)
+    zp = np.repeat(case.zip[:, 0], 3)
+    zi = np.repeat(case.zip[:, 1], 3)
+    zz = np.repeat(case.zip[:, 2], 3)
+    pl = case.p_load.reshape(-1)
+    ql = case.q_load.reshape(-1)
+    P = -pl * (zp + zi * m + zz * m * m)
+    Q = -ql * (zp + zi * m + zz * m * m)
+    dP = -pl * (zi + 2.0 * zz * m)  # dP/dm
+    dQ = -ql * (zi + 2.0 * zz * m)
+    free = cim_free_slots(case)
+    safe_m = np.where(free, m, 1.0)
+    g = 1.0 / safe_m ** 2
+    dg = -2.0 / safe_m ** 3
+    dm_dr = np.where(free, Vr / safe_m, 0.0)
+    dm_di = np.where(free, Vi / safe_m, 0.0)
+    re_num = P * Vr + Q * Vi
+    im_num = P * Vi - Q * Vr
+    c = g * (P + (dP * Vr + dQ * Vi) * dm_dr) + re_num * dg * dm_dr
+    d = g * (Q + (dP * Vr + dQ * Vi) * dm_di) + re_num * dg * dm_di
+    a = g * (-Q + (dP * Vi - dQ * Vr) * dm_dr) + im_num * dg * dm_dr
+    b = g * (P + (dP * Vi - dQ * Vr) * dm_di) + im_num * dg * dm_di
+    z = ~free
+    for arr in (a, b, c, d):
+        arr[z] = 0.0
+    return a, b, c, d
+
+
+def cim_jacobian(case, Y, V) -> sp.csr_matrix:
+    """Eq. 21-23 as a 6n x 6n real matrix.
+
+    Node-pair block (rows [Im a,b,c; Re a,b,c], columns [Re a,b,c; Im a,b,c]):
+    [[B, G], [G, -B]] with G + jB the 3x3 block of Y (Eq. 21); on the
+    diagonal a, b, c, d are subtracted (Eq. 23).
+    """
+    n = case.n_node
+    Yc = Y.tocoo()
+    r, c_, v = Yc.row, Yc.col, Yc.data
+    ni, si = r // 3, r % 3
+    nj, sj = c_ // 3, c_ % 3
+    G, B = v.real, v.imag
+    rows = np.concatenate([6 * ni + si, 6 * ni + si, 6 * ni + 3 + si, 6 * ni + 3 + si])
+    cols = np.concatenate([6 * nj + sj, 6 * nj + 3 + sj, 6 * nj + sj, 6 * nj + 3 + sj])
+    vals = np.concatenate([B, G, G, -B])
+    a, b, c, d = cim_load_derivatives(case, V)
+    k = np.arange(3 * n)
+    nk, sk = k // 3, k % 3
+    rows = np.concatenate([rows, 6 * nk + sk, 6 * nk + sk, 6 * nk + 3 + sk, 6 * nk + 3 + sk])
+    cols = np.concatenate([cols, 6 * nk + sk, 6 * nk + 3 + sk, 6 * nk + sk, 6 * nk + 3 + sk])
+    vals = np.concatenate([vals, -a, -b, -c, -d])
+    return sp.coo_matrix((vals, (rows, cols)), shape=(6 * n, 6 * n)).tocsr()
+
+
+def cim_unknowns(case):
+    """Indices into the 6n ordering of Eq. 20 that are free unknowns."""
+    free = cim_free_slots(case).reshape(case.n_node, 3)
+    mask = np.concatenate([free, free], axis=1).reshape(-1)
+    return np.flatnonzero(mask)
+
+
+def newton_cim(case, tol=1e-8, max_iter=30, linear="splu", V0=None,
+               gmres_restart=30, gmres_tol=1e-10, Y=None):
+    """Three-phase current-injection Newton, Sec. II.B algorithm box.
+
+    Each iteration forms Delta I (Eq. 12-20), stops when the power mismatch
+    V conj(Delta I) has infinity norm (over real and imaginary parts) <= tol,
+    otherwise solves J Delta V = Delta I (Eq. 22-23) on the free unknowns,
+    adds Delta V to the rectangular voltages and forms the complex V again.
+    """
+    if Y is None:
+        Y = ybus_three_phase(case)
+    V = cim_flat_start(case) if V0 is None else np.array(V0, dtype=np.complex128)
+    idx = cim_unknowns(case)
+    n = case.n_node
+    history, steps = [], []
+    k = 0
+    converged = False
+    while True:
+        dS = cim_power_mismatch(case, Y, V)
+        norm = float(max(np.max(np.abs(dS.real)), np.max(np.abs(dS.imag))))
+        history.append(norm)
+        if not np.isfinite(norm):
+            break
+        if norm <= tol:
+            converged = True
+            break
+        if k >= max_iter:
+            break
+        k += 1
+        F = cim_mismatch(case, Y, V)[idx]
+        J = cim_jacobian(case, Y, V)[idx][:, idx].tocsr()
+        dx = solve_linear(J, F, linear, gmres_restart, gmres_tol)
+        full = np.zeros(6 * n)
+        full[idx] = dx
+        full = full.reshape(n, 6)
+        V = V + (full[:, :3] + 1j * full[:, 3:]).reshape(-1)
+        steps.append(float(np.max(np.abs(dx))) if dx.size else 0.0)
+    return dict(V=V, iterations=k, mismatch=history[-1], history=history,
+                steps=steps, converged=converged)

@@ -1,0 +1,400 @@
+"""Pins of the FP64 oracle to facts other than itself.
+
+Each test ties one part of the oracle to a closed form, a physical identity,
+a brute-force or library computation, or an invariant, chosen so that a
+dropped term, a wrong sign or index, or a transposed operand in the oracle
+fails at least one of them.  CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.sparse as sp
+
+from oracle import pf_oracle as O
+from paper_1711_10579_gb300 import cases
+
+
+# -----------------------------------------------------------------------------
+# single phase
+# -----------------------------------------------------------------------------
+
+def two_bus_pq_closed_form(P, Q, r, x, v1=1.0):
+    """|V2| and angle of a load P + jQ fed through z = r + jx from v1 at 0.
+
+    From v1 = V2 + z conj(S / V2): with u = |V2|^2, a = rP + xQ, c = xP - rQ,
+    u^2 + (2a - v1^2) u + (r^2 + x^2)(P^2 + Q^2) = 0; the operable root is the
+    larger one, and delta2 = -atan2(c, u + a).
+    """
+    a = r * P + x * Q
+    c = x * P - r * Q
+    disc = (v1 * v1 - 2 * a) ** 2 - 4 * (r * r + x * x) * (P * P + Q * Q)
+    assert disc > 0, "load beyond the nose of the PV curve"
+    u = ((v1 * v1 - 2 * a) + math.sqrt(disc)) / 2
+    return math.sqrt(u), -math.atan2(c, u + a)
+
+
+@pytest.mark.parametrize("P,Q,r,x", [
+    (0.5, 0.2, 0.01, 0.1), (1.0, 0.3, 0.02, 0.2), (0.05, -0.3, 0.005, 0.04),
+    (1.5, 0.0, 0.05, 0.15)])
+@pytest.mark.parametrize("linear", ["dense", "splu", "gmres"])
+def test_two_bus_pq_closed_form(P, Q, r, x, linear):
+    case = cases.two_bus_case(P, Q, r, x)
+    res = O.newton_polar(case, tol=1e-12, linear=linear)
+    assert res["converged"]
+    vm2, va2 = two_bus_pq_closed_form(P, Q, r, x)
+    assert abs(res["vm"][1] - vm2) < 1e-10
+    assert abs(res["va"][1] - va2) < 1e-10
+    assert res["vm"][0] == 1.0 and res["va"][0] == 0.0
+
+
+@pytest.mark.parametrize("P,x,v2", [(0.8, 0.2, 1.02), (-0.5, 0.1, 0.98), (1.5, 0.3, 1.05)])
+def test_two_bus_lossless_pv_closed_form(P, x, v2):
+    case = cases.two_bus_case(P, 0.0, 0.0, x, pv=True, v2=v2)
+    res = O.newton_polar(case, tol=1e-12)
+    assert res["converged"]
+    # lossless line: P = V1 V2 sin(delta2 - delta1) / x
+    assert abs(res["va"][1] - math.asin(P * x / (1.0 * v2))) < 1e-11
+    assert res["vm"][1] == v2
+
+
+def _random_voltage(n, rng):
+    return rng.uniform(0.9, 1.1, n), rng.uniform(-0.3, 0.3, n)
+
+
+def test_power_balance_identity_single_phase():
+    """Tellegen: total injection = series I^2 z losses - charging Q, any V."""
+    rng = np.random.default_rng(3)
+    case = cases.case_14bus(1)
+    Y = O.ybus_single(case)
+    for _ in range(5):
+        vm, va = _random_voltage(case.n_bus, rng)
+        P, Q = O.power_polar(Y, vm, va)
+        V = vm * np.exp(1j * va)
+        f, t = case.br_from, case.br_to
+        i_series = (V[f] - V[t]) / (case.br_r + 1j * case.br_x)
+        loss_p = np.sum(case.br_r * np.abs(i_series) ** 2)
+        loss_q = (np.sum(case.br_x * np.abs(i_series) ** 2)
+                  - np.sum(case.br_b / 2 * (np.abs(V[f]) ** 2 + np.abs(V[t]) ** 2)))
+        assert abs(P.sum() - loss_p) < 1e-11 * max(1, loss_p)
+        assert abs(Q.sum() - loss_q) < 1e-11 * max(1, abs(loss_q))
+
+
+def test_power_balance_at_solution():
+    """At convergence the specified injections plus slack output equal losses."""
+    case = cases.case_14bus(0)
+    res = O.newton_polar(case, tol=1e-12)
+    Y = O.ybus_single(case)
+    V = res["vm"] * np.exp(1j * res["va"])
+    f, t = case.br_from, case.br_to
+    i_series = (V[f] - V[t]) / (case.br_r + 1j * case.br_x)
+    loss_p = np.sum(case.br_r * np.abs(i_series) ** 2)
+    P, _ = O.power_polar(Y, res["vm"], res["va"])
+    Psp, _ = O.specified_power(case, res["vm"])
+    nonslack = case.bus_type != cases.SLACK
+    total = Psp[nonslack].sum() + P[~nonslack].sum()
+    assert abs(total - loss_p) < 1e-10
+
+
+def _zip_case(seed):
+    case = cases.case_14bus(seed)
+    rng = np.random.default_rng(seed + 100)
+    z = rng.dirichlet([1, 1, 1], case.n_bus)
+    return case.__class__(**{**case.__dict__, "zip": z})
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_jacobian_matches_central_differences(seed):
+    case = _zip_case(seed)
+    Y = O.ybus_single(case)
+    rng = np.random.default_rng(seed)
+    vm, va = _random_voltage(case.n_bus, rng)
+    pvpq, pq = O.unknowns_polar(case)
+    J = O.jacobian_polar(case, Y, vm, va).toarray()
+    h = 1e-6
+    cols = []
+    for k in range(pvpq.size + pq.size):
+        vp, ap = vm.copy(), va.copy()
+        vmn, van = vm.copy(), va.copy()
+        if k < pvpq.size:
+            ap[pvpq[k]] += h
+            van[pvpq[k]] -= h
+        else:
+            vp[pq[k - pvpq.size]] += h
+            vmn[pq[k - pvpq.size]] -= h
+        # J is the derivative of the calculated power, i.e. of -mismatch
+        d = -(O.mismatch_polar(case, Y, vp, ap) - O.mismatch_polar(case, Y, vmn, van)) / (2 * h)
+        cols.append(d)
+    Jfd = np.array(cols).T
+    assert np.max(np.abs(J - Jfd)) <= 1e-6 * max(1.0, np.max(np.abs(J)))
+
+
+def test_newton_matches_generic_root_finder():
+    """A derivative-free root finder reaches the same fixed point."""
+    case = _zip_case(4)
+    Y = O.ybus_single(case)
+    pvpq, pq = O.unknowns_polar(case)
+    vm0, va0 = O.flat_start_polar(case)
+
+    def F(z):
+        vm, va = vm0.copy(), va0.copy()
+        va[pvpq] = z[:pvpq.size]
+        vm[pq] = z[pvpq.size:]
+        return O.mismatch_polar(case, Y, vm, va)
+
+    z0 = np.concatenate([va0[pvpq], vm0[pq]])
+    sol = so.root(F, z0, method="hybr", options={"xtol": 1e-13})
+    assert np.max(np.abs(F(sol.x))) < 1e-11
+    res = O.newton_polar(case, tol=1e-12)
+    assert res["converged"]
+    assert np.max(np.abs(res["va"][pvpq] - sol.x[:pvpq.size])) < 1e-9
+    assert np.max(np.abs(res["vm"][pq] - sol.x[pvpq.size:])) < 1e-9
+
+
+def test_quadratic_convergence():
+    for seed in range(3):
+        res = O.newton_polar(cases.case_14bus(seed), tol=1e-13)
+        h = res["history"]
+        assert res["converged"] and len(h) >= 4
+        # once in the basin: e_{k+1} <= C e_k^2
+        for a, b in zip(h[1:-1], h[2:]):
+            if a < 1e-1 and b > 1e-13:
+                assert b <= 50.0 * a * a
+
+
+def test_permutation_invariance():
+    case = cases.case_14bus(5)
+    res = O.newton_polar(case, tol=1e-12)
+    perm = np.random.default_rng(9).permutation(case.n_bus)
+    res2 = O.newton_polar(case.relabel(perm), tol=1e-12)
+    assert np.max(np.abs(res2["vm"] - res["vm"][perm])) < 1e-11
+    assert np.max(np.abs(res2["va"] - res["va"][perm])) < 1e-11
+
+
+def test_newton_raphson_and_newton_krylov_agree():
+    """NR (SuperLU, dense LU) and NK (GMRES + ILU(0)) reach the same V."""
+    for seed in range(3):
+        case = _zip_case(seed)
+        out = [O.newton_polar(case, tol=1e-11, linear=lin) for lin in ("dense", "splu", "gmres")]
+        for r in out:
+            assert r["converged"]
+        for r in out[1:]:
+            assert np.max(np.abs(r["vm"] - out[0]["vm"])) < 1e-9
+            assert np.max(np.abs(r["va"] - out[0]["va"])) < 1e-9
+
+
+def test_medium_grid_converges_with_both_sparse_solvers():
+    case = cases.case_2000bus(0)
+    r1 = O.newton_polar(case, linear="splu")
+    assert r1["converged"] and r1["iterations"] <= 8
+    # the 14-bus case is the spec'd load level; larger meshes are scaled
+    assert cases.case_14bus(0).load_scale == 1.0
+    assert 0 < case.load_scale < 1.0
+
+
+def test_flat_start_zero_load_needs_no_iteration():
+    case = cases.two_bus_case(0.0, 0.0, 0.01, 0.1)
+    res = O.newton_polar(case)
+    assert res["converged"] and res["iterations"] == 0
+
+
+# -----------------------------------------------------------------------------
+# Krylov pieces
+# -----------------------------------------------------------------------------
+
+def test_ilu0_is_exact_lu_without_fill():
+    """A tridiagonal matrix has no fill, so ILU(0) is its LU factorisation."""
+    rng = np.random.default_rng(0)
+    n = 40
+    A = sp.diags([rng.uniform(-1, 1, n - 1), rng.uniform(4, 5, n), rng.uniform(-1, 1, n - 1)],
+                 [-1, 0, 1], format="csr")
+    L, U = O.ilu0(A)
+    assert np.max(np.abs((L @ U - A).toarray())) < 1e-13
+    # against a dense Doolittle elimination without pivoting
+    M = A.toarray()
+    for k in range(n):
+        M[k + 1:, k] /= M[k, k]
+        M[k + 1:, k + 1:] -= np.outer(M[k + 1:, k], M[k, k + 1:])
+    assert np.max(np.abs(np.triu(M) - U.toarray())) < 1e-13
+    assert np.max(np.abs(np.tril(M, -1) + np.eye(n) - L.toarray())) < 1e-13
+
+
+def test_ilu0_matches_matrix_on_pattern():
+    rng = np.random.default_rng(1)
+    n = 60
+    A = sp.random(n, n, density=0.08, random_state=2, format="csr")
+    A = A + A.T + sp.eye(n) * 6.0
+    A.data += rng.uniform(-0.2, 0.2, A.data.size)
+    A = A.tocsr()
+    L, U = O.ilu0(A)
+    LU = (L @ U).toarray()
+    Ad = A.toarray()
+    mask = Ad != 0
+    assert np.max(np.abs(LU[mask] - Ad[mask])) < 1e-12
+    # and ILU(0) is not the exact factorisation (fill was dropped)
+    assert np.max(np.abs(LU - Ad)) > 1e-8
+    # the factors keep the pattern of A
+    assert not np.any((L.toarray() != 0) & ~mask & ~np.eye(n, dtype=bool))
+    assert not np.any((U.toarray() != 0) & ~mask)
+
+
+def test_gmres_with_full_restart_solves_exactly():
+    rng = np.random.default_rng(2)
+    n = 25
+    A = sp.csr_matrix(rng.standard_normal((n, n)) + 8 * np.eye(n))
+    b = rng.standard_normal(n)
+    x, it = O.gmres(A, b, restart=n, tol=1e-13)
+    assert np.max(np.abs(x - np.linalg.solve(A.toarray(), b))) < 1e-11
+    assert it <= n
+
+
+def test_gmres_restarted_with_ilu0():
+    rng = np.random.default_rng(3)
+    n = 120
+    A = sp.random(n, n, density=0.05, random_state=4, format="csr") + sp.eye(n) * 3.0
+    b = rng.standard_normal(n)
+    L, U = O.ilu0(A)
+    x, _ = O.gmres(A, b, L, U, restart=5, tol=1e-12, max_restarts=500)
+    assert np.linalg.norm(A @ x - b) <= 1e-11 * np.linalg.norm(b)
+
+
+# -----------------------------------------------------------------------------
+# three phase, current injection
+# -----------------------------------------------------------------------------
+
+def _line_feeder(n, zs, zm, p, q, zip_frac=(1.0, 0.0, 0.0), phases=None,
+                 br_phases=None):
+    """Chain 0 - 1 - ... - n-1 with identical branches and loads."""
+    base = np.full((3, 3), zm, dtype=np.complex128)
+    np.fill_diagonal(base, zs)
+    ph = np.full(n, 7, dtype=np.uint8) if phases is None else np.asarray(phases, np.uint8)
+    bph = ph[1:].copy() if br_phases is None else np.asarray(br_phases, np.uint8)
+    pl = np.zeros((n, 3))
+    ql = np.zeros((n, 3))
+    for k in range(1, n):
+        for s in range(3):
+            if (ph[k] >> s) & 1:
+                pl[k, s] = p[k - 1][s] if np.ndim(p) else p
+                ql[k, s] = q[k - 1][s] if np.ndim(q) else q
+    return cases.ThreePhaseCase(
+        n_node=n, source=0, phases=ph, p_load=pl, q_load=ql,
+        zip=np.tile(np.asarray(zip_frac, float), (n, 1)),
+        br_from=np.arange(n - 1, dtype=np.int32), br_to=np.arange(1, n, dtype=np.int32),
+        br_phases=bph, br_z=np.repeat(base[None], n - 1, axis=0))
+
+
+ROT = np.exp(-2j * np.pi / 3 * np.arange(3))
+
+
+@pytest.mark.parametrize("zm", [0.0, 0.004 + 0.015j])
+def test_cim_balanced_constant_power_is_two_bus_closed_form(zm):
+    """Balanced loads on a transposed line see the positive-sequence z1 = zs - zm."""
+    zs = 0.02 + 0.06j
+    P, Q = 0.8, 0.3
+    case = _line_feeder(2, zs, zm, P, Q)
+    res = O.newton_cim(case, tol=1e-13)
+    assert res["converged"]
+    z1 = zs - zm
+    vm2, va2 = two_bus_pq_closed_form(P, Q, z1.real, z1.imag)
+    V2 = res["V"][3:6]
+    assert np.max(np.abs(V2 - vm2 * np.exp(1j * va2) * ROT)) < 1e-10
+
+
+def test_cim_constant_impedance_closed_form():
+    """Constant-Z load S = S_Z |V|^2 is the admittance conj(S_Z): a divider."""
+    zs, zm = 0.03 + 0.08j, 0.01 + 0.03j
+    P, Q = 0.9, 0.4
+    case = _line_feeder(2, zs, zm, P, Q, zip_frac=(0.0, 0.0, 1.0))
+    res = O.newton_cim(case, tol=1e-13)
+    assert res["converged"]
+    V2 = 1.0 / (1.0 + (zs - zm) * np.conj(P + 1j * Q))
+    assert np.max(np.abs(res["V"][3:6] - V2 * ROT)) < 1e-11
+
+
+def test_cim_single_phase_lateral_is_two_bus_closed_form():
+    """A one-phase lateral has no mutual coupling: plain two-bus form, rotated."""
+    zs, zm = 0.02 + 0.06j, 0.005 + 0.02j
+    P, Q = 0.4, 0.1
+    case = _line_feeder(2, zs, zm, P, Q, phases=[7, 2])  # phase b only
+    res = O.newton_cim(case, tol=1e-13)
+    vm2, va2 = two_bus_pq_closed_form(P, Q, zs.real, zs.imag)
+    assert abs(res["V"][4] - vm2 * np.exp(1j * va2) * ROT[1]) < 1e-10
+    assert res["V"][3] == 0 and res["V"][5] == 0
+
+
+def _cim_random_case(seed, n=12):
+    return cases.feeder_case(n, seed, lateral_p=0.5, reduced_p=0.6, max_drop=0.08)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_cim_jacobian_matches_central_differences(seed):
+    case = _cim_random_case(seed)
+    Y = O.ybus_three_phase(case)
+    rng = np.random.default_rng(seed)
+    V = O.cim_flat_start(case)
+    V = V * rng.uniform(0.9, 1.05, V.size) * np.exp(1j * rng.uniform(-0.1, 0.1, V.size))
+    idx = O.cim_unknowns(case)
+    J = O.cim_jacobian(case, Y, V).toarray()[np.ix_(idx, idx)]
+    n = case.n_node
+    h = 1e-6
+    cols = []
+    for k in idx:
+        node, slot = divmod(int(k), 6)
+        dv = np.zeros(3 * n, dtype=np.complex128)
+        dv[3 * node + slot % 3] = h if slot < 3 else 1j * h
+        fp = O.cim_mismatch(case, Y, V + dv)[idx]
+        fm = O.cim_mismatch(case, Y, V - dv)[idx]
+        cols.append(-(fp - fm) / (2 * h))  # J = d(Y V - I_sp)/dV
+    Jfd = np.array(cols).T
+    assert np.max(np.abs(J - Jfd)) <= 1e-6 * max(1.0, np.max(np.abs(J)))
+
+
+def test_cim_power_balance_identity():
+    """Total injected complex power equals the series losses of all branches."""
+    case = _cim_random_case(4, n=30)
+    Y = O.ybus_three_phase(case)
+    rng = np.random.default_rng(1)
+    V = O.cim_flat_start(case) * rng.uniform(0.9, 1.1, 3 * case.n_node)
+    S = V * np.conj(Y @ V)
+    loss = 0.0
+    for e in range(case.n_branch):
+        ph = [s for s in range(3) if (case.br_phases[e] >> s) & 1]
+        f, t = case.br_from[e], case.br_to[e]
+        dV = V[3 * f + np.array(ph)] - V[3 * t + np.array(ph)]
+        Z = case.br_z[e][np.ix_(ph, ph)]
+        i_series = np.linalg.solve(Z, dV)
+        loss += np.conj(i_series) @ (Z @ i_series)  # I^H Z I
+    assert abs(S.sum() - loss) < 1e-10 * max(1.0, abs(loss))
+
+
+def test_cim_matches_generic_root_finder():
+    case = _cim_random_case(7)
+    Y = O.ybus_three_phase(case)
+    idx = O.cim_unknowns(case)
+    V0 = O.cim_flat_start(case)
+    n = case.n_node
+
+    def unpack(z):
+        full = np.zeros(6 * n)
+        full[idx] = z
+        full = full.reshape(n, 6)
+        return V0 * np.where(O.cim_free_slots(case), 0.0, 1.0) + (full[:, :3] + 1j * full[:, 3:]).reshape(-1)
+
+    V0c = O.cim_flat_start(case).copy()
+    z0 = np.stack([V0c.real.reshape(n, 3), V0c.imag.reshape(n, 3)], 1).reshape(n, 6).reshape(-1)[idx]
+    F = lambda z: O.cim_mismatch(case, Y, unpack(z))[idx]  # noqa: E731
+    sol = so.root(F, z0, method="hybr", options={"xtol": 1e-13})
+    assert np.max(np.abs(F(sol.x))) < 1e-11
+    res = O.newton_cim(case, tol=1e-12)
+    assert res["converged"]
+    assert np.max(np.abs(res["V"] - unpack(sol.x))) < 1e-9
+
+
+def test_cim_solvers_agree_on_generated_feeder():
+    case = cases.feeder_case(300, 3)
+    out = [O.newton_cim(case, tol=1e-11, linear=lin) for lin in ("dense", "splu", "gmres")]
+    for r in out:
+        assert r["converged"]
+    for r in out[1:]:
+        assert np.max(np.abs(r["V"] - out[0]["V"])) < 1e-9
