@@ -1,0 +1,297 @@
+/*
+ * pf.h -- C ABI of a GB300-native Newton power-flow library.
+ *
+ * The library implements the hot path of the ExaGridPF method (Wang, Bachan,
+ * Chan, arXiv 1711.10579): the Newton iteration of AC power flow.
+ *
+ *   single phase (Sec. II.A): polar Newton-Raphson.  Each iteration forms the
+ *     power mismatch Delta P, Delta Q (Eq. 8-9) from I = Y V (Eq. 1) and
+ *     S = V conj(I) (the quantity of Eq. 5-7), assembles the Jacobian of
+ *     Eq. 10 and solves for (Delta delta, Delta |V|);
+ *   three phase (Sec. II.B): current-injection Newton.  Each iteration forms
+ *     Delta I = I_sp - Y V (Eq. 12-19) and solves the 6x6-block system of
+ *     Eq. 21-23 for the rectangular voltage correction (Eq. 20).
+ *
+ * The Newton correction is solved either by a numeric sparse LU
+ * refactorisation on a symbolic pattern computed once per topology plus
+ * level-scheduled triangular solves (Newton-Raphson, Sec. III.A) or by
+ * restarted GMRES with an ILU(0) preconditioner (Newton-Krylov, Sec. III.B).
+ * Every step of the iteration runs in this library's own CUDA kernels on one
+ * GPU; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - The return value is a pf_status; negative values are errors.  No call
+ *    aborts or throws across the ABI.  pf_last_error() returns a message for
+ *    the last failing call of the calling thread.
+ *  - Pointers named h_* or without prefix are HOST memory owned by the caller;
+ *    the library copies inputs during the call and writes outputs only before
+ *    returning.  Pointers named d_* are DEVICE memory on the context's GPU,
+ *    owned by the caller; calls taking d_* pointers and a stream are
+ *    asynchronous on that stream.
+ *  - Arrays are dense, C order, float64 unless stated.  "Per bus" arrays have
+ *    n_bus entries in the caller's bus numbering; three-phase "per slot"
+ *    arrays have 3 * n_bus entries, slot 3*i + s for phase s (a=0, b=1, c=2)
+ *    of node i, the phase indexing of Sec. II.B.
+ *  - Units are per unit (pu) and radians.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_ctx_s* pf_ctx;   /* one GPU, its streams and serving runtime */
+typedef struct pf_case_s* pf_case; /* one topology: Ybus, symbolic patterns, warm start */
+typedef uint64_t pf_ticket;        /* handle of a submitted (served) solve */
+
+enum pf_status {
+  PF_OK = 0,
+  PF_PENDING = 1,         /* pf_poll: the solve has not finished yet */
+  PF_ERR_INVALID = -1,    /* bad argument or case description */
+  PF_ERR_NOMEM = -2,      /* device or host allocation failed / over budget */
+  PF_ERR_MAXITER = -3,    /* Newton stopped at max_iter above tolerance */
+  PF_ERR_DIVERGED = -4,   /* mismatch became non-finite or exploded */
+  PF_ERR_SINGULAR = -5,   /* zero or non-finite pivot block in the factorisation */
+  PF_ERR_TIMEOUT = -6,    /* a bounded wait ran out */
+  PF_ERR_BUSY = -7,       /* serving queue full; retry later */
+  PF_ERR_CUDA = -8,       /* a CUDA runtime call failed */
+  PF_ERR_UNSUPPORTED = -9 /* valid request this build does not implement */
+};
+
+enum pf_bus_type { PF_SLACK = 0, PF_PV = 1, PF_PQ = 2 };
+enum pf_method { PF_NR = 0, PF_NK = 1 };
+enum pf_precision { PF_FP64 = 0, PF_MIXED = 1 };
+enum pf_kind { PF_SINGLE_PHASE = 1, PF_THREE_PHASE = 3 };
+
+/*
+ * Case description (problem statement of Sec. II: P and Q drawn or injected
+ * per bus and phase, V magnitude and angle per bus and phase out).
+ *
+ * kind == PF_SINGLE_PHASE:
+ *   bus_type[n]   pf_bus_type; exactly one PF_SLACK.
+ *   v_set[n]      |V| set point of the slack and PV buses (ignored for PQ).
+ *   p_gen[n], q_gen[n]    generation (q_gen used for PQ buses only).
+ *   p_load[n], q_load[n]  load at |V| = 1 pu.
+ *   zip[n][3]     load fractions (constant power, constant current,
+ *                 constant impedance) of Eq. 14-15; NULL = constant power.
+ *                 Specified injection = gen - load(|V|)  (Eq. 12-15).
+ *   br_from/br_to[m], br_r/br_x/br_b[m]: pi-model branches, series r + jx,
+ *                 total line charging b split b/2 per end (Eq. 2-3).
+ * kind == PF_THREE_PHASE (no PV buses, as in Sec. II.B):
+ *   phases[n]     uint8 bit mask of present phases (a=1, b=2, c=4).
+ *   source        index of the ideal balanced source node (slack).
+ *   v_source      its magnitude; phase angles 0, -120, +120 degrees.
+ *   p_load[3n], q_load[3n]  wye load per slot at |V| = 1 pu.
+ *   zip[n][3]     ZIP fractions per node (NULL = constant power).
+ *   br_from/br_to[m], br_phases[m] (mask of phases on the branch, a subset
+ *                 of both end nodes' phases), br_z[m][3][3][2] the series
+ *                 impedance matrix (re, im); the branch admittance is the
+ *                 inverse of its submatrix over the branch's phases (Eq. 11).
+ * Unused fields may be NULL.
+ */
+typedef struct {
+  int kind;
+  int n_bus;
+  int n_branch;
+  const int32_t* bus_type;
+  const double* v_set;
+  const double* p_gen;
+  const double* q_gen;
+  const double* p_load;
+  const double* q_load;
+  const double* zip;
+  const int32_t* br_from;
+  const int32_t* br_to;
+  const double* br_r;
+  const double* br_x;
+  const double* br_b;
+  const uint8_t* phases;
+  int source;
+  double v_source;
+  const uint8_t* br_phases;
+  const double* br_z;
+} pf_case_desc;
+
+typedef struct {
+  int method;         /* pf_method, default PF_NR */
+  int precision;      /* pf_precision, default PF_MIXED */
+  double tol;         /* stop when the power-mismatch infinity norm <= tol (pu); default 1e-8 */
+  int max_iter;       /* Newton iterations; default 30 */
+  int refine_steps;   /* NR + PF_MIXED: FP64 iterative-refinement steps per solve; default 1 */
+  int gmres_restart;  /* NK: Krylov subspace size m of GMRES(m); default 30 */
+  int gmres_max_iter; /* NK: inner iterations per Newton step; default 300 */
+  double gmres_rtol;  /* NK: inner relative-residual floor; default 1e-6 */
+  int warm_start;     /* 1 = start from the case's last converged voltages */
+  int cluster_size;   /* single-solve launch: CTAs per cluster (0 = autotuned) */
+  int block_threads;  /* threads per CTA (0 = autotuned) */
+  int scen_per_cta;   /* batched launch: scenarios per CTA (0 = autotuned) */
+} pf_opts;
+
+typedef struct {
+  int status;            /* pf_status of this solve */
+  int iterations;        /* Newton iterations performed (solves of Eq. 10 / 22) */
+  int linear_iterations; /* NK: total GMRES iterations */
+  int reserved;
+  double mismatch;       /* final infinity norm of the power mismatch (pu) */
+  double max_step;       /* infinity norm of the last Newton correction */
+  double solve_us;       /* device time of the solve, microseconds */
+} pf_info;
+
+/* Sizes produced by the symbolic phase (per method's ordering). */
+typedef struct {
+  int kind, n_bus, block_size, n_unknowns;
+  long long nnz_y;        /* block entries of Ybus (incl. diagonal) */
+  long long nnz_lu;       /* block entries of L+U (NR, after fill) */
+  long long n_updates;    /* block multiply-subtracts of one NR factorisation */
+  int levels_factor;      /* level sets of the NR factorisation / forward solve */
+  int levels_backward;    /* level sets of the NR backward solve */
+  int levels_ilu;         /* level sets of ILU(0) (NK ordering) */
+  int levels_ilu_backward;
+  long long device_bytes; /* device memory held by the case (symbolic data) */
+  long long bytes_per_scenario; /* workspace per solved scenario */
+} pf_case_stats;
+
+/*
+ * Host-only analysis (no GPU needed): validates the description, assembles
+ * Ybus and runs the symbolic phase exactly as pf_create_case does, and fills
+ * *out (device_bytes = what pf_create_case would hold).  Lets a caller size a
+ * case before creating it.  Errors: PF_ERR_INVALID.
+ */
+int pf_analyze(const pf_case_desc* desc, pf_case_stats* out);
+/*
+ * Host-only: Ybus of Eq. 2-3 / Eq. 11 in the caller's numbering as block CSR.
+ * Call with rowptr == NULL to get *nnz only; otherwise rowptr[n+1],
+ * col[nnz], val[nnz][2*ybs*ybs] (re, im interleaved, ybs = 1 or 3) are
+ * filled.
+ */
+int pf_ybus(const pf_case_desc* desc, int64_t* nnz, int32_t* rowptr, int32_t* col,
+            double* val);
+/*
+ * Host-only: symbolic pattern of a method (PF_NR: minimum-degree ordering
+ * with LU fill; PF_NK: reverse Cuthill-McKee ordering, Ybus pattern for
+ * ILU(0)).  perm[n] maps new to caller numbering; rowptr[n+1], col[nnz] is
+ * the factor's block pattern in the new numbering (nnz = nnz_lu or nnz_y of
+ * pf_analyze); flevel[n] / blevel[n] the level of each new row in the
+ * factorisation / forward schedule and in the backward schedule.
+ */
+int pf_symbolic(const pf_case_desc* desc, int method, int32_t* perm, int32_t* rowptr,
+                int32_t* col, int32_t* flevel, int32_t* blevel);
+
+/* Fill *opts with the defaults listed in pf_opts. */
+void pf_opts_default(pf_opts* opts);
+/* Message of the last failing call on this thread ("" if none). */
+const char* pf_last_error(void);
+/* Name of a pf_status value. */
+const char* pf_status_str(int status);
+
+/*
+ * Context on CUDA device `device`.  hbm_budget_bytes bounds the device memory
+ * the serving runtime admits requests into (0 = 80% of free memory).
+ */
+int pf_ctx_create(int device, size_t hbm_budget_bytes, pf_ctx* out);
+int pf_ctx_destroy(pf_ctx ctx);
+
+/*
+ * Copies and validates the description, assembles Ybus (Eq. 2-3 or 11),
+ * computes orderings (minimum degree for the LU of Sec. III.A; reverse
+ * Cuthill-McKee for the Krylov solver, Sec. III.B), the block fill pattern,
+ * level sets and update lists, and uploads them.  Errors: PF_ERR_INVALID
+ * (no or several slack buses, indices out of range, disconnected grid,
+ * non-finite values, PV in three phase, zero impedance), PF_ERR_NOMEM,
+ * PF_ERR_CUDA.
+ */
+int pf_create_case(pf_ctx ctx, const pf_case_desc* desc, pf_case* out);
+int pf_destroy_case(pf_case c);
+int pf_case_get_stats(pf_case c, pf_case_stats* out);
+
+/*
+ * One solve of the case as described (flat start or warm start).
+ * vmag, vang: per bus (single phase) or per slot (three phase), host.
+ * info: host.  Returns PF_OK if the solve ran (its own outcome is in
+ * info->status) or an error if it could not run.
+ */
+int pf_solve(pf_case c, const pf_opts* opts, double* vmag, double* vang,
+             pf_info* info);
+
+/*
+ * B scenarios of one topology solved together (one persistent launch over
+ * the shared symbolic pattern).  Scenario b uses p_load[b][*], q_load[b][*]
+ * (per bus or per slot) and, single phase only, p_gen[b][n] (NULL = the
+ * case's own generation).  Outputs vmag[b][*], vang[b][*], info[b].
+ * Host arrays; the call blocks until done.
+ */
+int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
+                   const double* p_gen, const pf_opts* opts, double* vmag,
+                   double* vang, pf_info* info);
+
+/*
+ * Device-resident form of pf_solve_batch, asynchronous on `stream`
+ * (a cudaStream_t, NULL = legacy default stream).  d_info receives B pf_info
+ * records in device memory.  B = 1 runs the single-solve cluster launch.
+ * The device arrays must stay valid until the stream passes this call.
+ */
+int pf_solve_batch_device(pf_case c, int B, const double* d_p_load,
+                          const double* d_q_load, const double* d_p_gen,
+                          const pf_opts* opts, double* d_vmag, double* d_vang,
+                          pf_info* d_info, void* stream);
+
+/*
+ * Serving: queue one solve of case c with its own loads (host arrays as in
+ * pf_solve_batch with B = 1; NULL = the case's own).  The runtime admits
+ * queued requests onto the GPU as slots and device memory (the context's
+ * budget) allow, so requests overlap on the device.  Warm start from the
+ * case's last result if opts->warm_start.  PF_ERR_BUSY if the queue is full.
+ * Thread safe.
+ */
+int pf_submit(pf_ctx ctx, pf_case c, const double* p_load, const double* q_load,
+              const double* p_gen, const pf_opts* opts, pf_ticket* out);
+/*
+ * PF_PENDING while the request is queued or running; otherwise copies the
+ * result into vmag/vang/info (host, may be NULL), releases the ticket and
+ * returns PF_OK.  PF_ERR_INVALID for an unknown ticket.  Thread safe.
+ */
+int pf_poll(pf_ctx ctx, pf_ticket t, double* vmag, double* vang, pf_info* info);
+/* Block until every submitted request has finished (bounded by timeout_ms). */
+int pf_drain(pf_ctx ctx, int timeout_ms);
+
+/*
+ * Inspection entry points: single steps of the iteration on the GPU, for
+ * parity tests and diagnostics.  vmag, vang: host, per bus / per slot.
+ *
+ * pf_eval_mismatch: single phase mis[n][2] = (Delta P, Delta Q) of Eq. 8-9
+ *   (0 where the bus has no such equation: slack both, PV Delta Q);
+ *   three phase mis[n][6] = Delta I of Eq. 16-19 in the order
+ *   [Im a, b, c, Re a, b, c] (0 on absent phases and the source).
+ */
+int pf_eval_mismatch(pf_case c, const double* vmag, const double* vang,
+                     double* mis);
+/*
+ * pf_eval_jacobian: Jacobian blocks on the Ybus block pattern returned by
+ * pf_case_pattern (caller's numbering, rows = equations of bus i, columns =
+ * unknowns of bus j, row-major bs x bs, bs = 2 or 6).  Single phase block =
+ * [[dP/d delta, dP/d|V|], [dQ/d delta, dQ/d|V|]] (Eq. 10); three phase
+ * block = Eq. 21 / 23.  Rows and columns without an unknown (slack, PV |V|,
+ * absent phase, source) are zero except a 1 on the diagonal.
+ */
+int pf_eval_jacobian(pf_case c, const double* vmag, const double* vang,
+                     double* blocks);
+/* Block pattern of Ybus in the caller's numbering: rowptr[n+1], col[nnz_y]. */
+int pf_case_pattern(pf_case c, int32_t* rowptr, int32_t* col);
+/*
+ * pf_newton_step: one solve J dx = F at the given voltage with the method and
+ * precision of opts; dx[n][bs] per bus in the unknown order of Eq. 10
+ * (delta, |V|) or Eq. 20 (Re a,b,c, Im a,b,c), 0 where no unknown.
+ * info->linear_iterations reports GMRES iterations for PF_NK.
+ */
+int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag,
+                   const double* vang, double* dx, pf_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PF_H */

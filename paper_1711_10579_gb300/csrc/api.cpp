@@ -1,0 +1,540 @@
+// C ABI of the power-flow library: contexts, cases, solves and inspection
+// calls.  Host code only; every numeric step runs in the CUDA kernels of
+// newton.cu (and krylov.cu for the Newton-Krylov variant).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "api_internal.h"
+
+namespace pf {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return set_error(PF_ERR_CUDA, m);
+}
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+
+DevBuffer::~DevBuffer() { release(); }
+
+void DevBuffer::release() {
+  for (void* p : ptrs) cudaFree(p);
+  ptrs.clear();
+  bytes = 0;
+}
+
+cudaError_t DevBuffer::alloc(void** out, size_t nbytes) {
+  *out = nullptr;
+  if (nbytes == 0) nbytes = 16;
+  nbytes = (nbytes + 255) & ~size_t(255);
+  cudaError_t e = cudaMalloc(out, nbytes);
+  if (e == cudaSuccess) {
+    ptrs.push_back(*out);
+    bytes += nbytes;
+  }
+  return e;
+}
+
+template <class T>
+static cudaError_t upload(DevBuffer& buf, const std::vector<T>& v, const T** out) {
+  void* p;
+  cudaError_t e = buf.alloc(&p, v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  *out = static_cast<const T*>(p);
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// system upload
+// ---------------------------------------------------------------------------
+
+int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
+  analyze(y, ord, fill, sym);
+  const int n = c.n;
+  const Symbolic& s = sym;
+  DevSys& d = view;
+  std::memset(&d, 0, sizeof(d));
+  d.kind = c.kind;
+  d.n = n;
+  // Ybus values in the new numbering
+  const int vb = 2 * y.ybs * y.ybs;
+  std::vector<double> yv((size_t)s.nnz_y() * vb);
+  for (int e = 0; e < s.nnz_y(); ++e)
+    std::copy(y.val.begin() + (size_t)s.y_src[e] * vb, y.val.begin() + (size_t)(s.y_src[e] + 1) * vb,
+              yv.begin() + (size_t)e * vb);
+  std::vector<int8_t> bt(n);
+  std::vector<double> vset(n, 1.0), qg(n, 0.0), zip(3 * (size_t)n), pg(n, 0.0);
+  std::vector<double> pl, ql;
+  if (c.kind == PF_SINGLE_PHASE) {
+    pl.assign(n, 0.0);
+    ql.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      int o = s.perm[i];
+      bt[i] = c.bus_type[o];
+      vset[i] = c.v_set[o];
+      qg[i] = c.q_gen[o];
+      pg[i] = c.p_gen[o];
+      pl[i] = c.p_load[o];
+      ql[i] = c.q_load[o];
+      for (int k = 0; k < 3; ++k) zip[3 * (size_t)i + k] = c.zip[3 * (size_t)o + k];
+    }
+  } else {
+    pl.assign(3 * (size_t)n, 0.0);
+    ql.assign(3 * (size_t)n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      int o = s.perm[i];
+      bt[i] = (int8_t)((c.phases[o] & 7) | (o == c.source ? 8 : 0));
+      for (int k = 0; k < 3; ++k) {
+        zip[3 * (size_t)i + k] = c.zip[3 * (size_t)o + k];
+        pl[3 * (size_t)i + k] = c.p_load3[3 * (size_t)o + k];
+        ql[3 * (size_t)i + k] = c.q_load3[3 * (size_t)o + k];
+      }
+    }
+    d.v_source = c.v_source;
+  }
+  cudaError_t e = cudaSuccess;
+#define UP(vec, field) \
+  if (e == cudaSuccess) e = upload(mem, vec, &d.field)
+  UP(s.y_rowptr, y_rowptr);
+  UP(s.y_col, y_col);
+  UP(yv, y_val);
+  UP(s.lu_rowptr, lu_rowptr);
+  UP(s.lu_col, lu_col);
+  UP(s.lu_diag, lu_diag);
+  UP(s.lu2y, lu2y);
+  UP(s.upd_ptr, upd_ptr);
+  UP(s.upd_pos, upd_pos);
+  UP(s.flev_ptr, flev_ptr);
+  UP(s.flev_rows, flev_rows);
+  UP(s.blev_ptr, blev_ptr);
+  UP(s.blev_rows, blev_rows);
+  UP(bt, btype);
+  UP(vset, v_set);
+  UP(qg, q_gen);
+  UP(zip, zip);
+  UP(pg, p_gen0);
+  UP(pl, p_load0);
+  UP(ql, q_load0);
+  UP(s.perm, perm);
+#undef UP
+  d.nflev = (int)s.flev_ptr.size() - 1;
+  d.nblev = (int)s.blev_ptr.size() - 1;
+  if (e != cudaSuccess) return cuda_error(e, "uploading the symbolic analysis");
+  return PF_OK;
+}
+
+// Lanes-per-row tables for a given number of threads per cluster (cached).
+int SysBuf::lanes_for(int threads, DevSys& out) {
+  out = view;
+  auto it = g_cache.find(threads);
+  if (it == g_cache.end()) {
+    auto gf = lanes_per_level(sym.flev_ptr, sym.flev_ulen, threads);
+    auto gw = lanes_per_level(sym.flev_ptr, sym.flev_llen, threads);
+    auto gb = lanes_per_level(sym.blev_ptr, sym.blev_ulen, threads);
+    std::array<const int8_t*, 3> arr{};
+    cudaError_t e = upload(mem, gf, &arr[0]);
+    if (e == cudaSuccess) e = upload(mem, gw, &arr[1]);
+    if (e == cudaSuccess) e = upload(mem, gb, &arr[2]);
+    if (e != cudaSuccess) return cuda_error(e, "uploading lane tables");
+    it = g_cache.emplace(threads, arr).first;
+  }
+  out.g_fac = it->second[0];
+  out.g_fwd = it->second[1];
+  out.g_bwd = it->second[2];
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+
+size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B) {
+  const int bs = kind == PF_SINGLE_PHASE ? 2 : 6;
+  const int nsl = kind == PF_SINGLE_PHASE ? 1 : 3;
+  size_t nb = (size_t)n * B;
+  size_t t = 0;
+  t += nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8;      // spec
+  t += (kind == PF_SINGLE_PHASE ? 2 : 0) * nb * 8;      // vm, va
+  t += 3 * nb * nsl * 16;                               // V, I, dV
+  t += (kind == PF_SINGLE_PHASE ? 0 : 12) * nb * 8;     // abcd
+  t += 2 * nb * bs * 8;                                 // F, dx
+  t += (size_t)nnz_lu * B * bs * bs * 8;                // lu
+  t += nb * bs * bs * 8;                                // uinv
+  t += nb * bs * 8;                                     // y
+  t += (size_t)B * (2 * 8 + 2 * 8 + 4);                 // norm, step, flag
+  t += 3 * nb * nsl * 8;                                // staged inputs
+  t += 2 * nb * nsl * 8 + (size_t)B * sizeof(pf_info);  // staged outputs
+  return t;
+}
+
+int Workspace::ensure(int kind, int n, long long nnz_lu, int B) {
+  if (B <= cap) return PF_OK;
+  mem.release();
+  cap = 0;
+  const int bs = kind == PF_SINGLE_PHASE ? 2 : 6;
+  const int nsl = kind == PF_SINGLE_PHASE ? 1 : 3;
+  size_t nb = (size_t)n * B;
+  std::memset(&w, 0, sizeof(w));
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = mem.alloc(p, bytes);
+  };
+  A((void**)&w.spec, nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8);
+  if (kind == PF_SINGLE_PHASE) {
+    A((void**)&w.vm, nb * 8);
+    A((void**)&w.va, nb * 8);
+  }
+  A((void**)&w.V, nb * nsl * 16);
+  A((void**)&w.I, nb * nsl * 16);
+  A((void**)&w.dV, nb * nsl * 16);
+  if (kind == PF_THREE_PHASE) A((void**)&w.abcd, nb * 12 * 8);
+  A((void**)&w.F, nb * bs * 8);
+  A((void**)&w.dx, nb * bs * 8);
+  A(&w.lu, (size_t)nnz_lu * B * bs * bs * 8);
+  A(&w.uinv, nb * bs * bs * 8);
+  A(&w.y, nb * bs * 8);
+  A((void**)&w.norm, (size_t)2 * B * 8);
+  A((void**)&w.step, (size_t)2 * B * 8);
+  A((void**)&w.flag, (size_t)B * 4);
+  A((void**)&st_p_load, nb * nsl * 8);
+  A((void**)&st_q_load, nb * nsl * 8);
+  A((void**)&st_p_gen, nb * nsl * 8);
+  A((void**)&st_vm, nb * nsl * 8);
+  A((void**)&st_va, nb * nsl * 8);
+  A((void**)&st_info, (size_t)B * sizeof(pf_info));
+  if (e != cudaSuccess) {
+    mem.release();
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return set_error(PF_ERR_NOMEM, "device memory exhausted for the solve workspace");
+    }
+    return cuda_error(e, "allocating the solve workspace");
+  }
+  cap = B;
+  w.B = B;
+  return PF_OK;
+}
+
+}  // namespace pf
+
+using namespace pf;
+
+static void fill_stats(const CaseData& d, const Symbolic& nr, const Symbolic& nk,
+                       pf_case_stats* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->kind = d.kind;
+  out->n_bus = d.n;
+  out->block_size = d.kind == PF_SINGLE_PHASE ? 2 : 6;
+  int unknowns = 0;
+  if (d.kind == PF_SINGLE_PHASE) {
+    for (int8_t t : d.bus_type) unknowns += (t == PF_PQ) ? 2 : (t == PF_PV ? 1 : 0);
+  } else {
+    for (int i = 0; i < d.n; ++i)
+      if (i != d.source)
+        for (int a = 0; a < 3; ++a) unknowns += ((d.phases[i] >> a) & 1) * 2;
+  }
+  out->n_unknowns = unknowns;
+  out->nnz_y = nr.nnz_y();
+  out->nnz_lu = nr.nnz_lu();
+  out->n_updates = nr.n_updates;
+  out->levels_factor = (int)nr.flev_ptr.size() - 1;
+  out->levels_backward = (int)nr.blev_ptr.size() - 1;
+  out->levels_ilu = (int)nk.flev_ptr.size() - 1;
+  out->levels_ilu_backward = (int)nk.blev_ptr.size() - 1;
+  out->bytes_per_scenario = (long long)Workspace::bytes_for(d.kind, d.n, nr.nnz_lu(), 1);
+}
+
+
+// ---------------------------------------------------------------------------
+// exported functions
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void pf_opts_default(pf_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->method = PF_NR;
+  o->precision = PF_MIXED;
+  o->tol = 1e-8;
+  o->max_iter = 30;
+  o->refine_steps = 1;
+  o->gmres_restart = 30;
+  o->gmres_max_iter = 300;
+  o->gmres_rtol = 1e-6;
+  o->warm_start = 0;
+}
+
+const char* pf_last_error(void) { return g_last_error.c_str(); }
+
+const char* pf_status_str(int s) {
+  switch (s) {
+    case PF_OK: return "PF_OK";
+    case PF_PENDING: return "PF_PENDING";
+    case PF_ERR_INVALID: return "PF_ERR_INVALID";
+    case PF_ERR_NOMEM: return "PF_ERR_NOMEM";
+    case PF_ERR_MAXITER: return "PF_ERR_MAXITER";
+    case PF_ERR_DIVERGED: return "PF_ERR_DIVERGED";
+    case PF_ERR_SINGULAR: return "PF_ERR_SINGULAR";
+    case PF_ERR_TIMEOUT: return "PF_ERR_TIMEOUT";
+    case PF_ERR_BUSY: return "PF_ERR_BUSY";
+    case PF_ERR_CUDA: return "PF_ERR_CUDA";
+    case PF_ERR_UNSUPPORTED: return "PF_ERR_UNSUPPORTED";
+    default: return "unknown status";
+  }
+}
+
+int pf_ctx_create(int device, size_t budget, pf_ctx* out) {
+  if (!out) return set_error(PF_ERR_INVALID, "null output pointer");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return set_error(PF_ERR_INVALID, "no such CUDA device");
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceProperties");
+  auto ctx = std::make_unique<pf_ctx_s>();
+  ctx->device = device;
+  ctx->num_sms = prop.multiProcessorCount;
+  if (budget == 0) {
+    size_t fr = 0, tot = 0;
+    e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemGetInfo");
+    budget = (size_t)(0.8 * (double)fr);
+  }
+  ctx->budget = budget;
+  e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate");
+  *out = ctx.release();
+  return PF_OK;
+}
+
+int pf_ctx_destroy(pf_ctx ctx) {
+  if (!ctx) return set_error(PF_ERR_INVALID, "null context");
+  cudaSetDevice(ctx->device);
+  serve_shutdown(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return PF_OK;
+}
+
+int pf_create_case(pf_ctx ctx, const pf_case_desc* desc, pf_case* out) {
+  if (!ctx || !out) return set_error(PF_ERR_INVALID, "null context or output pointer");
+  *out = nullptr;
+  auto c = std::make_unique<pf_case_s>();
+  c->ctx = ctx;
+  std::string err;
+  int rc = copy_case(desc, c->data, err);
+  if (rc != PF_OK) return set_error(rc, err);
+  rc = build_ybus(c->data, c->y, err);
+  if (rc != PF_OK) return set_error(rc, err);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  c->bs = c->data.kind == PF_SINGLE_PHASE ? 2 : 6;
+  rc = c->nr.build(c->data, c->y, Ordering::MinDegree, true);
+  if (rc != PF_OK) return rc;
+  rc = c->nk.build(c->data, c->y, Ordering::RCM, false);
+  if (rc != PF_OK) return rc;
+  // warm-start storage (new numbering of the NR ordering)
+  const int n = c->data.n;
+  e = c->mem.alloc((void**)&c->warm_vm, (size_t)n * 8);
+  if (e == cudaSuccess) e = c->mem.alloc((void**)&c->warm_va, (size_t)n * 8);
+  if (e == cudaSuccess) e = c->mem.alloc((void**)&c->warm_V, (size_t)n * 3 * 16);
+  if (e != cudaSuccess) return cuda_error(e, "allocating warm-start storage");
+  *out = c.release();
+  return PF_OK;
+}
+
+int pf_destroy_case(pf_case c) {
+  if (!c) return set_error(PF_ERR_INVALID, "null case");
+  cudaSetDevice(c->ctx->device);
+  serve_forget_case(c->ctx, c);
+  cudaDeviceSynchronize();
+  delete c;
+  return PF_OK;
+}
+
+int pf_case_get_stats(pf_case c, pf_case_stats* out) {
+  if (!c || !out) return set_error(PF_ERR_INVALID, "null argument");
+  fill_stats(c->data, c->nr.sym, c->nk.sym, out);
+  out->device_bytes = (long long)(c->nr.mem.bytes + c->nk.mem.bytes + c->mem.bytes);
+  return PF_OK;
+}
+
+int pf_solve(pf_case c, const pf_opts* opts, double* vmag, double* vang, pf_info* info) {
+  if (!c) return set_error(PF_ERR_INVALID, "null case");
+  pf_opts o;
+  if (opts) o = *opts; else pf_opts_default(&o);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->ctx->device);
+  cudaStream_t st = c->ctx->stream;
+  int rc = run_solve(c, o, 1, nullptr, nullptr, nullptr, &c->ws1, st, RunMode::Solve, nullptr,
+                     nullptr);
+  if (rc != PF_OK) return rc;
+  return fetch_results(c, &c->ws1, 1, vmag, vang, info, st);
+}
+
+int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
+                   const double* p_gen, const pf_opts* opts, double* vmag, double* vang,
+                   pf_info* info) {
+  if (!c || B < 1) return set_error(PF_ERR_INVALID, "null case or B < 1");
+  if (p_gen && c->data.kind != PF_SINGLE_PHASE)
+    return set_error(PF_ERR_INVALID, "p_gen is for single-phase cases only");
+  pf_opts o;
+  if (opts) o = *opts; else pf_opts_default(&o);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->ctx->device);
+  cudaStream_t st = c->ctx->stream;
+  Workspace* ws = (B == 1) ? &c->ws1 : &c->wsB;
+  int rc = ws->ensure(c->data.kind, c->data.n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), B);
+  if (rc != PF_OK) return rc;
+  const size_t per = (size_t)c->data.n * (c->data.kind == PF_SINGLE_PHASE ? 1 : 3);
+  cudaError_t e = cudaSuccess;
+  if (p_load) e = cudaMemcpyAsync(ws->st_p_load, p_load, per * B * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && q_load)
+    e = cudaMemcpyAsync(ws->st_q_load, q_load, per * B * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && p_gen)
+    e = cudaMemcpyAsync(ws->st_p_gen, p_gen, per * B * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "copying scenario inputs");
+  rc = run_solve(c, o, B, p_load ? ws->st_p_load : nullptr, q_load ? ws->st_q_load : nullptr,
+                 p_gen ? ws->st_p_gen : nullptr, ws, st, RunMode::Solve, nullptr, nullptr);
+  if (rc != PF_OK) return rc;
+  return fetch_results(c, ws, B, vmag, vang, info, st);
+}
+
+int pf_solve_batch_device(pf_case c, int B, const double* d_p_load, const double* d_q_load,
+                          const double* d_p_gen, const pf_opts* opts, double* d_vmag,
+                          double* d_vang, pf_info* d_info, void* stream) {
+  if (!c || B < 1) return set_error(PF_ERR_INVALID, "null case or B < 1");
+  if (d_p_gen && c->data.kind != PF_SINGLE_PHASE)
+    return set_error(PF_ERR_INVALID, "p_gen is for single-phase cases only");
+  pf_opts o;
+  if (opts) o = *opts; else pf_opts_default(&o);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->ctx->device);
+  Workspace* ws = (B == 1) ? &c->ws1 : &c->wsB;
+  return run_solve(c, o, B, d_p_load, d_q_load, d_p_gen, ws, (cudaStream_t)stream,
+                   RunMode::Solve, d_vmag, d_vang, d_info);
+}
+
+int pf_analyze(const pf_case_desc* desc, pf_case_stats* out) {
+  if (!out) return set_error(PF_ERR_INVALID, "null output pointer");
+  CaseData d;
+  Ybus y;
+  std::string err;
+  int rc = copy_case(desc, d, err);
+  if (rc == PF_OK) rc = build_ybus(d, y, err);
+  if (rc != PF_OK) return set_error(rc, err);
+  Symbolic nr, nk;
+  analyze(y, Ordering::MinDegree, true, nr);
+  analyze(y, Ordering::RCM, false, nk);
+  fill_stats(d, nr, nk, out);
+  // what pf_create_case uploads: both systems' arrays and Ybus values
+  long long b = 0;
+  for (const Symbolic* s : {&nr, &nk}) {
+    b += 4LL * ((long long)s->y_rowptr.size() + s->y_col.size() + s->lu_rowptr.size() +
+                s->lu_col.size() + s->lu_diag.size() + s->lu2y.size() + s->upd_ptr.size() +
+                s->upd_pos.size() + s->flev_ptr.size() + s->flev_rows.size() +
+                s->blev_ptr.size() + s->blev_rows.size() + s->perm.size());
+    b += (long long)y.val.size() * 8 + (long long)d.n * (1 + 8 * 9);
+  }
+  out->device_bytes = b;
+  return PF_OK;
+}
+
+int pf_ybus(const pf_case_desc* desc, int64_t* nnz, int32_t* rowptr, int32_t* col,
+            double* val) {
+  if (!nnz) return set_error(PF_ERR_INVALID, "null nnz pointer");
+  CaseData d;
+  Ybus y;
+  std::string err;
+  int rc = copy_case(desc, d, err);
+  if (rc == PF_OK) rc = build_ybus(d, y, err);
+  if (rc != PF_OK) return set_error(rc, err);
+  *nnz = y.nnz();
+  if (!rowptr) return PF_OK;
+  if (!col || !val) return set_error(PF_ERR_INVALID, "col and val are required with rowptr");
+  std::copy(y.rowptr.begin(), y.rowptr.end(), rowptr);
+  std::copy(y.col.begin(), y.col.end(), col);
+  std::copy(y.val.begin(), y.val.end(), val);
+  return PF_OK;
+}
+
+int pf_symbolic(const pf_case_desc* desc, int method, int32_t* perm, int32_t* rowptr,
+                int32_t* col, int32_t* flevel, int32_t* blevel) {
+  if (method != PF_NR && method != PF_NK)
+    return set_error(PF_ERR_INVALID, "method must be PF_NR or PF_NK");
+  CaseData d;
+  Ybus y;
+  std::string err;
+  int rc = copy_case(desc, d, err);
+  if (rc == PF_OK) rc = build_ybus(d, y, err);
+  if (rc != PF_OK) return set_error(rc, err);
+  Symbolic s;
+  if (method == PF_NR) analyze(y, Ordering::MinDegree, true, s);
+  else analyze(y, Ordering::RCM, false, s);
+  if (perm) std::copy(s.perm.begin(), s.perm.end(), perm);
+  if (rowptr) std::copy(s.lu_rowptr.begin(), s.lu_rowptr.end(), rowptr);
+  if (col) std::copy(s.lu_col.begin(), s.lu_col.end(), col);
+  for (int l = 0; l + 1 < (int)s.flev_ptr.size(); ++l)
+    for (int t = s.flev_ptr[l]; t < s.flev_ptr[l + 1]; ++t)
+      if (flevel) flevel[s.flev_rows[t]] = l;
+  for (int l = 0; l + 1 < (int)s.blev_ptr.size(); ++l)
+    for (int t = s.blev_ptr[l]; t < s.blev_ptr[l + 1]; ++t)
+      if (blevel) blevel[s.blev_rows[t]] = l;
+  return PF_OK;
+}
+
+int pf_case_pattern(pf_case c, int32_t* rowptr, int32_t* col) {
+  if (!c || !rowptr || !col) return set_error(PF_ERR_INVALID, "null argument");
+  std::copy(c->y.rowptr.begin(), c->y.rowptr.end(), rowptr);
+  std::copy(c->y.col.begin(), c->y.col.end(), col);
+  return PF_OK;
+}
+
+int pf_eval_mismatch(pf_case c, const double* vmag, const double* vang, double* mis) {
+  if (!c || !vmag || !vang || !mis) return set_error(PF_ERR_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(c->mu);
+  return inspect(c, InspectKind::Mismatch, nullptr, vmag, vang, mis, nullptr);
+}
+
+int pf_eval_jacobian(pf_case c, const double* vmag, const double* vang, double* blocks) {
+  if (!c || !vmag || !vang || !blocks) return set_error(PF_ERR_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(c->mu);
+  return inspect(c, InspectKind::Jacobian, nullptr, vmag, vang, blocks, nullptr);
+}
+
+int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag, const double* vang,
+                   double* dx, pf_info* info) {
+  if (!c || !vmag || !vang || !dx) return set_error(PF_ERR_INVALID, "null argument");
+  pf_opts o;
+  if (opts) o = *opts; else pf_opts_default(&o);
+  std::lock_guard<std::mutex> lk(c->mu);
+  return inspect(c, InspectKind::Step, &o, vmag, vang, dx, info);
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal state behind the opaque handles of pf.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <array>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "device.h"
+#include "host.h"
+
+namespace pf {
+
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+
+// A set of cudaMalloc'ed blocks released together.
+struct DevBuffer {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  ~DevBuffer();
+  void release();
+  cudaError_t alloc(void** out, size_t nbytes);
+};
+
+// One ordering of a case: host symbolic analysis plus its device copy.
+struct SysBuf {
+  Symbolic sym;
+  DevSys view{};
+  DevBuffer mem;
+  std::map<int, std::array<const int8_t*, 3>> g_cache;
+  int build(const CaseData& c, const Ybus& y, Ordering ord, bool fill);
+  int lanes_for(int threads, DevSys& out);
+};
+
+// Per-solve device state for up to `cap` scenarios plus staging buffers.
+struct Workspace {
+  int cap = 0;
+  DevWork w{};
+  DevBuffer mem;
+  double *st_p_load = nullptr, *st_q_load = nullptr, *st_p_gen = nullptr;
+  double *st_vm = nullptr, *st_va = nullptr;
+  pf_info* st_info = nullptr;
+  int ensure(int kind, int n, long long nnz_lu, int B);
+  static size_t bytes_for(int kind, int n, long long nnz_lu, int B);
+};
+
+struct Server;
+
+}  // namespace pf
+
+struct pf_ctx_s {
+  int device = 0;
+  int num_sms = 0;
+  size_t budget = 0;
+  cudaStream_t stream = nullptr;
+  pf::Server* server = nullptr;  // owned; released by serve_shutdown
+  std::mutex server_mu;
+};
+
+struct pf_case_s {
+  pf_ctx ctx = nullptr;
+  pf::CaseData data;
+  pf::Ybus y;
+  int bs = 2;
+  pf::SysBuf nr;  // minimum degree + fill (LU)
+  pf::SysBuf nk;  // reverse Cuthill-McKee, Ybus pattern (ILU(0))
+  pf::Workspace ws1, wsB;
+  pf::DevBuffer mem;
+  double* warm_vm = nullptr;
+  double* warm_va = nullptr;
+  double2* warm_V = nullptr;
+  bool warm_valid = false;
+  std::mutex mu;
+};
+
+namespace pf {
+
+enum class RunMode { Solve, Eval, Step };
+enum class InspectKind { Mismatch, Jacobian, Step };
+
+// Launches one solve of B scenarios on `ws` (asynchronous on `st`).
+// Outputs go to out_vm / out_va / out_info when given, else to the
+// workspace's staging buffers.
+int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load,
+              const double* d_q_load, const double* d_p_gen, Workspace* ws,
+              cudaStream_t st, RunMode mode, double* out_vm, double* out_va,
+              pf_info* out_info = nullptr);
+// Copies staged results of the last run_solve on ws to host arrays.
+int fetch_results(pf_case c, Workspace* ws, int B, double* vmag, double* vang,
+                  pf_info* info, cudaStream_t st);
+int inspect(pf_case c, InspectKind k, const pf_opts* o, const double* vmag,
+            const double* vang, double* out, pf_info* info);
+
+// Launchers in newton.cu / krylov.cu.
+cudaError_t launch_newton(int bs, bool fp32, const DevSys& S, const DevWork& w,
+                          const DevOpts& o, int grid, int cluster, int threads,
+                          cudaStream_t st);
+int max_cluster(int bs, bool fp32, int threads);
+
+// Serving runtime (serve.cpp).
+void serve_shutdown(pf_ctx ctx);
+void serve_forget_case(pf_ctx ctx, pf_case c);
+
+}  // namespace pf

@@ -1,0 +1,96 @@
+// Views of device-resident data shared by the host driver and the kernels.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/pf.h"
+
+namespace pf {
+
+// Running status of a scenario inside a solve.
+constexpr int kRunning = PF_PENDING;
+
+// Symbolic structure and bus data of one case for one ordering (device
+// pointers, new numbering).  Shared by every scenario of the case.
+struct DevSys {
+  int kind;  // PF_SINGLE_PHASE or PF_THREE_PHASE
+  int n;     // buses / nodes
+  // Ybus: complex scalars (single phase) or 3x3 complex blocks, (re, im)
+  const int* y_rowptr;
+  const int* y_col;
+  const double* y_val;
+  // factor pattern (L, diagonal, U per row) and its maps
+  const int* lu_rowptr;
+  const int* lu_col;
+  const int* lu_diag;
+  const int* lu2y;
+  const int* upd_ptr;
+  const int* upd_pos;
+  // level schedules and lanes per row for a single-scenario launch
+  const int* flev_ptr;
+  const int* flev_rows;
+  int nflev;
+  const int* blev_ptr;
+  const int* blev_rows;
+  int nblev;
+  const int8_t* g_fac;
+  const int8_t* g_fwd;
+  const int8_t* g_bwd;
+  // bus data: single phase type 0/1/2; three phase phase mask | 8 at source
+  const int8_t* btype;
+  const double* v_set;
+  const double* q_gen;
+  const double* zip;     // 3 per bus / node
+  const double* p_gen0;  // case's own generation (single phase)
+  const double* p_load0; // case's own loads (per bus or per slot)
+  const double* q_load0;
+  const int* perm;       // new -> caller numbering
+  double v_source;
+};
+
+// Per-solve state for B scenarios, interleaved as [entry][scenario].
+struct DevWork {
+  int B;  // scenario stride
+  // inputs in caller numbering (NULL = the case's own)
+  const double* in_p_load;
+  const double* in_q_load;
+  const double* in_p_gen;
+  const double* in_vm;  // optional start voltage (inspection calls)
+  const double* in_va;
+  // outputs in caller numbering
+  double* out_vm;
+  double* out_va;
+  pf_info* out_info;
+  // warm start (new numbering, scenario 0 only): read if warm_in, written
+  // after a converged solve if warm_out
+  double* warm_vm;
+  double* warm_va;
+  double2* warm_V;
+  int warm_in, warm_out;
+  // state
+  double* spec;   // single: (p_load, q_load, p_gen); three: (p_load, q_load) x 3
+  double* vm;     // single phase
+  double* va;
+  double2* V;     // 1 or 3 per row
+  double2* I;     // I = Y V of the last mismatch evaluation
+  double2* dV;    // refinement: voltage change of the step
+  double* abcd;   // three phase: Eq. 23 adjustments, 12 per row
+  double* F;      // mismatch, bs per row
+  double* dx;     // Newton step, bs per row
+  void* lu;       // factor values, bs*bs per entry
+  void* uinv;     // inverse diagonal blocks, bs*bs per row
+  void* y;        // triangular-solve vector, bs per row
+  unsigned long long* norm;  // [2][B] max |mismatch| (bit pattern of a double)
+  unsigned long long* step;  // [2][B] max |step|
+  int* flag;                 // [B] singular pivot seen
+};
+
+struct DevOpts {
+  double tol;
+  int max_iter;
+  int refine;   // FP64 refinement steps (mixed NR)
+  int S;        // scenarios per cluster
+  int mode;     // 0 solve, 1 evaluate mismatch + Jacobian, 2 one Newton step
+};
+
+}  // namespace pf

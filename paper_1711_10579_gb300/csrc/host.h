@@ -1,0 +1,91 @@
+// Host-side data structures of the power-flow library: the admittance
+// matrix, the symbolic analysis of the Newton system and the level schedules.
+// Everything here is plain C++ (no CUDA) so it can be built and exercised on
+// a machine without a GPU.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pf.h"
+
+namespace pf {
+
+// Ybus in the caller's numbering as block CSR with sorted columns and every
+// diagonal block present.  ybs = 1: complex scalars (single phase, Eq. 2-3);
+// ybs = 3: 3x3 complex blocks (three phase, Eq. 11).  val holds 2*ybs*ybs
+// doubles per entry, (re, im) interleaved, blocks row-major.
+struct Ybus {
+  int n = 0;
+  int ybs = 1;
+  std::vector<int> rowptr, col;
+  std::vector<double> val;
+  int nnz() const { return (int)col.size(); }
+};
+
+// Validated, copied case description (caller's numbering).
+struct CaseData {
+  int kind = PF_SINGLE_PHASE;
+  int n = 0, m = 0;
+  // single phase, per bus
+  std::vector<int8_t> bus_type;
+  std::vector<double> v_set, p_gen, q_gen, p_load, q_load, zip;  // zip: n*3
+  // three phase: per node / per slot
+  std::vector<uint8_t> phases;
+  int source = 0;
+  double v_source = 1.0;
+  std::vector<double> p_load3, q_load3;  // 3n
+  // branches
+  std::vector<int> br_from, br_to;
+  std::vector<double> br_r, br_x, br_b;
+  std::vector<uint8_t> br_phases;
+  std::vector<double> br_z;  // m*18
+};
+
+// Copies and validates; returns PF_OK or PF_ERR_INVALID with a message.
+int copy_case(const pf_case_desc* d, CaseData& out, std::string& err);
+// Eq. 2-3 (pi-model branches) or Eq. 11 (3x3 blocks).
+int build_ybus(const CaseData& c, Ybus& y, std::string& err);
+
+// Ordering of the bus graph.
+enum class Ordering { MinDegree, RCM, Natural };
+
+// Symbolic analysis of the block Newton system for one ordering.  All
+// indices are in the new (permuted) numbering.
+struct Symbolic {
+  int n = 0;
+  std::vector<int> perm, iperm;  // perm[new] = old, iperm[old] = new
+  // Ybus pattern in the new numbering; y_src[e] = entry of the caller's CSR
+  std::vector<int> y_rowptr, y_col, y_src;
+  // block pattern of the factor (L strictly lower, diagonal, U strictly
+  // upper) -- with fill for LU, equal to the Ybus pattern for ILU(0)
+  std::vector<int> lu_rowptr, lu_col, lu_diag;
+  std::vector<int> lu2y;  // factor entry -> new-order Ybus entry or -1 (fill)
+  // update lists: for an L entry p = (i, k), upd_pos[upd_ptr[p] + t] is the
+  // factor entry (i, j) hit by the t-th U entry (k, j) of row k, or -1 when
+  // ILU(0) drops it
+  std::vector<int> upd_ptr, upd_pos;
+  long long n_updates = 0;
+  // level sets: rows of level l are flev_rows[flev_ptr[l] .. flev_ptr[l+1])
+  std::vector<int> flev_ptr, flev_rows;  // factor / forward solve (L deps)
+  std::vector<int> blev_ptr, blev_rows;  // backward solve (U deps)
+  // per level: the longest parallel inner loop (for choosing lanes per row)
+  std::vector<int> flev_ulen;  // factor: longest U row of any pivot used
+  std::vector<int> flev_llen;  // forward: longest L part of a row
+  std::vector<int> blev_ulen;  // backward: longest U part of a row
+  int nnz_lu() const { return (int)lu_col.size(); }
+  int nnz_y() const { return (int)y_col.size(); }
+};
+
+// Computes the ordering and, for MinDegree, the fill of the exact LU
+// factorisation (with_fill = true) or the ILU(0) pattern (with_fill = false).
+void analyze(const Ybus& y, Ordering ord, bool with_fill, Symbolic& s);
+
+// Lanes per row (1, 2, 4, ..., 32) for each level of a schedule, given the
+// longest inner loop per level, the level widths and the threads available.
+std::vector<int8_t> lanes_per_level(const std::vector<int>& lev_ptr,
+                                    const std::vector<int>& longest,
+                                    int threads);
+
+}  // namespace pf

@@ -1,0 +1,182 @@
+// Solve dispatch: launch configuration, result transfer and the inspection
+// entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "api_internal.h"
+
+namespace pf {
+
+namespace {
+
+int check_opts(const pf_opts& o) {
+  if (o.method != PF_NR && o.method != PF_NK)
+    return set_error(PF_ERR_INVALID, "opts.method must be PF_NR or PF_NK");
+  if (o.precision != PF_FP64 && o.precision != PF_MIXED)
+    return set_error(PF_ERR_INVALID, "opts.precision must be PF_FP64 or PF_MIXED");
+  if (!(o.tol > 0.0)) return set_error(PF_ERR_INVALID, "opts.tol must be positive");
+  if (o.max_iter < 0 || o.max_iter > 1000)
+    return set_error(PF_ERR_INVALID, "opts.max_iter must be in [0, 1000]");
+  if (o.refine_steps < 0 || o.refine_steps > 10)
+    return set_error(PF_ERR_INVALID, "opts.refine_steps must be in [0, 10]");
+  if (o.cluster_size < 0 || o.cluster_size > 16 || (o.cluster_size & (o.cluster_size - 1)))
+    return set_error(PF_ERR_INVALID, "opts.cluster_size must be 0 or a power of two <= 16");
+  if (o.block_threads < 0 || o.block_threads > 1024 || (o.block_threads % 32))
+    return set_error(PF_ERR_INVALID, "opts.block_threads must be 0 or a multiple of 32 <= 1024");
+  if (o.scen_per_cta < 0 || o.scen_per_cta > 32)
+    return set_error(PF_ERR_INVALID, "opts.scen_per_cta must be in [0, 32]");
+  return PF_OK;
+}
+
+struct ClusterKey {
+  int bs, fp32, threads;
+  bool operator<(const ClusterKey& k) const {
+    return std::tie(bs, fp32, threads) < std::tie(k.bs, k.fp32, k.threads);
+  }
+};
+
+int cached_max_cluster(int bs, bool fp32, int threads) {
+  static std::mutex mu;
+  static std::map<ClusterKey, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  ClusterKey k{bs, fp32 ? 1 : 0, threads};
+  auto it = cache.find(k);
+  if (it != cache.end()) return it->second;
+  int c = max_cluster(bs, fp32, threads);
+  cache[k] = c;
+  return c;
+}
+
+}  // namespace
+
+int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const double* d_q_load,
+              const double* d_p_gen, Workspace* ws, cudaStream_t st, RunMode mode, double* out_vm,
+              double* out_va, pf_info* out_info) {
+  int rc = check_opts(o);
+  if (rc != PF_OK) return rc;
+  if (o.method == PF_NK)
+    return set_error(PF_ERR_UNSUPPORTED, "the Newton-Krylov solver is not built yet");
+  const int kind = c->data.kind, n = c->data.n, bs = c->bs;
+  rc = ws->ensure(kind, n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), B);
+  if (rc != PF_OK) return rc;
+  SysBuf& sb = c->nr;
+  // inspection of the Jacobian reads the factor array as FP64
+  const bool fp32 = (o.precision == PF_MIXED) && mode != RunMode::Eval;
+  const int max_threads = (bs == 2) ? 1024 : 256;
+  int threads, cluster, S, grid;
+  if (B == 1) {
+    threads = o.block_threads ? std::min(o.block_threads, max_threads) : max_threads;
+    cluster = o.cluster_size ? o.cluster_size : cached_max_cluster(bs, fp32, threads);
+    S = 1;
+    grid = cluster;
+  } else {
+    threads = o.block_threads ? std::min(o.block_threads, max_threads) : 256;
+    cluster = 1;
+    S = o.scen_per_cta ? o.scen_per_cta : 2;
+    grid = (B + S - 1) / S;
+  }
+  DevSys sys;
+  rc = sb.lanes_for(cluster * threads, sys);
+  if (rc != PF_OK) return rc;
+  DevWork w = ws->w;
+  w.B = B;
+  w.in_p_load = d_p_load;
+  w.in_q_load = d_q_load;
+  w.in_p_gen = d_p_gen;
+  w.in_vm = nullptr;
+  w.in_va = nullptr;
+  w.out_vm = out_vm ? out_vm : ws->st_vm;
+  w.out_va = out_va ? out_va : ws->st_va;
+  w.out_info = out_info ? out_info : ws->st_info;
+  w.warm_vm = c->warm_vm;
+  w.warm_va = c->warm_va;
+  w.warm_V = c->warm_V;
+  w.warm_in = (o.warm_start && c->warm_valid && B == 1 && mode == RunMode::Solve) ? 1 : 0;
+  w.warm_out = (B == 1 && mode == RunMode::Solve) ? 1 : 0;
+  if (mode != RunMode::Solve) {
+    w.in_vm = ws->st_p_load;  // staged start voltage of an inspection call
+    w.in_va = ws->st_q_load;
+    w.in_p_load = w.in_q_load = w.in_p_gen = nullptr;
+  }
+  DevOpts d;
+  d.tol = o.tol;
+  d.max_iter = o.max_iter;
+  d.refine = fp32 && o.method == PF_NR ? o.refine_steps : 0;
+  d.S = S;
+  d.mode = mode == RunMode::Solve ? 0 : (mode == RunMode::Eval ? 1 : 2);
+  cudaError_t e = launch_newton(bs, fp32, sys, w, d, grid, cluster, threads, st);
+  if (e != cudaSuccess) return cuda_error(e, "launching the Newton kernel");
+  return PF_OK;
+}
+
+int fetch_results(pf_case c, Workspace* ws, int B, double* vmag, double* vang, pf_info* info,
+                  cudaStream_t st) {
+  const size_t per = (size_t)c->data.n * (c->data.kind == PF_SINGLE_PHASE ? 1 : 3);
+  std::vector<pf_info> inf(B);
+  cudaError_t e = cudaSuccess;
+  if (vmag) e = cudaMemcpyAsync(vmag, ws->st_vm, per * B * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && vang)
+    e = cudaMemcpyAsync(vang, ws->st_va, per * B * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(inf.data(), ws->st_info, B * sizeof(pf_info), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "running the solve");
+  if (info) std::copy(inf.begin(), inf.end(), info);
+  if (B == 1 && inf[0].status == PF_OK) c->warm_valid = true;
+  return PF_OK;
+}
+
+int inspect(pf_case c, InspectKind k, const pf_opts* po, const double* vmag, const double* vang,
+            double* out, pf_info* info) {
+  pf_opts o;
+  if (po) o = *po; else pf_opts_default(&o);
+  cudaSetDevice(c->ctx->device);
+  cudaStream_t st = c->ctx->stream;
+  Workspace* ws = &c->ws1;
+  const int kind = c->data.kind, n = c->data.n, bs = c->bs;
+  int rc = ws->ensure(kind, n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), 1);
+  if (rc != PF_OK) return rc;
+  const size_t per = (size_t)n * (kind == PF_SINGLE_PHASE ? 1 : 3);
+  cudaError_t e = cudaMemcpyAsync(ws->st_p_load, vmag, per * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws->st_q_load, vang, per * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "copying the voltage");
+  RunMode mode = (k == InspectKind::Step) ? RunMode::Step : RunMode::Eval;
+  if (k != InspectKind::Step) o.precision = PF_FP64;
+  rc = run_solve(c, o, 1, nullptr, nullptr, nullptr, ws, st, mode, nullptr, nullptr);
+  if (rc != PF_OK) return rc;
+  const Symbolic& s = c->nr.sym;
+  if (k == InspectKind::Jacobian) {
+    const int bb = bs * bs;
+    std::vector<double> lu((size_t)s.nnz_lu() * bb);
+    e = cudaMemcpyAsync(lu.data(), ws->w.lu, lu.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "evaluating the Jacobian");
+    for (int q = 0; q < s.nnz_lu(); ++q) {
+      const int ye = s.lu2y[q];
+      if (ye < 0) continue;
+      std::copy(lu.begin() + (size_t)q * bb, lu.begin() + (size_t)(q + 1) * bb,
+                out + (size_t)s.y_src[ye] * bb);
+    }
+    return PF_OK;
+  }
+  std::vector<double> v((size_t)n * bs);
+  const double* src = (k == InspectKind::Mismatch) ? ws->w.F : ws->w.dx;
+  e = cudaMemcpyAsync(v.data(), src, v.size() * 8, cudaMemcpyDeviceToHost, st);
+  pf_info inf{};
+  if (e == cudaSuccess && k == InspectKind::Step)
+    e = cudaMemcpyAsync(&inf, ws->st_info, sizeof(pf_info), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "running the inspection kernel");
+  for (int i = 0; i < n; ++i)
+    for (int t = 0; t < bs; ++t) out[(size_t)s.perm[i] * bs + t] = v[(size_t)i * bs + t];
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = PF_OK;
+  }
+  return PF_OK;
+}
+
+}  // namespace pf

@@ -1,0 +1,342 @@
+"""GPU parity: every step of the Newton iteration, through the C ABI, against
+the FP64 oracle on the same seeded inputs.
+
+Tolerances: mismatch and Jacobian entries are FP64 arithmetic on both sides
+(rectangular form on the GPU, trigonometric form in the oracle), so they
+agree to ~1e-12 relative; a converged solve must match the oracle within
+|dV| <= 1e-6 pu and |dtheta| <= 1e-6 rad at a mismatch <= 1e-8 pu.
+"""
+import numpy as np
+import pytest
+
+from oracle import pf_oracle as O
+from paper_1711_10579_gb300 import cases
+
+pytestmark = pytest.mark.gpu
+
+V_TOL = 1e-6
+A_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1711_10579_gb300 import pf as _pf
+
+    return _pf
+
+
+@pytest.fixture(scope="module")
+def ctx(pf):
+    h = pf.pf_ctx_create(0)
+    yield h
+    pf.pf_ctx_destroy(h)
+
+
+def _zip_case(case, seed):
+    import dataclasses as dc
+
+    z = np.random.default_rng(seed).dirichlet([1, 1, 1], case.n_bus)
+    return dc.replace(case, zip=z)
+
+
+def _rand_v(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.9, 1.1, n), rng.uniform(-0.3, 0.3, n)
+
+
+def _oracle_blocks(case, Y, vm, va):
+    """Oracle Jacobian (Eq. 10) regrouped into 2x2 blocks on the Ybus pattern."""
+    J = O.jacobian_polar(case, Y, vm, va).tocsr()
+    pvpq, pq = O.unknowns_polar(case)
+    n = case.n_bus
+    ip = np.full(n, -1)
+    ip[pvpq] = np.arange(pvpq.size)
+    iq = np.full(n, -1)
+    iq[pq] = pvpq.size + np.arange(pq.size)
+    Yc = Y.tocsr()
+    Yc.sort_indices()
+    out = np.zeros((Yc.nnz, 2, 2))
+    for i in range(n):
+        for p in range(Yc.indptr[i], Yc.indptr[i + 1]):
+            j = Yc.indices[p]
+            rows = (ip[i], iq[i])
+            cols = (ip[j], iq[j])
+            for a in range(2):
+                for b in range(2):
+                    if rows[a] >= 0 and cols[b] >= 0:
+                        out[p, a, b] = J[rows[a], cols[b]]
+                    elif i == j and a == b:
+                        out[p, a, b] = 1.0
+    return out
+
+
+def _gpu_mis_to_oracle_order(case, mis):
+    pvpq, pq = O.unknowns_polar(case)
+    return np.concatenate([mis[pvpq, 0], mis[pq, 1]])
+
+
+# ----------------------------------------------------------------------------
+# single phase, step by step
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["14", "300zip", "2000"])
+def test_mismatch_and_jacobian_single_phase(pf, ctx, name):
+    case = {"14": cases.case_14bus(0),
+            "300zip": _zip_case(cases.transmission_case(300, 405, 60, 2), 2),
+            "2000": cases.case_2000bus(0)}[name]
+    Y = O.ybus_single(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        for seed in range(3):
+            vm, va = _rand_v(case.n_bus, seed)
+            mis = pf.pf_eval_mismatch(c, vm, va)
+            ref = O.mismatch_polar(case, Y, vm, va)
+            got = _gpu_mis_to_oracle_order(case, mis)
+            assert np.max(np.abs(got - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref)))
+            # rows without an equation are exactly zero
+            assert np.all(mis[case.bus_type == cases.SLACK] == 0)
+            assert np.all(mis[case.bus_type == cases.PV, 1] == 0)
+            st = pf.pf_case_get_stats(c)
+            blocks = pf.pf_eval_jacobian(c, vm, va, st["nnz_y"])
+            ref_b = _oracle_blocks(case, Y, vm, va)
+            scale = max(1.0, np.max(np.abs(ref_b)))
+            assert np.max(np.abs(blocks - ref_b)) <= 1e-11 * scale
+    finally:
+        pf.pf_destroy_case(c)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
+@pytest.mark.parametrize("name", ["300zip", "2000"])
+def test_newton_step_matches_oracle_solve(pf, ctx, name, prec, tol):
+    case = {"300zip": _zip_case(cases.transmission_case(300, 405, 60, 2), 2),
+            "2000": cases.case_2000bus(0)}[name]
+    Y = O.ybus_single(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va = O.flat_start_polar(case)
+        vm = vm + np.where(case.bus_type == cases.PQ, 0.01 * np.sin(np.arange(case.n_bus)), 0)
+        va = va + np.where(case.bus_type != cases.SLACK, 0.02 * np.cos(np.arange(case.n_bus)), 0)
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        dx, _ = pf.pf_newton_step(c, vm, va, pf.make_opts(precision=p, refine_steps=2))
+        F = O.mismatch_polar(case, Y, vm, va)
+        ref = O.solve_linear(O.jacobian_polar(case, Y, vm, va), F, "splu")
+        got = _gpu_mis_to_oracle_order(case, dx)
+        assert np.max(np.abs(got - ref)) <= tol * max(1.0, np.max(np.abs(ref)))
+        assert np.all(dx[case.bus_type == cases.SLACK] == 0)
+        assert np.all(dx[case.bus_type == cases.PV, 1] == 0)
+    finally:
+        pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# single phase, full solves
+# ----------------------------------------------------------------------------
+
+def _check_solve(case, vm, va, info, ref):
+    assert info["status"] == 0, info
+    assert info["mismatch"] <= 1e-8
+    assert np.max(np.abs(vm - ref["vm"])) <= V_TOL
+    assert np.max(np.abs(va - ref["va"])) <= A_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["14", "300zip", "2000", "10000"])
+def test_solve_single_phase_matches_oracle(pf, ctx, name, prec):
+    case = {"14": cases.case_14bus(0),
+            "300zip": _zip_case(cases.transmission_case(300, 405, 60, 2), 2),
+            "2000": cases.case_2000bus(0), "10000": cases.case_10000bus(0)}[name]
+    ref = O.newton_polar(case)
+    assert ref["converged"]
+    c = pf.pf_create_case(ctx, case)
+    try:
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        vm, va, info = pf.pf_solve(c, pf.make_opts(precision=p))
+        _check_solve(case, vm, va, info, ref)
+        assert info["iterations"] <= ref["iterations"] + 2
+        assert info["solve_us"] > 0
+    finally:
+        pf.pf_destroy_case(c)
+
+
+@pytest.mark.parametrize("cluster,threads", [(1, 1024), (2, 512), (8, 256), (16, 1024), (4, 128)])
+def test_launch_shapes_agree(pf, ctx, cluster, threads):
+    case = cases.case_2000bus(1)
+    ref = O.newton_polar(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve(c, pf.make_opts(cluster_size=cluster, block_threads=threads))
+        _check_solve(case, vm, va, info, ref)
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_warm_start_reuses_the_last_solution(pf, ctx):
+    case = cases.case_2000bus(2)
+    ref = O.newton_polar(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve(c)
+        _check_solve(case, vm, va, info, ref)
+        vm2, va2, info2 = pf.pf_solve(c, pf.make_opts(warm_start=1))
+        _check_solve(case, vm2, va2, info2, ref)
+        assert info2["iterations"] <= 1
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_edge_cases(pf, ctx):
+    one = cases.SinglePhaseCase(
+        n_bus=1, bus_type=np.array([0], np.int32), v_set=np.array([1.02]), p_gen=np.zeros(1),
+        q_gen=np.zeros(1), p_load=np.zeros(1), q_load=np.zeros(1), zip=np.array([[1.0, 0, 0]]),
+        br_from=np.zeros(0, np.int32), br_to=np.zeros(0, np.int32), br_r=np.zeros(0),
+        br_x=np.zeros(0), br_b=np.zeros(0))
+    c = pf.pf_create_case(ctx, one)
+    vm, va, info = pf.pf_solve(c)
+    assert info["status"] == 0 and info["iterations"] == 0 and vm[0] == 1.02
+    pf.pf_destroy_case(c)
+    # two-bus closed form through the GPU
+    tb = cases.two_bus_case(0.9, 0.3, 0.02, 0.15)
+    ref = O.newton_polar(tb)
+    c = pf.pf_create_case(ctx, tb)
+    vm, va, info = pf.pf_solve(c, pf.make_opts(precision=pf.PF_FP64))
+    _check_solve(tb, vm, va, info, ref)
+    # no iteration allowed: reports MAXITER with the flat-start mismatch
+    vm, va, info = pf.pf_solve(c, pf.make_opts(max_iter=0))
+    assert info["status"] == pf.PF_ERR_MAXITER and info["iterations"] == 0
+    pf.pf_destroy_case(c)
+    # far beyond the nose of the PV curve: no solution exists
+    bad = cases.two_bus_case(50.0, 20.0, 0.02, 0.15)
+    c = pf.pf_create_case(ctx, bad)
+    vm, va, info = pf.pf_solve(c, pf.make_opts(max_iter=20))
+    assert info["status"] in (pf.PF_ERR_MAXITER, pf.PF_ERR_DIVERGED, pf.PF_ERR_SINGULAR)
+    pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# batches of scenarios
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("B,S", [(37, 2), (64, 4), (512, 0)])
+def test_batch_matches_oracle_and_single(pf, ctx, B, S):
+    case = cases.case_2000bus(0)
+    p_load, q_load, p_gen = cases.scenario_loads(case, B, seed=11)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve_batch(c, p_load, q_load, p_gen, pf.make_opts(scen_per_cta=S))
+        assert np.all(info["status"] == 0), info["status"]
+        assert np.all(info["mismatch"] <= 1e-8)
+        for b in sorted({0, B // 2, B - 1}):
+            ref = O.newton_polar(case.with_loads(p_load[b], q_load[b], p_gen[b]))
+            assert np.max(np.abs(vm[b] - ref["vm"])) <= V_TOL
+            assert np.max(np.abs(va[b] - ref["va"])) <= A_TOL
+            # the same scenario solved alone
+            c1 = pf.pf_create_case(ctx, case.with_loads(p_load[b], q_load[b], p_gen[b]))
+            vm1, va1, _ = pf.pf_solve(c1)
+            pf.pf_destroy_case(c1)
+            assert np.max(np.abs(vm[b] - vm1)) <= 1e-9
+            assert np.max(np.abs(va[b] - va1)) <= 1e-9
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_device_entry_point_matches_host_entry_point(pf, ctx):
+    torch = pytest.importorskip("torch")
+    case = cases.case_2000bus(3)
+    B = 16
+    p_load, q_load, p_gen = cases.scenario_loads(case, B, seed=5)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm_h, va_h, info_h = pf.pf_solve_batch(c, p_load, q_load, p_gen)
+        dev = torch.device("cuda:0")
+        t = [torch.tensor(a, device=dev) for a in (p_load, q_load, p_gen)]
+        vm_d = torch.zeros((B, case.n_bus), dtype=torch.float64, device=dev)
+        va_d = torch.zeros_like(vm_d)
+        info_d = torch.zeros((B, pf.INFO_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+        stream = torch.cuda.current_stream()
+        pf.pf_solve_batch_device(c, B, t[0], t[1], t[2], pf.make_opts(), vm_d, va_d, info_d,
+                                 stream.cuda_stream)
+        torch.cuda.synchronize()
+        info = np.frombuffer(info_d.cpu().numpy().tobytes(), dtype=pf.INFO_DTYPE)
+        assert np.all(info["status"] == 0)
+        assert np.max(np.abs(vm_d.cpu().numpy() - vm_h)) <= 1e-12
+        assert np.max(np.abs(va_d.cpu().numpy() - va_h)) <= 1e-12
+    finally:
+        pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# three phase (current injection)
+# ----------------------------------------------------------------------------
+
+def _rand_v3(case, seed):
+    rng = np.random.default_rng(seed)
+    V = O.cim_flat_start(case)
+    V = V * rng.uniform(0.92, 1.05, V.size) * np.exp(1j * rng.uniform(-0.1, 0.1, V.size))
+    return np.abs(V), np.where(np.abs(V) > 0, np.angle(V), 0.0), V
+
+
+@pytest.mark.parametrize("n", [12, 300])
+def test_mismatch_and_jacobian_three_phase(pf, ctx, n):
+    case = cases.feeder_case(n, 3, reduced_p=0.5, max_drop=0.08)
+    Y = O.ybus_three_phase(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        for seed in range(2):
+            vm, va, V = _rand_v3(case, seed)
+            V = vm * np.exp(1j * va)  # same rounding as the GPU input
+            mis = pf.pf_eval_mismatch(c, vm, va)
+            ref = O.cim_mismatch(case, Y, V).reshape(n, 6)
+            assert np.max(np.abs(mis - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref)))
+            st = pf.pf_case_get_stats(c)
+            blocks = pf.pf_eval_jacobian(c, vm, va, st["nnz_y"])
+            J = O.cim_jacobian(case, Y, V).toarray()
+            rp, col = pf.pf_case_pattern(c, st["nnz_y"])
+            free = np.concatenate([O.cim_free_slots(case).reshape(n, 3)] * 2, 1)
+            for i in range(n):
+                for p in range(rp[i], rp[i + 1]):
+                    j = col[p]
+                    rb = J[6 * i:6 * i + 6, 6 * j:6 * j + 6].copy()
+                    rb[~free[i], :] = 0
+                    rb[:, ~free[j]] = 0
+                    if i == j:
+                        rb[~free[i], ~free[i]] = 1
+                    assert np.max(np.abs(blocks[p] - rb)) <= 1e-10 * max(1, np.max(np.abs(rb)))
+    finally:
+        pf.pf_destroy_case(c)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [200, 8000])
+def test_solve_three_phase_matches_oracle(pf, ctx, n, prec):
+    case = cases.case_feeder8000(0) if n == 8000 else cases.feeder_case(n, 1)
+    ref = O.newton_cim(case)
+    assert ref["converged"]
+    c = pf.pf_create_case(ctx, case)
+    try:
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        vm, va, info = pf.pf_solve(c, pf.make_opts(precision=p))
+        assert info["status"] == 0 and info["mismatch"] <= 1e-8, info
+        assert np.max(np.abs(vm - np.abs(ref["V"]))) <= V_TOL
+        rv = np.where(np.abs(ref["V"]) > 0, np.angle(ref["V"]), 0.0)
+        d = np.angle(np.exp(1j * (va - rv)))
+        assert np.max(np.abs(d)) <= A_TOL
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_three_phase_batch_matches_single(pf, ctx):
+    case = cases.feeder_case(500, 2)
+    B = 9
+    pl, ql = cases.feeder_scenario_loads(case, B, seed=3)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve_batch(c, pl, ql, None, pf.make_opts(scen_per_cta=2))
+        assert np.all(info["status"] == 0)
+        for b in (0, B - 1):
+            ref = O.newton_cim(case.with_loads(pl[b], ql[b]))
+            assert np.max(np.abs(vm[b] - np.abs(ref["V"]))) <= V_TOL
+    finally:
+        pf.pf_destroy_case(c)

@@ -1,0 +1,198 @@
+"""Host-side logic of the library, CPU only: symbol exports, validation,
+admittance assembly and the symbolic analysis (no GPU calls)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import pf_oracle as O
+from paper_1711_10579_gb300 import build as B
+from paper_1711_10579_gb300 import cases
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pf():
+    B.build()
+    from paper_1711_10579_gb300 import pf as _pf
+
+    _pf.lib()
+    return _pf
+
+
+def test_library_exports_every_declared_symbol(pf):
+    header = open(os.path.join(ROOT, "include", "pf.h")).read()
+    header = re.sub(r"/\*.*?\*/", "", header, flags=re.S)
+    declared = set(re.findall(r"\b(pf_[a-z_]+)\s*\(", header))
+    assert len(declared) >= 20
+    lib = ctypes.CDLL(pf.LIB_PATH)
+    missing = [s for s in sorted(declared) if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_ybus_matches_oracle_single_phase(pf):
+    for seed in range(3):
+        case = cases.transmission_case(300, 405, 60, seed)
+        rp, col, val = pf.pf_ybus(case)
+        Y = sp.csr_matrix((val, col, rp), shape=(case.n_bus,) * 2)
+        assert abs(Y - O.ybus_single(case)).max() < 1e-10
+
+
+def test_ybus_matches_oracle_three_phase(pf):
+    f = cases.feeder_case(120, 4, reduced_p=0.6)
+    rp, col, val = pf.pf_ybus(f)
+    n = f.n_node
+    Yd = np.zeros((3 * n, 3 * n), complex)
+    for i in range(n):
+        for p in range(rp[i], rp[i + 1]):
+            Yd[3 * i:3 * i + 3, 3 * col[p]:3 * col[p] + 3] = val[p]
+    assert np.max(np.abs(Yd - O.ybus_three_phase(f).toarray())) < 1e-9
+
+
+def _brute_fill(n, edges, perm):
+    """Filled graph of symmetric elimination in the order perm (brute force)."""
+    inv = np.empty(n, int)
+    inv[perm] = np.arange(n)
+    adj = [set() for _ in range(n)]
+    for a, b in edges:
+        adj[inv[a]].add(inv[b])
+        adj[inv[b]].add(inv[a])
+    filled = set()
+    for k in range(n):
+        higher = sorted(v for v in adj[k] if v > k)
+        for i in higher:
+            filled.add((i, k))
+            filled.add((k, i))
+        for a in higher:
+            for b in higher:
+                if a != b:
+                    adj[a].add(b)
+    return filled | {(i, i) for i in range(n)}
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_symbolic_lu_pattern_is_the_exact_fill(pf, seed):
+    case = cases.transmission_case(60, 90, 10, seed)
+    perm, rp, col, fl, bl = pf.pf_symbolic(case, pf.PF_NR)
+    n = case.n_bus
+    assert sorted(perm) == list(range(n))
+    got = {(i, int(col[p])) for i in range(n) for p in range(rp[i], rp[i + 1])}
+    want = _brute_fill(n, zip(case.br_from, case.br_to), perm)
+    assert got == want
+
+
+@pytest.mark.parametrize("method", ["NR", "NK"])
+def test_level_sets_respect_dependencies(pf, method):
+    case = cases.transmission_case(500, 680, 100, 3)
+    m = pf.PF_NR if method == "NR" else pf.PF_NK
+    perm, rp, col, fl, bl = pf.pf_symbolic(case, m)
+    n = case.n_bus
+    for i in range(n):
+        cols = col[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(cols) > 0) and i in cols
+        lower, upper = cols[cols < i], cols[cols > i]
+        assert np.all(fl[lower] < fl[i]) and (lower.size == 0 or fl[i] == fl[lower].max() + 1)
+        assert np.all(bl[upper] < bl[i]) and (upper.size == 0 or bl[i] == bl[upper].max() + 1)
+
+
+def test_ilu_pattern_is_ybus_pattern(pf):
+    case = cases.transmission_case(400, 540, 80, 5)
+    perm, rp, col, _, _ = pf.pf_symbolic(case, pf.PF_NK)
+    yr, yc, _ = pf.pf_ybus(case)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    got = {(i, int(c)) for i in range(case.n_bus) for c in col[rp[i]:rp[i + 1]]}
+    want = {(int(inv[i]), int(inv[c])) for i in range(case.n_bus) for c in yc[yr[i]:yr[i + 1]]}
+    assert got == want
+
+
+def test_rcm_reduces_bandwidth(pf):
+    case = cases.transmission_case(2000, 2700, 400, 7)
+    perm, rp, col, _, _ = pf.pf_symbolic(case, pf.PF_NK)
+    rows = np.repeat(np.arange(case.n_bus), np.diff(rp))
+    bw_rcm = np.max(np.abs(rows - col))
+    yr, yc, _ = pf.pf_ybus(case)
+    rows0 = np.repeat(np.arange(case.n_bus), np.diff(yr))
+    assert bw_rcm < np.max(np.abs(rows0 - yc)) / 5
+
+
+def test_tree_feeder_has_no_fill(pf):
+    st = pf.pf_analyze(cases.feeder_case(2000, 1))
+    assert st["nnz_lu"] == st["nnz_y"]
+    assert st["block_size"] == 6
+
+
+def test_stats_of_the_10000_bus_case(pf):
+    st = pf.pf_analyze(cases.case_10000bus(0))
+    assert st["n_unknowns"] == 2 * 7999 + 2000
+    assert st["nnz_y"] == 10_000 + 2 * 13_500
+    assert st["nnz_y"] <= st["nnz_lu"] <= 3 * st["nnz_y"]
+    assert st["levels_factor"] < 200
+
+
+def _invalid(pf, case, match):
+    with pytest.raises(pf.PfError) as e:
+        pf.pf_analyze(case)
+    assert e.value.code == pf.PF_ERR_INVALID
+    assert re.search(match, str(e.value)), str(e.value)
+
+
+def test_validation_errors(pf):
+    import dataclasses as dc
+
+    base = cases.case_14bus(0)
+    bt = base.bus_type.copy()
+    bt[0] = cases.PQ
+    _invalid(pf, dc.replace(base, bus_type=bt), "exactly one slack")
+    bt = base.bus_type.copy()
+    bt[3] = cases.SLACK
+    _invalid(pf, dc.replace(base, bus_type=bt), "exactly one slack")
+    f = base.br_from.copy()
+    f[2] = 99
+    _invalid(pf, dc.replace(base, br_from=f), "out of range")
+    t = base.br_to.copy()
+    t[0] = base.br_from[0]
+    _invalid(pf, dc.replace(base, br_to=t), "self loop")
+    r, x = base.br_r.copy(), base.br_x.copy()
+    r[1] = x[1] = 0.0
+    _invalid(pf, dc.replace(base, br_r=r, br_x=x), "zero impedance")
+    pl = base.p_load.copy()
+    pl[5] = np.nan
+    _invalid(pf, dc.replace(base, p_load=pl), "non-finite")
+    # drop every branch of bus 13: disconnected
+    keep = (base.br_from != 13) & (base.br_to != 13)
+    _invalid(pf, dc.replace(base, br_from=base.br_from[keep], br_to=base.br_to[keep],
+                            br_r=base.br_r[keep], br_x=base.br_x[keep], br_b=base.br_b[keep]),
+             "not connected")
+    fd = cases.feeder_case(30, 0)
+    ph = fd.phases.copy()
+    ph[5] = 0
+    _invalid(pf, dc.replace(fd, phases=ph), "phase mask")
+    bp = fd.br_phases.copy()
+    bp[:] = 7
+    ph = fd.phases.copy()
+    ph[fd.br_to[4]] = 1
+    _invalid(pf, dc.replace(fd, phases=ph, br_phases=bp), "phases missing")
+
+
+def test_single_bus_case_is_valid(pf):
+    one = cases.SinglePhaseCase(
+        n_bus=1, bus_type=np.array([0], np.int32), v_set=np.ones(1), p_gen=np.zeros(1),
+        q_gen=np.zeros(1), p_load=np.zeros(1), q_load=np.zeros(1), zip=np.array([[1.0, 0, 0]]),
+        br_from=np.zeros(0, np.int32), br_to=np.zeros(0, np.int32), br_r=np.zeros(0),
+        br_x=np.zeros(0), br_b=np.zeros(0))
+    st = pf.pf_analyze(one)
+    assert st["n_unknowns"] == 0 and st["nnz_lu"] == 1
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1711_10579_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"(import\s+oracle|from\s+oracle|pf_oracle)", src), f
