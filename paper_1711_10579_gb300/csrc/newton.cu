@@ -828,7 +828,7 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
                      [&](int i, int gs, int lane, int G, unsigned gmask) {
                        forward_row<BS, TF>(S, w, i, gs, lane, G, gmask);
                      });
-      run_levels<CL>(tm, S.blev_ptr, S.blev_rows, S.nblev, S.g_bwd, true,
+      run_levels<CL>(tm, S.blev_ptr, S.blev_rows, S.nblev, S.g_bwd, false,
                      [&](int i, int gs, int lane, int G, unsigned gmask) {
                        backward_row<BS, TF>(S, w, i, gs, lane, G, gmask);
                      });
