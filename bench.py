@@ -298,6 +298,9 @@ def main():
         "e2e": e2e, "gpu_launches": K, "clocks": clk, "wall_s": t_wall,
     }
 
+    if rank == 0:
+        prof, pinfo = pf.pf_profile_solve(c, opts)
+        line["phase_us_one_solve"] = {k: round(v, 1) for k, v in prof.items()}
     if not args.no_variants and rank == 0:
         line["variants"] = variants(pf, ctx, torch, dev)
     if rank == 0 and not args.no_cpu:

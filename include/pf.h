@@ -122,6 +122,7 @@ typedef struct {
   double tol;         /* stop when the power-mismatch infinity norm <= tol (pu); default 1e-8 */
   int max_iter;       /* Newton iterations; default 30 */
   int refine_steps;   /* NR + PF_MIXED: FP64 iterative-refinement steps per solve; default 1 */
+  double refine_below; /* ... applied once the mismatch norm is <= this (pu); default 1e-3 */
   int gmres_restart;  /* NK: Krylov subspace size m of GMRES(m); default 30 */
   int gmres_max_iter; /* NK: inner iterations per Newton step; default 300 */
   double gmres_rtol;  /* NK: inner relative-residual floor; default 1e-6 */
@@ -289,6 +290,22 @@ int pf_case_pattern(pf_case c, int32_t* rowptr, int32_t* col);
  */
 int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag,
                    const double* vang, double* dx, pf_info* info);
+
+/*
+ * Launch shape a solve of B scenarios with these options would use:
+ * grid CTAs, CTAs per cluster, threads per CTA, scenarios per cluster.
+ */
+int pf_launch_config(pf_case c, const pf_opts* opts, int B, int* grid, int* cluster,
+                     int* threads, int* scen_per_cluster);
+
+/*
+ * One pf_solve of the case with per-phase device timers (diagnostics).
+ * phase_us[8] (host) receives microseconds spent in: set-up, mismatch +
+ * Jacobian, stop test, factorisation, triangular solves, right-hand sides and
+ * refinement residuals, voltage update, output -- as seen by one thread of
+ * the launch between its barriers, summed over the Newton iterations.
+ */
+int pf_profile_solve(pf_case c, const pf_opts* opts, double* phase_us, pf_info* info);
 
 #ifdef __cplusplus
 }

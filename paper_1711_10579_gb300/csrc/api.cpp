@@ -122,8 +122,13 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   UP(s.lu_col, lu_col);
   UP(s.lu_diag, lu_diag);
   UP(s.lu2y, lu2y);
-  UP(s.upd_ptr, upd_ptr);
-  UP(s.upd_pos, upd_pos);
+  UP(s.fac_ptr, fac_ptr);
+  UP(s.fac_items, fac_items);
+  UP(s.tgt_ptr, tgt_ptr);
+  UP(s.tgt_entry, tgt_entry);
+  UP(s.tgt_cptr, tgt_cptr);
+  UP(s.con_l, con_l);
+  UP(s.con_u, con_u);
   UP(s.flev_ptr, flev_ptr);
   UP(s.flev_rows, flev_rows);
   UP(s.blev_ptr, blev_ptr);
@@ -136,6 +141,26 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   UP(pl, p_load0);
   UP(ql, q_load0);
   UP(s.perm, perm);
+  // packed per-item records (one 16-byte load each) for the kernels' prefetch
+  std::vector<int4> fwd(n), bwd(n), fac(s.fac_items.size()), tgt(s.tgt_entry.size());
+  std::vector<int2> con(s.con_l.size());
+  for (int t = 0; t < n; ++t) {
+    const int i = s.flev_rows[t], j = s.blev_rows[t];
+    fwd[t] = make_int4(i, s.lu_rowptr[i], s.lu_diag[i], 0);
+    bwd[t] = make_int4(j, s.lu_diag[j] + 1, s.lu_rowptr[j + 1], 0);
+  }
+  for (size_t t = 0; t < fac.size(); ++t) {
+    const int e = s.fac_items[t], k = s.lu_col[e];
+    fac[t] = make_int4(e, k, s.lu_diag[k], 0);
+  }
+  for (size_t t = 0; t < tgt.size(); ++t)
+    tgt[t] = make_int4(s.tgt_entry[t], s.tgt_cptr[t], s.tgt_cptr[t + 1], 0);
+  for (size_t c = 0; c < con.size(); ++c) con[c] = make_int2(s.con_l[c], s.con_u[c]);
+  UP(fwd, fwd_rec);
+  UP(bwd, bwd_rec);
+  UP(fac, fac_rec);
+  UP(tgt, tgt_rec);
+  UP(con, con);
 #undef UP
   d.nflev = (int)s.flev_ptr.size() - 1;
   d.nblev = (int)s.blev_ptr.size() - 1;
@@ -148,19 +173,25 @@ int SysBuf::lanes_for(int threads, DevSys& out) {
   out = view;
   auto it = g_cache.find(threads);
   if (it == g_cache.end()) {
-    auto gf = lanes_per_level(sym.flev_ptr, sym.flev_ulen, threads);
     auto gw = lanes_per_level(sym.flev_ptr, sym.flev_llen, threads);
     auto gb = lanes_per_level(sym.blev_ptr, sym.blev_ulen, threads);
-    std::array<const int8_t*, 3> arr{};
-    cudaError_t e = upload(mem, gf, &arr[0]);
-    if (e == cudaSuccess) e = upload(mem, gw, &arr[1]);
-    if (e == cudaSuccess) e = upload(mem, gb, &arr[2]);
+    std::array<const int8_t*, 2> arr{};
+    cudaError_t e = upload(mem, gw, &arr[0]);
+    if (e == cudaSuccess) e = upload(mem, gb, &arr[1]);
     if (e != cudaSuccess) return cuda_error(e, "uploading lane tables");
     it = g_cache.emplace(threads, arr).first;
   }
-  out.g_fac = it->second[0];
-  out.g_fwd = it->second[1];
-  out.g_bwd = it->second[2];
+  out.g_fwd = it->second[0];
+  out.g_bwd = it->second[1];
+  // the suffix of factor levels narrow enough for one CTA of `threads`
+  int solo = (int)sym.flev_ptr.size() - 1;
+  while (solo > 0) {
+    const int l = solo - 1;
+    const int items = std::max(sym.fac_ptr[l + 1] - sym.fac_ptr[l], sym.tgt_ptr[l + 1] - sym.tgt_ptr[l]);
+    if (items > threads) break;
+    --solo;
+  }
+  out.fac_solo_from = solo;
   return PF_OK;
 }
 
@@ -176,8 +207,9 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B) {
   t += nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8;      // spec
   t += (kind == PF_SINGLE_PHASE ? 2 : 0) * nb * 8;      // vm, va
   t += 3 * nb * nsl * 16;                               // V, I, dV
+  t += (kind == PF_SINGLE_PHASE ? 16 : 0) * nb;         // U
   t += (kind == PF_SINGLE_PHASE ? 0 : 12) * nb * 8;     // abcd
-  t += 2 * nb * bs * 8;                                 // F, dx
+  t += 3 * nb * bs * 8;                                 // F, dx, r
   t += (size_t)nnz_lu * B * bs * bs * 8;                // lu
   t += nb * bs * bs * 8;                                // uinv
   t += nb * bs * 8;                                     // y
@@ -205,11 +237,13 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B) {
     A((void**)&w.va, nb * 8);
   }
   A((void**)&w.V, nb * nsl * 16);
+  if (kind == PF_SINGLE_PHASE) A((void**)&w.U, nb * 16);
   A((void**)&w.I, nb * nsl * 16);
   A((void**)&w.dV, nb * nsl * 16);
   if (kind == PF_THREE_PHASE) A((void**)&w.abcd, nb * 12 * 8);
   A((void**)&w.F, nb * bs * 8);
   A((void**)&w.dx, nb * bs * 8);
+  A((void**)&w.r, nb * bs * 8);
   A(&w.lu, (size_t)nnz_lu * B * bs * bs * 8);
   A(&w.uinv, nb * bs * bs * 8);
   A(&w.y, nb * bs * 8);
@@ -279,6 +313,7 @@ void pf_opts_default(pf_opts* o) {
   o->tol = 1e-8;
   o->max_iter = 30;
   o->refine_steps = 1;
+  o->refine_below = 1e-3;
   o->gmres_restart = 30;
   o->gmres_max_iter = 300;
   o->gmres_rtol = 1e-6;
@@ -457,8 +492,10 @@ int pf_analyze(const pf_case_desc* desc, pf_case_stats* out) {
   long long b = 0;
   for (const Symbolic* s : {&nr, &nk}) {
     b += 4LL * ((long long)s->y_rowptr.size() + s->y_col.size() + s->lu_rowptr.size() +
-                s->lu_col.size() + s->lu_diag.size() + s->lu2y.size() + s->upd_ptr.size() +
-                s->upd_pos.size() + s->flev_ptr.size() + s->flev_rows.size() +
+                s->lu_col.size() + s->lu_diag.size() + s->lu2y.size() + s->fac_ptr.size() +
+                s->fac_items.size() + s->tgt_ptr.size() + s->tgt_entry.size() +
+                s->tgt_cptr.size() + s->con_l.size() + s->con_u.size() +
+                s->flev_ptr.size() + s->flev_rows.size() +
                 s->blev_ptr.size() + s->blev_rows.size() + s->perm.size());
     b += (long long)y.val.size() * 8 + (long long)d.n * (1 + 8 * 9);
   }
@@ -535,6 +572,25 @@ int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag, const dou
   if (opts) o = *opts; else pf_opts_default(&o);
   std::lock_guard<std::mutex> lk(c->mu);
   return inspect(c, InspectKind::Step, &o, vmag, vang, dx, info);
+}
+
+int pf_launch_config(pf_case c, const pf_opts* opts, int B, int* grid, int* cluster,
+                     int* threads, int* scen) {
+  if (!c || B < 1 || !grid || !cluster || !threads || !scen)
+    return set_error(PF_ERR_INVALID, "null argument or B < 1");
+  pf_opts o;
+  if (opts) o = *opts; else pf_opts_default(&o);
+  cudaSetDevice(c->ctx->device);
+  launch_shape(c, o, B, o.precision == PF_MIXED, grid, cluster, threads, scen);
+  return PF_OK;
+}
+
+int pf_profile_solve(pf_case c, const pf_opts* opts, double* phase_us, pf_info* info) {
+  if (!c || !phase_us) return set_error(PF_ERR_INVALID, "null argument");
+  pf_opts o;
+  if (opts) o = *opts; else pf_opts_default(&o);
+  std::lock_guard<std::mutex> lk(c->mu);
+  return profile_solve(c, o, phase_us, info);
 }
 
 }  // extern "C"

@@ -32,7 +32,7 @@ struct SysBuf {
   Symbolic sym;
   DevSys view{};
   DevBuffer mem;
-  std::map<int, std::array<const int8_t*, 3>> g_cache;
+  std::map<int, std::array<const int8_t*, 2>> g_cache;
   int build(const CaseData& c, const Ybus& y, Ordering ord, bool fill);
   int lanes_for(int threads, DevSys& out);
 };
@@ -89,7 +89,10 @@ enum class InspectKind { Mismatch, Jacobian, Step };
 int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load,
               const double* d_q_load, const double* d_p_gen, Workspace* ws,
               cudaStream_t st, RunMode mode, double* out_vm, double* out_va,
-              pf_info* out_info = nullptr);
+              pf_info* out_info = nullptr, unsigned long long* prof = nullptr);
+void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int* cluster,
+                  int* threads, int* S);
+int profile_solve(pf_case c, const pf_opts& o, double* phase_us, pf_info* info);
 // Copies staged results of the last run_solve on ws to host arrays.
 int fetch_results(pf_case c, Workspace* ws, int B, double* vmag, double* vang,
                   pf_info* info, cudaStream_t st);

@@ -24,8 +24,14 @@ struct DevSys {
   const int* lu_col;
   const int* lu_diag;
   const int* lu2y;
-  const int* upd_ptr;
-  const int* upd_pos;
+  // fan-out factorisation schedule (see Symbolic)
+  const int* fac_ptr;
+  const int* fac_items;
+  const int* tgt_ptr;
+  const int* tgt_entry;
+  const int* tgt_cptr;
+  const int* con_l;
+  const int* con_u;
   // level schedules and lanes per row for a single-scenario launch
   const int* flev_ptr;
   const int* flev_rows;
@@ -33,7 +39,15 @@ struct DevSys {
   const int* blev_ptr;
   const int* blev_rows;
   int nblev;
-  const int8_t* g_fac;
+  int fac_solo_from;  // factor levels >= this run in CTA 0 alone (single solves)
+  // packed records: forward / backward rows {i, first, end} of the L / U
+  // part per level position; factor items {e, k, diag(k)}; targets
+  // {entry, first contribution, end}; contributions {L entry, U entry}
+  const int4* fwd_rec;
+  const int4* bwd_rec;
+  const int4* fac_rec;
+  const int4* tgt_rec;
+  const int2* con;
   const int8_t* g_fwd;
   const int8_t* g_bwd;
   // bus data: single phase type 0/1/2; three phase phase mask | 8 at source
@@ -72,11 +86,13 @@ struct DevWork {
   double* vm;     // single phase
   double* va;
   double2* V;     // 1 or 3 per row
+  double2* U;     // single phase: V / |V|
   double2* I;     // I = Y V of the last mismatch evaluation
   double2* dV;    // refinement: voltage change of the step
   double* abcd;   // three phase: Eq. 23 adjustments, 12 per row
   double* F;      // mismatch, bs per row
   double* dx;     // Newton step, bs per row
+  double* r;      // refinement residual, bs per row
   void* lu;       // factor values, bs*bs per entry
   void* uinv;     // inverse diagonal blocks, bs*bs per row
   void* y;        // triangular-solve vector, bs per row
@@ -89,8 +105,15 @@ struct DevOpts {
   double tol;
   int max_iter;
   int refine;   // FP64 refinement steps (mixed NR)
+  double refine_below;  // ... taken once the mismatch norm is at most this
   int S;        // scenarios per cluster
   int mode;     // 0 solve, 1 evaluate mismatch + Jacobian, 2 one Newton step
+  unsigned long long* prof;  // optional per-phase device time (ns), kProfPhases
+  int y_in_smem;             // the solve vector lives in dynamic shared memory
 };
+
+// Phases timed by the optional profile (cluster 0, CTA 0, between barriers).
+enum ProfPhase { kProfSetup = 0, kProfMismatch, kProfStop, kProfFactor, kProfSolve,
+                 kProfResidual, kProfUpdate, kProfOutput, kProfPhases };
 
 }  // namespace pf

@@ -62,16 +62,21 @@ struct Symbolic {
   // upper) -- with fill for LU, equal to the Ybus pattern for ILU(0)
   std::vector<int> lu_rowptr, lu_col, lu_diag;
   std::vector<int> lu2y;  // factor entry -> new-order Ybus entry or -1 (fill)
-  // update lists: for an L entry p = (i, k), upd_pos[upd_ptr[p] + t] is the
-  // factor entry (i, j) hit by the t-th U entry (k, j) of row k, or -1 when
-  // ILU(0) drops it
-  std::vector<int> upd_ptr, upd_pos;
+  // fan-out factorisation schedule, per level l of the factor's level sets:
+  //  fac_items[fac_ptr[l] .. fac_ptr[l+1]) are the factor entries finalised
+  //    at level l: the diagonal block of each pivot k of the level and every
+  //    L entry (i, k) of those pivot columns;
+  //  targets t in [tgt_ptr[l], tgt_ptr[l+1]) are the entries tgt_entry[t]
+  //    that the level's pivots update, A_t -= sum of L(con_l[c]) U(con_u[c])
+  //    over c in [tgt_cptr[t], tgt_cptr[t+1]) (con_l an L entry (i, k),
+  //    con_u a U entry (k, j) of a pivot k of the level).  ILU(0) drops the
+  //    updates whose target is not in the pattern.
+  std::vector<int> fac_ptr, fac_items, tgt_ptr, tgt_entry, tgt_cptr, con_l, con_u;
   long long n_updates = 0;
   // level sets: rows of level l are flev_rows[flev_ptr[l] .. flev_ptr[l+1])
   std::vector<int> flev_ptr, flev_rows;  // factor / forward solve (L deps)
   std::vector<int> blev_ptr, blev_rows;  // backward solve (U deps)
   // per level: the longest parallel inner loop (for choosing lanes per row)
-  std::vector<int> flev_ulen;  // factor: longest U row of any pivot used
   std::vector<int> flev_llen;  // forward: longest L part of a row
   std::vector<int> blev_ulen;  // backward: longest U part of a row
   int nnz_lu() const { return (int)lu_col.size(); }

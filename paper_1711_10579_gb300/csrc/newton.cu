@@ -232,46 +232,58 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
   nrm = fmax(fabs(f0), fabs(f1));
   if (!isfinite(f0) || !isfinite(f1)) nrm = __longlong_as_double(0x7ff8000000000000ULL);
 
+  // The Jacobian is formed in the factor's precision TF (it only feeds the
+  // factorisation; the mismatch above and the refinement residual stay FP64).
+  // U = V / |V| per bus (kept by the update) avoids divisions.
+  using T = TF;
+  const double2 Ui = ldc(w.U + b);
+  const T vix = (T)Vi.x, viy = (T)Vi.y, uix = (T)Ui.x, uiy = (T)Ui.y;
   TF* lu = reinterpret_cast<TF*>(w.lu);
   for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
     const int j = S.lu_col[e];
     const int yi = S.lu2y[e];
-    double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+    T j00 = 0, j01 = 0, j10 = 0, j11 = 0;
     if (yi >= 0) {
-      const double2 Yij = Y[yi];
+      const T yx = (T)Y[yi].x, yy = (T)Y[yi].y;
       if (j != i) {
         const int tj = S.btype[j];
         if (t != PF_SLACK && tj != PF_SLACK) {
           const size_t bj = (size_t)j * B + gs;
-          // dS_i/d delta_j = -j V_i conj(Y_ij V_j); dS_i/d|V_j| = V_i conj(Y_ij V_j)/|V_j|
-          const double2 c = cmulc(Vi, cmul(Yij, ldc(w.V + bj)));
-          j00 = c.y;
-          j10 = -c.x;
+          // dS_i/d|V_j| = V_i conj(Y_ij U_j); dS_i/d delta_j = -j |V_j| dS_i/d|V_j|
+          const double2 Uj = ldc(w.U + bj);
+          const T ux = (T)Uj.x, uy = (T)Uj.y;
+          const T yux = yx * ux - yy * uy, yuy = yx * uy + yy * ux;
+          const T cx = vix * yux + viy * yuy, cy = viy * yux - vix * yuy;
+          const T vmj = (T)__ldcg(w.vm + bj);
+          j00 = vmj * cy;
+          j10 = -vmj * cx;
           if (tj == PF_PQ) {
-            const double inv = 1.0 / __ldcg(w.vm + bj);
-            j01 = c.x * inv;
-            j11 = c.y * inv;
+            j01 = cx;
+            j11 = cy;
           }
-          if (t == PF_PV) j10 = j11 = 0.0;
+          if (t == PF_PV) j10 = j11 = T(0);
         }
       } else if (t == PF_SLACK) {
-        j00 = j11 = 1.0;
+        j00 = j11 = T(1);
       } else {
         // dS_i/d delta_i = j (S_i - V_i conj(Y_ii V_i));
-        // dS_i/d|V_i| = (S_i + V_i conj(Y_ii V_i)) / |V_i|, minus the load's slope
-        const double2 d = cmulc(Vi, cmul(Yij, Vi));
-        j00 = -(Sc.y - d.y);
-        j10 = Sc.x - d.x;
-        j01 = (Sc.x + d.x) / vmi + pl * dshape;
-        j11 = (Sc.y + d.y) / vmi + ql * dshape;
+        // dS_i/d|V_i| = U_i conj(I_i + Y_ii V_i), minus the load's slope
+        const T yvx = yx * vix - yy * viy, yvy = yx * viy + yy * vix;  // Y_ii V_i
+        const T dx = vix * yvx + viy * yvy, dy = viy * yvx - vix * yvy;
+        const T ax = (T)I.x + yvx, ay = (T)I.y + yvy;
+        const T ex = uix * ax + uiy * ay, ey = uiy * ax - uix * ay;
+        j00 = -((T)Sc.y - dy);
+        j10 = (T)Sc.x - dx;
+        j01 = ex + (T)(pl * dshape);
+        j11 = ey + (T)(ql * dshape);
         if (t == PF_PV) {
-          j01 = 0.0;
-          j10 = 0.0;
-          j11 = 1.0;
+          j01 = T(0);
+          j10 = T(0);
+          j11 = T(1);
         }
       }
     }
-    TF blk[4] = {(TF)j00, (TF)j01, (TF)j10, (TF)j11};
+    TF blk[4] = {j00, j01, j10, j11};
     blk_store<2>(lu + ((size_t)e * B + gs) * 4, blk);
   }
 }
@@ -293,10 +305,10 @@ __device__ __forceinline__ void load_slope(double2 V, double pl, double ql, doub
   const double dshape = zi + 2.0 * zz * m;
   const double2 cS = make_double2(-pl * shape, ql * shape);     // conj(S)
   const double2 cSp = make_double2(-pl * dshape, ql * dshape);  // conj(dS/dm)
-  const double inv2 = 1.0 / m2;
+  const double inv2 = 1.0 / m2;                                 // the one division
   const double2 cSV = cmul(cS, V);
   Isp = cscale(cSV, inv2);
-  const double2 base = cscale(cmul(cSp, V), inv2 / m);
+  const double2 base = cscale(cmul(cSp, V), inv2 * inv2 * m);   // / m^3
   dIdr = csub(cadd(cscale(base, V.x), cscale(cS, inv2)), cscale(cSV, 2.0 * V.x * inv2 * inv2));
   const double2 jcS = make_double2(-cS.y, cS.x);
   dIdi = csub(cadd(cscale(base, V.y), cscale(jcS, inv2)), cscale(cSV, 2.0 * V.y * inv2 * inv2));
@@ -404,68 +416,101 @@ __device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, 
 }
 
 // ---------------------------------------------------------------------------
-// steps B, C: factorisation and triangular solves of one row
+// cluster-wide schedule helpers
 // ---------------------------------------------------------------------------
 
-// Row i of the block LU (row-oriented, L with identity diagonal blocks):
-// for each L entry (i, k) in increasing k: L_ik = A_ik U_kk^-1, then
-// A_ij -= L_ik U_kj for the U entries of row k.  The G lanes of a group share
-// the inner loop; rows of one level are independent.
-template <int BS, typename TF>
-__device__ void factor_row(const DevSys& S, const DevWork& w, int i, int gs, int lane, int G,
-                           unsigned gmask) {
-  const int B = w.B;
-  TF* lu = reinterpret_cast<TF*>(w.lu);
-  TF* uinv = reinterpret_cast<TF*>(w.uinv);
-  constexpr int BB = BS * BS;
-  const int rp = S.lu_rowptr[i], dg = S.lu_diag[i];
-  for (int p = rp; p < dg; ++p) {
-    const int k = S.lu_col[p];
-    TF a[BB], u[BB], l[BB];
-    blk_load<BS>(lu + ((size_t)p * B + gs) * BB, a);
-    blk_load<BS>(uinv + ((size_t)k * B + gs) * BB, u);
-    blk_mul<BS>(a, u, l);
-    if (G > 1) __syncwarp(gmask);
-    if (lane == 0) blk_store<BS>(lu + ((size_t)p * B + gs) * BB, l);
-    const int kd = S.lu_diag[k], ke = S.lu_rowptr[k + 1], up = S.upd_ptr[p] - kd - 1;
-    for (int q = kd + 1 + lane; q < ke; q += G) {
-      const int pos = S.upd_pos[up + q];
-      if (pos < 0) continue;  // dropped by ILU(0)
-      TF c[BB], uu[BB];
-      blk_load<BS>(lu + ((size_t)pos * B + gs) * BB, c);
-      blk_load<BS>(lu + ((size_t)q * B + gs) * BB, uu);
-      blk_msub<BS>(c, l, uu);
-      blk_store<BS>(lu + ((size_t)pos * B + gs) * BB, c);
-    }
-    if (G > 1) __syncwarp(gmask);
+struct Team {
+  int tid;       // thread index within the cluster
+  int nthr;      // threads in the cluster (a multiple of S)
+  int S;         // scenario slots per cluster (a power of two)
+  int s0;        // first scenario of the cluster
+  int ns;        // scenarios of the cluster (<= S)
+  unsigned act;  // active scenarios (bit s = scenario s0 + s)
+};
+
+// Every thread serves the fixed scenario slot tid % S.  Runs fn(item, gs)
+// for items [0, count) and every active scenario, then a cluster barrier.
+template <bool CL, class Fn>
+__device__ void run_items(const Team& tm, int count, Fn fn) {
+  const int s = tm.tid & (tm.S - 1);
+  if (s < tm.ns && ((tm.act >> s) & 1u)) {
+    for (int it = tm.tid / tm.S; it < count; it += tm.nthr / tm.S) fn(it, tm.s0 + s);
   }
-  if (lane == 0) {
-    TF d[BB], di[BB];
-    blk_load<BS>(lu + ((size_t)dg * B + gs) * BB, d);
-    if (!blk_inv<BS>(d, di)) w.flag[gs] = 1;
-    blk_store<BS>(uinv + ((size_t)i * B + gs) * BB, di);
+  csync<CL>();
+}
+
+// Runs fn(i, gs) for every row and active scenario, then a cluster barrier.
+template <bool CL, class Fn>
+__device__ void run_rows(const Team& tm, int n, Fn fn) {
+  run_items<CL>(tm, n, fn);
+}
+
+// ---------------------------------------------------------------------------
+// level sweeps with prefetch of the next level's static data
+// ---------------------------------------------------------------------------
+
+// A thread's share of one row of a triangular sweep, loaded ahead: the row,
+// its first entry for this lane, that entry's column and (2x2 blocks) value,
+// and for the backward sweep the inverse diagonal block.  Factor values and
+// indices do not change during the sweeps, so all of this is loaded before
+// the previous level's barrier; only the solve vector is read after it.
+template <int BS, typename TF>
+struct RowPref {
+  static constexpr int NV = (BS == 2) ? 4 : 1;
+  int i, p, pe, k;
+  TF v[NV], d[NV];
+};
+
+template <int BS, typename TF, bool FWD>
+__device__ __forceinline__ void sweep_pref(const DevSys& S, const DevWork& w, const int4* rec,
+                                           int pos, bool have, int gs, int lane,
+                                           RowPref<BS, TF>& P) {
+  P.i = -1;
+  if (!have) return;
+  const int4 q = __ldg(rec + pos);
+  P.i = q.x;
+  P.p = q.y + lane;
+  P.pe = q.z;
+  const TF* lu = reinterpret_cast<const TF*>(w.lu);
+  if (P.p < P.pe) {
+    P.k = __ldg(S.lu_col + P.p);
+    if constexpr (BS == 2) blk_load<2>(lu + ((size_t)P.p * w.B + gs) * 4, P.v);
+  }
+  if constexpr (!FWD && BS == 2) {
+    if (lane == 0) blk_load<2>(reinterpret_cast<const TF*>(w.uinv) + ((size_t)P.i * w.B + gs) * 4, P.d);
   }
 }
 
-// Forward substitution, row i: y_i -= sum_k L_ik y_k.
-template <int BS, typename TF>
-__device__ void forward_row(const DevSys& S, const DevWork& w, int i, int gs, int lane, int G,
-                            unsigned gmask) {
+// Forward: y_i -= sum_k L_ik y_k.  Backward: y_i = U_ii^-1 (y_i - sum_j U_ij y_j).
+template <int BS, typename TF, bool FWD>
+__device__ __forceinline__ void sweep_row(const DevSys& S, const DevWork& w, TF* y,
+                                          const RowPref<BS, TF>& P, int gs, int lane, int G,
+                                          unsigned gmask) {
+  constexpr int BB = BS * BS;
   const int B = w.B;
   const TF* lu = reinterpret_cast<const TF*>(w.lu);
-  TF* y = reinterpret_cast<TF*>(w.y);
-  constexpr int BB = BS * BS;
   TF acc[BS];
 #pragma unroll
   for (int c = 0; c < BS; ++c) acc[c] = TF(0);
-  const int rp = S.lu_rowptr[i], dg = S.lu_diag[i];
-  for (int p = rp + lane; p < dg; p += G) {
-    const size_t bk = ((size_t)S.lu_col[p] * B + gs) * BS;
+  for (int p = P.p; p < P.pe; p += G) {
     TF L[BB];
-    blk_load<BS>(lu + ((size_t)p * B + gs) * BB, L);
+    int k;
+    if (p == P.p) {
+      k = P.k;
+      if constexpr (BS == 2) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) L[t] = P.v[t];
+      } else {
+        blk_load<BS>(lu + ((size_t)p * B + gs) * BB, L);
+      }
+    } else {
+      k = __ldg(S.lu_col + p);
+      blk_load<BS>(lu + ((size_t)p * B + gs) * BB, L);
+    }
+    const size_t bk = ((size_t)k * B + gs) * BS;
     TF yk[BS];
 #pragma unroll
-    for (int c = 0; c < BS; ++c) yk[c] = __ldcg(y + bk + c);
+    for (int c = 0; c < BS; ++c) yk[c] = y[bk + c];
 #pragma unroll
     for (int r = 0; r < BS; ++r)
 #pragma unroll
@@ -476,105 +521,167 @@ __device__ void forward_row(const DevSys& S, const DevWork& w, int i, int gs, in
     for (int c = 0; c < BS; ++c) acc[c] = group_sum(acc[c], G, gmask);
   }
   if (lane == 0) {
-    const size_t bi = ((size_t)i * B + gs) * BS;
+    const size_t bi = ((size_t)P.i * B + gs) * BS;
+    if constexpr (FWD) {
 #pragma unroll
-    for (int c = 0; c < BS; ++c) y[bi + c] = __ldcg(y + bi + c) - acc[c];
-  }
-}
-
-// Backward substitution, row i: x_i = U_ii^-1 (y_i - sum_j U_ij x_j).
-template <int BS, typename TF>
-__device__ void backward_row(const DevSys& S, const DevWork& w, int i, int gs, int lane, int G,
-                             unsigned gmask) {
-  const int B = w.B;
-  const TF* lu = reinterpret_cast<const TF*>(w.lu);
-  const TF* uinv = reinterpret_cast<const TF*>(w.uinv);
-  TF* y = reinterpret_cast<TF*>(w.y);
-  constexpr int BB = BS * BS;
-  TF acc[BS];
+      for (int c = 0; c < BS; ++c) y[bi + c] = y[bi + c] - acc[c];
+    } else {
+      TF t[BS], D[BB];
 #pragma unroll
-  for (int c = 0; c < BS; ++c) acc[c] = TF(0);
-  const int dg = S.lu_diag[i], re = S.lu_rowptr[i + 1];
-  for (int q = dg + 1 + lane; q < re; q += G) {
-    const size_t bj = ((size_t)S.lu_col[q] * B + gs) * BS;
-    TF U[BB];
-    blk_load<BS>(lu + ((size_t)q * B + gs) * BB, U);
-    TF xj[BS];
+      for (int c = 0; c < BS; ++c) t[c] = y[bi + c] - acc[c];
+      if constexpr (BS == 2) {
 #pragma unroll
-    for (int c = 0; c < BS; ++c) xj[c] = __ldcg(y + bj + c);
+        for (int q = 0; q < 4; ++q) D[q] = P.d[q];
+      } else {
+        blk_load<BS>(reinterpret_cast<const TF*>(w.uinv) + ((size_t)P.i * B + gs) * BB, D);
+      }
 #pragma unroll
-    for (int r = 0; r < BS; ++r)
+      for (int r = 0; r < BS; ++r) {
+        TF sacc = TF(0);
 #pragma unroll
-      for (int c = 0; c < BS; ++c) acc[r] += U[r * BS + c] * xj[c];
-  }
-  if (G > 1) {
-#pragma unroll
-    for (int c = 0; c < BS; ++c) acc[c] = group_sum(acc[c], G, gmask);
-  }
-  if (lane == 0) {
-    const size_t bi = ((size_t)i * B + gs) * BS;
-    TF t[BS], Di[BB];
-#pragma unroll
-    for (int c = 0; c < BS; ++c) t[c] = __ldcg(y + bi + c) - acc[c];
-    blk_load<BS>(uinv + ((size_t)i * B + gs) * BB, Di);
-#pragma unroll
-    for (int r = 0; r < BS; ++r) {
-      TF s = TF(0);
-#pragma unroll
-      for (int c = 0; c < BS; ++c) s += Di[r * BS + c] * t[c];
-      y[bi + r] = s;
+        for (int c = 0; c < BS; ++c) sacc += D[r * BS + c] * t[c];
+        y[bi + r] = sacc;
+      }
     }
   }
 }
 
-// ---------------------------------------------------------------------------
-// cluster-wide schedule helpers
-// ---------------------------------------------------------------------------
-
-struct Team {
-  int tid;    // thread index within the cluster
-  int nthr;   // threads in the cluster
-  int s0;     // first scenario of the cluster
-  int ns;     // scenarios of the cluster
-  unsigned act;  // active scenarios (bit s = scenario s0 + s)
-};
-
-// Runs `row(i, gs, lane, G, gmask)` for every row of every level in order,
-// with a cluster barrier after each level.
-template <bool CL, class RowFn>
-__device__ void run_levels(const Team& tm, const int* lev_ptr, const int* lev_rows, int nlev,
-                           const int8_t* gsz, bool reverse, RowFn row) {
-  for (int t = 0; t < nlev; ++t) {
-    const int l = reverse ? nlev - 1 - t : t;
-    const int base = lev_ptr[l], width = lev_ptr[l + 1] - base;
-    if (tm.ns == 1) {
-      if (tm.act & 1u) {
-        const int G = gsz[l];
-        const int group = tm.tid / G, lane = tm.tid % G, ngroups = tm.nthr / G;
-        const unsigned gmask =
-            (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-        for (int r = group; r < width; r += ngroups) row(lev_rows[base + r], tm.s0, lane, G, gmask);
-      }
+// One triangular sweep over all levels.  A single-scenario team gives each
+// row gsz[l] lanes; a batch team gives each (row, scenario) one thread.  The
+// first row of each group for level l+1 is prefetched while level l runs.
+template <int BS, typename TF, bool FWD, bool CL>
+__device__ void sweep(const DevSys& S, const DevWork& w, TF* y, const Team& tm,
+                      const int* lev_ptr, const int4* rec, int nlev, const int8_t* gsz) {
+  const bool single = (tm.S == 1);
+  const int slot = single ? 0 : (tm.tid & (tm.S - 1));
+  const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
+  const int gs = tm.s0 + slot;
+  auto geom = [&](int l, int& G, int& group, int& lane, int& ngroups) {
+    if (single) {
+      G = gsz[l];
+      group = tm.tid / G;
+      lane = tm.tid % G;
+      ngroups = tm.nthr / G;
     } else {
-      const int items = width * tm.ns;
-      for (int it = tm.tid; it < items; it += tm.nthr) {
-        const int r = it / tm.ns, s = it - r * tm.ns;
-        if ((tm.act >> s) & 1u) row(lev_rows[base + r], tm.s0 + s, 0, 1, 0u);
+      G = 1;
+      group = tm.tid / tm.S;
+      lane = 0;
+      ngroups = tm.nthr / tm.S;
+    }
+  };
+  RowPref<BS, TF> cur, nxt;
+  {
+    int G, group, lane, ngroups;
+    geom(0, G, group, lane, ngroups);
+    const int base = lev_ptr[0], width = lev_ptr[1] - base;
+    sweep_pref<BS, TF, FWD>(S, w, rec, base + group, on && nlev > 0 && group < width, gs, lane, cur);
+  }
+  for (int l = 0; l < nlev; ++l) {
+    int G, group, lane, ngroups;
+    geom(l, G, group, lane, ngroups);
+    const int base = lev_ptr[l], width = lev_ptr[l + 1] - base;
+    if (l + 1 < nlev) {
+      int G2, group2, lane2, ng2;
+      geom(l + 1, G2, group2, lane2, ng2);
+      const int b2 = lev_ptr[l + 1], w2 = lev_ptr[l + 2] - b2;
+      sweep_pref<BS, TF, FWD>(S, w, rec, b2 + group2, on && group2 < w2, gs, lane2, nxt);
+    }
+    if (on) {
+      const unsigned gmask =
+          (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+      if (group < width) sweep_row<BS, TF, FWD>(S, w, y, cur, gs, lane, G, gmask);
+      for (int r = group + ngroups; r < width; r += ngroups) {
+        RowPref<BS, TF> P;
+        sweep_pref<BS, TF, FWD>(S, w, rec, base + r, true, gs, lane, P);
+        sweep_row<BS, TF, FWD>(S, w, y, P, gs, lane, G, gmask);
       }
     }
     csync<CL>();
+    cur = nxt;
   }
 }
 
-// Runs `fn(i, gs)` for every row and active scenario, then a cluster barrier.
-template <bool CL, class Fn>
-__device__ void run_rows(const Team& tm, int n, Fn fn) {
-  const int items = n * tm.ns;
-  for (int it = tm.tid; it < items; it += tm.nthr) {
-    const int i = it / tm.ns, s = it - i * tm.ns;
-    if ((tm.act >> s) & 1u) fn(i, tm.s0 + s);
+// Fan-out (right-looking) block LU of levels [l0, l1), L with identity
+// diagonal blocks.  Level l, step 1: every pivot k of the level inverts its
+// diagonal block (U_kk^-1 is stored) and every L entry (i, k) of the pivot
+// columns becomes L_ik = A_ik U_kk^-1 -- all these entries received their
+// last update at an earlier level.  Step 2: every entry (i, j) the level's
+// pivots touch gathers A_ij -= sum_k L_ik U_kj in a fixed order (so results
+// are deterministic).  The next step's index records are prefetched across
+// each barrier.
+template <int BS, typename TF, bool CL>
+__device__ void factor_levels(const DevSys& S, const DevWork& w, const Team& tm, int l0, int l1) {
+  if (l0 >= l1) return;
+  const int slot = tm.tid & (tm.S - 1);
+  const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
+  const int gs = tm.s0 + slot;
+  const int first = tm.tid / tm.S, stride = tm.nthr / tm.S;
+  constexpr int BB = BS * BS;
+  TF* lu = reinterpret_cast<TF*>(w.lu);
+  auto fac_rec = [&](int l) {
+    const int f0 = S.fac_ptr[l], nf = S.fac_ptr[l + 1] - f0;
+    return (on && first < nf) ? __ldg(S.fac_rec + f0 + first) : make_int4(-1, 0, 0, 0);
+  };
+  auto tgt_rec = [&](int l, int2& c0) {
+    const int t0 = S.tgt_ptr[l], nt = S.tgt_ptr[l + 1] - t0;
+    if (on && first < nt) {
+      const int4 r = __ldg(S.tgt_rec + t0 + first);
+      c0 = __ldg(S.con + r.y);
+      return r;
+    }
+    return make_int4(-1, 0, 0, 0);
+  };
+  auto finalise = [&](int4 r) {
+    // r = {e, k, diag(k)}: U_kk^-1 for the diagonal, else L_ik = A_ik U_kk^-1
+    TF d[BB], di[BB];
+    blk_load<BS>(lu + ((size_t)r.z * w.B + gs) * BB, d);
+    const bool ok = blk_inv<BS>(d, di);
+    if (r.x == r.z) {
+      if (!ok) w.flag[gs] = 1;
+      blk_store<BS>(reinterpret_cast<TF*>(w.uinv) + ((size_t)r.y * w.B + gs) * BB, di);
+    } else {
+      TF a[BB], l[BB];
+      blk_load<BS>(lu + ((size_t)r.x * w.B + gs) * BB, a);
+      blk_mul<BS>(a, di, l);
+      blk_store<BS>(lu + ((size_t)r.x * w.B + gs) * BB, l);
+    }
+  };
+  auto update = [&](int4 r, int2 c0) {
+    // r = {e, c0, c1}: A_e -= sum L(con.x) U(con.y)
+    TF c[BB];
+    blk_load<BS>(lu + ((size_t)r.x * w.B + gs) * BB, c);
+    for (int q = r.y; q < r.z; ++q) {
+      const int2 cq = (q == r.y) ? c0 : __ldg(S.con + q);
+      TF l[BB], u[BB];
+      blk_load<BS>(lu + ((size_t)cq.x * w.B + gs) * BB, l);
+      blk_load<BS>(lu + ((size_t)cq.y * w.B + gs) * BB, u);
+      blk_msub<BS>(c, l, u);
+    }
+    blk_store<BS>(lu + ((size_t)r.x * w.B + gs) * BB, c);
+  };
+  int4 fr = fac_rec(l0);
+  for (int l = l0; l < l1; ++l) {
+    int2 tc0 = make_int2(0, 0);
+    const int4 tr = tgt_rec(l, tc0);  // prefetch for the second step
+    if (fr.x >= 0) finalise(fr);
+    if (on) {
+      const int f0 = S.fac_ptr[l], nf = S.fac_ptr[l + 1] - f0;
+      for (int t = first + stride; t < nf; t += stride) finalise(__ldg(S.fac_rec + f0 + t));
+    }
+    csync<CL>();
+    fr = (l + 1 < l1) ? fac_rec(l + 1) : make_int4(-1, 0, 0, 0);  // prefetch
+    const int t0 = S.tgt_ptr[l], nt = S.tgt_ptr[l + 1] - t0;
+    if (nt > 0) {
+      if (tr.x >= 0) update(tr, tc0);
+      if (on) {
+        for (int t = first + stride; t < nt; t += stride) {
+          const int4 r = __ldg(S.tgt_rec + t0 + t);
+          update(r, __ldg(S.con + r.y));
+        }
+      }
+      csync<CL>();
+    }
   }
-  csync<CL>();
 }
 
 // ---------------------------------------------------------------------------
@@ -582,21 +689,32 @@ __device__ void run_rows(const Team& tm, int n, Fn fn) {
 // ---------------------------------------------------------------------------
 
 template <int BS, typename TF, bool CL>
-__global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, DevWork w, DevOpts o) {
+__global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, DevWork w, DevOpts o) {
   constexpr bool THREE = (BS == 6);
   constexpr int NSL = THREE ? 3 : 1;  // complex voltages per row
   const int csize = CL ? (int)cg::this_cluster().num_blocks() : 1;
   const int crank = CL ? (int)cg::this_cluster().block_rank() : 0;
   const int cid = blockIdx.x / csize;
   Team tm;
-  tm.tid = crank * blockDim.x + threadIdx.x;
+  // consecutive items go to different CTAs of the cluster (all SMs busy on
+  // short loops); scenario slots stay in the low bits
+  tm.tid = (threadIdx.x / o.S) * (o.S * csize) + crank * o.S + (threadIdx.x & (o.S - 1));
   tm.nthr = csize * blockDim.x;
+  tm.S = o.S;
   tm.s0 = cid * o.S;
   tm.ns = min(o.S, w.B - tm.s0);
   if (tm.ns <= 0) return;  // whole cluster exits together
   const int n = S.n, B = w.B;
+  // CTA 0 alone ("solo") runs the narrow levels and the triangular solves of a
+  // single solve: __syncthreads instead of cluster barriers and their fences
+  Team solo = tm;
+  solo.tid = threadIdx.x;
+  solo.nthr = blockDim.x;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  TF* yv = o.y_in_smem ? reinterpret_cast<TF*>(dsm) : reinterpret_cast<TF*>(w.y);
   __shared__ int sh_status[32];
   __shared__ unsigned sh_act;
+  __shared__ int sh_refine;
   __shared__ unsigned long long sh_t0;
   if (threadIdx.x == 0) {
     sh_t0 = global_ns();
@@ -605,6 +723,16 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
   }
   __syncthreads();
   tm.act = sh_act;
+  // optional per-phase timing, kept by one thread of the first cluster
+  const bool prof = o.prof != nullptr && cid == 0 && crank == 0 && threadIdx.x == 0;
+  unsigned long long t_last = prof ? global_ns() : 0ull;
+  auto tick = [&](int phase) {
+    if (prof) {
+      const unsigned long long t = global_ns();
+      o.prof[phase] += t - t_last;
+      t_last = t;
+    }
+  };
 
   // ---- set-up: specified injections, start voltage, accumulators ----
   run_rows<CL>(tm, n, [&](int i, int gs) {
@@ -630,6 +758,7 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
       w.va[b] = va;
       double sn, cs;
       sincos(va, &sn, &cs);
+      w.U[b] = make_double2(cs, sn);
       w.V[b] = make_double2(vm * cs, vm * sn);
     } else {
       const int mask = S.btype[i] & 7;
@@ -663,6 +792,7 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
       w.flag[gs] = 0;
     }
   });
+  tick(kProfSetup);
 
   int it = 0;
   for (;; ++it) {
@@ -676,11 +806,13 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
       }
       atomic_max_pos(w.norm + (size_t)(it & 1) * B + gs, nrm);
     });
+    tick(kProfMismatch);
     if (o.mode == 1) return;  // inspection: F and J stay in the workspace
 
     // ---- stop test (every CTA decides identically from global values) ----
     if (threadIdx.x == 0) {
       unsigned act = 0;
+      int refine = 0;
       for (int s = 0; s < tm.ns; ++s) {
         const int gs = tm.s0 + s;
         if (sh_status[s] != kRunning) continue;
@@ -691,6 +823,7 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
         else if (o.mode == 0 && it >= o.max_iter) st = PF_ERR_MAXITER;
         sh_status[s] = st;
         if (st == kRunning) act |= 1u << s;
+        if (st == kRunning && nrm <= o.refine_below) refine = 1;
         if (crank == 0) {
           if (st != kRunning && w.out_info) {
             pf_info inf;
@@ -709,16 +842,23 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
         }
       }
       sh_act = act;
+      sh_refine = refine;
     }
     __syncthreads();
     tm.act = sh_act;
+    const int n_refine = (sh_refine || o.mode == 2) ? o.refine : 0;
+    tick(kProfStop);
     if (tm.act == 0) break;
 
-    // ---- B: numeric factorisation ----
-    run_levels<CL>(tm, S.flev_ptr, S.flev_rows, S.nflev, S.g_fac, false,
-                   [&](int i, int gs, int lane, int G, unsigned gmask) {
-                     factor_row<BS, TF>(S, w, i, gs, lane, G, gmask);
-                   });
+    // ---- B: numeric factorisation, two parallel steps per level; the narrow
+    // top levels of a single solve run in CTA 0 alone ----
+    factor_levels<BS, TF, CL>(S, w, tm, 0, S.fac_solo_from);
+    solo.act = tm.act;
+    if (S.fac_solo_from < S.nflev) {
+      if (crank == 0) factor_levels<BS, TF, false>(S, w, solo, S.fac_solo_from, S.nflev);
+      csync<CL>();
+    }
+    tick(kProfFactor);
     if (threadIdx.x == 0) {
       unsigned act = tm.act;
       for (int s = 0; s < tm.ns; ++s) {
@@ -746,15 +886,9 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
     if (tm.act == 0) break;
 
     // ---- C: triangular solves, then FP64 refinement ----
-    for (int pass = 0; pass <= o.refine; ++pass) {
+    for (int pass = 0; pass <= n_refine; ++pass) {
       // right-hand side: F, or the FP64 residual of the current step
-      if (pass == 0) {
-        run_rows<CL>(tm, n, [&](int i, int gs) {
-          const size_t b = (size_t)i * B + gs;
-          TF* y = reinterpret_cast<TF*>(w.y);
-          for (int c = 0; c < BS; ++c) y[b * BS + c] = (TF)__ldcg(w.F + b * BS + c);
-        });
-      } else {
+      if (pass > 0) {
         // voltage change of the step (complex), for J dx evaluated from Y and V
         run_rows<CL>(tm, n, [&](int i, int gs) {
           const size_t b = (size_t)i * B + gs;
@@ -762,16 +896,15 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
             for (int a = 0; a < 3; ++a)
               w.dV[b * 3 + a] = make_double2(__ldcg(w.dx + b * 6 + a), __ldcg(w.dx + b * 6 + 3 + a));
           } else {
-            // dV = V (j d_delta + d|V| / |V|)
-            const double2 V = ldc(w.V + b);
+            // dV = j d_delta V + d|V| U
+            const double2 V = ldc(w.V + b), U = ldc(w.U + b);
             const double dd = __ldcg(w.dx + b * 2), dm = __ldcg(w.dx + b * 2 + 1);
-            const double2 f = make_double2(dm / __ldcg(w.vm + b), dd);
-            w.dV[b] = cmul(V, f);
+            w.dV[b] = make_double2(-dd * V.y + dm * U.x, dd * V.x + dm * U.y);
           }
         });
         run_rows<CL>(tm, n, [&](int i, int gs) {
           const size_t b = (size_t)i * B + gs;
-          TF* y = reinterpret_cast<TF*>(w.y);
+          double* y = w.r;
           const double2* Y = reinterpret_cast<const double2*>(S.y_val);
           if constexpr (THREE) {
             double2 YdV[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
@@ -799,8 +932,8 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
                 rim = -dr;
                 rre = -di;
               }
-              y[b * 6 + a] = (TF)rim;
-              y[b * 6 + 3 + a] = (TF)rre;
+              y[b * 6 + a] = rim;
+              y[b * 6 + 3 + a] = rre;
             }
           } else {
             double2 YdV = make_double2(0.0, 0.0);
@@ -819,27 +952,32 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
             const double r1 = (t == PF_PQ)
                                   ? __ldcg(w.F + b * 2 + 1) - (dS.y + __ldcg(w.spec + b * 3 + 1) * dshape * dm)
                                   : -dm;
-            y[b * 2] = (TF)r0;
-            y[b * 2 + 1] = (TF)r1;
+            y[b * 2] = r0;
+            y[b * 2 + 1] = r1;
           }
         });
       }
-      run_levels<CL>(tm, S.flev_ptr, S.flev_rows, S.nflev, S.g_fwd, false,
-                     [&](int i, int gs, int lane, int G, unsigned gmask) {
-                       forward_row<BS, TF>(S, w, i, gs, lane, G, gmask);
-                     });
-      run_levels<CL>(tm, S.blev_ptr, S.blev_rows, S.nblev, S.g_bwd, false,
-                     [&](int i, int gs, int lane, int G, unsigned gmask) {
-                       backward_row<BS, TF>(S, w, i, gs, lane, G, gmask);
-                     });
-      run_rows<CL>(tm, n, [&](int i, int gs) {
-        const size_t b = ((size_t)i * B + gs) * BS;
-        const TF* y = reinterpret_cast<const TF*>(w.y);
-        for (int c = 0; c < BS; ++c) {
-          const double v = (double)__ldcg(y + b + c);
-          w.dx[b + c] = (pass == 0) ? v : __ldcg(w.dx + b + c) + v;
-        }
-      });
+      tick(kProfResidual);
+      // forward and backward sweeps: CTA 0 alone for a single solve
+      solo.act = tm.act;
+      if (crank == 0) {
+        const double* rhs = (pass == 0) ? w.F : w.r;
+        run_rows<false>(solo, n, [&](int i, int gs) {
+          const size_t b = ((size_t)i * B + gs) * BS;
+          for (int c = 0; c < BS; ++c) yv[b + c] = (TF)__ldcg(rhs + b + c);
+        });
+        sweep<BS, TF, true, false>(S, w, yv, solo, S.flev_ptr, S.fwd_rec, S.nflev, S.g_fwd);
+        sweep<BS, TF, false, false>(S, w, yv, solo, S.blev_ptr, S.bwd_rec, S.nblev, S.g_bwd);
+        run_rows<false>(solo, n, [&](int i, int gs) {
+          const size_t b = ((size_t)i * B + gs) * BS;
+          for (int c = 0; c < BS; ++c) {
+            const double v = (double)yv[b + c];
+            w.dx[b + c] = (pass == 0) ? v : w.dx[b + c] + v;
+          }
+        });
+      }
+      csync<CL>();
+      tick(kProfSolve);
     }
 
     if (o.mode == 2) return;  // inspection: the step stays in the workspace
@@ -863,10 +1001,12 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
         w.va[b] = va;
         double sn, cs;
         sincos(va, &sn, &cs);
+        w.U[b] = make_double2(cs, sn);
         w.V[b] = make_double2(vm * cs, vm * sn);
       }
       atomic_max_pos(w.step + (size_t)(it & 1) * B + gs, stp);
     });
+    tick(kProfUpdate);
   }
 
   // ---- results in the caller's numbering ----
@@ -896,6 +1036,7 @@ __global__ void __launch_bounds__(BS == 2 ? 1024 : 256) newton_kernel(DevSys S, 
       }
     }
   });
+  tick(kProfOutput);
   if (crank == 0 && threadIdx.x == 0 && w.out_info) {
     const double us = (double)(global_ns() - sh_t0) * 1e-3;
     for (int s = 0; s < tm.ns; ++s) w.out_info[tm.s0 + s].solve_us = us;
@@ -913,7 +1054,12 @@ static cudaError_t launch_t(const DevSys& S, const DevWork& w, const DevOpts& o,
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = o.y_in_smem ? (size_t)S.n * BS * sizeof(TF) : 0;
+  if (cfg.dynamicSmemBytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cfg.dynamicSmemBytes);
+    if (e != cudaSuccess) return e;
+  }
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   if (CL) {

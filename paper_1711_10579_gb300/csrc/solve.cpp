@@ -20,14 +20,16 @@ int check_opts(const pf_opts& o) {
   if (!(o.tol > 0.0)) return set_error(PF_ERR_INVALID, "opts.tol must be positive");
   if (o.max_iter < 0 || o.max_iter > 1000)
     return set_error(PF_ERR_INVALID, "opts.max_iter must be in [0, 1000]");
+  if (!(o.refine_below >= 0.0))
+    return set_error(PF_ERR_INVALID, "opts.refine_below must be >= 0");
   if (o.refine_steps < 0 || o.refine_steps > 10)
     return set_error(PF_ERR_INVALID, "opts.refine_steps must be in [0, 10]");
   if (o.cluster_size < 0 || o.cluster_size > 16 || (o.cluster_size & (o.cluster_size - 1)))
     return set_error(PF_ERR_INVALID, "opts.cluster_size must be 0 or a power of two <= 16");
   if (o.block_threads < 0 || o.block_threads > 1024 || (o.block_threads % 32))
     return set_error(PF_ERR_INVALID, "opts.block_threads must be 0 or a multiple of 32 <= 1024");
-  if (o.scen_per_cta < 0 || o.scen_per_cta > 32)
-    return set_error(PF_ERR_INVALID, "opts.scen_per_cta must be in [0, 32]");
+  if (o.scen_per_cta < 0 || o.scen_per_cta > 32 || (o.scen_per_cta & (o.scen_per_cta - 1)))
+    return set_error(PF_ERR_INVALID, "opts.scen_per_cta must be 0 or a power of two <= 32");
   return PF_OK;
 }
 
@@ -52,9 +54,26 @@ int cached_max_cluster(int bs, bool fp32, int threads) {
 
 }  // namespace
 
+void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int* cluster,
+                  int* threads, int* S) {
+  const int bs = c->bs;
+  const int max_threads = (bs == 2) ? 512 : 256;
+  if (B == 1) {
+    *threads = o.block_threads ? std::min(o.block_threads, max_threads) : max_threads;
+    *cluster = o.cluster_size ? o.cluster_size : cached_max_cluster(bs, fp32, *threads);
+    *S = 1;
+    *grid = *cluster;
+  } else {
+    *threads = o.block_threads ? std::min(o.block_threads, max_threads) : 256;
+    *cluster = 1;
+    *S = o.scen_per_cta ? o.scen_per_cta : 2;
+    *grid = (B + *S - 1) / *S;
+  }
+}
+
 int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const double* d_q_load,
               const double* d_p_gen, Workspace* ws, cudaStream_t st, RunMode mode, double* out_vm,
-              double* out_va, pf_info* out_info) {
+              double* out_va, pf_info* out_info, unsigned long long* prof) {
   int rc = check_opts(o);
   if (rc != PF_OK) return rc;
   if (o.method == PF_NK)
@@ -65,21 +84,10 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   SysBuf& sb = c->nr;
   // inspection of the Jacobian reads the factor array as FP64
   const bool fp32 = (o.precision == PF_MIXED) && mode != RunMode::Eval;
-  const int max_threads = (bs == 2) ? 1024 : 256;
   int threads, cluster, S, grid;
-  if (B == 1) {
-    threads = o.block_threads ? std::min(o.block_threads, max_threads) : max_threads;
-    cluster = o.cluster_size ? o.cluster_size : cached_max_cluster(bs, fp32, threads);
-    S = 1;
-    grid = cluster;
-  } else {
-    threads = o.block_threads ? std::min(o.block_threads, max_threads) : 256;
-    cluster = 1;
-    S = o.scen_per_cta ? o.scen_per_cta : 2;
-    grid = (B + S - 1) / S;
-  }
+  launch_shape(c, o, B, fp32, &grid, &cluster, &threads, &S);
   DevSys sys;
-  rc = sb.lanes_for(cluster * threads, sys);
+  rc = sb.lanes_for(threads, sys);
   if (rc != PF_OK) return rc;
   DevWork w = ws->w;
   w.B = B;
@@ -105,8 +113,13 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   d.tol = o.tol;
   d.max_iter = o.max_iter;
   d.refine = fp32 && o.method == PF_NR ? o.refine_steps : 0;
+  d.refine_below = o.refine_below;
   d.S = S;
   d.mode = mode == RunMode::Solve ? 0 : (mode == RunMode::Eval ? 1 : 2);
+  d.prof = prof;
+  // single solves keep the triangular-solve vector in shared memory when it fits
+  const size_t ybytes = (size_t)n * bs * (fp32 ? 4 : 8);
+  d.y_in_smem = (B == 1 && ybytes <= 200 * 1024) ? 1 : 0;
   cudaError_t e = launch_newton(bs, fp32, sys, w, d, grid, cluster, threads, st);
   if (e != cudaSuccess) return cuda_error(e, "launching the Newton kernel");
   return PF_OK;
@@ -177,6 +190,35 @@ int inspect(pf_case c, InspectKind k, const pf_opts* po, const double* vmag, con
     info->status = PF_OK;
   }
   return PF_OK;
+}
+
+int profile_solve(pf_case c, const pf_opts& o, double* phase_us, pf_info* info) {
+  cudaSetDevice(c->ctx->device);
+  cudaStream_t st = c->ctx->stream;
+  Workspace* ws = &c->ws1;
+  int rc = ws->ensure(c->data.kind, c->data.n,
+                      std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), 1);
+  if (rc != PF_OK) return rc;
+  unsigned long long* d_prof = nullptr;
+  cudaError_t e = cudaMalloc(&d_prof, kProfPhases * sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_error(e, "allocating the profile counters");
+  e = cudaMemsetAsync(d_prof, 0, kProfPhases * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    rc = run_solve(c, o, 1, nullptr, nullptr, nullptr, ws, st, RunMode::Solve, nullptr, nullptr,
+                   nullptr, d_prof);
+    unsigned long long h[kProfPhases];
+    if (rc == PF_OK) rc = fetch_results(c, ws, 1, nullptr, nullptr, info, st);
+    if (rc == PF_OK) {
+      e = cudaMemcpy(h, d_prof, sizeof(h), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) rc = cuda_error(e, "reading the profile counters");
+      else
+        for (int k = 0; k < kProfPhases; ++k) phase_us[k] = 1e-3 * (double)h[k];
+    }
+  } else {
+    rc = cuda_error(e, "clearing the profile counters");
+  }
+  cudaFree(d_prof);
+  return rc;
 }
 
 }  // namespace pf

@@ -11,8 +11,11 @@
 // From the pattern the analysis derives, for the GPU:
 //  * level sets of the factorisation / forward solve (a row depends on the
 //    rows of its L part) and of the backward solve (U part);
-//  * update lists: for every L entry (i, k) the positions (i, j) touched by
-//    the U entries (k, j), so the numeric kernel never searches a row.
+//  * a fan-out (right-looking) schedule of the numeric factorisation: at
+//    level l every pivot of the level and every L entry of its column is
+//    finalised in parallel, then every entry those pivots update gathers its
+//    updates in parallel, so no row is walked sequentially and the critical
+//    path is two parallel steps per level.
 #include <algorithm>
 #include <cstdint>
 #include <deque>
@@ -229,29 +232,6 @@ void analyze(const Ybus& y, Ordering ord, bool with_fill, Symbolic& s) {
     }
   }
 
-  // update lists
-  s.upd_ptr.assign(nnz + 1, 0);
-  s.upd_pos.clear();
-  s.n_updates = 0;
-  std::vector<int> where(n, -1);
-  for (int i = 0; i < n; ++i) {
-    for (int q = s.lu_rowptr[i]; q < s.lu_rowptr[i + 1]; ++q)
-      where[s.lu_col[q]] = q;
-    for (int p = s.lu_rowptr[i]; p < s.lu_rowptr[i + 1]; ++p) {
-      s.upd_ptr[p] = (int)s.upd_pos.size();
-      if (p >= s.lu_diag[i]) continue;
-      int k = s.lu_col[p];
-      for (int q = s.lu_diag[k] + 1; q < s.lu_rowptr[k + 1]; ++q) {
-        int t = where[s.lu_col[q]];
-        s.upd_pos.push_back(t);
-        if (t >= 0) ++s.n_updates;
-      }
-    }
-    for (int q = s.lu_rowptr[i]; q < s.lu_rowptr[i + 1]; ++q)
-      where[s.lu_col[q]] = -1;
-  }
-  s.upd_ptr[nnz] = (int)s.upd_pos.size();
-
   // level sets
   std::vector<int> flev(n, 0), blev(n, 0);
   for (int i = 0; i < n; ++i) {
@@ -269,25 +249,74 @@ void analyze(const Ybus& y, Ordering ord, bool with_fill, Symbolic& s) {
   build_levels(n, flev, s.flev_ptr, s.flev_rows);
   build_levels(n, blev, s.blev_ptr, s.blev_rows);
   const int nf = (int)s.flev_ptr.size() - 1, nb = (int)s.blev_ptr.size() - 1;
-  s.flev_ulen.assign(nf, 0);
   s.flev_llen.assign(nf, 0);
   s.blev_ulen.assign(nb, 0);
   for (int l = 0; l < nf; ++l)
     for (int t = s.flev_ptr[l]; t < s.flev_ptr[l + 1]; ++t) {
       int i = s.flev_rows[t];
       s.flev_llen[l] = std::max(s.flev_llen[l], s.lu_diag[i] - s.lu_rowptr[i]);
-      for (int p = s.lu_rowptr[i]; p < s.lu_diag[i]; ++p) {
-        int k = s.lu_col[p];
-        s.flev_ulen[l] =
-            std::max(s.flev_ulen[l], s.lu_rowptr[k + 1] - s.lu_diag[k] - 1);
-      }
     }
   for (int l = 0; l < nb; ++l)
     for (int t = s.blev_ptr[l]; t < s.blev_ptr[l + 1]; ++t) {
       int i = s.blev_rows[t];
-      s.blev_ulen[l] =
-          std::max(s.blev_ulen[l], s.lu_rowptr[i + 1] - s.lu_diag[i] - 1);
+      s.blev_ulen[l] = std::max(s.blev_ulen[l], s.lu_rowptr[i + 1] - s.lu_diag[i] - 1);
     }
+
+  // fan-out schedule: L entries by column, then per level the finalised
+  // entries and the gathered updates
+  std::vector<int> rowof(nnz);
+  std::vector<std::vector<int>> colL(n);
+  for (int i = 0; i < n; ++i)
+    for (int p = s.lu_rowptr[i]; p < s.lu_rowptr[i + 1]; ++p) {
+      rowof[p] = i;
+      if (p < s.lu_diag[i]) colL[s.lu_col[p]].push_back(p);
+    }
+  auto find = [&](int i, int j) {
+    const int* b = s.lu_col.data() + s.lu_rowptr[i];
+    const int* e = s.lu_col.data() + s.lu_rowptr[i + 1];
+    const int* q = std::lower_bound(b, e, j);
+    return (q != e && *q == j) ? (int)(q - s.lu_col.data()) : -1;
+  };
+  s.fac_ptr.assign(nf + 1, 0);
+  s.tgt_ptr.assign(nf + 1, 0);
+  s.fac_items.clear();
+  s.tgt_entry.clear();
+  s.tgt_cptr.assign(1, 0);
+  s.con_l.clear();
+  s.con_u.clear();
+  s.n_updates = 0;
+  struct Tri { int t, k, p, q; };
+  std::vector<Tri> tri;
+  for (int l = 0; l < nf; ++l) {
+    tri.clear();
+    for (int r = s.flev_ptr[l]; r < s.flev_ptr[l + 1]; ++r) {
+      const int k = s.flev_rows[r];
+      s.fac_items.push_back(s.lu_diag[k]);
+      for (int p : colL[k]) {
+        s.fac_items.push_back(p);
+        const int i = rowof[p];
+        for (int q = s.lu_diag[k] + 1; q < s.lu_rowptr[k + 1]; ++q) {
+          const int t = find(i, s.lu_col[q]);
+          if (t >= 0) tri.push_back({t, k, p, q});
+        }
+      }
+    }
+    std::sort(tri.begin(), tri.end(), [](const Tri& a, const Tri& b) {
+      return a.t != b.t ? a.t < b.t : a.k < b.k;
+    });
+    for (size_t u = 0; u < tri.size(); ++u) {
+      if (u == 0 || tri[u].t != tri[u - 1].t) {
+        if (u > 0) s.tgt_cptr.push_back((int)s.con_l.size());
+        s.tgt_entry.push_back(tri[u].t);
+      }
+      s.con_l.push_back(tri[u].p);
+      s.con_u.push_back(tri[u].q);
+    }
+    if (!tri.empty()) s.tgt_cptr.push_back((int)s.con_l.size());
+    s.n_updates += (long long)tri.size();
+    s.fac_ptr[l + 1] = (int)s.fac_items.size();
+    s.tgt_ptr[l + 1] = (int)s.tgt_entry.size();
+  }
 }
 
 std::vector<int8_t> lanes_per_level(const std::vector<int>& lev_ptr,

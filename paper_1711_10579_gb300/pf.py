@@ -45,6 +45,7 @@ class pf_case_desc(C.Structure):
 class pf_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("precision", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("refine_steps", C.c_int),
+                ("refine_below", C.c_double),
                 ("gmres_restart", C.c_int), ("gmres_max_iter", C.c_int),
                 ("gmres_rtol", C.c_double), ("warm_start", C.c_int),
                 ("cluster_size", C.c_int), ("block_threads", C.c_int),
@@ -118,6 +119,8 @@ def lib():
             "pf_eval_jacobian": (C.c_int, [vp, _dp, _dp, _dp]),
             "pf_newton_step": (C.c_int, [vp, C.POINTER(pf_opts), _dp, _dp, _dp,
                                          C.POINTER(pf_info)]),
+            "pf_profile_solve": (C.c_int, [vp, C.POINTER(pf_opts), _dp, C.POINTER(pf_info)]),
+            "pf_launch_config": (C.c_int, [vp, C.POINTER(pf_opts), C.c_int, _ip, _ip, _ip, _ip]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -409,3 +412,24 @@ def pf_newton_step(c: CaseHandle, vmag, vang, opts: pf_opts | None = None):
     _check(lib().pf_newton_step(c.handle, C.byref(opts) if opts else None, _ptr(vm, C.c_double),
                                 _ptr(va, C.c_double), _ptr(out, C.c_double), C.byref(info)))
     return out, info.as_dict()
+
+
+PROFILE_PHASES = ("setup", "mismatch_jacobian", "stop_test", "factor", "triangular_solves",
+                  "rhs_refinement", "update", "output")
+
+
+def pf_profile_solve(c: CaseHandle, opts: pf_opts | None = None):
+    """(phase microseconds dict, info) of one timed single solve."""
+    ph = np.zeros(len(PROFILE_PHASES))
+    info = pf_info()
+    _check(lib().pf_profile_solve(c.handle, C.byref(opts) if opts else None,
+                                  _ptr(ph, C.c_double), C.byref(info)))
+    return dict(zip(PROFILE_PHASES, ph.tolist())), info.as_dict()
+
+
+def pf_launch_config(c: CaseHandle, opts: pf_opts | None = None, B: int = 1) -> dict:
+    """Launch shape of a solve: grid, cluster, threads, scenarios per cluster."""
+    v = [C.c_int32() for _ in range(4)]
+    _check(lib().pf_launch_config(c.handle, C.byref(opts) if opts else None, B,
+                                  *[C.byref(x) for x in v]))
+    return dict(zip(("grid", "cluster", "threads", "scen_per_cluster"), [x.value for x in v]))
