@@ -199,7 +199,7 @@ int SysBuf::lanes_for(int threads, DevSys& out) {
 // workspace
 // ---------------------------------------------------------------------------
 
-size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B) {
+size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
   const int bs = kind == PF_SINGLE_PHASE ? 2 : 6;
   const int nsl = kind == PF_SINGLE_PHASE ? 1 : 3;
   size_t nb = (size_t)n * B;
@@ -216,13 +216,21 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B) {
   t += (size_t)B * (2 * 8 + 2 * 8 + 4);                 // norm, step, flag
   t += 3 * nb * nsl * 8;                                // staged inputs
   t += 2 * nb * nsl * 8 + (size_t)B * sizeof(pf_info);  // staged outputs
+  if (m > 0) {                                          // Newton-Krylov (FP64 bound)
+    t += (size_t)nnz_lu * B * bs * bs * 8;              // Jacobian copy
+    t += (size_t)(m + 1 + 3) * nb * bs * 8;             // basis, w, z, x
+    t += (size_t)2 * 16 * B * kMaxJ * 8;                // reduction slots
+  }
   return t;
 }
 
-int Workspace::ensure(int kind, int n, long long nnz_lu, int B) {
-  if (B <= cap) return PF_OK;
+int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
+  if (B <= cap && m <= cap_m) return PF_OK;
+  B = std::max(B, cap);
+  m = std::max(m, cap_m);
   mem.release();
   cap = 0;
+  cap_m = -1;
   const int bs = kind == PF_SINGLE_PHASE ? 2 : 6;
   const int nsl = kind == PF_SINGLE_PHASE ? 1 : 3;
   size_t nb = (size_t)n * B;
@@ -256,6 +264,14 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B) {
   A((void**)&st_vm, nb * nsl * 8);
   A((void**)&st_va, nb * nsl * 8);
   A((void**)&st_info, (size_t)B * sizeof(pf_info));
+  if (m > 0) {
+    A(&w.jm, (size_t)nnz_lu * B * bs * bs * 8);
+    A(&w.vb, (size_t)(m + 1) * nb * bs * 8);
+    A(&w.wv, nb * bs * 8);
+    A(&w.zg, nb * bs * 8);
+    A(&w.xg, nb * bs * 8);
+    A(&w.gred, (size_t)2 * 16 * B * kMaxJ * 8);
+  }
   if (e != cudaSuccess) {
     mem.release();
     if (e == cudaErrorMemoryAllocation) {
@@ -265,6 +281,7 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B) {
     return cuda_error(e, "allocating the solve workspace");
   }
   cap = B;
+  cap_m = m;
   w.B = B;
   return PF_OK;
 }
@@ -445,7 +462,8 @@ int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
   cudaSetDevice(c->ctx->device);
   cudaStream_t st = c->ctx->stream;
   Workspace* ws = (B == 1) ? &c->ws1 : &c->wsB;
-  int rc = ws->ensure(c->data.kind, c->data.n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), B);
+  int rc = ws->ensure(c->data.kind, c->data.n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), B,
+                      o.method == PF_NK ? o.gmres_restart : 0);
   if (rc != PF_OK) return rc;
   const size_t per = (size_t)c->data.n * (c->data.kind == PF_SINGLE_PHASE ? 1 : 3);
   cudaError_t e = cudaSuccess;

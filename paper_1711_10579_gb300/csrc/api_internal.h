@@ -40,13 +40,14 @@ struct SysBuf {
 // Per-solve device state for up to `cap` scenarios plus staging buffers.
 struct Workspace {
   int cap = 0;
+  int cap_m = -1;  // Krylov restart length the buffers were sized for
   DevWork w{};
   DevBuffer mem;
   double *st_p_load = nullptr, *st_q_load = nullptr, *st_p_gen = nullptr;
   double *st_vm = nullptr, *st_va = nullptr;
   pf_info* st_info = nullptr;
-  int ensure(int kind, int n, long long nnz_lu, int B);
-  static size_t bytes_for(int kind, int n, long long nnz_lu, int B);
+  int ensure(int kind, int n, long long nnz_lu, int B, int m = 0);
+  static size_t bytes_for(int kind, int n, long long nnz_lu, int B, int m = 0);
 };
 
 struct Server;
@@ -100,10 +101,10 @@ int inspect(pf_case c, InspectKind k, const pf_opts* o, const double* vmag,
             const double* vang, double* out, pf_info* info);
 
 // Launchers in newton.cu / krylov.cu.
-cudaError_t launch_newton(int bs, bool fp32, const DevSys& S, const DevWork& w,
+cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const DevWork& w,
                           const DevOpts& o, int grid, int cluster, int threads,
                           cudaStream_t st);
-int max_cluster(int bs, bool fp32, int threads);
+int max_cluster(int bs, bool fp32, bool nk, int threads);
 
 // Serving runtime (serve.cpp).
 void serve_shutdown(pf_ctx ctx);

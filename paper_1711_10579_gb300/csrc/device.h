@@ -9,6 +9,8 @@ namespace pf {
 
 // Running status of a scenario inside a solve.
 constexpr int kRunning = PF_PENDING;
+// Krylov basis vectors per GMRES cycle (restart m <= kMaxJ - 1).
+constexpr int kMaxJ = 64;
 
 // Symbolic structure and bus data of one case for one ordering (device
 // pointers, new numbering).  Shared by every scenario of the case.
@@ -96,6 +98,15 @@ struct DevWork {
   void* lu;       // factor values, bs*bs per entry
   void* uinv;     // inverse diagonal blocks, bs*bs per row
   void* y;        // triangular-solve vector, bs per row
+  // Newton-Krylov (factor precision): the Jacobian for products, the Krylov
+  // basis [m+1][rows][B][bs], work vectors and reduction slots
+  // [2][cluster][B][kMaxJ]
+  void* jm;
+  void* vb;
+  void* wv;
+  void* zg;
+  void* xg;
+  void* gred;
   unsigned long long* norm;  // [2][B] max |mismatch| (bit pattern of a double)
   unsigned long long* step;  // [2][B] max |step|
   int* flag;                 // [B] singular pivot seen
@@ -110,7 +121,12 @@ struct DevOpts {
   int mode;     // 0 solve, 1 evaluate mismatch + Jacobian, 2 one Newton step
   unsigned long long* prof;  // optional per-phase device time (ns), kProfPhases
   int y_in_smem;             // the solve vector lives in dynamic shared memory
+  int m;                     // Newton-Krylov: GMRES restart length
+  int max_lin;               // ... inner iterations per Newton step
+  double rtol;               // ... inner relative-residual floor
 };
+
+size_t dynamic_smem_bytes(int bs, size_t tf, bool nk, int n, const DevOpts& o, int threads);
 
 // Phases timed by the optional profile (cluster 0, CTA 0, between barriers).
 enum ProfPhase { kProfSetup = 0, kProfMismatch, kProfStop, kProfFactor, kProfSolve,

@@ -206,7 +206,7 @@ __device__ __forceinline__ T group_sum(T v, int G, unsigned gmask) {
 // and their columns zero, which keeps the system of Eq. 10 unchanged.
 template <typename TF>
 __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, int gs,
-                                      double& nrm) {
+                                      double& nrm, TF* jcopy) {
   const int B = w.B;
   const size_t b = (size_t)i * B + gs;
   const double2 Vi = ldc(w.V + b);
@@ -285,6 +285,7 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
     }
     TF blk[4] = {j00, j01, j10, j11};
     blk_store<2>(lu + ((size_t)e * B + gs) * 4, blk);
+    if (jcopy) blk_store<2>(jcopy + ((size_t)e * B + gs) * 4, blk);
   }
 }
 
@@ -316,7 +317,7 @@ __device__ __forceinline__ void load_slope(double2 V, double pl, double ql, doub
 
 template <typename TF>
 __device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, int gs,
-                                      double& nrm) {
+                                      double& nrm, TF* jcopy) {
   const int B = w.B;
   const size_t b = (size_t)i * B + gs;
   const int mask = S.btype[i] & 7;
@@ -412,6 +413,7 @@ __device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, 
       }
     }
     blk_store<6>(lu + ((size_t)e * B + gs) * 36, blk);
+    if (jcopy) blk_store<6>(jcopy + ((size_t)e * B + gs) * 36, blk);
   }
 }
 
@@ -685,10 +687,77 @@ __device__ void factor_levels(const DevSys& S, const DevWork& w, const Team& tm,
 }
 
 // ---------------------------------------------------------------------------
+// Newton-Krylov: restarted GMRES(m), right-preconditioned by ILU(0)
+// ---------------------------------------------------------------------------
+
+
+// Team-wide sums of per-scenario partials.  part(j) is the calling thread's
+// partial of index j for its scenario slot; every thread must call (inactive
+// ones return 0).  Lanes of a slot are summed with shuffles, warps through
+// shared memory, and the CTAs of a cluster through per-rank global slots read
+// back after a cluster barrier -- a fixed order, so results are deterministic.
+// Results: rs[j * S + slot], valid for every thread of the CTA on return.
+template <bool CL, typename T, class Part>
+__device__ void team_sum(const Team& tm, int J, Part part, T* redw, T* rs, T* gred, int par,
+                         int csize, int crank, int B) {
+  const int S = tm.S;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < J; ++j) {
+    T v = part(j);
+    for (int off = 16; off >= S; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane < S) redw[(warp * J + j) * S + lane] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < J * S; t += blockDim.x) {
+    const int j = t / S, s = t - j * S;
+    T a = T(0);
+    for (int q = 0; q < nw; ++q) a += redw[(q * J + j) * S + s];
+    if constexpr (CL) {
+      if (s < tm.ns) gred[(((size_t)par * csize + crank) * B + tm.s0 + s) * kMaxJ + j] = a;
+    } else {
+      rs[j * S + s] = a;
+    }
+  }
+  if constexpr (CL) {
+    csync<CL>();
+    for (int t = threadIdx.x; t < J * S; t += blockDim.x) {
+      const int j = t / S, s = t - j * S;
+      T a = T(0);
+      if (s < tm.ns)
+        for (int r = 0; r < csize; ++r)
+          a += __ldcg(gred + (((size_t)par * csize + r) * B + tm.s0 + s) * kMaxJ + j);
+      rs[j * S + s] = a;
+    }
+  }
+  __syncthreads();
+}
+
+// Per-slot GMRES state kept by every CTA in shared memory (identical copies,
+// updated from identical reduction results): H column-major with leading
+// dimension m+1, Givens cosines / sines, the rotated right-hand side g and
+// the coefficients y.
+template <typename T>
+struct GmresState {
+  T* H;
+  T* cs;
+  T* sn;
+  T* g;
+  T* y;
+  __device__ static int words(int m) { return (m + 1) * m + 4 * m + 1; }
+  __device__ void bind(T* base, int m, int slot) {
+    H = base + (size_t)slot * words(m);
+    cs = H + (m + 1) * m;
+    sn = cs + m;
+    g = sn + m;
+    y = g + m + 1;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
 
-template <int BS, typename TF, bool CL>
+template <int BS, typename TF, bool CL, bool NK>
 __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, DevWork w, DevOpts o) {
   constexpr bool THREE = (BS == 6);
   constexpr int NSL = THREE ? 3 : 1;  // complex voltages per row
@@ -712,13 +781,26 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
   solo.nthr = blockDim.x;
   extern __shared__ __align__(16) unsigned char dsm[];
   TF* yv = o.y_in_smem ? reinterpret_cast<TF*>(dsm) : reinterpret_cast<TF*>(w.y);
+  // Newton-Krylov shared memory after the solve vector: per-slot GMRES state,
+  // per-warp reduction partials and reduction results
+  TF* nk_state = reinterpret_cast<TF*>(dsm + (o.y_in_smem ? (size_t)n * BS * sizeof(TF) : 0));
+  TF* nk_redw = nk_state + (NK ? (size_t)o.S * GmresState<TF>::words(o.m) : 0);
+  TF* nk_rs = nk_redw + (NK ? (size_t)(blockDim.x / 32) * kMaxJ * o.S : 0);
+  __shared__ int sh_lin[32];       // inner iterations, whole solve
+  __shared__ int sh_lin_step[32];  // inner iterations, this Newton step
+  __shared__ int sh_kk[32];
+  __shared__ unsigned sh_inner;
+  __shared__ TF sh_bnorm[32], sh_eta[32], sh_hk1[32];
   __shared__ int sh_status[32];
   __shared__ unsigned sh_act;
   __shared__ int sh_refine;
   __shared__ unsigned long long sh_t0;
   if (threadIdx.x == 0) {
     sh_t0 = global_ns();
-    for (int s = 0; s < 32; ++s) sh_status[s] = kRunning;
+    for (int s = 0; s < 32; ++s) {
+      sh_status[s] = kRunning;
+      sh_lin[s] = 0;
+    }
     sh_act = (tm.ns >= 32) ? 0xffffffffu : ((1u << tm.ns) - 1u);
   }
   __syncthreads();
@@ -748,8 +830,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
         vm = w.in_vm[oi];
         va = w.in_va[oi];
       } else if (w.warm_in) {
-        vm = w.warm_vm[i];
-        va = w.warm_va[i];
+        vm = w.warm_vm[oi];
+        va = w.warm_va[oi];
       } else {
         vm = (S.btype[i] == PF_PQ) ? 1.0 : S.v_set[i];
         va = 0.0;
@@ -773,7 +855,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
             sincos(w.in_va[(size_t)oi * 3 + a], &sn, &cs);
             v = make_double2(w.in_vm[(size_t)oi * 3 + a] * cs, w.in_vm[(size_t)oi * 3 + a] * sn);
           } else if (w.warm_in) {
-            v = w.warm_V[(size_t)i * 3 + a];
+            v = w.warm_V[(size_t)oi * 3 + a];
           } else {
             // balanced source angles 0, -120, +120 degrees
             double sn, cs;
@@ -799,10 +881,11 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
     // ---- A: mismatch + Jacobian ----
     run_rows<CL>(tm, n, [&](int i, int gs) {
       double nrm;
+      TF* jcopy = NK ? reinterpret_cast<TF*>(w.jm) : nullptr;
       if constexpr (THREE) {
-        mismatch_jacobian_3ph<TF>(S, w, i, gs, nrm);
+        mismatch_jacobian_3ph<TF>(S, w, i, gs, nrm, jcopy);
       } else {
-        mismatch_jacobian_1ph<TF>(S, w, i, gs, nrm);
+        mismatch_jacobian_1ph<TF>(S, w, i, gs, nrm, jcopy);
       }
       atomic_max_pos(w.norm + (size_t)(it & 1) * B + gs, nrm);
     });
@@ -829,7 +912,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
             pf_info inf;
             inf.status = st;
             inf.iterations = it;
-            inf.linear_iterations = 0;
+            inf.linear_iterations = sh_lin[s];
             inf.reserved = 0;
             inf.mismatch = nrm;
             inf.max_step = it > 0 ? __longlong_as_double((long long)__ldcg(w.step + (size_t)((it - 1) & 1) * B + gs)) : 0.0;
@@ -870,7 +953,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
             pf_info inf;
             inf.status = PF_ERR_SINGULAR;
             inf.iterations = it;
-            inf.linear_iterations = 0;
+            inf.linear_iterations = sh_lin[s];
             inf.reserved = 0;
             inf.mismatch = __longlong_as_double((long long)__ldcg(w.norm + (size_t)(it & 1) * B + gs));
             inf.max_step = 0.0;
@@ -885,6 +968,263 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
     tm.act = sh_act;
     if (tm.act == 0) break;
 
+    // ---- C (Newton-Krylov): GMRES(m) on J dx = F, right ILU(0) ----
+    if constexpr (NK) {
+      const int m = o.m;
+      const int slot = tm.tid & (tm.S - 1);
+      const int gs = tm.s0 + slot;
+      TF* const V0 = reinterpret_cast<TF*>(w.vb);
+      TF* const W = reinterpret_cast<TF*>(w.wv);
+      TF* const Z = reinterpret_cast<TF*>(w.zg);
+      TF* const X = reinterpret_cast<TF*>(w.xg);
+      const TF* const JM = reinterpret_cast<const TF*>(w.jm);
+      const size_t NV = (size_t)n * B * BS;
+      const int first = tm.tid / tm.S, stride = tm.nthr / tm.S;
+      int par = 0;
+      auto slot_on = [&](unsigned bits) { return slot < tm.ns && ((bits >> slot) & 1u); };
+      auto rs = [&](int j) { return nk_rs[j * tm.S + slot]; };
+      auto tsum = [&](int J, auto part) {
+        team_sum<CL, TF>(tm, J, part, nk_redw, nk_rs, reinterpret_cast<TF*>(w.gred), par, csize,
+                         crank, B);
+        par ^= 1;
+      };
+      // J u for row i (block SpMV on the Jacobian's own pattern)
+      auto jrow = [&](int i, const TF* u, TF (&out)[BS]) {
+#pragma unroll
+        for (int c = 0; c < BS; ++c) out[c] = TF(0);
+        for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
+          TF Jb[BS * BS];
+          blk_load<BS>(JM + ((size_t)e * B + gs) * BS * BS, Jb);
+          const size_t bj = ((size_t)S.lu_col[e] * B + gs) * BS;
+          TF uj[BS];
+#pragma unroll
+          for (int c = 0; c < BS; ++c) uj[c] = __ldcg(u + bj + c);
+#pragma unroll
+          for (int r = 0; r < BS; ++r)
+#pragma unroll
+            for (int c = 0; c < BS; ++c) out[r] += Jb[r * BS + c] * uj[c];
+        }
+      };
+      // z = M^-1 u by the ILU(0) sweeps in CTA 0 (u, z in global memory)
+      auto precond = [&](const TF* u, TF* zout, bool accumulate, unsigned bits) {
+        solo.act = bits;
+        if (crank == 0) {
+          run_rows<false>(solo, n, [&](int i, int g2) {
+            const size_t bb = ((size_t)i * B + g2) * BS;
+            for (int c = 0; c < BS; ++c) yv[bb + c] = __ldcg(u + bb + c);
+          });
+          sweep<BS, TF, true, false>(S, w, yv, solo, S.flev_ptr, S.fwd_rec, S.nflev, S.g_fwd);
+          sweep<BS, TF, false, false>(S, w, yv, solo, S.blev_ptr, S.bwd_rec, S.nblev, S.g_bwd);
+          run_rows<false>(solo, n, [&](int i, int g2) {
+            const size_t bb = ((size_t)i * B + g2) * BS;
+            for (int c = 0; c < BS; ++c) zout[bb + c] = accumulate ? zout[bb + c] + yv[bb + c] : yv[bb + c];
+          });
+        }
+        csync<CL>();
+      };
+      // ||F||_2 and the inner tolerance eta = clamp(||F||_inf, rtol, 0.1)
+      tsum(1, [&](int) {
+        TF a = TF(0);
+        if (slot_on(tm.act))
+          for (int i = first; i < n; i += stride)
+            for (int c = 0; c < BS; ++c) {
+              const TF f = (TF)__ldcg(w.F + ((size_t)i * B + gs) * BS + c);
+              a += f * f;
+              X[((size_t)i * B + gs) * BS + c] = TF(0);
+            }
+        return a;
+      });
+      if (threadIdx.x < tm.ns) {
+        const int t = threadIdx.x;
+        sh_lin_step[t] = 0;
+        const double ninf = __longlong_as_double((long long)__ldcg(w.norm + (size_t)(it & 1) * B + tm.s0 + t));
+        sh_bnorm[t] = sqrt(nk_rs[t]);
+        const double eta = (o.mode == 2) ? o.rtol : fmin(0.1, fmax(o.rtol, ninf));
+        sh_eta[t] = (TF)eta;
+      }
+      __syncthreads();
+      for (int restart = 0;; ++restart) {
+        // r = F - J x into V_0, and ||r||_2
+        tsum(1, [&](int) {
+          TF a = TF(0);
+          if (slot_on(tm.act))
+            for (int i = first; i < n; i += stride) {
+              TF jx[BS];
+              if (restart > 0) jrow(i, X, jx);
+              for (int c = 0; c < BS; ++c) {
+                const size_t q = ((size_t)i * B + gs) * BS + c;
+                const TF r = (TF)__ldcg(w.F + q) - (restart > 0 ? jx[c] : TF(0));
+                V0[q] = r;
+                a += r * r;
+              }
+            }
+          return a;
+        });
+        if (threadIdx.x == 0) {
+          unsigned bits = 0;
+          for (int t = 0; t < tm.ns; ++t) {
+            sh_kk[t] = 0;
+            if (!((tm.act >> t) & 1u)) continue;
+            GmresState<TF> G;
+            G.bind(nk_state, m, t);
+            const TF beta = sqrt(nk_rs[t]);
+            G.g[0] = beta;
+            if (beta > sh_eta[t] * sh_bnorm[t] && sh_lin_step[t] < o.max_lin) bits |= 1u << t;
+          }
+          sh_inner = bits;
+        }
+        __syncthreads();
+        unsigned inner = sh_inner;
+        const unsigned started = inner;
+        if (inner == 0) break;
+        // v_0 = r / beta
+        run_items<CL>(tm, n, [&](int i, int g2) {
+          const int t = g2 - tm.s0;
+          if (!((inner >> t) & 1u)) return;
+          GmresState<TF> G;
+          G.bind(nk_state, m, t);
+          const TF inv = TF(1) / G.g[0];
+          for (int c = 0; c < BS; ++c) V0[((size_t)i * B + g2) * BS + c] *= inv;
+        });
+        for (int k = 0; k < m; ++k) {
+          // z = M^-1 v_k, then w = J z
+          precond(V0 + (size_t)k * NV, Z, false, inner);
+          if (slot_on(inner))
+            for (int i = first; i < n; i += stride) {
+              TF jz[BS];
+              jrow(i, Z, jz);
+              for (int c = 0; c < BS; ++c) W[((size_t)i * B + gs) * BS + c] = jz[c];
+            }
+          auto dots = [&](int j) {
+            TF a = TF(0);
+            if (slot_on(inner))
+              for (int i = first; i < n; i += stride)
+                for (int c = 0; c < BS; ++c) {
+                  const size_t q = ((size_t)i * B + gs) * BS + c;
+                  a += V0[(size_t)j * NV + q] * W[q];
+                }
+            return a;
+          };
+          auto orth = [&](const TF* hv) {  // w -= V_{0..k} hv (own rows)
+            if (slot_on(inner))
+              for (int i = first; i < n; i += stride)
+                for (int c = 0; c < BS; ++c) {
+                  const size_t q = ((size_t)i * B + gs) * BS + c;
+                  TF v = W[q];
+                  for (int j = 0; j <= k; ++j) v -= hv[j] * V0[(size_t)j * NV + q];
+                  W[q] = v;
+                }
+          };
+          const bool keeper = threadIdx.x < tm.ns && ((inner >> threadIdx.x) & 1u);
+          GmresState<TF> G;
+          G.bind(nk_state, m, keeper ? threadIdx.x : 0);
+          TF* Hk = G.H + (size_t)k * (m + 1);
+          // classical Gram-Schmidt, twice (CGS2)
+          TF hv[kMaxJ];
+          tsum(k + 1, dots);
+          for (int j = 0; j <= k; ++j) hv[j] = rs(j);
+          if (keeper)
+            for (int j = 0; j <= k; ++j) Hk[j] = nk_rs[j * tm.S + threadIdx.x];
+          orth(hv);
+          tsum(k + 1, dots);
+          for (int j = 0; j <= k; ++j) hv[j] = rs(j);
+          if (keeper)
+            for (int j = 0; j <= k; ++j) Hk[j] += nk_rs[j * tm.S + threadIdx.x];
+          orth(hv);
+          tsum(1, [&](int) {
+            TF a = TF(0);
+            if (slot_on(inner))
+              for (int i = first; i < n; i += stride)
+                for (int c = 0; c < BS; ++c) {
+                  const TF v = W[((size_t)i * B + gs) * BS + c];
+                  a += v * v;
+                }
+            return a;
+          });
+          // Hessenberg column k: apply the earlier rotations, make a new one
+          if (keeper) {
+            const int t = threadIdx.x;
+            const TF hk1 = sqrt(nk_rs[t]);
+            sh_hk1[t] = hk1;
+            for (int j = 0; j < k; ++j) {
+              const TF a0 = Hk[j], a1 = Hk[j + 1];
+              Hk[j] = G.cs[j] * a0 + G.sn[j] * a1;
+              Hk[j + 1] = -G.sn[j] * a0 + G.cs[j] * a1;
+            }
+            const TF den = sqrt(Hk[k] * Hk[k] + hk1 * hk1);
+            bool stop = false;
+            if (den > TF(0)) {
+              G.cs[k] = Hk[k] / den;
+              G.sn[k] = hk1 / den;
+              Hk[k] = den;
+              Hk[k + 1] = TF(0);
+              G.g[k + 1] = -G.sn[k] * G.g[k];
+              G.g[k] = G.cs[k] * G.g[k];
+              sh_kk[t] = k + 1;
+            } else {
+              stop = true;  // breakdown with a zero column: keep the first k steps
+            }
+            sh_lin[t] += 1;
+            sh_lin_step[t] += 1;
+            const TF res = G.g[k + 1] < TF(0) ? -G.g[k + 1] : G.g[k + 1];
+            if (stop || res <= sh_eta[t] * sh_bnorm[t] || sh_lin_step[t] >= o.max_lin ||
+                !(hk1 > TF(0)))
+              atomicAnd(&sh_inner, ~(1u << t));
+          }
+          __syncthreads();
+          const unsigned nxt = sh_inner;
+          // v_{k+1} = w / h_{k+1,k} for the slots that go on
+          if (k + 1 < m && nxt != 0) {
+            run_items<CL>(tm, n, [&](int i, int g2) {
+              const int t = g2 - tm.s0;
+              if (!((nxt >> t) & 1u)) return;
+              const TF inv = TF(1) / sh_hk1[t];
+              for (int c = 0; c < BS; ++c) {
+                const size_t q = ((size_t)i * B + g2) * BS + c;
+                V0[(size_t)(k + 1) * NV + q] = W[q] * inv;
+              }
+            });
+          }
+          inner = nxt;
+          if (inner == 0) break;
+        }
+        // y = R^-1 g per slot; x += M^-1 (V y)
+        if (threadIdx.x < tm.ns && ((started >> threadIdx.x) & 1u)) {
+          const int t = threadIdx.x, kk = sh_kk[t];
+          GmresState<TF> G;
+          G.bind(nk_state, m, t);
+          for (int j = kk - 1; j >= 0; --j) {
+            TF v = G.g[j];
+            for (int l = j + 1; l < kk; ++l) v -= G.H[j + (size_t)l * (m + 1)] * G.y[l];
+            G.y[j] = v / G.H[j + (size_t)j * (m + 1)];
+          }
+        }
+        __syncthreads();
+        run_items<CL>(tm, n, [&](int i, int g2) {
+          const int t = g2 - tm.s0;
+          const size_t bq = ((size_t)i * B + g2) * BS;
+          if (!((started >> t) & 1u)) {
+            for (int c = 0; c < BS; ++c) W[bq + c] = TF(0);
+            return;
+          }
+          GmresState<TF> G;
+          G.bind(nk_state, m, t);
+          const int kk = sh_kk[t];
+          for (int c = 0; c < BS; ++c) {
+            TF v = TF(0);
+            for (int j = 0; j < kk; ++j) v += G.y[j] * V0[(size_t)j * NV + bq + c];
+            W[bq + c] = v;
+          }
+        });
+        precond(W, X, true, started);
+      }
+      // the Newton step
+      run_rows<CL>(tm, n, [&](int i, int g2) {
+        const size_t bq = ((size_t)i * B + g2) * BS;
+        for (int c = 0; c < BS; ++c) w.dx[bq + c] = (double)__ldcg(X + bq + c);
+      });
+      tick(kProfSolve);
+    } else {
     // ---- C: triangular solves, then FP64 refinement ----
     for (int pass = 0; pass <= n_refine; ++pass) {
       // right-hand side: F, or the FP64 residual of the current step
@@ -980,6 +1320,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
       tick(kProfSolve);
     }
 
+    }
     if (o.mode == 2) return;  // inspection: the step stays in the workspace
 
     // ---- E: voltage update ----
@@ -1023,7 +1364,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
         const size_t dst = ((size_t)gs * n + oi) * 3 + a;
         if (w.out_vm) w.out_vm[dst] = pres ? hypot(v.x, v.y) : 0.0;
         if (w.out_va) w.out_va[dst] = pres ? atan2(v.y, v.x) : 0.0;
-        if (w.warm_out && gs == 0 && ok) w.warm_V[(size_t)i * 3 + a] = v;
+        if (w.warm_out && gs == 0 && ok) w.warm_V[(size_t)oi * 3 + a] = v;
       }
     } else {
       const size_t dst = (size_t)gs * n + oi;
@@ -1031,8 +1372,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
       if (w.out_vm) w.out_vm[dst] = vm;
       if (w.out_va) w.out_va[dst] = va;
       if (w.warm_out && gs == 0 && ok) {
-        w.warm_vm[i] = vm;
-        w.warm_va[i] = va;
+        w.warm_vm[oi] = vm;
+        w.warm_va[oi] = va;
       }
     }
   });
@@ -1047,14 +1388,14 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
 // launcher
 // ---------------------------------------------------------------------------
 
-template <int BS, typename TF, bool CL>
+template <int BS, typename TF, bool CL, bool NK>
 static cudaError_t launch_t(const DevSys& S, const DevWork& w, const DevOpts& o, int grid,
                             int cluster, int threads, cudaStream_t st) {
-  auto kern = newton_kernel<BS, TF, CL>;
+  auto kern = newton_kernel<BS, TF, CL, NK>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = o.y_in_smem ? (size_t)S.n * BS * sizeof(TF) : 0;
+  cfg.dynamicSmemBytes = dynamic_smem_bytes(BS, sizeof(TF), NK, S.n, o, threads);
   if (cfg.dynamicSmemBytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.dynamicSmemBytes);
@@ -1078,9 +1419,9 @@ static cudaError_t launch_t(const DevSys& S, const DevWork& w, const DevOpts& o,
 }
 
 // Maximum cluster size the device can co-schedule for this kernel.
-template <int BS, typename TF>
+template <int BS, typename TF, bool NK>
 static int max_cluster_t(int threads) {
-  auto kern = newton_kernel<BS, TF, true>;
+  auto kern = newton_kernel<BS, TF, true, NK>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   for (int c = 16; c >= 1; c >>= 1) {
     cudaLaunchConfig_t cfg = {};
@@ -1100,25 +1441,41 @@ static int max_cluster_t(int threads) {
   return 1;
 }
 
-cudaError_t launch_newton(int bs, bool fp32, const DevSys& S, const DevWork& w,
-                          const DevOpts& o, int grid, int cluster, int threads,
-                          cudaStream_t st) {
-  const bool cl = cluster > 1;
-  if (bs == 2) {
-    if (fp32) return cl ? launch_t<2, float, true>(S, w, o, grid, cluster, threads, st)
-                        : launch_t<2, float, false>(S, w, o, grid, cluster, threads, st);
-    return cl ? launch_t<2, double, true>(S, w, o, grid, cluster, threads, st)
-              : launch_t<2, double, false>(S, w, o, grid, cluster, threads, st);
+size_t dynamic_smem_bytes(int bs, size_t tf, bool nk, int n, const DevOpts& o, int threads) {
+  size_t b = o.y_in_smem ? (size_t)n * bs * tf : 0;
+  if (nk) {
+    const size_t words = (size_t)(o.m + 1) * o.m + 4 * o.m + 1;
+    b += (size_t)o.S * words * tf;
+    b += (size_t)(threads / 32) * kMaxJ * o.S * tf;
+    b += (size_t)kMaxJ * o.S * tf;
   }
-  if (fp32) return cl ? launch_t<6, float, true>(S, w, o, grid, cluster, threads, st)
-                      : launch_t<6, float, false>(S, w, o, grid, cluster, threads, st);
-  return cl ? launch_t<6, double, true>(S, w, o, grid, cluster, threads, st)
-            : launch_t<6, double, false>(S, w, o, grid, cluster, threads, st);
+  return b;
 }
 
-int max_cluster(int bs, bool fp32, int threads) {
-  if (bs == 2) return fp32 ? max_cluster_t<2, float>(threads) : max_cluster_t<2, double>(threads);
-  return fp32 ? max_cluster_t<6, float>(threads) : max_cluster_t<6, double>(threads);
+cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const DevWork& w,
+                          const DevOpts& o, int grid, int cluster, int threads, cudaStream_t st) {
+  const bool cl = cluster > 1;
+#define PF_LAUNCH(BSV, TFT)                                                                   \
+  if (nk) return cl ? launch_t<BSV, TFT, true, true>(S, w, o, grid, cluster, threads, st)      \
+                    : launch_t<BSV, TFT, false, true>(S, w, o, grid, cluster, threads, st);    \
+  return cl ? launch_t<BSV, TFT, true, false>(S, w, o, grid, cluster, threads, st)             \
+            : launch_t<BSV, TFT, false, false>(S, w, o, grid, cluster, threads, st);
+  if (bs == 2) {
+    if (fp32) { PF_LAUNCH(2, float) }
+    PF_LAUNCH(2, double)
+  }
+  if (fp32) { PF_LAUNCH(6, float) }
+  PF_LAUNCH(6, double)
+#undef PF_LAUNCH
+}
+
+int max_cluster(int bs, bool fp32, bool nk, int threads) {
+  if (bs == 2) {
+    if (fp32) return nk ? max_cluster_t<2, float, true>(threads) : max_cluster_t<2, float, false>(threads);
+    return nk ? max_cluster_t<2, double, true>(threads) : max_cluster_t<2, double, false>(threads);
+  }
+  if (fp32) return nk ? max_cluster_t<6, float, true>(threads) : max_cluster_t<6, float, false>(threads);
+  return nk ? max_cluster_t<6, double, true>(threads) : max_cluster_t<6, double, false>(threads);
 }
 
 }  // namespace pf

@@ -30,24 +30,33 @@ int check_opts(const pf_opts& o) {
     return set_error(PF_ERR_INVALID, "opts.block_threads must be 0 or a multiple of 32 <= 1024");
   if (o.scen_per_cta < 0 || o.scen_per_cta > 32 || (o.scen_per_cta & (o.scen_per_cta - 1)))
     return set_error(PF_ERR_INVALID, "opts.scen_per_cta must be 0 or a power of two <= 32");
+  if (o.method == PF_NK) {
+    if (o.gmres_restart < 1 || o.gmres_restart >= kMaxJ)
+      return set_error(PF_ERR_INVALID, "opts.gmres_restart must be in [1, 63]");
+    if (o.gmres_max_iter < 1) return set_error(PF_ERR_INVALID, "opts.gmres_max_iter must be >= 1");
+    if (!(o.gmres_rtol > 0.0 && o.gmres_rtol < 1.0))
+      return set_error(PF_ERR_INVALID, "opts.gmres_rtol must be in (0, 1)");
+    if (o.scen_per_cta > 8)
+      return set_error(PF_ERR_INVALID, "opts.scen_per_cta must be <= 8 for PF_NK");
+  }
   return PF_OK;
 }
 
 struct ClusterKey {
-  int bs, fp32, threads;
+  int bs, fp32, nk, threads;
   bool operator<(const ClusterKey& k) const {
-    return std::tie(bs, fp32, threads) < std::tie(k.bs, k.fp32, k.threads);
+    return std::tie(bs, fp32, nk, threads) < std::tie(k.bs, k.fp32, k.nk, k.threads);
   }
 };
 
-int cached_max_cluster(int bs, bool fp32, int threads) {
+int cached_max_cluster(int bs, bool fp32, bool nk, int threads) {
   static std::mutex mu;
   static std::map<ClusterKey, int> cache;
   std::lock_guard<std::mutex> lk(mu);
-  ClusterKey k{bs, fp32 ? 1 : 0, threads};
+  ClusterKey k{bs, fp32 ? 1 : 0, nk ? 1 : 0, threads};
   auto it = cache.find(k);
   if (it != cache.end()) return it->second;
-  int c = max_cluster(bs, fp32, threads);
+  int c = max_cluster(bs, fp32, nk, threads);
   cache[k] = c;
   return c;
 }
@@ -57,16 +66,19 @@ int cached_max_cluster(int bs, bool fp32, int threads) {
 void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int* cluster,
                   int* threads, int* S) {
   const int bs = c->bs;
-  const int max_threads = (bs == 2) ? 512 : 256;
+  // 2x2 blocks: 512 threads (128 registers each); 6x6 blocks and the
+  // Newton-Krylov kernels: 256
+  const int max_threads = (bs == 2 && o.method != PF_NK) ? 512 : 256;
   if (B == 1) {
     *threads = o.block_threads ? std::min(o.block_threads, max_threads) : max_threads;
-    *cluster = o.cluster_size ? o.cluster_size : cached_max_cluster(bs, fp32, *threads);
+    *cluster = o.cluster_size ? o.cluster_size
+                              : cached_max_cluster(bs, fp32, o.method == PF_NK, *threads);
     *S = 1;
     *grid = *cluster;
   } else {
     *threads = o.block_threads ? std::min(o.block_threads, max_threads) : 256;
     *cluster = 1;
-    *S = o.scen_per_cta ? o.scen_per_cta : 2;
+    *S = o.scen_per_cta ? o.scen_per_cta : (o.method == PF_NK ? 4 : 2);
     *grid = (B + *S - 1) / *S;
   }
 }
@@ -76,12 +88,12 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
               double* out_va, pf_info* out_info, unsigned long long* prof) {
   int rc = check_opts(o);
   if (rc != PF_OK) return rc;
-  if (o.method == PF_NK)
-    return set_error(PF_ERR_UNSUPPORTED, "the Newton-Krylov solver is not built yet");
+  const bool nk = o.method == PF_NK;
   const int kind = c->data.kind, n = c->data.n, bs = c->bs;
-  rc = ws->ensure(kind, n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), B);
+  rc = ws->ensure(kind, n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), B,
+                  nk ? o.gmres_restart : 0);
   if (rc != PF_OK) return rc;
-  SysBuf& sb = c->nr;
+  SysBuf& sb = nk ? c->nk : c->nr;
   // inspection of the Jacobian reads the factor array as FP64
   const bool fp32 = (o.precision == PF_MIXED) && mode != RunMode::Eval;
   int threads, cluster, S, grid;
@@ -117,10 +129,15 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   d.S = S;
   d.mode = mode == RunMode::Solve ? 0 : (mode == RunMode::Eval ? 1 : 2);
   d.prof = prof;
+  d.m = nk ? o.gmres_restart : 0;
+  d.max_lin = o.gmres_max_iter;
+  d.rtol = o.gmres_rtol;
   // single solves keep the triangular-solve vector in shared memory when it fits
-  const size_t ybytes = (size_t)n * bs * (fp32 ? 4 : 8);
-  d.y_in_smem = (B == 1 && ybytes <= 200 * 1024) ? 1 : 0;
-  cudaError_t e = launch_newton(bs, fp32, sys, w, d, grid, cluster, threads, st);
+  const size_t tf = fp32 ? 4 : 8;
+  d.y_in_smem = 0;
+  const size_t extra = dynamic_smem_bytes(bs, tf, nk, n, d, threads);
+  d.y_in_smem = (B == 1 && (size_t)n * bs * tf + extra <= 200 * 1024) ? 1 : 0;
+  cudaError_t e = launch_newton(bs, fp32, nk, sys, w, d, grid, cluster, threads, st);
   if (e != cudaSuccess) return cuda_error(e, "launching the Newton kernel");
   return PF_OK;
 }
@@ -150,17 +167,21 @@ int inspect(pf_case c, InspectKind k, const pf_opts* po, const double* vmag, con
   cudaStream_t st = c->ctx->stream;
   Workspace* ws = &c->ws1;
   const int kind = c->data.kind, n = c->data.n, bs = c->bs;
-  int rc = ws->ensure(kind, n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), 1);
+  int rc = ws->ensure(kind, n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), 1,
+                      o.method == PF_NK ? o.gmres_restart : 0);
   if (rc != PF_OK) return rc;
   const size_t per = (size_t)n * (kind == PF_SINGLE_PHASE ? 1 : 3);
   cudaError_t e = cudaMemcpyAsync(ws->st_p_load, vmag, per * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ws->st_q_load, vang, per * 8, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_error(e, "copying the voltage");
   RunMode mode = (k == InspectKind::Step) ? RunMode::Step : RunMode::Eval;
-  if (k != InspectKind::Step) o.precision = PF_FP64;
+  if (k != InspectKind::Step) {
+    o.precision = PF_FP64;
+    o.method = PF_NR;
+  }
   rc = run_solve(c, o, 1, nullptr, nullptr, nullptr, ws, st, mode, nullptr, nullptr);
   if (rc != PF_OK) return rc;
-  const Symbolic& s = c->nr.sym;
+  const Symbolic& s = (k == InspectKind::Step && o.method == PF_NK) ? c->nk.sym : c->nr.sym;
   if (k == InspectKind::Jacobian) {
     const int bb = bs * bs;
     std::vector<double> lu((size_t)s.nnz_lu() * bb);

@@ -340,3 +340,82 @@ def test_three_phase_batch_matches_single(pf, ctx):
             assert np.max(np.abs(vm[b] - np.abs(ref["V"]))) <= V_TOL
     finally:
         pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# Newton-Krylov: GMRES(m) + ILU(0)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["14", "300zip", "2000", "10000"])
+def test_newton_krylov_matches_oracle(pf, ctx, name, prec):
+    case = {"14": cases.case_14bus(0),
+            "300zip": _zip_case(cases.transmission_case(300, 405, 60, 2), 2),
+            "2000": cases.case_2000bus(0), "10000": cases.case_10000bus(0)}[name]
+    ref = O.newton_polar(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        vm, va, info = pf.pf_solve(c, pf.make_opts(method=pf.PF_NK, precision=p))
+        _check_solve(case, vm, va, info, ref)
+        assert info["linear_iterations"] >= info["iterations"] > 0
+        # NR and NK reach the same voltages
+        vm2, va2, info2 = pf.pf_solve(c, pf.make_opts(method=pf.PF_NR, precision=p))
+        assert np.max(np.abs(vm - vm2)) <= V_TOL and np.max(np.abs(va - va2)) <= A_TOL
+    finally:
+        pf.pf_destroy_case(c)
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_gmres_step_meets_its_residual_bound(pf, ctx, prec, rtol):
+    case = _zip_case(cases.transmission_case(300, 405, 60, 2), 2)
+    Y = O.ybus_single(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va = O.flat_start_polar(case)
+        vm = vm + np.where(case.bus_type == cases.PQ, 0.01 * np.sin(np.arange(case.n_bus)), 0)
+        va = va + np.where(case.bus_type != cases.SLACK, 0.02 * np.cos(np.arange(case.n_bus)), 0)
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        dx, _ = pf.pf_newton_step(c, vm, va, pf.make_opts(method=pf.PF_NK, precision=p,
+                                                        gmres_rtol=rtol, gmres_max_iter=2000))
+        F = O.mismatch_polar(case, Y, vm, va)
+        J = O.jacobian_polar(case, Y, vm, va)
+        got = _gpu_mis_to_oracle_order(case, dx)
+        # FP32 products add rounding on top of the GMRES bound
+        slack = 1.5 if prec == "fp64" else 20.0
+        assert np.linalg.norm(F - J @ got) <= slack * rtol * np.linalg.norm(F)
+        ref = O.solve_linear(J, F, "splu")
+        assert np.max(np.abs(got - ref)) <= 1e4 * slack * rtol * np.max(np.abs(ref))
+    finally:
+        pf.pf_destroy_case(c)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_newton_krylov_three_phase(pf, ctx, prec):
+    case = cases.feeder_case(400, 5)
+    ref = O.newton_cim(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        vm, va, info = pf.pf_solve(c, pf.make_opts(method=pf.PF_NK, precision=p))
+        assert info["status"] == 0 and info["mismatch"] <= 1e-8, info
+        assert np.max(np.abs(vm - np.abs(ref["V"]))) <= V_TOL
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_newton_krylov_batch_matches_single(pf, ctx):
+    case = cases.case_2000bus(4)
+    B = 12
+    p_load, q_load, p_gen = cases.scenario_loads(case, B, seed=8)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve_batch(c, p_load, q_load, p_gen,
+                                         pf.make_opts(method=pf.PF_NK, scen_per_cta=4))
+        assert np.all(info["status"] == 0), info
+        for b in (0, B - 1):
+            ref = O.newton_polar(case.with_loads(p_load[b], q_load[b], p_gen[b]))
+            assert np.max(np.abs(vm[b] - ref["vm"])) <= V_TOL
+            assert np.max(np.abs(va[b] - ref["va"])) <= A_TOL
+    finally:
+        pf.pf_destroy_case(c)
