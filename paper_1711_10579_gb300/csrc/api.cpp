@@ -170,6 +170,7 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
 
 // Lanes-per-row tables for a given number of threads per cluster (cached).
 int SysBuf::lanes_for(int threads, DevSys& out) {
+  std::lock_guard<std::mutex> lk(g_mu);
   out = view;
   auto it = g_cache.find(threads);
   if (it == g_cache.end()) {
@@ -225,12 +226,19 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
 }
 
 int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
-  if (B <= cap && m <= cap_m) return PF_OK;
-  B = std::max(B, cap);
-  m = std::max(m, cap_m);
+  if (kind == cap_kind && B <= cap && m <= cap_m && n <= cap_n && nnz_lu <= cap_nnz) return PF_OK;
+  if (kind == cap_kind) {  // grow every dimension, never shrink
+    B = std::max(B, cap);
+    m = std::max(m, cap_m);
+    n = std::max(n, cap_n);
+    nnz_lu = std::max(nnz_lu, cap_nnz);
+  }
   mem.release();
   cap = 0;
   cap_m = -1;
+  cap_kind = 0;
+  cap_n = 0;
+  cap_nnz = 0;
   const int bs = kind == PF_SINGLE_PHASE ? 2 : 6;
   const int nsl = kind == PF_SINGLE_PHASE ? 1 : 3;
   size_t nb = (size_t)n * B;
@@ -282,6 +290,9 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
   }
   cap = B;
   cap_m = m;
+  cap_kind = kind;
+  cap_n = n;
+  cap_nnz = nnz_lu;
   w.B = B;
   return PF_OK;
 }

@@ -33,14 +33,20 @@ struct SysBuf {
   DevSys view{};
   DevBuffer mem;
   std::map<int, std::array<const int8_t*, 2>> g_cache;
+  std::mutex g_mu;  // the serving thread and callers share g_cache
   int build(const CaseData& c, const Ybus& y, Ordering ord, bool fill);
   int lanes_for(int threads, DevSys& out);
 };
 
 // Per-solve device state for up to `cap` scenarios plus staging buffers.
 struct Workspace {
+  // capacity the buffers were sized for: scenarios, Krylov restart length,
+  // case kind, rows and factor block entries
   int cap = 0;
-  int cap_m = -1;  // Krylov restart length the buffers were sized for
+  int cap_m = -1;
+  int cap_kind = 0;
+  int cap_n = 0;
+  long long cap_nnz = 0;
   DevWork w{};
   DevBuffer mem;
   double *st_p_load = nullptr, *st_q_load = nullptr, *st_p_gen = nullptr;
