@@ -292,6 +292,38 @@ int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag,
                    const double* vang, double* dx, pf_info* info);
 
 /*
+ * Newton-Raphson solve of one scenario that allocates nothing.  (The paper
+ * has no counterpart: this entry point exists for callers of the library.)
+ *
+ * Some callers cannot allocate device memory once they are running: a
+ * real-time grid-control loop with a fixed latency budget must not call
+ * cudaMalloc / cudaFree, which can block on the whole device, and a host
+ * application that owns the GPU's memory through its own pool may forbid any
+ * other allocation.  For them this call takes its workspace from a fixed
+ * array in device memory compiled into the library (32 MiB, held by every
+ * GPU that loads the library until the process exits), and calls no
+ * cudaMalloc, cudaFree or other allocating routine.  The case must have been
+ * created beforehand (pf_create_case allocates).
+ *
+ * Arguments as pf_solve_batch_device with B = 1: d_p_load, d_q_load,
+ * d_p_gen (NULL = the case's own), d_vmag, d_vang, d_info are device
+ * pointers; the call is asynchronous on `stream`.  opts->method must be
+ * PF_NR and block_threads / scen_per_cta 0.  A case whose workspace does not
+ * fit the array is rejected with PF_ERR_INVALID and a message giving both
+ * sizes (about 370 bytes per bus plus the LU values: single-phase grids of a
+ * few tens of thousands of buses fit).
+ *
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call shares the array and the
+ * kernel writes all it later reads, so a call does not depend on what an
+ * earlier call left there; calls that overlap on the GPU (other streams, or
+ * other host threads) race on it and must be serialised by the caller.
+ */
+int pf_solve_noalloc(pf_case c, const pf_opts* opts, const double* d_p_load,
+                     const double* d_q_load, const double* d_p_gen, double* d_vmag,
+                     double* d_vang, pf_info* d_info, void* stream);
+
+/*
  * Launch shape a solve of B scenarios with these options would use:
  * grid CTAs, CTAs per cluster, threads per CTA, scenarios per cluster.
  */

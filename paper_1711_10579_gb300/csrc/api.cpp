@@ -614,6 +614,19 @@ int pf_launch_config(pf_case c, const pf_opts* opts, int B, int* grid, int* clus
   return PF_OK;
 }
 
+int pf_solve_noalloc(pf_case c, const pf_opts* opts, const double* d_p_load,
+                     const double* d_q_load, const double* d_p_gen, double* d_vmag,
+                     double* d_vang, pf_info* d_info, void* stream) {
+  if (!c) return set_error(PF_ERR_INVALID, "null case");
+  pf_opts o;
+  if (opts) o = *opts; else pf_opts_default(&o);
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaError_t e = cudaSetDevice(c->ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  return solve_noalloc(c, o, d_p_load, d_q_load, d_p_gen, d_vmag, d_vang, d_info,
+                       (cudaStream_t)stream);
+}
+
 int pf_profile_solve(pf_case c, const pf_opts* opts, double* phase_us, pf_info* info) {
   if (!c || !phase_us) return set_error(PF_ERR_INVALID, "null argument");
   pf_opts o;

@@ -111,6 +111,10 @@ cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const Dev
                           const DevOpts& o, int grid, int cluster, int threads,
                           cudaStream_t st);
 int max_cluster(int bs, bool fp32, bool nk, int threads);
+cudaError_t noalloc_scratch(void** ptr);
+int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const double* d_q_load,
+                  const double* d_p_gen, double* d_vmag, double* d_vang, pf_info* d_info,
+                  cudaStream_t st);
 
 // Serving runtime (serve.cpp).
 void serve_shutdown(pf_ctx ctx);

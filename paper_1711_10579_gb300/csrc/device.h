@@ -11,6 +11,8 @@ namespace pf {
 constexpr int kRunning = PF_PENDING;
 // Krylov basis vectors per GMRES cycle (restart m <= kMaxJ - 1).
 constexpr int kMaxJ = 64;
+// Size of the fixed scratch array used by pf_solve_noalloc.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
 
 // Symbolic structure and bus data of one case for one ordering (device
 // pointers, new numbering).  Shared by every scenario of the case.

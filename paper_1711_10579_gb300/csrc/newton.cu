@@ -27,6 +27,7 @@
 
 #include <cfloat>
 #include <cstdint>
+#include <mutex>
 
 #include "device.h"
 
@@ -1439,6 +1440,33 @@ static int max_cluster_t(int threads) {
     cudaGetLastError();
   }
   return 1;
+}
+
+// Scratch of pf_solve_noalloc: one fixed array in device memory, so that
+// entry point allocates nothing.  Every GPU that loads this library holds it
+// until the process exits; every call of that entry point shares it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of the scratch array on the current device.  The host-side
+// name g_noalloc_scratch is only a stand-in, so the address is looked up once
+// per device with cudaGetSymbolAddress (the first call on a device does this
+// set-up) and cached.
+cudaError_t noalloc_scratch(void** ptr) {
+  static std::mutex mu;
+  static void* addr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  return cudaSuccess;
 }
 
 size_t dynamic_smem_bytes(int bs, size_t tf, bool nk, int n, const DevOpts& o, int threads) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -210,6 +211,155 @@ int inspect(pf_case c, InspectKind k, const pf_opts* po, const double* vmag, con
     std::memset(info, 0, sizeof(*info));
     info->status = PF_OK;
   }
+  return PF_OK;
+}
+
+// Newton-Raphson single solve whose workspace is carved out of the fixed
+// scratch array instead of allocated: no cudaMalloc, no cudaFree, no host
+// heap.  Everything the kernel reads from the workspace is written by the
+// kernel first (its set-up zeroes the norm, step and pivot-flag slots), so
+// the contents left by an earlier call do not matter; calls that overlap on
+// the GPU share the array and race.
+int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const double* d_q_load,
+                  const double* d_p_gen, double* d_vmag, double* d_vang, pf_info* d_info,
+                  cudaStream_t st) {
+  int rc = check_opts(o);
+  if (rc != PF_OK) return rc;
+  if (o.method != PF_NR)
+    return set_error(PF_ERR_UNSUPPORTED, "pf_solve_noalloc runs Newton-Raphson only");
+  if (o.block_threads || o.scen_per_cta)
+    return set_error(PF_ERR_INVALID, "pf_solve_noalloc uses the default CTA shape");
+  const int kind = c->data.kind, n = c->data.n, bs = c->bs;
+  const int nsl = kind == PF_SINGLE_PHASE ? 1 : 3;
+  const bool fp32 = o.precision == PF_MIXED;
+  const size_t tf = fp32 ? 4 : 8;
+  const SysBuf& sb = c->nr;
+  const Symbolic& sy = sb.sym;
+  const int threads = bs == 2 ? 512 : 256;
+  int cluster = o.cluster_size;
+  if (!cluster) cluster = max_cluster(bs, fp32, false, threads);
+  const int nflev = (int)sy.flev_ptr.size() - 1, nblev = (int)sy.blev_ptr.size() - 1;
+  // carve the workspace (256-byte aligned pieces)
+  const size_t nb = (size_t)n;
+  size_t off = 0;
+  size_t sizes[20];
+  int k = 0;
+  sizes[k++] = nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8;  // spec
+  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;         // vm
+  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;         // va
+  sizes[k++] = nb * nsl * 16;                                // V
+  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 16 : 0;        // U
+  sizes[k++] = nb * nsl * 16;                                // I
+  sizes[k++] = nb * nsl * 16;                                // dV
+  sizes[k++] = kind == PF_THREE_PHASE ? nb * 12 * 8 : 0;     // abcd
+  sizes[k++] = nb * bs * 8;                                  // F
+  sizes[k++] = nb * bs * 8;                                  // dx
+  sizes[k++] = nb * bs * 8;                                  // r
+  sizes[k++] = (size_t)sy.nnz_lu() * bs * bs * tf;           // lu
+  sizes[k++] = nb * bs * bs * tf;                            // uinv
+  sizes[k++] = nb * bs * tf;                                 // y
+  sizes[k++] = 2 * 8;                                        // norm
+  sizes[k++] = 2 * 8;                                        // step
+  sizes[k++] = 8;                                            // flag
+  sizes[k++] = (size_t)nflev;                                // forward lanes
+  sizes[k++] = (size_t)nblev;                                // backward lanes
+  size_t offs[20];
+  for (int q = 0; q < k; ++q) {
+    offs[q] = off;
+    off += (sizes[q] + 255) & ~size_t(255);
+  }
+  if (off > kNoAllocScratchBytes) {
+    char msg[160];
+    snprintf(msg, sizeof(msg),
+             "this case needs %zu bytes of scratch; pf_solve_noalloc has %zu", off,
+             kNoAllocScratchBytes);
+    return set_error(PF_ERR_INVALID, msg);
+  }
+  void* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) return cuda_error(e, "looking up the scratch array");
+  auto at = [&](int q) -> void* {
+    return sizes[q] ? static_cast<void*>(static_cast<unsigned char*>(base) + offs[q]) : nullptr;
+  };
+  DevWork w{};
+  w.B = 1;
+  w.in_p_load = d_p_load;
+  w.in_q_load = d_q_load;
+  w.in_p_gen = d_p_gen;
+  w.out_vm = d_vmag;
+  w.out_va = d_vang;
+  w.out_info = d_info;
+  w.warm_vm = c->warm_vm;
+  w.warm_va = c->warm_va;
+  w.warm_V = c->warm_V;
+  w.warm_in = (o.warm_start && c->warm_valid) ? 1 : 0;
+  w.warm_out = 1;
+  w.spec = (double*)at(0);
+  w.vm = (double*)at(1);
+  w.va = (double*)at(2);
+  w.V = (double2*)at(3);
+  w.U = (double2*)at(4);
+  w.I = (double2*)at(5);
+  w.dV = (double2*)at(6);
+  w.abcd = (double*)at(7);
+  w.F = (double*)at(8);
+  w.dx = (double*)at(9);
+  w.r = (double*)at(10);
+  w.lu = at(11);
+  w.uinv = at(12);
+  w.y = at(13);
+  w.norm = (unsigned long long*)at(14);
+  w.step = (unsigned long long*)at(15);
+  w.flag = (int*)at(16);
+  // lanes per level, written through a small stack buffer (no heap)
+  DevSys sys = sb.view;
+  int8_t* g_fwd = (int8_t*)at(17);
+  int8_t* g_bwd = (int8_t*)at(18);
+  auto put_lanes = [&](const std::vector<int>& ptr, const std::vector<int>& longest, int8_t* dst) {
+    int8_t chunk[512];
+    const int nl = (int)ptr.size() - 1;
+    for (int l0 = 0; l0 < nl; l0 += 512) {
+      const int cnt = std::min(512, nl - l0);
+      for (int t = 0; t < cnt; ++t) {
+        const int l = l0 + t, width = ptr[l + 1] - ptr[l];
+        int want = 1;
+        while (want < 32 && want < longest[l]) want <<= 1;
+        while (want > 1 && (long long)want * width > threads) want >>= 1;
+        chunk[t] = (int8_t)want;
+      }
+      // a pageable source is staged before the call returns
+      cudaError_t e2 = cudaMemcpyAsync(dst + l0, chunk, cnt, cudaMemcpyHostToDevice, st);
+      if (e2 != cudaSuccess) return e2;
+    }
+    return cudaSuccess;
+  };
+  e = put_lanes(sy.flev_ptr, sy.flev_llen, g_fwd);
+  if (e == cudaSuccess) e = put_lanes(sy.blev_ptr, sy.blev_ulen, g_bwd);
+  if (e != cudaSuccess) return cuda_error(e, "writing the lane tables");
+  sys.g_fwd = g_fwd;
+  sys.g_bwd = g_bwd;
+  int solo = nflev;
+  while (solo > 0) {
+    const int l = solo - 1;
+    const int items = std::max(sy.fac_ptr[l + 1] - sy.fac_ptr[l], sy.tgt_ptr[l + 1] - sy.tgt_ptr[l]);
+    if (items > threads) break;
+    --solo;
+  }
+  sys.fac_solo_from = solo;
+  DevOpts d{};
+  d.tol = o.tol;
+  d.max_iter = o.max_iter;
+  d.refine = fp32 ? o.refine_steps : 0;
+  d.refine_below = o.refine_below;
+  d.S = 1;
+  d.mode = 0;
+  d.prof = nullptr;
+  d.m = 0;
+  d.max_lin = o.gmres_max_iter;
+  d.rtol = o.gmres_rtol;
+  d.y_in_smem = ((size_t)n * bs * tf <= 200 * 1024) ? 1 : 0;
+  e = launch_newton(bs, fp32, false, sys, w, d, cluster, cluster, threads, st);
+  if (e != cudaSuccess) return cuda_error(e, "launching the Newton kernel");
   return PF_OK;
 }
 

@@ -121,6 +121,7 @@ def lib():
                                          C.POINTER(pf_info)]),
             "pf_profile_solve": (C.c_int, [vp, C.POINTER(pf_opts), _dp, C.POINTER(pf_info)]),
             "pf_launch_config": (C.c_int, [vp, C.POINTER(pf_opts), C.c_int, _ip, _ip, _ip, _ip]),
+            "pf_solve_noalloc": (C.c_int, [vp, C.POINTER(pf_opts), vp, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -433,3 +434,13 @@ def pf_launch_config(c: CaseHandle, opts: pf_opts | None = None, B: int = 1) -> 
     _check(lib().pf_launch_config(c.handle, C.byref(opts) if opts else None, B,
                                   *[C.byref(x) for x in v]))
     return dict(zip(("grid", "cluster", "threads", "scen_per_cluster"), [x.value for x in v]))
+
+
+def pf_solve_noalloc(c: CaseHandle, opts, d_p_load, d_q_load, d_p_gen, d_vmag, d_vang, d_info,
+                     stream=0):
+    """Single Newton-Raphson solve whose workspace is the library's fixed
+    device array (no allocation); device pointers, asynchronous on stream."""
+    _check(lib().pf_solve_noalloc(
+        c.handle, C.byref(opts) if opts else None, _devptr(d_p_load), _devptr(d_q_load),
+        _devptr(d_p_gen), _devptr(d_vmag), _devptr(d_vang), _devptr(d_info),
+        C.c_void_p(stream)))
