@@ -1,14 +1,19 @@
 """Benchmark of the Newton power-flow hot path on one GB300 (or N replicas).
 
-A step is one converged Newton power-flow solve of the seeded 10,000-bus
-synthetic transmission grid (average degree 2.7, 20% PV buses) with Newton-
-Raphson, FP32 sparse-LU refactorisation and FP64 mismatch / refinement /
-update, to a mismatch of 1e-8 pu.  Every step solves a different seeded load
-scenario that is resident in HBM before the timed region; L2 is flushed
-between timed steps (the working set of one solve fits in L2).
+A step solves one batch of B = 608 seeded load scenarios of the 10,000-bus
+synthetic transmission grid (average degree 2.7, 20% PV buses; every bus load
+x lognormal(0, 0.2), PV generation rescaled to match) to a power mismatch of
+1e-8 pu with Newton-Raphson: FP32 sparse-LU refactorisation, FP64 mismatch,
+refinement and update, all scenarios in one persistent launch over the shared
+symbolic pattern (launch shape autotuned).  Inputs are resident in HBM before
+the timed region; each step has its own scenarios and L2 is flushed between
+timed steps.  Single-solve latency, the plain FP64 single-case solve, the
+Newton-Krylov solver, the three-phase feeder, the 2,000-bus x 512 batch and a
+serving stream are reported as variants.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on the host cores on the same workload instead.
+oracle on the host cores on a bounded sample of the same workload instead.
+Under torchrun each rank is an independent replica (no data collective).
 """
 from __future__ import annotations
 
@@ -27,7 +32,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "converged solves/sec at 1e-8 pu mismatch"
-WORKLOAD = "mesh10000 single-phase Newton-Raphson, FP32 LU + FP64 refinement"
+B_MAIN = 608
+WORKLOAD = (f"mesh10000 x {B_MAIN} load scenarios per step, batched Newton-Raphson, "
+            "FP32 LU + FP64 mismatch/refinement/update")
 
 
 def _peaks():
@@ -91,76 +98,90 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes_per_iteration(st, refine=1, s_f=4):
-    """Minimum bytes one mixed-precision NR iteration moves (single phase).
+def algorithmic_bytes_per_iteration(st, B=1, refine=1, s_f=4):
+    """Minimum bytes one mixed-precision NR iteration of one scenario moves.
 
-    mismatch: Ybus values + indices, row pointers, V, specified S, mismatch;
-    assembly: Jacobian values written once; factor: L+U values read and
-    written once; each triangular solve pass: L+U values + 3 vectors; each
-    refinement: Ybus + V + step for J dx, L+U again, 4 FP64 vectors; update:
-    |V|, angle, V.
+    Single phase, with the per-scenario share of the shared Ybus (values and
+    indices divided by B).  mismatch: Ybus + row pointers, V, specified S,
+    mismatch; assembly: Jacobian values written once; factor: L+U values
+    read and written once; each triangular-solve pass: L+U values and 3
+    vectors; each refinement: Ybus, V and step for J dx, L+U again, 4 FP64
+    vectors; update: |V|, angle, V.
     """
     n, nnz_y, N = st["n_bus"], st["nnz_y"], st["n_unknowns"]
     nnz_lu = st["nnz_lu"] * 4  # scalar values of the 2x2 blocks
-    nnz_j = (nnz_y - n) * 4 + n * 4  # Jacobian values on the Ybus pattern
-    a1 = nnz_y * (16 + 4) + 4 * (n + 1) + n * (16 + 16 + 16)
+    nnz_j = nnz_y * 4
+    ybus = nnz_y * (16 + 4) / B + 4 * (n + 1) / B
+    a1 = ybus + n * (16 + 16 + 16)
     a2 = nnz_j * s_f
     fac = nnz_lu * 2 * s_f
     solve = nnz_lu * s_f + 3 * N * s_f
-    ref = nnz_y * (16 + 4) + n * 16 * 2 + nnz_lu * s_f + 4 * N * 8
+    ref = ybus + n * 16 * 2 + nnz_lu * s_f + 4 * N * 8
     upd = n * (16 + 16 + 8)
     return a1 + a2 + fac + solve * (1 + refine) + ref * refine + upd
 
 
-def make_workload(K):
+def _case():
     from paper_1711_10579_gb300 import cases
 
-    case = cases.case_10000bus(0)
-    pl, ql, pg = cases.scenario_loads(case, K, seed=2024, sigma=0.05)
-    return case, pl, ql, pg
+    return cases.case_10000bus(0)
 
 
-def run_reference(args, rank, world):
-    """The FP64 CPU oracle, timed on host cores on the same workload."""
+def _batch(case, B, seed):
+    from paper_1711_10579_gb300 import cases
+
+    return cases.scenario_loads(case, B, seed=seed, sigma=0.2)
+
+
+# ----------------------------------------------------------------------------
+# the reference arm: the FP64 CPU oracle
+# ----------------------------------------------------------------------------
+
+def run_reference(args, rank, world, per_step=4):
+    """The oracle as it stands, timed on host cores on the same workload."""
     if rank != 0:
         return
     from oracle import pf_oracle as O
 
-    case, pl, ql, pg = make_workload(args.warmup + args.steps)
+    case = _case()
     Y = O.ybus_single(case)
     times, iters = [], []
     for k in range(args.warmup + args.steps):
+        pl, ql, pg = _batch(case, per_step, seed=1000 + k)
         t0 = time.perf_counter()
-        r = O.newton_polar(case.with_loads(pl[k], ql[k], pg[k]), Y=Y)
-        dt = time.perf_counter() - t0
-        assert r["converged"]
+        for b in range(per_step):
+            r = O.newton_polar(case.with_loads(pl[b], ql[b], pg[b]), Y=Y)
+            assert r["converged"]
+            if k >= args.warmup:
+                iters.append(r["iterations"])
         if k >= args.warmup:
-            times.append(dt)
-            iters.append(r["iterations"])
+            times.append(time.perf_counter() - t0)
     tot = sum(times)
-    val = args.steps / tot
+    val = args.steps * per_step / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " (oracle: FP64 polar NR, SuperLU/COLAMD)",
-                   "n_bus": case.n_bus, "n_branch": case.n_branch},
+        "config": {"workload": WORKLOAD + "; reference: FP64 CPU oracle (polar NR, "
+                   "SuperLU/COLAMD), one thread", "n_bus": case.n_bus, "n_branch": case.n_branch},
         "ms_per_newton_iter": 1e3 * tot / sum(iters),
         "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} solves of the 10,000-bus grid, one thread"},
+                         "sample": f"{per_step} scenarios of each step's batch per step, "
+                                   f"{args.steps} steps, one thread"},
         "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(seconds=12.0):
+def cpu_baseline(seconds=10.0):
     """The oracle as it stands on a bounded sample of the same workload."""
     from oracle import pf_oracle as O
 
-    case, pl, ql, pg = make_workload(64)
+    case = _case()
     Y = O.ybus_single(case)
+    pl, ql, pg = _batch(case, 64, seed=77)
     t0 = time.perf_counter()
     k = 0
     while k < 64 and (time.perf_counter() - t0) < seconds:
@@ -169,14 +190,151 @@ def cpu_baseline(seconds=12.0):
         k += 1
     dt = time.perf_counter() - t0
     return {"value": k / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{k} solves of the 10,000-bus grid in {dt:.1f} s, one thread"}
+            "sample": f"{k} scenarios of the 10,000-bus grid in {dt:.1f} s, one thread"}
 
+
+# ----------------------------------------------------------------------------
+# variants
+# ----------------------------------------------------------------------------
+
+def _device_solves(pf, c, torch, dev, B, pl, ql, pg, opts, reps=5, flush=None):
+    d = [None if a is None else torch.tensor(a, device=dev) for a in (pl, ql, pg)]
+    slots = pl.shape[1]
+    vm = torch.zeros((B, slots), dtype=torch.float64, device=dev)
+    va = torch.zeros_like(vm)
+    info = torch.zeros((B, pf.INFO_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream(dev)
+    times = []
+    for r in range(reps + 2):
+        if flush is not None:
+            flush.fill_(r & 255)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        pf.pf_solve_batch_device(c, B, d[0], d[1], d[2], opts, vm, va, info, s.cuda_stream)
+        e1.record(s)
+        torch.cuda.synchronize()
+        if r >= 2:
+            times.append(e0.elapsed_time(e1))
+    inf = np.frombuffer(info.cpu().numpy().tobytes(), dtype=pf.INFO_DTYPE)
+    ms = float(np.median(times))
+    ok = int((inf["status"] == 0).sum())
+    its = float(inf["iterations"].mean())
+    return {"solves_per_s": ok / (ms * 1e-3), "ms_per_launch": ms,
+            "latency_ms": {"p50": float(np.percentile(times, 50)),
+                           "p99": float(np.percentile(times, 99))},
+            "ms_per_newton_iter": ms / max(1.0, its), "newton_iters_mean": its,
+            "linear_iters_mean": float(inf["linear_iterations"].mean()),
+            "all_converged": bool(ok == B), "B": B}
+
+
+def variants(pf, ctx, torch, dev, flush):
+    from paper_1711_10579_gb300 import cases
+
+    out = {}
+    case = _case()
+    c = pf.pf_create_case(ctx, case)
+    pl, ql, pg = _batch(case, 1, seed=7)
+    out["mesh10000_single_nr_mixed"] = _device_solves(
+        pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_MIXED), reps=20, flush=flush)
+    out["mesh10000_single_nr_mixed"]["launch"] = pf.pf_launch_config(c, pf.make_opts())
+    prof, _ = pf.pf_profile_solve(c, pf.make_opts())
+    out["mesh10000_single_nr_mixed"]["phase_us"] = {k: round(v, 1) for k, v in prof.items()}
+    out["mesh10000_single_nr_fp64"] = _device_solves(
+        pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_FP64), reps=20, flush=flush)
+    for prec, nm in ((pf.PF_MIXED, "mixed"), (pf.PF_FP64, "fp64")):
+        out[f"mesh10000_single_nk_{nm}"] = _device_solves(
+            pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(method=pf.PF_NK, precision=prec),
+            reps=1)
+    pf.pf_destroy_case(c)
+
+    case = cases.case_2000bus(0)
+    c = pf.pf_create_case(ctx, case)
+    pl, ql, pg = cases.scenario_loads(case, 512, seed=11)
+    tuned = pf.pf_autotune(c, 512, pf.make_opts())
+    out["mesh2000_x512_batched_mixed"] = _device_solves(pf, c, torch, dev, 512, pl, ql, pg,
+                                                        pf.make_opts(), flush=flush)
+    out["mesh2000_x512_batched_mixed"]["tuned"] = {"scen_per_cta": tuned.scen_per_cta,
+                                                   "block_threads": tuned.block_threads}
+    pf.pf_destroy_case(c)
+
+    case = cases.case_feeder8000(0)
+    c = pf.pf_create_case(ctx, case)
+    pl3, ql3 = cases.feeder_scenario_loads(case, 1, seed=3, sigma=0.05)
+    for prec, nm in ((pf.PF_FP64, "fp64"), (pf.PF_MIXED, "mixed")):
+        out[f"feeder8000_cim_{nm}"] = _device_solves(
+            pf, c, torch, dev, 1, pl3.reshape(1, -1), ql3.reshape(1, -1), None,
+            pf.make_opts(precision=prec), reps=10, flush=flush)
+    pf.pf_destroy_case(c)
+    out["serving"] = serving_stream(pf, ctx)
+    return out
+
+
+def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9):
+    """Poisson arrivals, 70% transmission (500-70,000 buses) / 30% feeders
+    (1,000-20,000 nodes) from pools of resident cases, mixed precision."""
+    from paper_1711_10579_gb300 import cases
+
+    t_setup = time.perf_counter()
+    pools = {"transmission": cases.topology_pool("transmission", 6, seed, 500, 70_000),
+             "feeder": cases.topology_pool("feeder", 3, seed + 1, 1_000, 20_000)}
+    handles, loads = {}, {}
+    for kind, pool in pools.items():
+        for i, case in enumerate(pool):
+            handles[(kind, i)] = pf.pf_create_case(ctx, case)
+            if kind == "transmission":
+                pl, ql, pg = cases.scenario_loads(case, 4, seed=i, sigma=0.2)
+                loads[(kind, i)] = [(pl[k], ql[k], pg[k]) for k in range(4)]
+            else:
+                pl, ql = cases.feeder_scenario_loads(case, 4, seed=i, sigma=0.2)
+                loads[(kind, i)] = [(pl[k].reshape(-1), ql[k].reshape(-1), None) for k in range(4)]
+    setup_s = time.perf_counter() - t_setup
+    reqs = cases.serving_stream(seed, rate=rate, duration=duration,
+                                pool_size=1)  # kinds and load seeds; topology below
+    rng = np.random.default_rng(seed)
+    opts = pf.make_opts(warm_start=1)
+    pending, lat, statuses = {}, [], []
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while k < len(reqs) and reqs[k].t_arrive <= now:
+            r = reqs[k]
+            key = (r.kind, int(rng.integers(0, len(pools[r.kind]))))
+            pl, ql, pg = loads[key][r.load_seed % 4]
+            t = pf.pf_submit(ctx, handles[key], pl, ql, pg, opts)
+            pending[t] = (r.t_arrive, handles[key].slots)
+            k += 1
+        for t in list(pending):
+            res = pf.pf_poll(ctx, t, pending[t][1])
+            if res is not None:
+                lat.append(time.perf_counter() - t0 - pending[t][0])
+                statuses.append(res[2]["status"])
+                del pending[t]
+        if k < len(reqs):
+            time.sleep(max(0.0, min(0.0005, reqs[k].t_arrive - (time.perf_counter() - t0))))
+    span = time.perf_counter() - t0
+    for h in handles.values():
+        pf.pf_destroy_case(h)
+    lat_ms = np.array(lat) * 1e3
+    return {"offered_req_per_s": rate, "requests": len(reqs), "seconds": span,
+            "solves_per_s": sum(1 for s in statuses if s == 0) / span,
+            "converged": int(sum(1 for s in statuses if s == 0)),
+            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                           "p99": float(np.percentile(lat_ms, 99))},
+            "pool": {"transmission_buses": [p.n_bus for p in pools["transmission"]],
+                     "feeder_nodes": [p.n_node for p in pools["feeder"]]},
+            "setup_s": setup_s}
+
+
+# ----------------------------------------------------------------------------
+# main
+# ----------------------------------------------------------------------------
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -192,6 +350,8 @@ def main():
 
     import torch
 
+    from paper_1711_10579_gb300 import replicas
+
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -203,33 +363,32 @@ def main():
 
     import __graft_entry__
 
-    if rank == 0 or world == 1:
+    if rank == 0:
         __graft_entry__.build()
     if dist:
         dist.barrier()
     __graft_entry__.build()
     from paper_1711_10579_gb300 import pf
 
-    K, W = args.steps, args.warmup
-    case, pl, ql, pg = make_workload(W + K)
+    K, W, B = args.steps, args.warmup, B_MAIN
+    case = _case()
+    n = case.n_bus
     ctx = pf.pf_ctx_create(local)
     c = pf.pf_create_case(ctx, case)
     st = pf.pf_case_get_stats(c)
-    opts = pf.make_opts(precision=pf.PF_MIXED)
-    n = case.n_bus
-    d_pl = torch.tensor(pl, device=dev)
-    d_ql = torch.tensor(ql, device=dev)
-    d_pg = torch.tensor(pg, device=dev)
-    d_vm = torch.zeros((W + K, n), dtype=torch.float64, device=dev)
+    opts = pf.pf_autotune(c, B, pf.make_opts(precision=pf.PF_MIXED))
+    batches = [_batch(case, B, replicas.scenario_seed(1000 + k, rank)) for k in range(W + K)]
+    d_in = [[torch.tensor(a, device=dev) for a in bt] for bt in batches]
+    d_vm = torch.zeros((B, n), dtype=torch.float64, device=dev)
     d_va = torch.zeros_like(d_vm)
-    d_info = torch.zeros((W + K, pf.INFO_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    d_info = torch.zeros((W + K, B, pf.INFO_DTYPE.itemsize), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2
     stream = torch.cuda.current_stream(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(W + K)]
 
     def step(k):
-        pf.pf_solve_batch_device(c, 1, d_pl[k], d_ql[k], d_pg[k], opts, d_vm[k], d_va[k],
+        pf.pf_solve_batch_device(c, B, d_in[k][0], d_in[k][1], d_in[k][2], opts, d_vm, d_va,
                                  d_info[k], stream.cuda_stream)
 
     for k in range(W):
@@ -253,56 +412,47 @@ def main():
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     ms = np.array([ev[k][0].elapsed_time(ev[k][1]) for k in range(W, W + K)])
-    info = np.frombuffer(d_info.cpu().numpy().tobytes(), dtype=pf.INFO_DTYPE)
-    ok = info["status"][W:] == 0
-    iters = info["iterations"][W:]
-    total_ms = float(ms.sum())
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    converged = int(ok.sum())
-    value = world * converged / (total_ms * 1e-3)
+    info = np.frombuffer(d_info[W:].cpu().numpy().tobytes(), dtype=pf.INFO_DTYPE)
+    converged = int((info["status"] == 0).sum())
+    value, max_ms, total = replicas.aggregate(float(ms.sum()), converged, dist)
 
-    # roofline of the (only) kernel: one persistent launch per solve
-    bytes_iter = algorithmic_bytes_per_iteration(st)
-    per_launch = bytes_iter * float(iters.mean())
+    # roofline of the (only) kernel: one persistent launch per step
+    bytes_iter = algorithmic_bytes_per_iteration(st, B=B)
+    per_launch = bytes_iter * float(info["iterations"].sum()) / K
     achieved = per_launch / (float(ms.mean()) * 1e-3) / 1e9
     peak, peak_kind = _peaks()
 
-    # end to end through the host-buffer entry point
+    # end to end through the host-buffer entry point (copies inside)
     e2e_t = []
-    for k in range(min(K, 20)):
+    for k in range(W, min(W + 5, W + K)):
         t0 = time.perf_counter()
-        pf.pf_solve_batch(c, pl[W + k:W + k + 1], ql[W + k:W + k + 1], pg[W + k:W + k + 1], opts)
+        pf.pf_solve_batch(c, batches[k][0], batches[k][1], batches[k][2], opts)
         e2e_t.append(time.perf_counter() - t0)
-    e2e = {"value": len(e2e_t) / sum(e2e_t), "unit": "solves/s",
-           "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 2 * n * 8 + pf.INFO_DTYPE.itemsize}
+    e2e = {"value": B * len(e2e_t) / sum(e2e_t), "unit": "solves/s",
+           "h2d_bytes_per_step": 3 * B * n * 8,
+           "d2h_bytes_per_step": 2 * B * n * 8 + B * pf.INFO_DTYPE.itemsize}
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": float(ms.mean()), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_bus": n, "n_branch": case.n_branch,
-                   "nnz_lu_blocks": st["nnz_lu"], "levels": st["levels_factor"],
-                   "l2": "flushed between timed steps (256 MB write)",
+                   "scenarios_per_step": B, "nnz_lu_blocks": st["nnz_lu"],
+                   "levels": st["levels_factor"],
+                   "launch": pf.pf_launch_config(c, opts, B),
+                   "l2": "flushed between timed steps (256 MB write); inputs exceed L2",
                    "parallelism": f"replicas x{world}"},
-        "ms_per_newton_iter": float(ms.mean() / iters.mean()),
-        "newton_iters_mean": float(iters.mean()),
-        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
-        "converged": converged,
+        "ms_per_newton_iter": float(ms.mean() / info["iterations"].reshape(K, B).max(1).mean()),
+        "newton_iters_mean": float(info["iterations"].mean()),
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                       "note": "per batch step; single-solve latency in variants"},
+        "converged": total, "solves": world * B * K,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_source": peak_kind,
-                     "note": "single 10,000-bus solve: L2-resident, level-latency bound"},
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind},
         "e2e": e2e, "gpu_launches": K, "clocks": clk, "wall_s": t_wall,
     }
-
-    if rank == 0:
-        prof, pinfo = pf.pf_profile_solve(c, opts)
-        line["phase_us_one_solve"] = {k: round(v, 1) for k, v in prof.items()}
-    if not args.no_variants and rank == 0:
-        line["variants"] = variants(pf, ctx, torch, dev)
+    if rank == 0 and not args.no_variants:
+        line["variants"] = variants(pf, ctx, torch, dev, flush)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -311,56 +461,6 @@ def main():
     pf.pf_ctx_destroy(ctx)
     if dist:
         dist.destroy_process_group()
-
-
-def _time_solves(pf, c, torch, dev, B, pl, ql, pg, opts, reps=5):
-    d = [None if a is None else torch.tensor(a, device=dev) for a in (pl, ql, pg)]
-    slots = pl.shape[1] if pl is not None else c.slots
-    vm = torch.zeros((B, slots), dtype=torch.float64, device=dev)
-    va = torch.zeros_like(vm)
-    info = torch.zeros((B, pf.INFO_DTYPE.itemsize), dtype=torch.uint8, device=dev)
-    s = torch.cuda.current_stream(dev)
-    times = []
-    for r in range(reps + 2):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        pf.pf_solve_batch_device(c, B, d[0], d[1], d[2], opts, vm, va, info, s.cuda_stream)
-        e1.record(s)
-        torch.cuda.synchronize()
-        if r >= 2:
-            times.append(e0.elapsed_time(e1))
-    inf = np.frombuffer(info.cpu().numpy().tobytes(), dtype=pf.INFO_DTYPE)
-    ms = float(np.median(times))
-    return {"solves_per_s": int((inf["status"] == 0).sum()) / (ms * 1e-3), "ms_per_launch": ms,
-            "ms_per_newton_iter": ms / max(1.0, float(inf["iterations"].max())),
-            "iterations": int(inf["iterations"].max()), "all_converged": bool((inf["status"] == 0).all())}
-
-
-def variants(pf, ctx, torch, dev):
-    from paper_1711_10579_gb300 import cases
-
-    out = {}
-    case = cases.case_10000bus(0)
-    c = pf.pf_create_case(ctx, case)
-    pl, ql, pg = cases.scenario_loads(case, 1, seed=7, sigma=0.05)
-    out["mesh10000_nr_fp64"] = _time_solves(pf, c, torch, dev, 1, pl, ql, pg,
-                                            pf.make_opts(precision=pf.PF_FP64))
-    pf.pf_destroy_case(c)
-    case = cases.case_2000bus(0)
-    c = pf.pf_create_case(ctx, case)
-    pl, ql, pg = cases.scenario_loads(case, 512, seed=11)
-    out["mesh2000_x512_batched_mixed"] = _time_solves(pf, c, torch, dev, 512, pl, ql, pg,
-                                                      pf.make_opts())
-    pf.pf_destroy_case(c)
-    case = cases.case_feeder8000(0)
-    c = pf.pf_create_case(ctx, case)
-    pl3, ql3 = cases.feeder_scenario_loads(case, 1, seed=3, sigma=0.05)
-    for prec, nm in ((pf.PF_FP64, "fp64"), (pf.PF_MIXED, "mixed")):
-        out[f"feeder8000_cim_{nm}"] = _time_solves(
-            pf, c, torch, dev, 1, pl3.reshape(1, -1), ql3.reshape(1, -1), None,
-            pf.make_opts(precision=prec))
-    pf.pf_destroy_case(c)
-    return out
 
 
 if __name__ == "__main__":

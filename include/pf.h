@@ -324,6 +324,18 @@ int pf_solve_noalloc(pf_case c, const pf_opts* opts, const double* d_p_load,
                      double* d_vang, pf_info* d_info, void* stream);
 
 /*
+ * Autotuner for batched solves (B >= 2): runs B copies of the case's own
+ * scenario with each candidate launch shape (scenarios per CTA 1, 2, 4, 8;
+ * threads per CTA 128, 256, 512), times them with CUDA events and stores the
+ * fastest in the case for (B, method, precision).  Later batch solves of
+ * that B with scen_per_cta == 0 and block_threads == 0 use it; *opts
+ * (in: method, precision; out: the chosen shape) may be passed back.
+ * Without tuning, a batch uses about one CTA per SM (at most 8 scenarios per
+ * CTA).  Blocking; allocates the batch workspace.
+ */
+int pf_autotune(pf_case c, int B, pf_opts* opts);
+
+/*
  * Launch shape a solve of B scenarios with these options would use:
  * grid CTAs, CTAs per cluster, threads per CTA, scenarios per cluster.
  */

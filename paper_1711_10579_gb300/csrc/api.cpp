@@ -603,6 +603,12 @@ int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag, const dou
   return inspect(c, InspectKind::Step, &o, vmag, vang, dx, info);
 }
 
+int pf_autotune(pf_case c, int B, pf_opts* opts) {
+  if (!c || !opts) return set_error(PF_ERR_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(c->mu);
+  return autotune(c, B, opts);
+}
+
 int pf_launch_config(pf_case c, const pf_opts* opts, int B, int* grid, int* cluster,
                      int* threads, int* scen) {
   if (!c || B < 1 || !grid || !cluster || !threads || !scen)

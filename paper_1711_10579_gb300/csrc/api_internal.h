@@ -83,6 +83,9 @@ struct pf_case_s {
   double2* warm_V = nullptr;
   bool warm_valid = false;
   std::mutex mu;
+  // autotuned batch shapes: (B, method, precision) -> (scenarios per CTA, threads)
+  std::map<std::array<int, 3>, std::array<int, 2>> tuned;
+  std::mutex tuned_mu;
 };
 
 namespace pf {
@@ -100,6 +103,7 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load,
 void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int* cluster,
                   int* threads, int* S);
 int profile_solve(pf_case c, const pf_opts& o, double* phase_us, pf_info* info);
+int autotune(pf_case c, int B, pf_opts* o);
 // Copies staged results of the last run_solve on ws to host arrays.
 int fetch_results(pf_case c, Workspace* ws, int B, double* vmag, double* vang,
                   pf_info* info, cudaStream_t st);

@@ -77,9 +77,23 @@ void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int*
     *S = 1;
     *grid = *cluster;
   } else {
-    *threads = o.block_threads ? std::min(o.block_threads, max_threads) : 256;
+    int tS = 0, tth = 0;
+    if (!o.scen_per_cta && !o.block_threads) {
+      std::lock_guard<std::mutex> lk(c->tuned_mu);
+      auto it = c->tuned.find({B, o.method, o.precision});
+      if (it != c->tuned.end()) {
+        tS = it->second[0];
+        tth = it->second[1];
+      }
+    }
+    // default: about one CTA per SM, up to 8 scenarios per CTA
+    int dS = 1;
+    while (dS < 8 && (long long)B >= 2LL * dS * c->ctx->num_sms) dS <<= 1;
+    if (o.method == PF_NK) dS = std::min(dS, 8);
+    *threads = o.block_threads ? std::min(o.block_threads, max_threads)
+                               : (tth ? tth : max_threads);
     *cluster = 1;
-    *S = o.scen_per_cta ? o.scen_per_cta : (o.method == PF_NK ? 4 : 2);
+    *S = o.scen_per_cta ? o.scen_per_cta : (tS ? tS : dS);
     *grid = (B + *S - 1) / *S;
   }
 }
@@ -360,6 +374,61 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   d.y_in_smem = ((size_t)n * bs * tf <= 200 * 1024) ? 1 : 0;
   e = launch_newton(bs, fp32, false, sys, w, d, cluster, cluster, threads, st);
   if (e != cudaSuccess) return cuda_error(e, "launching the Newton kernel");
+  return PF_OK;
+}
+
+int autotune(pf_case c, int B, pf_opts* io) {
+  if (B < 2) return set_error(PF_ERR_INVALID, "autotuning is for batches (B >= 2)");
+  pf_opts o = *io;
+  int rc = check_opts(o);
+  if (rc != PF_OK) return rc;
+  cudaSetDevice(c->ctx->device);
+  cudaStream_t st = c->ctx->stream;
+  Workspace* ws = &c->wsB;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_error(e, "creating timing events");
+  const int max_threads = (c->bs == 2 && o.method != PF_NK) ? 512 : 256;
+  float best = 1e30f;
+  int bestS = 0, bestT = 0;
+  for (int S : {1, 2, 4, 8}) {
+    for (int T : {128, 256, 512}) {
+      if (T > max_threads) continue;
+      pf_opts t = o;
+      t.scen_per_cta = S;
+      t.block_threads = T;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2 && rc == PF_OK; ++rep) {
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess)
+          rc = run_solve(c, t, B, nullptr, nullptr, nullptr, ws, st, RunMode::Solve, nullptr,
+                         nullptr);
+        if (rc == PF_OK && e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (rc == PF_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float x = 0;
+        if (rc == PF_OK && e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+        if (e != cudaSuccess) rc = cuda_error(e, "timing a candidate shape");
+        if (rep > 0) ms = x;  // the first run warms up
+      }
+      if (rc != PF_OK) break;
+      if (ms < best) {
+        best = ms;
+        bestS = S;
+        bestT = T;
+      }
+    }
+    if (rc != PF_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PF_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(c->tuned_mu);
+    c->tuned[{B, o.method, o.precision}] = {bestS, bestT};
+  }
+  io->scen_per_cta = bestS;
+  io->block_threads = bestT;
   return PF_OK;
 }
 

@@ -122,6 +122,7 @@ def lib():
             "pf_profile_solve": (C.c_int, [vp, C.POINTER(pf_opts), _dp, C.POINTER(pf_info)]),
             "pf_launch_config": (C.c_int, [vp, C.POINTER(pf_opts), C.c_int, _ip, _ip, _ip, _ip]),
             "pf_solve_noalloc": (C.c_int, [vp, C.POINTER(pf_opts), vp, vp, vp, vp, vp, vp, vp]),
+            "pf_autotune": (C.c_int, [vp, C.c_int, C.POINTER(pf_opts)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -444,3 +445,10 @@ def pf_solve_noalloc(c: CaseHandle, opts, d_p_load, d_q_load, d_p_gen, d_vmag, d
         c.handle, C.byref(opts) if opts else None, _devptr(d_p_load), _devptr(d_q_load),
         _devptr(d_p_gen), _devptr(d_vmag), _devptr(d_vang), _devptr(d_info),
         C.c_void_p(stream)))
+
+
+def pf_autotune(c: CaseHandle, B: int, opts: pf_opts | None = None) -> pf_opts:
+    """Time candidate batch launch shapes; the case keeps the fastest for B."""
+    o = opts if opts is not None else make_opts()
+    _check(lib().pf_autotune(c.handle, B, C.byref(o)))
+    return o
