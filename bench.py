@@ -271,7 +271,10 @@ def variants(pf, ctx, torch, dev, flush):
 
 def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9):
     """Poisson arrivals, 70% transmission (500-70,000 buses) / 30% feeders
-    (1,000-20,000 nodes) from pools of resident cases, mixed precision."""
+    (1,000-20,000 nodes) from pools of resident cases, mixed precision with
+    warm starts.  The offered rate runs first; if it exceeds capacity the
+    sustained rate is reported and a second stream at 70% of it gives the
+    latency percentiles."""
     from paper_1711_10579_gb300 import cases
 
     t_setup = time.perf_counter()
@@ -288,42 +291,57 @@ def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9):
                 pl, ql = cases.feeder_scenario_loads(case, 4, seed=i, sigma=0.2)
                 loads[(kind, i)] = [(pl[k].reshape(-1), ql[k].reshape(-1), None) for k in range(4)]
     setup_s = time.perf_counter() - t_setup
-    reqs = cases.serving_stream(seed, rate=rate, duration=duration,
-                                pool_size=1)  # kinds and load seeds; topology below
-    rng = np.random.default_rng(seed)
     opts = pf.make_opts(warm_start=1)
-    pending, lat, statuses = {}, [], []
-    t0 = time.perf_counter()
-    k = 0
-    while k < len(reqs) or pending:
-        now = time.perf_counter() - t0
-        while k < len(reqs) and reqs[k].t_arrive <= now:
-            r = reqs[k]
-            key = (r.kind, int(rng.integers(0, len(pools[r.kind]))))
-            pl, ql, pg = loads[key][r.load_seed % 4]
-            t = pf.pf_submit(ctx, handles[key], pl, ql, pg, opts)
-            pending[t] = (r.t_arrive, handles[key].slots)
-            k += 1
-        for t in list(pending):
-            res = pf.pf_poll(ctx, t, pending[t][1])
-            if res is not None:
-                lat.append(time.perf_counter() - t0 - pending[t][0])
-                statuses.append(res[2]["status"])
-                del pending[t]
-        if k < len(reqs):
-            time.sleep(max(0.0, min(0.0005, reqs[k].t_arrive - (time.perf_counter() - t0))))
-    span = time.perf_counter() - t0
+
+    def run(rate_, seed_):
+        reqs = cases.serving_stream(seed_, rate=rate_, duration=duration, pool_size=1)
+        rng = np.random.default_rng(seed_)
+        pending, lat, statuses, done_t = [], [], [], []
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while k < len(reqs) and reqs[k].t_arrive <= now:
+                r = reqs[k]
+                key = (r.kind, int(rng.integers(0, len(pools[r.kind]))))
+                pl, ql, pg = loads[key][r.load_seed % 4]
+                t = pf.pf_submit(ctx, handles[key], pl, ql, pg, opts)
+                pending.append((t, r.t_arrive, handles[key].slots))
+                k += 1
+            still = []
+            for j, (t, ta, sl) in enumerate(pending):
+                if j >= 64:  # completions come roughly in submission order
+                    still.extend(pending[j:])
+                    break
+                res = pf.pf_poll(ctx, t, sl)
+                if res is None:
+                    still.append((t, ta, sl))
+                else:
+                    tn = time.perf_counter() - t0
+                    lat.append(tn - ta)
+                    done_t.append(tn)
+                    statuses.append(res[2]["status"])
+            pending = still
+            if k < len(reqs) and not pending:
+                time.sleep(max(0.0, min(0.0005, reqs[k].t_arrive - (time.perf_counter() - t0))))
+        span = time.perf_counter() - t0
+        lat_ms = np.array(lat) * 1e3
+        ok = sum(1 for s_ in statuses if s_ == 0)
+        return {"offered_req_per_s": rate_, "requests": len(reqs), "seconds": span,
+                "solves_per_s": ok / span, "converged": ok,
+                "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                               "p99": float(np.percentile(lat_ms, 99))}}
+
+    first = run(rate, seed)
+    out = {"offered": first}
+    if first["solves_per_s"] < 0.9 * rate:
+        out["at_70pct_of_sustained"] = run(0.7 * first["solves_per_s"], seed + 100)
     for h in handles.values():
         pf.pf_destroy_case(h)
-    lat_ms = np.array(lat) * 1e3
-    return {"offered_req_per_s": rate, "requests": len(reqs), "seconds": span,
-            "solves_per_s": sum(1 for s in statuses if s == 0) / span,
-            "converged": int(sum(1 for s in statuses if s == 0)),
-            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
-                           "p99": float(np.percentile(lat_ms, 99))},
-            "pool": {"transmission_buses": [p.n_bus for p in pools["transmission"]],
-                     "feeder_nodes": [p.n_node for p in pools["feeder"]]},
-            "setup_s": setup_s}
+    out["pool"] = {"transmission_buses": [p.n_bus for p in pools["transmission"]],
+                   "feeder_nodes": [p.n_node for p in pools["feeder"]]}
+    out["setup_s"] = setup_s
+    return out
 
 
 # ----------------------------------------------------------------------------

@@ -215,7 +215,7 @@ def _dc_angle_spread(n, f, t, x, p_net):
 
 def transmission_case(n: int, m: int, n_pv: int, seed: int,
                       name: str = "", pv_share: float = 1.05,
-                      max_angle: float = 0.4) -> SinglePhaseCase:
+                      max_angle: float = 0.3) -> SinglePhaseCase:
     """Meshed single-phase grid with the distributions of the 14-bus case.
 
     r ~ U[0.002, 0.02], x = r * U[5, 15], b ~ U[0, 0.05]; bus 0 is the slack
@@ -228,6 +228,10 @@ def transmission_case(n: int, m: int, n_pv: int, seed: int,
     generation are scaled by one factor s <= 1 chosen so that a linear (DC)
     estimate of the largest angle across a branch is at most ``max_angle``
     radians; s is recorded in ``load_scale`` (it is 1 for the 14-bus case).
+    Line charging is capped so that its total (at 1 pu) does not exceed the
+    total reactive load: on a lightly loaded large grid the drawn charging
+    lifts voltages (1.3 pu and more) beyond the reach of a flat-start Newton
+    iteration, while normally loaded grids (the 14-bus case) keep it as drawn.
     """
     rng = np.random.default_rng(seed)
     edges, _ = mesh_topology(n, m, rng)
@@ -252,11 +256,12 @@ def transmission_case(n: int, m: int, n_pv: int, seed: int,
     zipf[:, 0] = 1.0
     spread = _dc_angle_spread(n, edges[:, 0], edges[:, 1], x, p_gen - p_load)
     scale = min(1.0, max_angle / spread) if spread > 0 else 1.0
+    b_scale = min(1.0, scale * q_load.sum() / b.sum()) if b.sum() > 0 else 1.0
     return SinglePhaseCase(
         n_bus=n, bus_type=bus_type, v_set=v_set, p_gen=p_gen * scale,
         q_gen=np.zeros(n), p_load=p_load * scale, q_load=q_load * scale,
         zip=zipf, br_from=edges[:, 0].copy(), br_to=edges[:, 1].copy(),
-        br_r=r, br_x=x, br_b=b, name=name or f"mesh{n}", seed=seed,
+        br_r=r, br_x=x, br_b=b * b_scale, name=name or f"mesh{n}", seed=seed,
         load_scale=scale)
 
 

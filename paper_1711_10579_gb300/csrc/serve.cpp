@@ -48,7 +48,9 @@ struct Request {
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
-  Workspace ws;
+  // one workspace per case kind, so alternating single- and three-phase
+  // requests do not reallocate (cudaFree would synchronise the device)
+  Workspace ws1ph, ws3ph;
   Request* req = nullptr;
   double* h_in = nullptr;  // pinned: p_load, q_load, p_gen (3 * cap)
   double* h_out = nullptr; // pinned: vm, va (2 * cap)
@@ -97,12 +99,13 @@ struct Server {
       cudaError_t e = cudaMallocHost(&s.h_info, sizeof(pf_info));
       if (e != cudaSuccess) return cuda_error(e, "allocating pinned staging");
     }
-    int rc = s.ws.ensure(c->data.kind, c->data.n,
-                         std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), 1,
-                         r->o.method == PF_NK ? r->o.gmres_restart : 0);
+    Workspace& ws = (c->data.kind == PF_SINGLE_PHASE) ? s.ws1ph : s.ws3ph;
+    int rc = ws.ensure(c->data.kind, c->data.n,
+                       std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), 1,
+                       r->o.method == PF_NK ? r->o.gmres_restart : 0);
     if (rc != PF_OK) return rc;
     const double* d_in[3] = {nullptr, nullptr, nullptr};
-    double* dst[3] = {s.ws.st_p_load, s.ws.st_q_load, s.ws.st_p_gen};
+    double* dst[3] = {ws.st_p_load, ws.st_q_load, ws.st_p_gen};
     const std::vector<double>* src[3] = {&r->p_load, &r->q_load, &r->p_gen};
     for (int k = 0; k < 3; ++k) {
       if (src[k]->empty()) continue;
@@ -114,16 +117,18 @@ struct Server {
     }
     pf_opts o = r->o;
     if (!c->warm_valid) o.warm_start = 0;
-    rc = run_solve(c, o, 1, d_in[0], d_in[1], d_in[2], &s.ws, s.st, RunMode::Solve, nullptr,
+    // served solves run on 8-CTA clusters so that every slot fits on the GPU
+    if (!o.cluster_size) o.cluster_size = 8;
+    rc = run_solve(c, o, 1, d_in[0], d_in[1], d_in[2], &ws, s.st, RunMode::Solve, nullptr,
                    nullptr);
     if (rc != PF_OK) return rc;
-    cudaError_t e = cudaMemcpyAsync(s.h_out, s.ws.st_vm, per * sizeof(double),
+    cudaError_t e = cudaMemcpyAsync(s.h_out, ws.st_vm, per * sizeof(double),
                                     cudaMemcpyDeviceToHost, s.st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s.h_out + per, s.ws.st_va, per * sizeof(double),
+      e = cudaMemcpyAsync(s.h_out + per, ws.st_va, per * sizeof(double),
                           cudaMemcpyDeviceToHost, s.st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s.h_info, s.ws.st_info, sizeof(pf_info), cudaMemcpyDeviceToHost, s.st);
+      e = cudaMemcpyAsync(s.h_info, ws.st_info, sizeof(pf_info), cudaMemcpyDeviceToHost, s.st);
     if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
     if (e != cudaSuccess) return cuda_error(e, "launching a served solve");
     r->state = 1;
