@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "converged solves/sec at 1e-8 pu mismatch"
 B_MAIN = 608
+# DRAM traffic of one launch of the main step, from the ncu capture summarised
+# in profiles/newton_kernel_mesh10000x608.md; valid only for the kernel source
+# it was measured on (sha256 prefix of csrc/newton.cu).
+NCU_TRAFFIC = {"newton_cu_sha256": "1be08630aaa74824", "bytes_per_launch": 26.28e9}
 WORKLOAD = (f"mesh10000 x {B_MAIN} load scenarios per step, batched Newton-Raphson, "
             "FP32 LU + FP64 mismatch/refinement/update")
 
@@ -119,6 +123,15 @@ def algorithmic_bytes_per_iteration(st, B=1, refine=1, s_f=4):
     ref = ybus + n * 16 * 2 + nnz_lu * s_f + 4 * N * 8
     upd = n * (16 + 16 + 8)
     return a1 + a2 + fac + solve * (1 + refine) + ref * refine + upd
+
+
+def _ncu_traffic():
+    """Measured DRAM bytes per launch if the kernel is the one profiled."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1711_10579_gb300", "csrc", "newton.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return NCU_TRAFFIC["bytes_per_launch"] if sha == NCU_TRAFFIC["newton_cu_sha256"] else None
 
 
 def _case():
@@ -344,6 +357,36 @@ def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9):
     return out
 
 
+def profile_launches(count, S=4, threads=512):
+    """The main step's batched launch, ``count`` times, with a fixed shape."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1711_10579_gb300 import pf
+
+    dev = torch.device("cuda:0")
+    ctx = pf.pf_ctx_create(0)
+    case = _case()
+    c = pf.pf_create_case(ctx, case)
+    pl, ql, pg = _batch(case, B_MAIN, seed=1)
+    d = [torch.tensor(a, device=dev) for a in (pl, ql, pg)]
+    vm = torch.zeros((B_MAIN, case.n_bus), dtype=torch.float64, device=dev)
+    va = torch.zeros_like(vm)
+    info = torch.zeros((B_MAIN, pf.INFO_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    o = pf.make_opts(scen_per_cta=S, block_threads=threads)
+    s = torch.cuda.current_stream()
+    for _ in range(count):
+        pf.pf_solve_batch_device(c, B_MAIN, d[0], d[1], d[2], o, vm, va, info, s.cuda_stream)
+    torch.cuda.synchronize()
+    inf = np.frombuffer(info.cpu().numpy().tobytes(), dtype=pf.INFO_DTYPE)
+    print(json.dumps({"launches": count, "launch": pf.pf_launch_config(c, o, B_MAIN),
+                      "all_converged": bool((inf["status"] == 0).all())}))
+    pf.pf_destroy_case(c)
+    pf.pf_ctx_destroy(ctx)
+
+
 # ----------------------------------------------------------------------------
 # main
 # ----------------------------------------------------------------------------
@@ -356,6 +399,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-launches", type=int, default=0,
+                    help="only launch the main batched solve this many times (for ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -364,6 +409,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile_launches:
+        profile_launches(args.profile_launches)
         return
 
     import torch
@@ -466,7 +514,8 @@ def main():
                        "note": "per batch step; single-solve latency in variants"},
         "converged": total, "solves": world * B * K,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind},
+                     "frac": achieved / peak, "traffic": _ncu_traffic(),
+                     "peak_source": peak_kind},
         "e2e": e2e, "gpu_launches": K, "clocks": clk, "wall_s": t_wall,
     }
     if rank == 0 and not args.no_variants:
