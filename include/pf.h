@@ -343,13 +343,14 @@ int pf_launch_config(pf_case c, const pf_opts* opts, int B, int* grid, int* clus
                      int* threads, int* scen_per_cluster);
 
 /*
- * One pf_solve of the case with per-phase device timers (diagnostics).
- * phase_us[8] (host) receives microseconds spent in: set-up, mismatch +
- * Jacobian, stop test, factorisation, triangular solves, right-hand sides and
- * refinement residuals, voltage update, output -- as seen by one thread of
- * the launch between its barriers, summed over the Newton iterations.
+ * A solve of B copies of the case's own scenario with per-phase device timers
+ * (diagnostics).  phase_us[8] (host) receives microseconds spent in: set-up,
+ * mismatch + Jacobian, stop test, factorisation, triangular solves,
+ * right-hand sides and refinement residuals, voltage update, output -- as
+ * seen by one thread of the first CTA of the launch between its barriers,
+ * summed over the Newton iterations.  info: B records (host, may be NULL).
  */
-int pf_profile_solve(pf_case c, const pf_opts* opts, double* phase_us, pf_info* info);
+int pf_profile_solve(pf_case c, int B, const pf_opts* opts, double* phase_us, pf_info* info);
 
 #ifdef __cplusplus
 }

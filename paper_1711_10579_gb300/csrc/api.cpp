@@ -118,6 +118,12 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   UP(s.y_rowptr, y_rowptr);
   UP(s.y_col, y_col);
   UP(yv, y_val);
+  std::vector<float2> y32;
+  if (c.kind == PF_SINGLE_PHASE) {
+    y32.resize(s.nnz_y());
+    for (int e = 0; e < s.nnz_y(); ++e) y32[e] = make_float2((float)yv[2 * e], (float)yv[2 * e + 1]);
+  }
+  UP(y32, y32);
   UP(s.lu_rowptr, lu_rowptr);
   UP(s.lu_col, lu_col);
   UP(s.lu_diag, lu_diag);
@@ -208,7 +214,7 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
   t += nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8;      // spec
   t += (kind == PF_SINGLE_PHASE ? 2 : 0) * nb * 8;      // vm, va
   t += 3 * nb * nsl * 16;                               // V, I, dV
-  t += (kind == PF_SINGLE_PHASE ? 16 : 0) * nb;         // U
+  t += (kind == PF_SINGLE_PHASE ? 32 : 0) * nb;         // U, FP32 (U, |V|)
   t += (kind == PF_SINGLE_PHASE ? 0 : 12) * nb * 8;     // abcd
   t += 3 * nb * bs * 8;                                 // F, dx, r
   t += (size_t)nnz_lu * B * bs * bs * 8;                // lu
@@ -254,6 +260,7 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
   }
   A((void**)&w.V, nb * nsl * 16);
   if (kind == PF_SINGLE_PHASE) A((void**)&w.U, nb * 16);
+  if (kind == PF_SINGLE_PHASE) A((void**)&w.uvm32, nb * 16);
   A((void**)&w.I, nb * nsl * 16);
   A((void**)&w.dV, nb * nsl * 16);
   if (kind == PF_THREE_PHASE) A((void**)&w.abcd, nb * 12 * 8);
@@ -633,12 +640,12 @@ int pf_solve_noalloc(pf_case c, const pf_opts* opts, const double* d_p_load,
                        (cudaStream_t)stream);
 }
 
-int pf_profile_solve(pf_case c, const pf_opts* opts, double* phase_us, pf_info* info) {
-  if (!c || !phase_us) return set_error(PF_ERR_INVALID, "null argument");
+int pf_profile_solve(pf_case c, int B, const pf_opts* opts, double* phase_us, pf_info* info) {
+  if (!c || !phase_us || B < 1) return set_error(PF_ERR_INVALID, "null argument or B < 1");
   pf_opts o;
   if (opts) o = *opts; else pf_opts_default(&o);
   std::lock_guard<std::mutex> lk(c->mu);
-  return profile_solve(c, o, phase_us, info);
+  return profile_solve(c, B, o, phase_us, info);
 }
 
 }  // extern "C"

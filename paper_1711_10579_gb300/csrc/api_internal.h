@@ -102,7 +102,7 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load,
               pf_info* out_info = nullptr, unsigned long long* prof = nullptr);
 void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int* cluster,
                   int* threads, int* S);
-int profile_solve(pf_case c, const pf_opts& o, double* phase_us, pf_info* info);
+int profile_solve(pf_case c, int B, const pf_opts& o, double* phase_us, pf_info* info);
 int autotune(pf_case c, int B, pf_opts* o);
 // Copies staged results of the last run_solve on ws to host arrays.
 int fetch_results(pf_case c, Workspace* ws, int B, double* vmag, double* vang,

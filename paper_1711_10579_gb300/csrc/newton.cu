@@ -213,6 +213,7 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
   const double2 Vi = ldc(w.V + b);
   double2 I = make_double2(0.0, 0.0);
   const double2* Y = reinterpret_cast<const double2*>(S.y_val);
+#pragma unroll 4
   for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
     const int j = S.y_col[e];
     I = cadd(I, cmul(Y[e], ldc(w.V + (size_t)j * B + gs)));
@@ -235,27 +236,48 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
 
   // The Jacobian is formed in the factor's precision TF (it only feeds the
   // factorisation; the mismatch above and the refinement residual stay FP64).
-  // U = V / |V| per bus (kept by the update) avoids divisions.
+  // U = V / |V| per bus (kept by the update) avoids divisions; in FP32 the
+  // inputs come from FP32 copies of Ybus and of (U, |V|), so the loop does no
+  // FP64 work (FP64 instructions are scarce on this GPU).
   using T = TF;
+  constexpr bool F32 = sizeof(TF) == 4;
   const double2 Ui = ldc(w.U + b);
   const T vix = (T)Vi.x, viy = (T)Vi.y, uix = (T)Ui.x, uiy = (T)Ui.y;
   TF* lu = reinterpret_cast<TF*>(w.lu);
+#pragma unroll 2
   for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
     const int j = S.lu_col[e];
     const int yi = S.lu2y[e];
     T j00 = 0, j01 = 0, j10 = 0, j11 = 0;
     if (yi >= 0) {
-      const T yx = (T)Y[yi].x, yy = (T)Y[yi].y;
+      T yx, yy;
+      if constexpr (F32) {
+        const float2 y32 = S.y32[yi];
+        yx = y32.x;
+        yy = y32.y;
+      } else {
+        yx = (T)Y[yi].x;
+        yy = (T)Y[yi].y;
+      }
       if (j != i) {
         const int tj = S.btype[j];
         if (t != PF_SLACK && tj != PF_SLACK) {
           const size_t bj = (size_t)j * B + gs;
           // dS_i/d|V_j| = V_i conj(Y_ij U_j); dS_i/d delta_j = -j |V_j| dS_i/d|V_j|
-          const double2 Uj = ldc(w.U + bj);
-          const T ux = (T)Uj.x, uy = (T)Uj.y;
+          T ux, uy, vmj;
+          if constexpr (F32) {
+            const float4 q = __ldcg(w.uvm32 + bj);  // (Re U, Im U, |V|, 0)
+            ux = q.x;
+            uy = q.y;
+            vmj = q.z;
+          } else {
+            const double2 Uj = ldc(w.U + bj);
+            ux = (T)Uj.x;
+            uy = (T)Uj.y;
+            vmj = (T)__ldcg(w.vm + bj);
+          }
           const T yux = yx * ux - yy * uy, yuy = yx * uy + yy * ux;
           const T cx = vix * yux + viy * yuy, cy = viy * yux - vix * yuy;
-          const T vmj = (T)__ldcg(w.vm + bj);
           j00 = vmj * cy;
           j10 = -vmj * cx;
           if (tj == PF_PQ) {
@@ -843,6 +865,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
       sincos(va, &sn, &cs);
       w.U[b] = make_double2(cs, sn);
       w.V[b] = make_double2(vm * cs, vm * sn);
+      w.uvm32[b] = make_float4((float)cs, (float)sn, (float)vm, 0.0f);
     } else {
       const int mask = S.btype[i] & 7;
       for (int a = 0; a < 3; ++a) {
@@ -1345,6 +1368,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
         sincos(va, &sn, &cs);
         w.U[b] = make_double2(cs, sn);
         w.V[b] = make_double2(vm * cs, vm * sn);
+        w.uvm32[b] = make_float4((float)cs, (float)sn, (float)vm, 0.0f);
       }
       atomic_max_pos(w.step + (size_t)(it & 1) * B + gs, stp);
     });

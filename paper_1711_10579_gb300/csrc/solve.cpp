@@ -256,7 +256,7 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   // carve the workspace (256-byte aligned pieces)
   const size_t nb = (size_t)n;
   size_t off = 0;
-  size_t sizes[20];
+  size_t sizes[24];
   int k = 0;
   sizes[k++] = nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8;  // spec
   sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;         // vm
@@ -277,7 +277,8 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   sizes[k++] = 8;                                            // flag
   sizes[k++] = (size_t)nflev;                                // forward lanes
   sizes[k++] = (size_t)nblev;                                // backward lanes
-  size_t offs[20];
+  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 16 : 0;        // FP32 (U, |V|)
+  size_t offs[24];
   for (int q = 0; q < k; ++q) {
     offs[q] = off;
     off += (sizes[q] + 255) & ~size_t(255);
@@ -329,6 +330,7 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   DevSys sys = sb.view;
   int8_t* g_fwd = (int8_t*)at(17);
   int8_t* g_bwd = (int8_t*)at(18);
+  w.uvm32 = (float4*)at(19);
   auto put_lanes = [&](const std::vector<int>& ptr, const std::vector<int>& longest, int8_t* dst) {
     int8_t chunk[512];
     const int nl = (int)ptr.size() - 1;
@@ -432,22 +434,23 @@ int autotune(pf_case c, int B, pf_opts* io) {
   return PF_OK;
 }
 
-int profile_solve(pf_case c, const pf_opts& o, double* phase_us, pf_info* info) {
+int profile_solve(pf_case c, int B, const pf_opts& o, double* phase_us, pf_info* info) {
   cudaSetDevice(c->ctx->device);
   cudaStream_t st = c->ctx->stream;
-  Workspace* ws = &c->ws1;
+  Workspace* ws = (B == 1) ? &c->ws1 : &c->wsB;
   int rc = ws->ensure(c->data.kind, c->data.n,
-                      std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), 1);
+                      std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), B,
+                      o.method == PF_NK ? o.gmres_restart : 0);
   if (rc != PF_OK) return rc;
   unsigned long long* d_prof = nullptr;
   cudaError_t e = cudaMalloc(&d_prof, kProfPhases * sizeof(unsigned long long));
   if (e != cudaSuccess) return cuda_error(e, "allocating the profile counters");
   e = cudaMemsetAsync(d_prof, 0, kProfPhases * sizeof(unsigned long long), st);
   if (e == cudaSuccess) {
-    rc = run_solve(c, o, 1, nullptr, nullptr, nullptr, ws, st, RunMode::Solve, nullptr, nullptr,
+    rc = run_solve(c, o, B, nullptr, nullptr, nullptr, ws, st, RunMode::Solve, nullptr, nullptr,
                    nullptr, d_prof);
     unsigned long long h[kProfPhases];
-    if (rc == PF_OK) rc = fetch_results(c, ws, 1, nullptr, nullptr, info, st);
+    if (rc == PF_OK) rc = fetch_results(c, ws, B, nullptr, nullptr, info, st);
     if (rc == PF_OK) {
       e = cudaMemcpy(h, d_prof, sizeof(h), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) rc = cuda_error(e, "reading the profile counters");

@@ -119,7 +119,7 @@ def lib():
             "pf_eval_jacobian": (C.c_int, [vp, _dp, _dp, _dp]),
             "pf_newton_step": (C.c_int, [vp, C.POINTER(pf_opts), _dp, _dp, _dp,
                                          C.POINTER(pf_info)]),
-            "pf_profile_solve": (C.c_int, [vp, C.POINTER(pf_opts), _dp, C.POINTER(pf_info)]),
+            "pf_profile_solve": (C.c_int, [vp, C.c_int, C.POINTER(pf_opts), _dp, vp]),
             "pf_launch_config": (C.c_int, [vp, C.POINTER(pf_opts), C.c_int, _ip, _ip, _ip, _ip]),
             "pf_solve_noalloc": (C.c_int, [vp, C.POINTER(pf_opts), vp, vp, vp, vp, vp, vp, vp]),
             "pf_autotune": (C.c_int, [vp, C.c_int, C.POINTER(pf_opts)]),
@@ -420,13 +420,17 @@ PROFILE_PHASES = ("setup", "mismatch_jacobian", "stop_test", "factor", "triangul
                   "rhs_refinement", "update", "output")
 
 
-def pf_profile_solve(c: CaseHandle, opts: pf_opts | None = None):
-    """(phase microseconds dict, info) of one timed single solve."""
+def pf_profile_solve(c: CaseHandle, opts: pf_opts | None = None, B: int = 1):
+    """(phase microseconds dict, info records) of one timed solve of B copies
+    of the case's own scenario (info: dict for B = 1, structured array else)."""
     ph = np.zeros(len(PROFILE_PHASES))
-    info = pf_info()
-    _check(lib().pf_profile_solve(c.handle, C.byref(opts) if opts else None,
-                                  _ptr(ph, C.c_double), C.byref(info)))
-    return dict(zip(PROFILE_PHASES, ph.tolist())), info.as_dict()
+    info = np.zeros(B, INFO_DTYPE)
+    _check(lib().pf_profile_solve(c.handle, B, C.byref(opts) if opts else None,
+                                  _ptr(ph, C.c_double), info.ctypes.data_as(C.c_void_p)))
+    prof = dict(zip(PROFILE_PHASES, ph.tolist()))
+    if B == 1:
+        return prof, {k: (info[k][0].item()) for k in info.dtype.names if k != "reserved"}
+    return prof, info
 
 
 def pf_launch_config(c: CaseHandle, opts: pf_opts | None = None, B: int = 1) -> dict:
