@@ -124,6 +124,10 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
     for (int e = 0; e < s.nnz_y(); ++e) y32[e] = make_float2((float)yv[2 * e], (float)yv[2 * e + 1]);
   }
   UP(y32, y32);
+  std::vector<double2> trig(2 * kTrigHalf + 1);
+  for (int j = -kTrigHalf; j <= kTrigHalf; ++j)
+    trig[j + kTrigHalf] = make_double2(std::cos(j * 0.0078125), std::sin(j * 0.0078125));
+  UP(trig, trig);
   UP(s.lu_rowptr, lu_rowptr);
   UP(s.lu_col, lu_col);
   UP(s.lu_diag, lu_diag);
@@ -149,7 +153,7 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   UP(s.perm, perm);
   // packed per-item records (one 16-byte load each) for the kernels' prefetch
   std::vector<int4> fwd(n), bwd(n), fac(s.fac_items.size()), tgt(s.tgt_entry.size());
-  std::vector<int2> con(s.con_l.size());
+  std::vector<int2> con;
   for (int t = 0; t < n; ++t) {
     const int i = s.flev_rows[t], j = s.blev_rows[t];
     fwd[t] = make_int4(i, s.lu_rowptr[i], s.lu_diag[i], 0);
@@ -159,9 +163,20 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
     const int e = s.fac_items[t], k = s.lu_col[e];
     fac[t] = make_int4(e, k, s.lu_diag[k], 0);
   }
-  for (size_t t = 0; t < tgt.size(); ++t)
-    tgt[t] = make_int4(s.tgt_entry[t], s.tgt_cptr[t], s.tgt_cptr[t + 1], 0);
-  for (size_t c = 0; c < con.size(); ++c) con[c] = make_int2(s.con_l[c], s.con_u[c]);
+  // a target carries its first contribution; the others (rare: most targets
+  // receive one per level) follow in `con`, each list ended by (-1, -1)
+  con.clear();
+  for (size_t t = 0; t < tgt.size(); ++t) {
+    const int c0 = s.tgt_cptr[t], c1 = s.tgt_cptr[t + 1];
+    int rest = -1;
+    if (c1 - c0 > 1) {
+      rest = (int)con.size();
+      for (int c = c0 + 1; c < c1; ++c) con.push_back(make_int2(s.con_l[c], s.con_u[c]));
+      con.push_back(make_int2(-1, -1));
+    }
+    tgt[t] = make_int4(s.tgt_entry[t], s.con_l[c0], s.con_u[c0], rest);
+  }
+  if (con.empty()) con.push_back(make_int2(-1, -1));
   UP(fwd, fwd_rec);
   UP(bwd, bwd_rec);
   UP(fac, fac_rec);
@@ -175,18 +190,24 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
 }
 
 // Lanes-per-row tables for a given number of threads per cluster (cached).
-int SysBuf::lanes_for(int threads, DevSys& out) {
+// A single solve gives a row up to one warp of lanes; a batch of S scenarios
+// per CTA has threads / S row slots and gives a long row up to 64 lanes
+// (summed across warps through shared memory).
+int SysBuf::lanes_for(int threads, int S, DevSys& out) {
   std::lock_guard<std::mutex> lk(g_mu);
   out = view;
-  auto it = g_cache.find(threads);
+  const int rows = S > 1 ? threads / S : threads;
+  const int key = 2 * rows + (S > 1 ? 1 : 0);
+  auto it = g_cache.find(key);
   if (it == g_cache.end()) {
-    auto gw = lanes_per_level(sym.flev_ptr, sym.flev_llen, threads);
-    auto gb = lanes_per_level(sym.blev_ptr, sym.blev_ulen, threads);
+    const int cap = S > 1 ? 64 : 32;
+    auto gw = lanes_per_level(sym.flev_ptr, sym.flev_llen, rows, cap);
+    auto gb = lanes_per_level(sym.blev_ptr, sym.blev_ulen, rows, cap);
     std::array<const int8_t*, 2> arr{};
     cudaError_t e = upload(mem, gw, &arr[0]);
     if (e == cudaSuccess) e = upload(mem, gb, &arr[1]);
     if (e != cudaSuccess) return cuda_error(e, "uploading lane tables");
-    it = g_cache.emplace(threads, arr).first;
+    it = g_cache.emplace(key, arr).first;
   }
   out.g_fwd = it->second[0];
   out.g_bwd = it->second[1];

@@ -35,7 +35,7 @@ struct SysBuf {
   std::map<int, std::array<const int8_t*, 2>> g_cache;
   std::mutex g_mu;  // the serving thread and callers share g_cache
   int build(const CaseData& c, const Ybus& y, Ordering ord, bool fill);
-  int lanes_for(int threads, DevSys& out);
+  int lanes_for(int threads, int S, DevSys& out);
 };
 
 // Per-solve device state for up to `cap` scenarios plus staging buffers.

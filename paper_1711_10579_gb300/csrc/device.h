@@ -11,6 +11,8 @@ namespace pf {
 constexpr int kRunning = PF_PENDING;
 // Krylov basis vectors per GMRES cycle (restart m <= kMaxJ - 1).
 constexpr int kMaxJ = 64;
+// Half width of the sine / cosine table: angles j 2^-7 for |j| <= kTrigHalf.
+constexpr int kTrigHalf = 512;
 // Size of the fixed scratch array used by pf_solve_noalloc.
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
 
@@ -24,6 +26,7 @@ struct DevSys {
   const int* y_col;
   const double* y_val;
   const float2* y32;  // single phase: FP32 copy of y_val for the Jacobian
+  const double2* trig;  // (cos jh, sin jh), h = 2^-7, j = -kTrigHalf..kTrigHalf
   // factor pattern (L, diagonal, U per row) and its maps
   const int* lu_rowptr;
   const int* lu_col;
@@ -37,7 +40,7 @@ struct DevSys {
   const int* tgt_cptr;
   const int* con_l;
   const int* con_u;
-  // level schedules and lanes per row for a single-scenario launch
+  // level schedules, and lanes per row for the launch's shape
   const int* flev_ptr;
   const int* flev_rows;
   int nflev;
@@ -46,8 +49,10 @@ struct DevSys {
   int nblev;
   int fac_solo_from;  // factor levels >= this run in CTA 0 alone (single solves)
   // packed records: forward / backward rows {i, first, end} of the L / U
-  // part per level position; factor items {e, k, diag(k)}; targets
-  // {entry, first contribution, end}; contributions {L entry, U entry}
+  // part per level position; factor items {e, k, diag(k)}; targets {entry,
+  // L entry, U entry of the first contribution, start in `con` of the other
+  // contributions or -1}; contributions {L entry, U entry}, each target's
+  // list ended by {-1, -1}
   const int4* fwd_rec;
   const int4* bwd_rec;
   const int4* fac_rec;

@@ -87,10 +87,11 @@ struct Symbolic {
 // factorisation (with_fill = true) or the ILU(0) pattern (with_fill = false).
 void analyze(const Ybus& y, Ordering ord, bool with_fill, Symbolic& s);
 
-// Lanes per row (1, 2, 4, ..., 32) for each level of a schedule, given the
-// longest inner loop per level, the level widths and the threads available.
+// Lanes per row (1, 2, 4, ..., cap, cap a power of two <= 64) for each level
+// of a schedule, given the longest inner loop per level, the level widths and
+// the threads (row slots) available.
 std::vector<int8_t> lanes_per_level(const std::vector<int>& lev_ptr,
                                     const std::vector<int>& longest,
-                                    int threads);
+                                    int threads, int cap = 32);
 
 }  // namespace pf

@@ -56,10 +56,37 @@ __device__ __forceinline__ double2 cscale(double2 a, double s) {
 }
 __device__ __forceinline__ double2 ldc(const double2* p) { return __ldcg(p); }
 
-__device__ __forceinline__ void atomic_max_pos(unsigned long long* p, double v) {
-  // non-negative doubles order like their bit patterns; NaN maps above +inf
-  if (!(v >= 0.0)) v = __longlong_as_double(0x7ff8000000000000ULL);
-  atomicMax(p, (unsigned long long)__double_as_longlong(v));
+// |v| as an ordered bit pattern: non-negative doubles order like their bits,
+// and a NaN of either sign maps above +inf.  Integer work only.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+// sin a and cos a in FP64 by table lookup and angle addition (the
+// table-driven method of P. T. P. Tang, 1990): a = j h + r with h = 2^-7,
+// (cos jh, sin jh) from a table built on the host for |j| <= kTrigHalf, and
+// |r| <= 2^-8, where the Taylor series sin r = r - r^3/6 + r^5/120 and
+// cos r = 1 - r^2/2 + r^4/24 are exact to FP64 rounding (the next terms are
+// below 1e-17).  About fifteen FP64 operations; outside the table's range it
+// uses sincos().
+__device__ __forceinline__ void sincos_tab(const double2* tab, double a, double* s, double* c) {
+  if (!(fabs(a) <= kTrigHalf * 0.0078125)) {
+    sincos(a, s, c);
+    return;
+  }
+  // j = nearest integer to 128 a: adding 1.5 * 2^52 rounds it into the low
+  // bits of the sum (no conversion instruction, which is slow in FP64)
+  const double big = a * 128.0 + 6755399441055744.0;
+  const int k = __double2loint(big);
+  const double j = big - 6755399441055744.0;
+  const double r = fma(j, -0.0078125, a);  // exact
+  const double r2 = r * r;
+  const double q = (r2 * (1.0 / 6.0)) * fma(r2, -0.05, 1.0);
+  const double sr = fma(-r, q, r);
+  const double cr = fma(-0.5 * r2, fma(r2, -1.0 / 12.0, 1.0), 1.0);
+  const double2 t = __ldg(tab + k + kTrigHalf);  // (cos jh, sin jh)
+  *c = fma(t.x, cr, -(t.y * sr));
+  *s = fma(t.y, cr, t.x * sr);
 }
 
 template <bool CL>
@@ -156,7 +183,7 @@ __device__ __forceinline__ bool blk_inv(T (&a)[BS * BS], T (&inv)[BS * BS]) {
         piv = r;
       }
     }
-    if (!(best > T(0)) || !isfinite((double)best)) ok = false;
+    if (!(best > T(0)) || !isfinite(best)) ok = false;
     // swap rows c and piv (unrolled selects keep the arrays in registers)
 #pragma unroll
     for (int r = c + 1; r < BS; ++r) {
@@ -231,18 +258,41 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
   const double f1 = (t == PF_PQ) ? (S.q_gen[i] - ql * shape) - Sc.y : 0.0;
   w.F[b * 2] = f0;
   w.F[b * 2 + 1] = f1;
-  nrm = fmax(fabs(f0), fabs(f1));
-  if (!isfinite(f0) || !isfinite(f1)) nrm = __longlong_as_double(0x7ff8000000000000ULL);
+  // max(|f0|, |f1|) on the bit patterns (NaN above +inf), no FP64 instruction
+  nrm = __longlong_as_double((long long)max(abs_bits(f0), abs_bits(f1)));
 
   // The Jacobian is formed in the factor's precision TF (it only feeds the
   // factorisation; the mismatch above and the refinement residual stay FP64).
   // U = V / |V| per bus (kept by the update) avoids divisions; in FP32 the
   // inputs come from FP32 copies of Ybus and of (U, |V|), so the loop does no
   // FP64 work (FP64 instructions are scarce on this GPU).
+  // Conversions between FP64 and FP32 are as costly as FP64 arithmetic here,
+  // so the FP32 path takes V_i and U_i from the FP32 copy and converts only
+  // I_i and the two load-slope terms.
   using T = TF;
   constexpr bool F32 = sizeof(TF) == 4;
-  const double2 Ui = ldc(w.U + b);
-  const T vix = (T)Vi.x, viy = (T)Vi.y, uix = (T)Ui.x, uiy = (T)Ui.y;
+  T vix, viy, uix, uiy, Ix, Iy, Scx, Scy;
+  if constexpr (F32) {
+    const float4 q = __ldcg(w.uvm32 + b);
+    uix = q.x;
+    uiy = q.y;
+    vix = q.z * q.x;
+    viy = q.z * q.y;
+    Ix = (T)I.x;
+    Iy = (T)I.y;
+    Scx = vix * Ix + viy * Iy;  // V_i conj(I_i)
+    Scy = viy * Ix - vix * Iy;
+  } else {
+    const double2 Ui = ldc(w.U + b);
+    vix = (T)Vi.x;
+    viy = (T)Vi.y;
+    uix = (T)Ui.x;
+    uiy = (T)Ui.y;
+    Ix = (T)I.x;
+    Iy = (T)I.y;
+    Scx = (T)Sc.x;
+    Scy = (T)Sc.y;
+  }
   TF* lu = reinterpret_cast<TF*>(w.lu);
 #pragma unroll 2
   for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
@@ -293,10 +343,10 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
         // dS_i/d|V_i| = U_i conj(I_i + Y_ii V_i), minus the load's slope
         const T yvx = yx * vix - yy * viy, yvy = yx * viy + yy * vix;  // Y_ii V_i
         const T dx = vix * yvx + viy * yvy, dy = viy * yvx - vix * yvy;
-        const T ax = (T)I.x + yvx, ay = (T)I.y + yvy;
+        const T ax = Ix + yvx, ay = Iy + yvy;
         const T ex = uix * ax + uiy * ay, ey = uiy * ax - uix * ay;
-        j00 = -((T)Sc.y - dy);
-        j10 = (T)Sc.x - dx;
+        j00 = -(Scy - dy);
+        j10 = Scx - dx;
         j01 = ex + (T)(pl * dshape);
         j11 = ey + (T)(ql * dshape);
         if (t == PF_PV) {
@@ -470,6 +520,24 @@ __device__ void run_rows(const Team& tm, int n, Fn fn) {
   run_items<CL>(tm, n, fn);
 }
 
+// Like run_rows for an fn that returns a non-negative value per row: the
+// largest value of each scenario (NaN above +inf) goes to base[gs], with one
+// atomic per warp and scenario slot instead of one per row.
+template <bool CL, class Fn>
+__device__ void run_rows_max(const Team& tm, int n, unsigned long long* base, Fn fn) {
+  const int s = tm.tid & (tm.S - 1);
+  unsigned long long m = 0ull;
+  if (s < tm.ns && ((tm.act >> s) & 1u)) {
+    for (int it = tm.tid / tm.S; it < n; it += tm.nthr / tm.S) {
+      m = max(m, abs_bits(fn(it, tm.s0 + s)));
+    }
+  }
+  // the lanes of a warp with the same slot sit S apart
+  for (int off = tm.S; off < 32; off <<= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((int)(threadIdx.x & 31) < tm.S && m != 0ull) atomicMax(base + tm.s0 + s, m);
+  csync<CL>();
+}
+
 // ---------------------------------------------------------------------------
 // level sweeps with prefetch of the next level's static data
 // ---------------------------------------------------------------------------
@@ -491,6 +559,7 @@ __device__ __forceinline__ void sweep_pref(const DevSys& S, const DevWork& w, co
                                            int pos, bool have, int gs, int lane,
                                            RowPref<BS, TF>& P) {
   P.i = -1;
+  P.p = P.pe = 0;
   if (!have) return;
   const int4 q = __ldg(rec + pos);
   P.i = q.x;
@@ -571,12 +640,258 @@ __device__ __forceinline__ void sweep_row(const DevSys& S, const DevWork& w, TF*
   }
 }
 
+// ---------------------------------------------------------------------------
+// batched triangular sweeps (one CTA, S scenarios per CTA)
+// ---------------------------------------------------------------------------
+
+// A thread's share of one row of a batched sweep, loaded before any result of
+// its level is stored: the row, this lane's first entry (column and, for 2x2
+// blocks, value) and, for lane 0, the row's own right-hand side and (backward,
+// 2x2 blocks) its inverse diagonal block.
+template <int BS, typename TF>
+struct BRow {
+  static constexpr int NV = (BS == 2) ? 4 : 1;
+  int i, p, pe, k;
+  TF v[NV], d[NV], own[BS];
+};
+
+// Pointers and sizes of one batched sweep.
+template <typename TF>
+struct BSweep {
+  const TF* lu;        // factor values [entry][scenario][BS x BS]
+  const TF* uinv;      // inverse diagonal blocks [row][scenario][BS x BS]
+  const int* col;      // factor columns
+  TF* y;               // solve vector [row][scenario][BS]
+  const double* rhs;   // forward: right-hand side (else y holds it)
+  double* dx;          // backward: also written here (else only y)
+  int accumulate;      // backward: dx += y instead of dx = y
+  int B;
+  const int* lev_ptr;  // level schedule and its row records
+  const int4* rec;
+  int nlev;
+  const int8_t* gsz;   // lanes per row for each level
+  TF* red;             // shared memory for the partial sums of lanes
+};
+
+template <int BS, typename TF, bool FWD>
+__device__ __forceinline__ void brow_load(BRow<BS, TF>& P, const BSweep<TF>& a, int pos, bool have,
+                                          int lane, int gs) {
+  P.i = -1;
+  P.p = P.pe = 0;
+  if (!have) return;
+  const int4 q = __ldg(a.rec + pos);
+  P.i = q.x;
+  P.p = q.y + lane;
+  P.pe = q.z;
+  if (P.p < P.pe) {
+    P.k = __ldg(a.col + P.p);
+    if constexpr (BS == 2) blk_load<2>(a.lu + ((size_t)P.p * a.B + gs) * 4, P.v);
+  }
+  if (lane == 0) {
+    const size_t bi = ((size_t)P.i * a.B + gs) * BS;
+#pragma unroll
+    for (int c = 0; c < BS; ++c) P.own[c] = (FWD && a.rhs) ? (TF)__ldcg(a.rhs + bi + c) : a.y[bi + c];
+    if constexpr (!FWD && BS == 2) blk_load<2>(a.uinv + ((size_t)P.i * a.B + gs) * 4, P.d);
+  }
+}
+
+// Entry p of a row: its column and block (from the row's prefetch when p is
+// the lane's first entry).
+template <int BS, typename TF>
+__device__ __forceinline__ void brow_entry(const BRow<BS, TF>& P, const BSweep<TF>& a, int p,
+                                           int gs, int& k, TF (&L)[BS * BS]) {
+  if (BS == 2 && p == P.p) {
+    k = P.k;
+#pragma unroll
+    for (int t = 0; t < BS * BS; ++t) L[t] = P.v[(BS == 2) ? t : 0];
+  } else {
+    k = (p == P.p) ? P.k : __ldg(a.col + p);
+    blk_load<BS>(a.lu + ((size_t)p * a.B + gs) * BS * BS, L);
+  }
+}
+
+// Forward: y_i = b_i - acc.  Backward: y_i = U_ii^-1 (y_i - acc), and dx.
+template <int BS, typename TF, bool FWD>
+__device__ __forceinline__ void brow_finish(const BRow<BS, TF>& P, const BSweep<TF>& a, int gs,
+                                            const TF (&acc)[BS]) {
+  constexpr int BB = BS * BS;
+  const size_t bi = ((size_t)P.i * a.B + gs) * BS;
+  TF t[BS];
+#pragma unroll
+  for (int c = 0; c < BS; ++c) t[c] = P.own[c] - acc[c];
+  if constexpr (!FWD) {
+    TF D[BB];
+    if constexpr (BS == 2) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) D[q] = P.d[q];
+    } else {
+      blk_load<BS>(a.uinv + ((size_t)P.i * a.B + gs) * BB, D);
+    }
+    TF u[BS];
+#pragma unroll
+    for (int r = 0; r < BS; ++r) {
+      u[r] = TF(0);
+#pragma unroll
+      for (int c = 0; c < BS; ++c) u[r] += D[r * BS + c] * t[c];
+    }
+#pragma unroll
+    for (int c = 0; c < BS; ++c) t[c] = u[c];
+  }
+#pragma unroll
+  for (int c = 0; c < BS; ++c) a.y[bi + c] = t[c];
+  if (!FWD && a.dx) {
+#pragma unroll
+    for (int c = 0; c < BS; ++c)
+      a.dx[bi + c] = a.accumulate ? __ldcg(a.dx + bi + c) + (double)t[c] : (double)t[c];
+  }
+}
+
+// Batched triangular sweep.  Every thread serves the scenario slot tid % S;
+// the nthr / S row slots take a level's rows with G = gsz[l] lanes per row
+// (G from the level's width and its longest row), so the long rows near the
+// top of the elimination tree are split across lanes instead of being walked
+// by one thread.  Lanes in one warp are summed with shuffles, lanes in
+// different warps through shared memory, in a fixed order.  Levels with one
+// lane per row take R rows at a time and issue all their loads before any
+// store.  Each thread's first row of level l+1 is loaded while level l runs.
+// Not inlined: it has the registers to itself.
+template <int BS, typename TF, bool FWD>
+__device__ __noinline__ void sweep_batch(const BSweep<TF> a, const Team tm) {
+  constexpr int BB = BS * BS;
+  // rows in flight per thread: more than one measured no faster (the extra
+  // registers spill)
+  constexpr int R = 1;
+  const int NS = tm.S;
+  const int slot = tm.tid & (NS - 1);
+  const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
+  const int gs = tm.s0 + slot;
+  const int q = tm.tid / NS, nq = tm.nthr / NS;
+  auto pref = [&](int l, BRow<BS, TF>& P) {
+    const int G = a.gsz[l], base = a.lev_ptr[l], width = a.lev_ptr[l + 1] - base;
+    const int group = q / G;
+    brow_load<BS, TF, FWD>(P, a, base + group, on && group < width, q & (G - 1), gs);
+  };
+  BRow<BS, TF> cur, nxt;
+  if (a.nlev > 0) pref(0, cur);
+  for (int l = 0; l < a.nlev; ++l) {
+    const int G = a.gsz[l], base = a.lev_ptr[l], width = a.lev_ptr[l + 1] - base;
+    if (l + 1 < a.nlev) pref(l + 1, nxt);
+    if (G == 1) {
+      if (on) {
+        for (int r0 = q; r0 < width; r0 += R * nq) {
+          BRow<BS, TF> P[R];
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            const int r = r0 + u * nq;
+            if (u == 0 && r0 == q) P[0] = cur;
+            else brow_load<BS, TF, FWD>(P[u], a, base + r, r < width, 0, gs);
+          }
+          TF acc[R][BS];
+#pragma unroll
+          for (int u = 0; u < R; ++u)
+#pragma unroll
+            for (int c = 0; c < BS; ++c) acc[u][c] = TF(0);
+          for (int e = 0;; ++e) {
+            bool any = false;
+            int k[R];
+            TF L[R][BB];
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+              if (P[u].p + e < P[u].pe) {
+                any = true;
+                brow_entry<BS, TF>(P[u], a, P[u].p + e, gs, k[u], L[u]);
+              }
+            }
+            if (!any) break;
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+              if (P[u].p + e < P[u].pe) {
+                const size_t bk = ((size_t)k[u] * a.B + gs) * BS;
+#pragma unroll
+                for (int rr = 0; rr < BS; ++rr)
+#pragma unroll
+                  for (int c = 0; c < BS; ++c) acc[u][rr] += L[u][rr * BS + c] * a.y[bk + c];
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < R; ++u)
+            if (P[u].i >= 0) brow_finish<BS, TF, FWD>(P[u], a, gs, acc[u]);
+        }
+      }
+    } else {
+      // one row per group of G lanes (G * width <= nq)
+      const int lane = q & (G - 1), group = q / G;
+      TF acc[BS];
+#pragma unroll
+      for (int c = 0; c < BS; ++c) acc[c] = TF(0);
+      for (int pp = cur.p; pp < cur.pe; pp += G) {
+        int k;
+        TF L[BB];
+        brow_entry<BS, TF>(cur, a, pp, gs, k, L);
+        const size_t bk = ((size_t)k * a.B + gs) * BS;
+#pragma unroll
+        for (int rr = 0; rr < BS; ++rr)
+#pragma unroll
+          for (int c = 0; c < BS; ++c) acc[rr] += L[rr * BS + c] * a.y[bk + c];
+      }
+      // lanes of one (row, slot) sit S threads apart
+      const int GW = min(G, 32 / NS);
+      for (int off = NS; off < NS * GW; off <<= 1) {
+#pragma unroll
+        for (int c = 0; c < BS; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+      }
+      const bool row = cur.i >= 0;
+      if (G > GW) {
+        const int NW = G / GW;
+        if (row && (lane & (GW - 1)) == 0) {
+#pragma unroll
+          for (int c = 0; c < BS; ++c) a.red[((group * NW + lane / GW) * NS + slot) * BS + c] = acc[c];
+        }
+        __syncthreads();
+        if (row && lane == 0) {
+#pragma unroll
+          for (int c = 0; c < BS; ++c) acc[c] = TF(0);
+          for (int wp = 0; wp < NW; ++wp) {
+#pragma unroll
+            for (int c = 0; c < BS; ++c) acc[c] += a.red[((group * NW + wp) * NS + slot) * BS + c];
+          }
+        }
+      }
+      if (row && lane == 0) brow_finish<BS, TF, FWD>(cur, a, gs, acc);
+    }
+    __syncthreads();
+    cur = nxt;
+  }
+}
+
 // One triangular sweep over all levels.  A single-scenario team gives each
 // row gsz[l] lanes; a batch team gives each (row, scenario) one thread.  The
 // first row of each group for level l+1 is prefetched while level l runs.
 template <int BS, typename TF, bool FWD, bool CL>
 __device__ void sweep(const DevSys& S, const DevWork& w, TF* y, const Team& tm,
-                      const int* lev_ptr, const int4* rec, int nlev, const int8_t* gsz) {
+                      const int* lev_ptr, const int4* rec, int nlev, const int8_t* gsz,
+                      TF* red) {
+  if constexpr (!CL) {
+    if (tm.S > 1) {
+      BSweep<TF> a;
+      a.lu = reinterpret_cast<const TF*>(w.lu);
+      a.uinv = reinterpret_cast<const TF*>(w.uinv);
+      a.col = S.lu_col;
+      a.y = y;
+      a.rhs = nullptr;
+      a.dx = nullptr;
+      a.accumulate = 0;
+      a.B = w.B;
+      a.lev_ptr = lev_ptr;
+      a.rec = rec;
+      a.nlev = nlev;
+      a.gsz = gsz;
+      a.red = red;
+      sweep_batch<BS, TF, FWD>(a, tm);
+      return;
+    }
+  }
   const bool single = (tm.S == 1);
   const int slot = single ? 0 : (tm.tid & (tm.S - 1));
   const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
@@ -632,81 +947,141 @@ __device__ void sweep(const DevSys& S, const DevWork& w, TF* y, const Team& tm,
 // columns becomes L_ik = A_ik U_kk^-1 -- all these entries received their
 // last update at an earlier level.  Step 2: every entry (i, j) the level's
 // pivots touch gathers A_ij -= sum_k L_ik U_kj in a fixed order (so results
-// are deterministic).  The next step's index records are prefetched across
-// each barrier.
+// are deterministic).  A thread takes R items of a step at a time so that
+// their loads overlap; the first record of each step is loaded before the
+// barrier that precedes the step.  Not inlined: it has the registers to
+// itself.
+template <typename TF>
+struct FactorArgs {
+  TF* lu;
+  TF* uinv;
+  int* flag;
+  int B;
+  const int* fac_ptr;
+  const int4* fac_rec;
+  const int* tgt_ptr;
+  const int4* tgt_rec;
+  const int2* con;
+};
+
 template <int BS, typename TF, bool CL>
-__device__ void factor_levels(const DevSys& S, const DevWork& w, const Team& tm, int l0, int l1) {
+__device__ __noinline__ void factor_run(const FactorArgs<TF> S, const Team tm, int l0, int l1) {
   if (l0 >= l1) return;
+  constexpr int BB = BS * BS;
+  // items in flight per thread: more than one measured no faster (the
+  // extra registers spill)
+  constexpr int R = 1;
   const int slot = tm.tid & (tm.S - 1);
   const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
   const int gs = tm.s0 + slot;
   const int first = tm.tid / tm.S, stride = tm.nthr / tm.S;
-  constexpr int BB = BS * BS;
-  TF* lu = reinterpret_cast<TF*>(w.lu);
-  auto fac_rec = [&](int l) {
+  TF* lu = S.lu;
+  auto blk = [&](int e) { return lu + ((size_t)e * S.B + gs) * BB; };
+  const int4 none = make_int4(-1, 0, 0, -1);
+  auto fac_first = [&](int l) {
     const int f0 = S.fac_ptr[l], nf = S.fac_ptr[l + 1] - f0;
-    return (on && first < nf) ? __ldg(S.fac_rec + f0 + first) : make_int4(-1, 0, 0, 0);
+    return (on && first < nf) ? __ldg(S.fac_rec + f0 + first) : none;
   };
-  auto tgt_rec = [&](int l, int2& c0) {
+  auto tgt_first = [&](int l) {
     const int t0 = S.tgt_ptr[l], nt = S.tgt_ptr[l + 1] - t0;
-    if (on && first < nt) {
-      const int4 r = __ldg(S.tgt_rec + t0 + first);
-      c0 = __ldg(S.con + r.y);
-      return r;
-    }
-    return make_int4(-1, 0, 0, 0);
+    return (on && first < nt) ? __ldg(S.tgt_rec + t0 + first) : none;
   };
-  auto finalise = [&](int4 r) {
-    // r = {e, k, diag(k)}: U_kk^-1 for the diagonal, else L_ik = A_ik U_kk^-1
-    TF d[BB], di[BB];
-    blk_load<BS>(lu + ((size_t)r.z * w.B + gs) * BB, d);
-    const bool ok = blk_inv<BS>(d, di);
-    if (r.x == r.z) {
-      if (!ok) w.flag[gs] = 1;
-      blk_store<BS>(reinterpret_cast<TF*>(w.uinv) + ((size_t)r.y * w.B + gs) * BB, di);
-    } else {
-      TF a[BB], l[BB];
-      blk_load<BS>(lu + ((size_t)r.x * w.B + gs) * BB, a);
-      blk_mul<BS>(a, di, l);
-      blk_store<BS>(lu + ((size_t)r.x * w.B + gs) * BB, l);
-    }
-  };
-  auto update = [&](int4 r, int2 c0) {
-    // r = {e, c0, c1}: A_e -= sum L(con.x) U(con.y)
-    TF c[BB];
-    blk_load<BS>(lu + ((size_t)r.x * w.B + gs) * BB, c);
-    for (int q = r.y; q < r.z; ++q) {
-      const int2 cq = (q == r.y) ? c0 : __ldg(S.con + q);
-      TF l[BB], u[BB];
-      blk_load<BS>(lu + ((size_t)cq.x * w.B + gs) * BB, l);
-      blk_load<BS>(lu + ((size_t)cq.y * w.B + gs) * BB, u);
-      blk_msub<BS>(c, l, u);
-    }
-    blk_store<BS>(lu + ((size_t)r.x * w.B + gs) * BB, c);
-  };
-  int4 fr = fac_rec(l0);
+  int4 fr = fac_first(l0);
   for (int l = l0; l < l1; ++l) {
-    int2 tc0 = make_int2(0, 0);
-    const int4 tr = tgt_rec(l, tc0);  // prefetch for the second step
-    if (fr.x >= 0) finalise(fr);
+    const int4 tr = tgt_first(l);  // for step 2, loaded ahead
+    // step 1: r = {e, k, diag(k)}: U_kk^-1 for the diagonal, else L_ik = A_ik U_kk^-1
     if (on) {
       const int f0 = S.fac_ptr[l], nf = S.fac_ptr[l + 1] - f0;
-      for (int t = first + stride; t < nf; t += stride) finalise(__ldg(S.fac_rec + f0 + t));
+      for (int t = first; t < nf; t += R * stride) {
+        int4 r[R];
+        TF d[R][BB], a[R][BB];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          const int tu = t + u * stride;
+          r[u] = (u == 0 && t == first) ? fr : (tu < nf ? __ldg(S.fac_rec + f0 + tu) : none);
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          if (r[u].x >= 0) {
+            blk_load<BS>(blk(r[u].z), d[u]);
+            if (r[u].x != r[u].z) blk_load<BS>(blk(r[u].x), a[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          if (r[u].x < 0) continue;
+          TF di[BB];
+          const bool ok = blk_inv<BS>(d[u], di);
+          if (r[u].x == r[u].z) {
+            if (!ok) S.flag[gs] = 1;
+            blk_store<BS>(S.uinv + ((size_t)r[u].y * S.B + gs) * BB, di);
+          } else {
+            TF lk[BB];
+            blk_mul<BS>(a[u], di, lk);
+            blk_store<BS>(blk(r[u].x), lk);
+          }
+        }
+      }
     }
     csync<CL>();
-    fr = (l + 1 < l1) ? fac_rec(l + 1) : make_int4(-1, 0, 0, 0);  // prefetch
+    fr = (l + 1 < l1) ? fac_first(l + 1) : none;  // for the next level's step 1
+    // step 2: r = {e, L entry, U entry, rest}: A_e -= L U, then the rest
     const int t0 = S.tgt_ptr[l], nt = S.tgt_ptr[l + 1] - t0;
     if (nt > 0) {
-      if (tr.x >= 0) update(tr, tc0);
       if (on) {
-        for (int t = first + stride; t < nt; t += stride) {
-          const int4 r = __ldg(S.tgt_rec + t0 + t);
-          update(r, __ldg(S.con + r.y));
+        for (int t = first; t < nt; t += R * stride) {
+          int4 r[R];
+          TF c[R][BB], lv[R][BB], uv[R][BB];
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            const int tu = t + u * stride;
+            r[u] = (u == 0 && t == first) ? tr : (tu < nt ? __ldg(S.tgt_rec + t0 + tu) : none);
+          }
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            if (r[u].x >= 0) {
+              blk_load<BS>(blk(r[u].x), c[u]);
+              blk_load<BS>(blk(r[u].y), lv[u]);
+              blk_load<BS>(blk(r[u].z), uv[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            if (r[u].x < 0) continue;
+            blk_msub<BS>(c[u], lv[u], uv[u]);
+            if (r[u].w >= 0) {
+              for (int q = r[u].w;; ++q) {
+                const int2 cq = __ldg(S.con + q);
+                if (cq.x < 0) break;
+                TF l2[BB], u2[BB];
+                blk_load<BS>(blk(cq.x), l2);
+                blk_load<BS>(blk(cq.y), u2);
+                blk_msub<BS>(c[u], l2, u2);
+              }
+            }
+            blk_store<BS>(blk(r[u].x), c[u]);
+          }
         }
       }
       csync<CL>();
     }
   }
+}
+
+template <int BS, typename TF, bool CL>
+__device__ __forceinline__ void factor_levels(const DevSys& S, const DevWork& w, const Team& tm,
+                                              int l0, int l1) {
+  FactorArgs<TF> f;
+  f.lu = reinterpret_cast<TF*>(w.lu);
+  f.uinv = reinterpret_cast<TF*>(w.uinv);
+  f.flag = w.flag;
+  f.B = w.B;
+  f.fac_ptr = S.fac_ptr;
+  f.fac_rec = S.fac_rec;
+  f.tgt_ptr = S.tgt_ptr;
+  f.tgt_rec = S.tgt_rec;
+  f.con = S.con;
+  factor_run<BS, TF, CL>(f, tm, l0, l1);
 }
 
 // ---------------------------------------------------------------------------
@@ -809,6 +1184,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
   TF* nk_state = reinterpret_cast<TF*>(dsm + (o.y_in_smem ? (size_t)n * BS * sizeof(TF) : 0));
   TF* nk_redw = nk_state + (NK ? (size_t)o.S * GmresState<TF>::words(o.m) : 0);
   TF* nk_rs = nk_redw + (NK ? (size_t)(blockDim.x / 32) * kMaxJ * o.S : 0);
+  // batched sweeps: partial sums of a row's lanes in different warps
+  TF* sw_red = nk_rs + (NK ? (size_t)kMaxJ * o.S : 0);
   __shared__ int sh_lin[32];       // inner iterations, whole solve
   __shared__ int sh_lin_step[32];  // inner iterations, this Newton step
   __shared__ int sh_kk[32];
@@ -862,7 +1239,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
       w.vm[b] = vm;
       w.va[b] = va;
       double sn, cs;
-      sincos(va, &sn, &cs);
+      sincos_tab(S.trig, va, &sn, &cs);
       w.U[b] = make_double2(cs, sn);
       w.V[b] = make_double2(vm * cs, vm * sn);
       w.uvm32[b] = make_float4((float)cs, (float)sn, (float)vm, 0.0f);
@@ -903,7 +1280,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
   int it = 0;
   for (;; ++it) {
     // ---- A: mismatch + Jacobian ----
-    run_rows<CL>(tm, n, [&](int i, int gs) {
+    run_rows_max<CL>(tm, n, w.norm + (size_t)(it & 1) * B, [&](int i, int gs) {
       double nrm;
       TF* jcopy = NK ? reinterpret_cast<TF*>(w.jm) : nullptr;
       if constexpr (THREE) {
@@ -911,7 +1288,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
       } else {
         mismatch_jacobian_1ph<TF>(S, w, i, gs, nrm, jcopy);
       }
-      atomic_max_pos(w.norm + (size_t)(it & 1) * B + gs, nrm);
+      return nrm;
     });
     tick(kProfMismatch);
     if (o.mode == 1) return;  // inspection: F and J stay in the workspace
@@ -1037,8 +1414,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
             const size_t bb = ((size_t)i * B + g2) * BS;
             for (int c = 0; c < BS; ++c) yv[bb + c] = __ldcg(u + bb + c);
           });
-          sweep<BS, TF, true, false>(S, w, yv, solo, S.flev_ptr, S.fwd_rec, S.nflev, S.g_fwd);
-          sweep<BS, TF, false, false>(S, w, yv, solo, S.blev_ptr, S.bwd_rec, S.nblev, S.g_bwd);
+          sweep<BS, TF, true, false>(S, w, yv, solo, S.flev_ptr, S.fwd_rec, S.nflev, S.g_fwd, sw_red);
+          sweep<BS, TF, false, false>(S, w, yv, solo, S.blev_ptr, S.bwd_rec, S.nblev, S.g_bwd, sw_red);
           run_rows<false>(solo, n, [&](int i, int g2) {
             const size_t bb = ((size_t)i * B + g2) * BS;
             for (int c = 0; c < BS; ++c) zout[bb + c] = accumulate ? zout[bb + c] + yv[bb + c] : yv[bb + c];
@@ -1324,14 +1701,39 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
       tick(kProfResidual);
       // forward and backward sweeps: CTA 0 alone for a single solve
       solo.act = tm.act;
-      if (crank == 0) {
+      if (!CL && tm.S > 1) {
+        // a batch: the sweeps read the right-hand side and write dx themselves
+        BSweep<TF> a;
+        a.lu = reinterpret_cast<const TF*>(w.lu);
+        a.uinv = reinterpret_cast<const TF*>(w.uinv);
+        a.col = S.lu_col;
+        a.y = yv;
+        a.rhs = (pass == 0) ? w.F : w.r;
+        a.dx = nullptr;
+        a.accumulate = 0;
+        a.B = B;
+        a.lev_ptr = S.flev_ptr;
+        a.rec = S.fwd_rec;
+        a.nlev = S.nflev;
+        a.gsz = S.g_fwd;
+        a.red = sw_red;
+        sweep_batch<BS, TF, true>(a, solo);
+        a.rhs = nullptr;
+        a.dx = w.dx;
+        a.accumulate = (pass == 0) ? 0 : 1;
+        a.lev_ptr = S.blev_ptr;
+        a.rec = S.bwd_rec;
+        a.nlev = S.nblev;
+        a.gsz = S.g_bwd;
+        sweep_batch<BS, TF, false>(a, solo);
+      } else if (crank == 0) {
         const double* rhs = (pass == 0) ? w.F : w.r;
         run_rows<false>(solo, n, [&](int i, int gs) {
           const size_t b = ((size_t)i * B + gs) * BS;
           for (int c = 0; c < BS; ++c) yv[b + c] = (TF)__ldcg(rhs + b + c);
         });
-        sweep<BS, TF, true, false>(S, w, yv, solo, S.flev_ptr, S.fwd_rec, S.nflev, S.g_fwd);
-        sweep<BS, TF, false, false>(S, w, yv, solo, S.blev_ptr, S.bwd_rec, S.nblev, S.g_bwd);
+        sweep<BS, TF, true, false>(S, w, yv, solo, S.flev_ptr, S.fwd_rec, S.nflev, S.g_fwd, sw_red);
+        sweep<BS, TF, false, false>(S, w, yv, solo, S.blev_ptr, S.bwd_rec, S.nblev, S.g_bwd, sw_red);
         run_rows<false>(solo, n, [&](int i, int gs) {
           const size_t b = ((size_t)i * B + gs) * BS;
           for (int c = 0; c < BS; ++c) {
@@ -1348,7 +1750,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
     if (o.mode == 2) return;  // inspection: the step stays in the workspace
 
     // ---- E: voltage update ----
-    run_rows<CL>(tm, n, [&](int i, int gs) {
+    run_rows_max<CL>(tm, n, w.step + (size_t)(it & 1) * B, [&](int i, int gs) {
       const size_t b = (size_t)i * B + gs;
       double stp = 0.0;
       if constexpr (THREE) {
@@ -1360,17 +1762,17 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
         }
       } else {
         const double dd = __ldcg(w.dx + b * 2), dm = __ldcg(w.dx + b * 2 + 1);
-        stp = fmax(fabs(dd), fabs(dm));
+        stp = __longlong_as_double((long long)max(abs_bits(dd), abs_bits(dm)));
         const double vm = __ldcg(w.vm + b) + dm, va = __ldcg(w.va + b) + dd;
         w.vm[b] = vm;
         w.va[b] = va;
         double sn, cs;
-        sincos(va, &sn, &cs);
+        sincos_tab(S.trig, va, &sn, &cs);
         w.U[b] = make_double2(cs, sn);
         w.V[b] = make_double2(vm * cs, vm * sn);
         w.uvm32[b] = make_float4((float)cs, (float)sn, (float)vm, 0.0f);
       }
-      atomic_max_pos(w.step + (size_t)(it & 1) * B + gs, stp);
+      return stp;
     });
     tick(kProfUpdate);
   }
@@ -1501,6 +1903,7 @@ size_t dynamic_smem_bytes(int bs, size_t tf, bool nk, int n, const DevOpts& o, i
     b += (size_t)(threads / 32) * kMaxJ * o.S * tf;
     b += (size_t)kMaxJ * o.S * tf;
   }
+  if (o.S > 1) b += (size_t)threads * bs * tf;  // batched sweep partials
   return b;
 }
 

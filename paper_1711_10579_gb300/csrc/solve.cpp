@@ -114,7 +114,7 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   int threads, cluster, S, grid;
   launch_shape(c, o, B, fp32, &grid, &cluster, &threads, &S);
   DevSys sys;
-  rc = sb.lanes_for(threads, sys);
+  rc = sb.lanes_for(threads, S, sys);
   if (rc != PF_OK) return rc;
   DevWork w = ws->w;
   w.B = B;

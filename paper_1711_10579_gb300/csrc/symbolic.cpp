@@ -321,13 +321,13 @@ void analyze(const Ybus& y, Ordering ord, bool with_fill, Symbolic& s) {
 
 std::vector<int8_t> lanes_per_level(const std::vector<int>& lev_ptr,
                                     const std::vector<int>& longest,
-                                    int threads) {
+                                    int threads, int cap) {
   const int nl = (int)lev_ptr.size() - 1;
   std::vector<int8_t> g(nl, 1);
   for (int l = 0; l < nl; ++l) {
     int width = lev_ptr[l + 1] - lev_ptr[l];
     int want = 1;
-    while (want < 32 && want < longest[l]) want <<= 1;
+    while (want < cap && want < longest[l]) want <<= 1;
     // keep every row of the level in flight at once when possible
     while (want > 1 && (long long)want * width > threads) want >>= 1;
     g[l] = (int8_t)want;

@@ -271,6 +271,32 @@ def test_device_entry_point_matches_host_entry_point(pf, ctx):
 # three phase (current injection)
 # ----------------------------------------------------------------------------
 
+def test_mismatch_over_the_whole_angle_range(pf, ctx):
+    """Bus voltages are formed from angles by a table of sin / cos at
+    multiples of 2^-7 rad plus a short Taylor series, with sincos() beyond
+    |angle| = 4 rad; the mismatch must match the oracle's (numpy sin / cos)
+    over the table's range, at its edges and past them."""
+    case = cases.case_2000bus(0)
+    Y = O.ybus_single(case)
+    rng = np.random.default_rng(11)
+    n = case.n_bus
+    edges = np.array([0.0, 4.0, -4.0, 4.0 - 2.0**-9, -(4.0 - 2.0**-9), 2.0**-8, -2.0**-8,
+                      3 * 2.0**-8, 4.0 + 1e-12, -4.0 - 1e-12, 7.5, -12.0, np.pi, -np.pi])
+    c = pf.pf_create_case(ctx, case)
+    try:
+        for seed in range(3):
+            vm = rng.uniform(0.9, 1.1, n)
+            va = rng.uniform(-6.0, 6.0, n)
+            va[: edges.size] = edges
+            rng.shuffle(va)
+            mis = pf.pf_eval_mismatch(c, vm, va)
+            ref = O.mismatch_polar(case, Y, vm, va)
+            got = _gpu_mis_to_oracle_order(case, mis)
+            assert np.max(np.abs(got - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref)))
+    finally:
+        pf.pf_destroy_case(c)
+
+
 def _rand_v3(case, seed):
     rng = np.random.default_rng(seed)
     V = O.cim_flat_start(case)
