@@ -110,11 +110,15 @@ int fetch_results(pf_case c, Workspace* ws, int B, double* vmag, double* vang,
 int inspect(pf_case c, InspectKind k, const pf_opts* o, const double* vmag,
             const double* vang, double* out, pf_info* info);
 
-// Launchers in newton.cu / krylov.cu.
+// Launchers in newton.cu and batch.cu.
 cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const DevWork& w,
                           const DevOpts& o, int grid, int cluster, int threads,
                           cudaStream_t st);
 int max_cluster(int bs, bool fp32, bool nk, int threads);
+// Batched Newton-Raphson as phase kernels (batch.cu); prof, if given, is a
+// host array of kProfPhases device times (ns) to add to.
+cudaError_t launch_batch_nr(int bs, bool fp32, const DevSys& S, const DevWork& w, const DevOpts& o,
+                            int threads, cudaStream_t st, unsigned long long* prof);
 cudaError_t noalloc_scratch(void** ptr);
 int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const double* d_q_load,
                   const double* d_p_gen, double* d_vmag, double* d_vang, pf_info* d_info,

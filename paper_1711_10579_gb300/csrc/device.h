@@ -119,6 +119,10 @@ struct DevWork {
   unsigned long long* norm;  // [2][B] max |mismatch| (bit pattern of a double)
   unsigned long long* step;  // [2][B] max |step|
   int* flag;                 // [B] singular pivot seen
+  // batched phase kernels: per-scenario state between launches
+  int* status;               // [B] kRunning or the final pf_status
+  int* refine;               // [B] this iteration takes the FP64 refinement
+  unsigned long long* t0;    // start time of the launch sequence (ns)
 };
 
 struct DevOpts {
@@ -133,6 +137,8 @@ struct DevOpts {
   int m;                     // Newton-Krylov: GMRES restart length
   int max_lin;               // ... inner iterations per Newton step
   double rtol;               // ... inner relative-residual floor
+  int ring;                  // batches of 2x2 blocks: the factorisation stages
+                             // its gathers in dynamic shared memory
 };
 
 size_t dynamic_smem_bytes(int bs, size_t tf, bool nk, int n, const DevOpts& o, int threads);

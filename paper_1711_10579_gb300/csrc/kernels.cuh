@@ -1,0 +1,1498 @@
+// Device building blocks of the Newton power-flow kernels for sm_103a:
+// complex and block arithmetic, the fused mismatch + Jacobian of one row
+// (Eq. 1-10 single phase, Eq. 12-23 three phase), the team helpers, the
+// level-scheduled block LU refactorisation and triangular sweeps, the GMRES
+// reductions, and the per-row steps of an iteration.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+#include <mutex>
+
+#include "device.h"
+
+namespace cg = cooperative_groups;
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a conj(b)
+  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 csub(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) {
+  return make_double2(a.x * s, a.y * s);
+}
+__device__ __forceinline__ double2 ldc(const double2* p) { return __ldcg(p); }
+
+// Asynchronous 16-byte copies global -> shared (cp.async, L2 only): a copy
+// holds no register while in flight, so a thread can keep many gathers
+// outstanding.  Each thread waits for its own groups of copies.
+__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// |v| as an ordered bit pattern: non-negative doubles order like their bits,
+// and a NaN of either sign maps above +inf.  Integer work only.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+// sin a and cos a in FP64 by table lookup and angle addition (the
+// table-driven method of P. T. P. Tang, 1990): a = j h + r with h = 2^-7,
+// (cos jh, sin jh) from a table built on the host for |j| <= kTrigHalf, and
+// |r| <= 2^-8, where the Taylor series sin r = r - r^3/6 + r^5/120 and
+// cos r = 1 - r^2/2 + r^4/24 are exact to FP64 rounding (the next terms are
+// below 1e-17).  About fifteen FP64 operations; outside the table's range it
+// uses sincos().
+__device__ __forceinline__ void sincos_tab(const double2* tab, double a, double* s, double* c) {
+  if (!(fabs(a) <= kTrigHalf * 0.0078125)) {
+    sincos(a, s, c);
+    return;
+  }
+  // j = nearest integer to 128 a: adding 1.5 * 2^52 rounds it into the low
+  // bits of the sum (no conversion instruction, which is slow in FP64)
+  const double big = a * 128.0 + 6755399441055744.0;
+  const int k = __double2loint(big);
+  const double j = big - 6755399441055744.0;
+  const double r = fma(j, -0.0078125, a);  // exact
+  const double r2 = r * r;
+  const double q = (r2 * (1.0 / 6.0)) * fma(r2, -0.05, 1.0);
+  const double sr = fma(-r, q, r);
+  const double cr = fma(-0.5 * r2, fma(r2, -1.0 / 12.0, 1.0), 1.0);
+  const double2 t = __ldg(tab + k + kTrigHalf);  // (cos jh, sin jh)
+  *c = fma(t.x, cr, -(t.y * sr));
+  *s = fma(t.y, cr, t.x * sr);
+}
+
+template <bool CL>
+__device__ __forceinline__ void csync() {
+  if constexpr (CL) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// dense bs x bs blocks (row-major) in registers
+// ---------------------------------------------------------------------------
+
+template <int BS, typename T>
+__device__ __forceinline__ void blk_load(const T* p, T (&a)[BS * BS]) {
+  static_assert((BS * BS * sizeof(T)) % 16 == 0, "block must be 16-byte sized");
+  constexpr int NV = BS * BS * (int)sizeof(T) / 16;
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    float4 t = __ldcg(q + v);
+    const T* tt = reinterpret_cast<const T*>(&t);
+#pragma unroll
+    for (int k = 0; k < 16 / (int)sizeof(T); ++k) a[v * (16 / sizeof(T)) + k] = tt[k];
+  }
+}
+
+template <int BS, typename T>
+__device__ __forceinline__ void blk_store(T* p, const T (&a)[BS * BS]) {
+  constexpr int NV = BS * BS * (int)sizeof(T) / 16;
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    float4 t;
+    T* tt = reinterpret_cast<T*>(&t);
+#pragma unroll
+    for (int k = 0; k < 16 / (int)sizeof(T); ++k) tt[k] = a[v * (16 / sizeof(T)) + k];
+    q[v] = t;
+  }
+}
+
+template <int BS, typename T>
+__device__ __forceinline__ void blk_mul(const T (&a)[BS * BS], const T (&b)[BS * BS],
+                                        T (&c)[BS * BS]) {
+#pragma unroll
+  for (int i = 0; i < BS; ++i)
+#pragma unroll
+    for (int j = 0; j < BS; ++j) {
+      T s = 0;
+#pragma unroll
+      for (int k = 0; k < BS; ++k) s += a[i * BS + k] * b[k * BS + j];
+      c[i * BS + j] = s;
+    }
+}
+
+template <int BS, typename T>
+__device__ __forceinline__ void blk_msub(T (&c)[BS * BS], const T (&a)[BS * BS],
+                                         const T (&b)[BS * BS]) {
+#pragma unroll
+  for (int i = 0; i < BS; ++i)
+#pragma unroll
+    for (int j = 0; j < BS; ++j) {
+      T s = c[i * BS + j];
+#pragma unroll
+      for (int k = 0; k < BS; ++k) s -= a[i * BS + k] * b[k * BS + j];
+      c[i * BS + j] = s;
+    }
+}
+
+// Inverse by Gauss-Jordan elimination with partial pivoting inside the block.
+// Returns false for a zero or non-finite pivot.
+template <int BS, typename T>
+__device__ __forceinline__ bool blk_inv(T (&a)[BS * BS], T (&inv)[BS * BS]) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < BS * BS; ++i) inv[i] = (i % (BS + 1) == 0) ? T(1) : T(0);
+#pragma unroll
+  for (int c = 0; c < BS; ++c) {
+    int piv = c;
+    T best = a[c * BS + c] < 0 ? -a[c * BS + c] : a[c * BS + c];
+#pragma unroll
+    for (int r = c + 1; r < BS; ++r) {
+      T v = a[r * BS + c] < 0 ? -a[r * BS + c] : a[r * BS + c];
+      if (v > best) {
+        best = v;
+        piv = r;
+      }
+    }
+    if (!(best > T(0)) || !isfinite(best)) ok = false;
+    // swap rows c and piv (unrolled selects keep the arrays in registers)
+#pragma unroll
+    for (int r = c + 1; r < BS; ++r) {
+      if (r == piv) {
+#pragma unroll
+        for (int j = 0; j < BS; ++j) {
+          T t = a[c * BS + j];
+          a[c * BS + j] = a[r * BS + j];
+          a[r * BS + j] = t;
+          t = inv[c * BS + j];
+          inv[c * BS + j] = inv[r * BS + j];
+          inv[r * BS + j] = t;
+        }
+      }
+    }
+    T d = T(1) / a[c * BS + c];
+#pragma unroll
+    for (int j = 0; j < BS; ++j) {
+      a[c * BS + j] *= d;
+      inv[c * BS + j] *= d;
+    }
+#pragma unroll
+    for (int r = 0; r < BS; ++r) {
+      if (r == c) continue;
+      T f = a[r * BS + c];
+#pragma unroll
+      for (int j = 0; j < BS; ++j) {
+        a[r * BS + j] -= f * a[c * BS + j];
+        inv[r * BS + j] -= f * inv[c * BS + j];
+      }
+    }
+  }
+  return ok;
+}
+
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int G, unsigned gmask) {
+  for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, G);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// step A: mismatch + Jacobian, single phase (polar unknowns, 2x2 blocks)
+// ---------------------------------------------------------------------------
+
+// Rows: (P, Q) equations of bus i; columns: (delta, |V|) of bus j.  The slack
+// has no unknown and PV buses no |V| unknown: their rows become identity rows
+// and their columns zero, which keeps the system of Eq. 10 unchanged.
+template <typename TF>
+__device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, int gs,
+                                      double& nrm, TF* jcopy) {
+  const int B = w.B;
+  const size_t b = (size_t)i * B + gs;
+  const double2 Vi = ldc(w.V + b);
+  double2 I = make_double2(0.0, 0.0);
+  const double2* Y = reinterpret_cast<const double2*>(S.y_val);
+#pragma unroll 4
+  for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
+    const int j = S.y_col[e];
+    I = cadd(I, cmul(Y[e], ldc(w.V + (size_t)j * B + gs)));
+  }
+  w.I[b] = I;
+  const double vmi = __ldcg(w.vm + b);
+  const double2 Sc = cmulc(Vi, I);
+  const double pl = __ldcg(w.spec + b * 3), ql = __ldcg(w.spec + b * 3 + 1),
+               pg = __ldcg(w.spec + b * 3 + 2);
+  const double zp = S.zip[3 * i], zi = S.zip[3 * i + 1], zz = S.zip[3 * i + 2];
+  const double shape = zp + zi * vmi + zz * vmi * vmi;
+  const double dshape = zi + 2.0 * zz * vmi;
+  const int t = S.btype[i];
+  const double f0 = (t != PF_SLACK) ? (pg - pl * shape) - Sc.x : 0.0;
+  const double f1 = (t == PF_PQ) ? (S.q_gen[i] - ql * shape) - Sc.y : 0.0;
+  w.F[b * 2] = f0;
+  w.F[b * 2 + 1] = f1;
+  // max(|f0|, |f1|) on the bit patterns (NaN above +inf), no FP64 instruction
+  nrm = __longlong_as_double((long long)max(abs_bits(f0), abs_bits(f1)));
+
+  // The Jacobian is formed in the factor's precision TF (it only feeds the
+  // factorisation; the mismatch above and the refinement residual stay FP64).
+  // U = V / |V| per bus (kept by the update) avoids divisions; in FP32 the
+  // inputs come from FP32 copies of Ybus and of (U, |V|), so the loop does no
+  // FP64 work (FP64 instructions are scarce on this GPU).
+  // Conversions between FP64 and FP32 are as costly as FP64 arithmetic here,
+  // so the FP32 path takes V_i and U_i from the FP32 copy and converts only
+  // I_i and the two load-slope terms.
+  using T = TF;
+  constexpr bool F32 = sizeof(TF) == 4;
+  T vix, viy, uix, uiy, Ix, Iy, Scx, Scy;
+  if constexpr (F32) {
+    const float4 q = __ldcg(w.uvm32 + b);
+    uix = q.x;
+    uiy = q.y;
+    vix = q.z * q.x;
+    viy = q.z * q.y;
+    Ix = (T)I.x;
+    Iy = (T)I.y;
+    Scx = vix * Ix + viy * Iy;  // V_i conj(I_i)
+    Scy = viy * Ix - vix * Iy;
+  } else {
+    const double2 Ui = ldc(w.U + b);
+    vix = (T)Vi.x;
+    viy = (T)Vi.y;
+    uix = (T)Ui.x;
+    uiy = (T)Ui.y;
+    Ix = (T)I.x;
+    Iy = (T)I.y;
+    Scx = (T)Sc.x;
+    Scy = (T)Sc.y;
+  }
+  TF* lu = reinterpret_cast<TF*>(w.lu);
+#pragma unroll 2
+  for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
+    const int j = S.lu_col[e];
+    const int yi = S.lu2y[e];
+    T j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+    if (yi >= 0) {
+      T yx, yy;
+      if constexpr (F32) {
+        const float2 y32 = S.y32[yi];
+        yx = y32.x;
+        yy = y32.y;
+      } else {
+        yx = (T)Y[yi].x;
+        yy = (T)Y[yi].y;
+      }
+      if (j != i) {
+        const int tj = S.btype[j];
+        if (t != PF_SLACK && tj != PF_SLACK) {
+          const size_t bj = (size_t)j * B + gs;
+          // dS_i/d|V_j| = V_i conj(Y_ij U_j); dS_i/d delta_j = -j |V_j| dS_i/d|V_j|
+          T ux, uy, vmj;
+          if constexpr (F32) {
+            const float4 q = __ldcg(w.uvm32 + bj);  // (Re U, Im U, |V|, 0)
+            ux = q.x;
+            uy = q.y;
+            vmj = q.z;
+          } else {
+            const double2 Uj = ldc(w.U + bj);
+            ux = (T)Uj.x;
+            uy = (T)Uj.y;
+            vmj = (T)__ldcg(w.vm + bj);
+          }
+          const T yux = yx * ux - yy * uy, yuy = yx * uy + yy * ux;
+          const T cx = vix * yux + viy * yuy, cy = viy * yux - vix * yuy;
+          j00 = vmj * cy;
+          j10 = -vmj * cx;
+          if (tj == PF_PQ) {
+            j01 = cx;
+            j11 = cy;
+          }
+          if (t == PF_PV) j10 = j11 = T(0);
+        }
+      } else if (t == PF_SLACK) {
+        j00 = j11 = T(1);
+      } else {
+        // dS_i/d delta_i = j (S_i - V_i conj(Y_ii V_i));
+        // dS_i/d|V_i| = U_i conj(I_i + Y_ii V_i), minus the load's slope
+        const T yvx = yx * vix - yy * viy, yvy = yx * viy + yy * vix;  // Y_ii V_i
+        const T dx = vix * yvx + viy * yvy, dy = viy * yvx - vix * yvy;
+        const T ax = Ix + yvx, ay = Iy + yvy;
+        const T ex = uix * ax + uiy * ay, ey = uiy * ax - uix * ay;
+        j00 = -(Scy - dy);
+        j10 = Scx - dx;
+        j01 = ex + (T)(pl * dshape);
+        j11 = ey + (T)(ql * dshape);
+        if (t == PF_PV) {
+          j01 = T(0);
+          j10 = T(0);
+          j11 = T(1);
+        }
+      }
+    }
+    TF blk[4] = {j00, j01, j10, j11};
+    blk_store<2>(lu + ((size_t)e * B + gs) * 4, blk);
+    if (jcopy) blk_store<2>(jcopy + ((size_t)e * B + gs) * 4, blk);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// step A: current mismatch + Jacobian, three phase (6x6 blocks)
+// ---------------------------------------------------------------------------
+
+// Derivatives of the specified current I = conj(S(m)) V / m^2 (Eq. 17 with
+// the ZIP load of Eq. 14-15, m = |V|) with respect to Re V and Im V, formed
+// in complex arithmetic: dI/dVr = [conj(S') (Vr/m) V + conj(S)] / m^2
+// - 2 conj(S) V Vr / m^4 and dI/dVi likewise with j conj(S).
+__device__ __forceinline__ void load_slope(double2 V, double pl, double ql, double zp,
+                                           double zi, double zz, double2& Isp,
+                                           double2& dIdr, double2& dIdi) {
+  const double m2 = V.x * V.x + V.y * V.y;
+  const double m = sqrt(m2);
+  const double shape = zp + zi * m + zz * m2;
+  const double dshape = zi + 2.0 * zz * m;
+  const double2 cS = make_double2(-pl * shape, ql * shape);     // conj(S)
+  const double2 cSp = make_double2(-pl * dshape, ql * dshape);  // conj(dS/dm)
+  const double inv2 = 1.0 / m2;                                 // the one division
+  const double2 cSV = cmul(cS, V);
+  Isp = cscale(cSV, inv2);
+  const double2 base = cscale(cmul(cSp, V), inv2 * inv2 * m);   // / m^3
+  dIdr = csub(cadd(cscale(base, V.x), cscale(cS, inv2)), cscale(cSV, 2.0 * V.x * inv2 * inv2));
+  const double2 jcS = make_double2(-cS.y, cS.x);
+  dIdi = csub(cadd(cscale(base, V.y), cscale(jcS, inv2)), cscale(cSV, 2.0 * V.y * inv2 * inv2));
+}
+
+template <typename TF>
+__device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, int gs,
+                                      double& nrm, TF* jcopy) {
+  const int B = w.B;
+  const size_t b = (size_t)i * B + gs;
+  const int mask = S.btype[i] & 7;
+  const bool src = (S.btype[i] & 8) != 0;
+  double2 Vi[3], I[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Vi[a] = ldc(w.V + b * 3 + a);
+    I[a] = make_double2(0.0, 0.0);
+  }
+  const double2* Y = reinterpret_cast<const double2*>(S.y_val);
+  for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
+    const size_t bj = ((size_t)S.y_col[e] * B + gs) * 3;
+    double2 Vj[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Vj[c] = ldc(w.V + bj + c);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) I[a] = cadd(I[a], cmul(Y[(size_t)e * 9 + a * 3 + c], Vj[c]));
+  }
+  nrm = 0.0;
+  double adj[12];  // a[3], b[3], c[3], d[3] of Eq. 23
+  const double zp = S.zip[3 * i], zi = S.zip[3 * i + 1], zz = S.zip[3 * i + 2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    w.I[b * 3 + a] = I[a];
+    const bool freea = ((mask >> a) & 1) && !src;
+    double fim = 0.0, fre = 0.0;
+    adj[a] = adj[3 + a] = adj[6 + a] = adj[9 + a] = 0.0;
+    if (freea) {
+      const double pl = __ldcg(w.spec + b * 6 + a), ql = __ldcg(w.spec + b * 6 + 3 + a);
+      double2 Isp, dr, di;
+      load_slope(Vi[a], pl, ql, zp, zi, zz, Isp, dr, di);
+      const double2 dI = csub(Isp, I[a]);
+      fim = dI.y;
+      fre = dI.x;
+      const double2 dS = cmulc(Vi[a], dI);
+      double v = fmax(fabs(dS.x), fabs(dS.y));
+      if (!isfinite(v)) v = __longlong_as_double(0x7ff8000000000000ULL);
+      nrm = fmax(nrm, v);
+      adj[a] = dr.y;      // a = d Im I_sp / d Vr
+      adj[3 + a] = di.y;  // b = d Im I_sp / d Vi
+      adj[6 + a] = dr.x;  // c = d Re I_sp / d Vr
+      adj[9 + a] = di.x;  // d = d Re I_sp / d Vi
+    }
+    w.F[b * 6 + a] = fim;
+    w.F[b * 6 + 3 + a] = fre;
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) w.abcd[b * 12 + k] = adj[k];
+
+  TF* lu = reinterpret_cast<TF*>(w.lu);
+  for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
+    const int j = S.lu_col[e];
+    const int yi = S.lu2y[e];
+    TF blk[36];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) blk[k] = TF(0);
+    if (yi >= 0) {
+      const int maskj = S.btype[j] & 7;
+      const bool srcj = (S.btype[j] & 8) != 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const bool fa = ((mask >> a) & 1) && !src;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const bool fc = ((maskj >> c) & 1) && !srcj;
+          if (fa && fc) {
+            const double2 y = Y[(size_t)yi * 9 + a * 3 + c];
+            // Eq. 21: rows (Im, Re) of the current, columns (Re, Im) of V
+            blk[a * 6 + c] = (TF)y.y;
+            blk[a * 6 + 3 + c] = (TF)y.x;
+            blk[(3 + a) * 6 + c] = (TF)y.x;
+            blk[(3 + a) * 6 + 3 + c] = (TF)(-y.y);
+          }
+        }
+      }
+      if (j == i) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const bool fa = ((mask >> a) & 1) && !src;
+          if (fa) {  // Eq. 23
+            blk[a * 6 + a] -= (TF)adj[a];
+            blk[a * 6 + 3 + a] -= (TF)adj[3 + a];
+            blk[(3 + a) * 6 + a] -= (TF)adj[6 + a];
+            blk[(3 + a) * 6 + 3 + a] -= (TF)adj[9 + a];
+          } else {
+            blk[a * 6 + a] = TF(1);
+            blk[(3 + a) * 6 + 3 + a] = TF(1);
+          }
+        }
+      }
+    }
+    blk_store<6>(lu + ((size_t)e * B + gs) * 36, blk);
+    if (jcopy) blk_store<6>(jcopy + ((size_t)e * B + gs) * 36, blk);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// cluster-wide schedule helpers
+// ---------------------------------------------------------------------------
+
+struct Team {
+  int tid;       // thread index within the cluster
+  int nthr;      // threads in the cluster (a multiple of S)
+  int S;         // scenario slots per cluster (a power of two)
+  int s0;        // first scenario of the cluster
+  int ns;        // scenarios of the cluster (<= S)
+  unsigned act;  // active scenarios (bit s = scenario s0 + s)
+};
+
+// Every thread serves the fixed scenario slot tid % S.  Runs fn(item, gs)
+// for items [0, count) and every active scenario, then a cluster barrier.
+template <bool CL, class Fn>
+__device__ void run_items(const Team& tm, int count, Fn fn) {
+  const int s = tm.tid & (tm.S - 1);
+  if (s < tm.ns && ((tm.act >> s) & 1u)) {
+    for (int it = tm.tid / tm.S; it < count; it += tm.nthr / tm.S) fn(it, tm.s0 + s);
+  }
+  csync<CL>();
+}
+
+// Runs fn(i, gs) for every row and active scenario, then a cluster barrier.
+template <bool CL, class Fn>
+__device__ void run_rows(const Team& tm, int n, Fn fn) {
+  run_items<CL>(tm, n, fn);
+}
+
+// Like run_rows for an fn that returns a non-negative value per row: the
+// largest value of each scenario (NaN above +inf) goes to base[gs], with one
+// atomic per warp and scenario slot instead of one per row.
+template <bool CL, class Fn>
+__device__ void run_rows_max(const Team& tm, int n, unsigned long long* base, Fn fn) {
+  const int s = tm.tid & (tm.S - 1);
+  unsigned long long m = 0ull;
+  if (s < tm.ns && ((tm.act >> s) & 1u)) {
+    for (int it = tm.tid / tm.S; it < n; it += tm.nthr / tm.S) {
+      m = max(m, abs_bits(fn(it, tm.s0 + s)));
+    }
+  }
+  // the lanes of a warp with the same slot sit S apart
+  for (int off = tm.S; off < 32; off <<= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((int)(threadIdx.x & 31) < tm.S && m != 0ull) atomicMax(base + tm.s0 + s, m);
+  csync<CL>();
+}
+
+// ---------------------------------------------------------------------------
+// level sweeps with prefetch of the next level's static data
+// ---------------------------------------------------------------------------
+
+// A thread's share of one row of a triangular sweep, loaded ahead: the row,
+// its first entry for this lane, that entry's column and (2x2 blocks) value,
+// and for the backward sweep the inverse diagonal block.  Factor values and
+// indices do not change during the sweeps, so all of this is loaded before
+// the previous level's barrier; only the solve vector is read after it.
+template <int BS, typename TF>
+struct RowPref {
+  static constexpr int NV = (BS == 2) ? 4 : 1;
+  int i, p, pe, k;
+  TF v[NV], d[NV];
+};
+
+template <int BS, typename TF, bool FWD>
+__device__ __forceinline__ void sweep_pref(const DevSys& S, const DevWork& w, const int4* rec,
+                                           int pos, bool have, int gs, int lane,
+                                           RowPref<BS, TF>& P) {
+  P.i = -1;
+  P.p = P.pe = 0;
+  if (!have) return;
+  const int4 q = __ldg(rec + pos);
+  P.i = q.x;
+  P.p = q.y + lane;
+  P.pe = q.z;
+  const TF* lu = reinterpret_cast<const TF*>(w.lu);
+  if (P.p < P.pe) {
+    P.k = __ldg(S.lu_col + P.p);
+    if constexpr (BS == 2) blk_load<2>(lu + ((size_t)P.p * w.B + gs) * 4, P.v);
+  }
+  if constexpr (!FWD && BS == 2) {
+    if (lane == 0) blk_load<2>(reinterpret_cast<const TF*>(w.uinv) + ((size_t)P.i * w.B + gs) * 4, P.d);
+  }
+}
+
+// Forward: y_i -= sum_k L_ik y_k.  Backward: y_i = U_ii^-1 (y_i - sum_j U_ij y_j).
+template <int BS, typename TF, bool FWD>
+__device__ __forceinline__ void sweep_row(const DevSys& S, const DevWork& w, TF* y,
+                                          const RowPref<BS, TF>& P, int gs, int lane, int G,
+                                          unsigned gmask) {
+  constexpr int BB = BS * BS;
+  const int B = w.B;
+  const TF* lu = reinterpret_cast<const TF*>(w.lu);
+  TF acc[BS];
+#pragma unroll
+  for (int c = 0; c < BS; ++c) acc[c] = TF(0);
+  for (int p = P.p; p < P.pe; p += G) {
+    TF L[BB];
+    int k;
+    if (p == P.p) {
+      k = P.k;
+      if constexpr (BS == 2) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) L[t] = P.v[t];
+      } else {
+        blk_load<BS>(lu + ((size_t)p * B + gs) * BB, L);
+      }
+    } else {
+      k = __ldg(S.lu_col + p);
+      blk_load<BS>(lu + ((size_t)p * B + gs) * BB, L);
+    }
+    const size_t bk = ((size_t)k * B + gs) * BS;
+    TF yk[BS];
+#pragma unroll
+    for (int c = 0; c < BS; ++c) yk[c] = y[bk + c];
+#pragma unroll
+    for (int r = 0; r < BS; ++r)
+#pragma unroll
+      for (int c = 0; c < BS; ++c) acc[r] += L[r * BS + c] * yk[c];
+  }
+  if (G > 1) {
+#pragma unroll
+    for (int c = 0; c < BS; ++c) acc[c] = group_sum(acc[c], G, gmask);
+  }
+  if (lane == 0) {
+    const size_t bi = ((size_t)P.i * B + gs) * BS;
+    if constexpr (FWD) {
+#pragma unroll
+      for (int c = 0; c < BS; ++c) y[bi + c] = y[bi + c] - acc[c];
+    } else {
+      TF t[BS], D[BB];
+#pragma unroll
+      for (int c = 0; c < BS; ++c) t[c] = y[bi + c] - acc[c];
+      if constexpr (BS == 2) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) D[q] = P.d[q];
+      } else {
+        blk_load<BS>(reinterpret_cast<const TF*>(w.uinv) + ((size_t)P.i * B + gs) * BB, D);
+      }
+#pragma unroll
+      for (int r = 0; r < BS; ++r) {
+        TF sacc = TF(0);
+#pragma unroll
+        for (int c = 0; c < BS; ++c) sacc += D[r * BS + c] * t[c];
+        y[bi + r] = sacc;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched triangular sweeps (one CTA, S scenarios per CTA)
+// ---------------------------------------------------------------------------
+
+// A thread's share of one row of a batched sweep, loaded before any result of
+// its level is stored: the row, this lane's first entry (column and, for 2x2
+// blocks, value) and, for lane 0, the row's own right-hand side and (backward,
+// 2x2 blocks) its inverse diagonal block.
+template <int BS, typename TF>
+struct BRow {
+  static constexpr int NV = (BS == 2) ? 4 : 1;
+  int i, p, pe, k;
+  TF v[NV], d[NV], own[BS];
+};
+
+// Pointers and sizes of one batched sweep.
+template <typename TF>
+struct BSweep {
+  const TF* lu;        // factor values [entry][scenario][BS x BS]
+  const TF* uinv;      // inverse diagonal blocks [row][scenario][BS x BS]
+  const int* col;      // factor columns
+  TF* y;               // solve vector [row][scenario][BS]
+  const double* rhs;   // forward: right-hand side (else y holds it)
+  double* dx;          // backward: also written here (else only y)
+  int accumulate;      // backward: dx += y instead of dx = y
+  int B;
+  const int* lev_ptr;  // level schedule and its row records
+  const int4* rec;
+  int nlev;
+  const int8_t* gsz;   // lanes per row for each level
+  TF* red;             // shared memory for the partial sums of lanes
+};
+
+template <int BS, typename TF, bool FWD>
+__device__ __forceinline__ void brow_load(BRow<BS, TF>& P, const BSweep<TF>& a, int pos, bool have,
+                                          int lane, int gs) {
+  P.i = -1;
+  P.p = P.pe = 0;
+  if (!have) return;
+  const int4 q = __ldg(a.rec + pos);
+  P.i = q.x;
+  P.p = q.y + lane;
+  P.pe = q.z;
+  if (P.p < P.pe) {
+    P.k = __ldg(a.col + P.p);
+    if constexpr (BS == 2) blk_load<2>(a.lu + ((size_t)P.p * a.B + gs) * 4, P.v);
+  }
+  if (lane == 0) {
+    const size_t bi = ((size_t)P.i * a.B + gs) * BS;
+#pragma unroll
+    for (int c = 0; c < BS; ++c) P.own[c] = (FWD && a.rhs) ? (TF)__ldcg(a.rhs + bi + c) : a.y[bi + c];
+    if constexpr (!FWD && BS == 2) blk_load<2>(a.uinv + ((size_t)P.i * a.B + gs) * 4, P.d);
+  }
+}
+
+// Entry p of a row: its column and block (from the row's prefetch when p is
+// the lane's first entry).
+template <int BS, typename TF>
+__device__ __forceinline__ void brow_entry(const BRow<BS, TF>& P, const BSweep<TF>& a, int p,
+                                           int gs, int& k, TF (&L)[BS * BS]) {
+  if (BS == 2 && p == P.p) {
+    k = P.k;
+#pragma unroll
+    for (int t = 0; t < BS * BS; ++t) L[t] = P.v[(BS == 2) ? t : 0];
+  } else {
+    k = (p == P.p) ? P.k : __ldg(a.col + p);
+    blk_load<BS>(a.lu + ((size_t)p * a.B + gs) * BS * BS, L);
+  }
+}
+
+// Forward: y_i = b_i - acc.  Backward: y_i = U_ii^-1 (y_i - acc), and dx.
+template <int BS, typename TF, bool FWD>
+__device__ __forceinline__ void brow_finish(const BRow<BS, TF>& P, const BSweep<TF>& a, int gs,
+                                            const TF (&acc)[BS]) {
+  constexpr int BB = BS * BS;
+  const size_t bi = ((size_t)P.i * a.B + gs) * BS;
+  TF t[BS];
+#pragma unroll
+  for (int c = 0; c < BS; ++c) t[c] = P.own[c] - acc[c];
+  if constexpr (!FWD) {
+    TF D[BB];
+    if constexpr (BS == 2) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) D[q] = P.d[q];
+    } else {
+      blk_load<BS>(a.uinv + ((size_t)P.i * a.B + gs) * BB, D);
+    }
+    TF u[BS];
+#pragma unroll
+    for (int r = 0; r < BS; ++r) {
+      u[r] = TF(0);
+#pragma unroll
+      for (int c = 0; c < BS; ++c) u[r] += D[r * BS + c] * t[c];
+    }
+#pragma unroll
+    for (int c = 0; c < BS; ++c) t[c] = u[c];
+  }
+#pragma unroll
+  for (int c = 0; c < BS; ++c) a.y[bi + c] = t[c];
+  if (!FWD && a.dx) {
+#pragma unroll
+    for (int c = 0; c < BS; ++c)
+      a.dx[bi + c] = a.accumulate ? __ldcg(a.dx + bi + c) + (double)t[c] : (double)t[c];
+  }
+}
+
+// Batched triangular sweep.  Every thread serves the scenario slot tid % S;
+// the nthr / S row slots take a level's rows with G = gsz[l] lanes per row
+// (G from the level's width and its longest row), so the long rows near the
+// top of the elimination tree are split across lanes instead of being walked
+// by one thread.  Lanes in one warp are summed with shuffles, lanes in
+// different warps through shared memory, in a fixed order.  Levels with one
+// lane per row take R rows at a time and issue all their loads before any
+// store.  Each thread's first row of level l+1 is loaded while level l runs.
+// Not inlined: it has the registers to itself.
+template <int BS, typename TF, bool FWD>
+__device__ __noinline__ void sweep_batch(const BSweep<TF> a, const Team tm) {
+  constexpr int BB = BS * BS;
+  // rows in flight per thread: more than one measured no faster (the extra
+  // registers spill)
+  constexpr int R = 1;
+  const int NS = tm.S;
+  const int slot = tm.tid & (NS - 1);
+  const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
+  const int gs = tm.s0 + slot;
+  const int q = tm.tid / NS, nq = tm.nthr / NS;
+  auto pref = [&](int l, BRow<BS, TF>& P) {
+    const int G = a.gsz[l], base = a.lev_ptr[l], width = a.lev_ptr[l + 1] - base;
+    const int group = q / G;
+    brow_load<BS, TF, FWD>(P, a, base + group, on && group < width, q & (G - 1), gs);
+  };
+  BRow<BS, TF> cur, nxt;
+  if (a.nlev > 0) pref(0, cur);
+  for (int l = 0; l < a.nlev; ++l) {
+    const int G = a.gsz[l], base = a.lev_ptr[l], width = a.lev_ptr[l + 1] - base;
+    if (l + 1 < a.nlev) pref(l + 1, nxt);
+    if (G == 1) {
+      if (on) {
+        for (int r0 = q; r0 < width; r0 += R * nq) {
+          BRow<BS, TF> P[R];
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            const int r = r0 + u * nq;
+            if (u == 0 && r0 == q) P[0] = cur;
+            else brow_load<BS, TF, FWD>(P[u], a, base + r, r < width, 0, gs);
+          }
+          TF acc[R][BS];
+#pragma unroll
+          for (int u = 0; u < R; ++u)
+#pragma unroll
+            for (int c = 0; c < BS; ++c) acc[u][c] = TF(0);
+          for (int e = 0;; ++e) {
+            bool any = false;
+            int k[R];
+            TF L[R][BB];
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+              if (P[u].p + e < P[u].pe) {
+                any = true;
+                brow_entry<BS, TF>(P[u], a, P[u].p + e, gs, k[u], L[u]);
+              }
+            }
+            if (!any) break;
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+              if (P[u].p + e < P[u].pe) {
+                const size_t bk = ((size_t)k[u] * a.B + gs) * BS;
+#pragma unroll
+                for (int rr = 0; rr < BS; ++rr)
+#pragma unroll
+                  for (int c = 0; c < BS; ++c) acc[u][rr] += L[u][rr * BS + c] * a.y[bk + c];
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < R; ++u)
+            if (P[u].i >= 0) brow_finish<BS, TF, FWD>(P[u], a, gs, acc[u]);
+        }
+      }
+    } else {
+      // one row per group of G lanes (G * width <= nq)
+      const int lane = q & (G - 1), group = q / G;
+      TF acc[BS];
+#pragma unroll
+      for (int c = 0; c < BS; ++c) acc[c] = TF(0);
+      for (int pp = cur.p; pp < cur.pe; pp += G) {
+        int k;
+        TF L[BB];
+        brow_entry<BS, TF>(cur, a, pp, gs, k, L);
+        const size_t bk = ((size_t)k * a.B + gs) * BS;
+#pragma unroll
+        for (int rr = 0; rr < BS; ++rr)
+#pragma unroll
+          for (int c = 0; c < BS; ++c) acc[rr] += L[rr * BS + c] * a.y[bk + c];
+      }
+      // lanes of one (row, slot) sit S threads apart
+      const int GW = min(G, 32 / NS);
+      for (int off = NS; off < NS * GW; off <<= 1) {
+#pragma unroll
+        for (int c = 0; c < BS; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+      }
+      const bool row = cur.i >= 0;
+      if (G > GW) {
+        const int NW = G / GW;
+        if (row && (lane & (GW - 1)) == 0) {
+#pragma unroll
+          for (int c = 0; c < BS; ++c) a.red[((group * NW + lane / GW) * NS + slot) * BS + c] = acc[c];
+        }
+        __syncthreads();
+        if (row && lane == 0) {
+#pragma unroll
+          for (int c = 0; c < BS; ++c) acc[c] = TF(0);
+          for (int wp = 0; wp < NW; ++wp) {
+#pragma unroll
+            for (int c = 0; c < BS; ++c) acc[c] += a.red[((group * NW + wp) * NS + slot) * BS + c];
+          }
+        }
+      }
+      if (row && lane == 0) brow_finish<BS, TF, FWD>(cur, a, gs, acc);
+    }
+    __syncthreads();
+    cur = nxt;
+  }
+}
+
+// One triangular sweep over all levels.  A single-scenario team gives each
+// row gsz[l] lanes; a batch team gives each (row, scenario) one thread.  The
+// first row of each group for level l+1 is prefetched while level l runs.
+template <int BS, typename TF, bool FWD, bool CL>
+__device__ void sweep(const DevSys& S, const DevWork& w, TF* y, const Team& tm,
+                      const int* lev_ptr, const int4* rec, int nlev, const int8_t* gsz,
+                      TF* red) {
+  if constexpr (!CL) {
+    if (tm.S > 1) {
+      BSweep<TF> a;
+      a.lu = reinterpret_cast<const TF*>(w.lu);
+      a.uinv = reinterpret_cast<const TF*>(w.uinv);
+      a.col = S.lu_col;
+      a.y = y;
+      a.rhs = nullptr;
+      a.dx = nullptr;
+      a.accumulate = 0;
+      a.B = w.B;
+      a.lev_ptr = lev_ptr;
+      a.rec = rec;
+      a.nlev = nlev;
+      a.gsz = gsz;
+      a.red = red;
+      sweep_batch<BS, TF, FWD>(a, tm);
+      return;
+    }
+  }
+  const bool single = (tm.S == 1);
+  const int slot = single ? 0 : (tm.tid & (tm.S - 1));
+  const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
+  const int gs = tm.s0 + slot;
+  auto geom = [&](int l, int& G, int& group, int& lane, int& ngroups) {
+    if (single) {
+      G = gsz[l];
+      group = tm.tid / G;
+      lane = tm.tid % G;
+      ngroups = tm.nthr / G;
+    } else {
+      G = 1;
+      group = tm.tid / tm.S;
+      lane = 0;
+      ngroups = tm.nthr / tm.S;
+    }
+  };
+  RowPref<BS, TF> cur, nxt;
+  {
+    int G, group, lane, ngroups;
+    geom(0, G, group, lane, ngroups);
+    const int base = lev_ptr[0], width = lev_ptr[1] - base;
+    sweep_pref<BS, TF, FWD>(S, w, rec, base + group, on && nlev > 0 && group < width, gs, lane, cur);
+  }
+  for (int l = 0; l < nlev; ++l) {
+    int G, group, lane, ngroups;
+    geom(l, G, group, lane, ngroups);
+    const int base = lev_ptr[l], width = lev_ptr[l + 1] - base;
+    if (l + 1 < nlev) {
+      int G2, group2, lane2, ng2;
+      geom(l + 1, G2, group2, lane2, ng2);
+      const int b2 = lev_ptr[l + 1], w2 = lev_ptr[l + 2] - b2;
+      sweep_pref<BS, TF, FWD>(S, w, rec, b2 + group2, on && group2 < w2, gs, lane2, nxt);
+    }
+    if (on) {
+      const unsigned gmask =
+          (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+      if (group < width) sweep_row<BS, TF, FWD>(S, w, y, cur, gs, lane, G, gmask);
+      for (int r = group + ngroups; r < width; r += ngroups) {
+        RowPref<BS, TF> P;
+        sweep_pref<BS, TF, FWD>(S, w, rec, base + r, true, gs, lane, P);
+        sweep_row<BS, TF, FWD>(S, w, y, P, gs, lane, G, gmask);
+      }
+    }
+    csync<CL>();
+    cur = nxt;
+  }
+}
+
+// Fan-out (right-looking) block LU of levels [l0, l1), L with identity
+// diagonal blocks.  Level l, step 1: every pivot k of the level inverts its
+// diagonal block (U_kk^-1 is stored) and every L entry (i, k) of the pivot
+// columns becomes L_ik = A_ik U_kk^-1 -- all these entries received their
+// last update at an earlier level.  Step 2: every entry (i, j) the level's
+// pivots touch gathers A_ij -= sum_k L_ik U_kj in a fixed order (so results
+// are deterministic).  A thread takes R items of a step at a time so that
+// their loads overlap; the first record of each step is loaded before the
+// barrier that precedes the step.  Not inlined: it has the registers to
+// itself.
+template <typename TF>
+struct FactorArgs {
+  TF* lu;
+  TF* uinv;
+  int* flag;
+  int B;
+  const int* fac_ptr;
+  const int4* fac_rec;
+  const int* tgt_ptr;
+  const int4* tgt_rec;
+  const int2* con;
+  unsigned char* ring;  // shared memory for factor_pipe (batches of 2x2 blocks)
+};
+
+template <int BS, typename TF, bool CL>
+__device__ __noinline__ void factor_run(const FactorArgs<TF> S, const Team tm, int l0, int l1) {
+  if (l0 >= l1) return;
+  constexpr int BB = BS * BS;
+  // items in flight per thread: more than one measured no faster (the
+  // extra registers spill)
+  constexpr int R = 1;
+  const int slot = tm.tid & (tm.S - 1);
+  const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
+  const int gs = tm.s0 + slot;
+  const int first = tm.tid / tm.S, stride = tm.nthr / tm.S;
+  TF* lu = S.lu;
+  auto blk = [&](int e) { return lu + ((size_t)e * S.B + gs) * BB; };
+  const int4 none = make_int4(-1, 0, 0, -1);
+  auto fac_first = [&](int l) {
+    const int f0 = S.fac_ptr[l], nf = S.fac_ptr[l + 1] - f0;
+    return (on && first < nf) ? __ldg(S.fac_rec + f0 + first) : none;
+  };
+  auto tgt_first = [&](int l) {
+    const int t0 = S.tgt_ptr[l], nt = S.tgt_ptr[l + 1] - t0;
+    return (on && first < nt) ? __ldg(S.tgt_rec + t0 + first) : none;
+  };
+  int4 fr = fac_first(l0);
+  for (int l = l0; l < l1; ++l) {
+    const int4 tr = tgt_first(l);  // for step 2, loaded ahead
+    // step 1: r = {e, k, diag(k)}: U_kk^-1 for the diagonal, else L_ik = A_ik U_kk^-1
+    if (on) {
+      const int f0 = S.fac_ptr[l], nf = S.fac_ptr[l + 1] - f0;
+      for (int t = first; t < nf; t += R * stride) {
+        int4 r[R];
+        TF d[R][BB], a[R][BB];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          const int tu = t + u * stride;
+          r[u] = (u == 0 && t == first) ? fr : (tu < nf ? __ldg(S.fac_rec + f0 + tu) : none);
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          if (r[u].x >= 0) {
+            blk_load<BS>(blk(r[u].z), d[u]);
+            if (r[u].x != r[u].z) blk_load<BS>(blk(r[u].x), a[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          if (r[u].x < 0) continue;
+          TF di[BB];
+          const bool ok = blk_inv<BS>(d[u], di);
+          if (r[u].x == r[u].z) {
+            if (!ok) S.flag[gs] = 1;
+            blk_store<BS>(S.uinv + ((size_t)r[u].y * S.B + gs) * BB, di);
+          } else {
+            TF lk[BB];
+            blk_mul<BS>(a[u], di, lk);
+            blk_store<BS>(blk(r[u].x), lk);
+          }
+        }
+      }
+    }
+    csync<CL>();
+    fr = (l + 1 < l1) ? fac_first(l + 1) : none;  // for the next level's step 1
+    // step 2: r = {e, L entry, U entry, rest}: A_e -= L U, then the rest
+    const int t0 = S.tgt_ptr[l], nt = S.tgt_ptr[l + 1] - t0;
+    if (nt > 0) {
+      if (on) {
+        for (int t = first; t < nt; t += R * stride) {
+          int4 r[R];
+          TF c[R][BB], lv[R][BB], uv[R][BB];
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            const int tu = t + u * stride;
+            r[u] = (u == 0 && t == first) ? tr : (tu < nt ? __ldg(S.tgt_rec + t0 + tu) : none);
+          }
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            if (r[u].x >= 0) {
+              blk_load<BS>(blk(r[u].x), c[u]);
+              blk_load<BS>(blk(r[u].y), lv[u]);
+              blk_load<BS>(blk(r[u].z), uv[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            if (r[u].x < 0) continue;
+            blk_msub<BS>(c[u], lv[u], uv[u]);
+            if (r[u].w >= 0) {
+              for (int q = r[u].w;; ++q) {
+                const int2 cq = __ldg(S.con + q);
+                if (cq.x < 0) break;
+                TF l2[BB], u2[BB];
+                blk_load<BS>(blk(cq.x), l2);
+                blk_load<BS>(blk(cq.y), u2);
+                blk_msub<BS>(c[u], l2, u2);
+              }
+            }
+            blk_store<BS>(blk(r[u].x), c[u]);
+          }
+        }
+      }
+      csync<CL>();
+    }
+  }
+}
+
+// Depth of factor_pipe's per-thread ring of items (2x2 blocks).
+template <typename TF>
+struct FactorPipe {
+  static constexpr int D = sizeof(TF) == 4 ? 4 : 2;  // items in flight
+  static constexpr int NV = 4 * (int)sizeof(TF) / 16;  // 16-byte pieces per block
+  // bytes per thread: D slots of three blocks and 2 D records
+  static constexpr int bytes = D * 3 * NV * 16 + 2 * D * 16;
+};
+
+// The factorisation of factor_run for a batch of 2x2 blocks (one CTA), with
+// its gathers staged through shared memory: every thread keeps the blocks of
+// its next D items and the records of the D after those in flight by
+// cp.async while it computes the current item, so the wide levels are not
+// bound by one load latency per item.  Shared memory is laid out [piece]
+// [thread] in 16-byte units so that a warp's accesses do not conflict.  The
+// next step's first records are requested before each barrier.
+template <typename TF>
+__device__ __noinline__ void factor_pipe(const FactorArgs<TF> S, const Team tm, int l0, int l1) {
+  if (l0 >= l1) return;
+  using P = FactorPipe<TF>;
+  constexpr int D = P::D, NV = P::NV, BB = 4;
+  const int slot = tm.tid & (tm.S - 1);
+  const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
+  const int gs = tm.s0 + slot;
+  const int first = tm.tid / tm.S, stride = tm.nthr / tm.S;
+  const int T = blockDim.x;
+  uint4* R = reinterpret_cast<uint4*>(S.ring);
+  // block c (0..2) of item slot d, piece v; record slot m (0..2D-1)
+  auto blk_at = [&](int d, int c, int v) { return R + ((d * 3 + c) * NV + v) * T + threadIdx.x; };
+  auto rec_at = [&](int m) { return R + (D * 3 * NV + m) * T + threadIdx.x; };
+  auto gblk = [&](int e) { return S.lu + ((size_t)e * S.B + gs) * BB; };
+  auto fetch_blk = [&](int d, int c, int e) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cp16(blk_at(d, c, v), gblk(e) + v * (16 / sizeof(TF)));
+  };
+  auto read_blk = [&](int d, int c, TF (&a)[BB]) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const uint4 q = *blk_at(d, c, v);
+      const TF* t = reinterpret_cast<const TF*>(&q);
+#pragma unroll
+      for (int k = 0; k < 16 / (int)sizeof(TF); ++k) a[v * (16 / sizeof(TF)) + k] = t[k];
+    }
+  };
+  // items of one step: records rec[base + first + k * stride], k < K
+  auto count = [&](int n) { return (on && first < n) ? (n - first + stride - 1) / stride : 0; };
+  auto fetch_recs = [&](const int4* rec, int K) {
+    for (int k = 0; k < D && k < K; ++k) cp16(rec_at(k), rec + first + k * stride);
+    cp_commit();
+  };
+  // one step: fetch(d, r) requests the blocks of record r into item slot d,
+  // work(d, r) computes the item and stores its result
+  auto step = [&](const int4* rec, int K, auto fetch, auto work) {
+    cp_wait<0>();  // this step's first records
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (k < K) {
+        const int4 r = *reinterpret_cast<const int4*>(rec_at(k));
+        fetch(k, r);
+        if (k + D < K) cp16(rec_at(k + D), rec + first + (k + D) * stride);
+      }
+      cp_commit();
+    }
+    for (int k = 0; k < K; ++k) {
+      cp_wait<D - 1>();
+      const int4 r = *reinterpret_cast<const int4*>(rec_at(k % (2 * D)));
+      work(k % D, r);
+      const int k2 = k + D;
+      if (k2 < K) {
+        const int4 r2 = *reinterpret_cast<const int4*>(rec_at(k2 % (2 * D)));
+        fetch(k % D, r2);
+        if (k2 + D < K) cp16(rec_at(k % (2 * D)), rec + first + (k2 + D) * stride);
+      }
+      cp_commit();
+    }
+  };
+  // step 1: r = {e, k, diag(k)}: U_kk^-1 for the diagonal, else L_ik = A_ik U_kk^-1
+  auto fetch1 = [&](int d, int4 r) {
+    fetch_blk(d, 0, r.z);
+    if (r.x != r.z) fetch_blk(d, 1, r.x);
+  };
+  auto work1 = [&](int d, int4 r) {
+    TF a[BB], di[BB];
+    read_blk(d, 0, a);
+    const bool ok = blk_inv<2>(a, di);
+    if (r.x == r.z) {
+      if (!ok) S.flag[gs] = 1;
+      blk_store<2>(S.uinv + ((size_t)r.y * S.B + gs) * BB, di);
+    } else {
+      TF x[BB], lk[BB];
+      read_blk(d, 1, x);
+      blk_mul<2>(x, di, lk);
+      blk_store<2>(gblk(r.x), lk);
+    }
+  };
+  // step 2: r = {e, L entry, U entry, rest}: A_e -= L U, then the rest
+  auto fetch2 = [&](int d, int4 r) {
+    fetch_blk(d, 0, r.x);
+    fetch_blk(d, 1, r.y);
+    fetch_blk(d, 2, r.z);
+  };
+  auto work2 = [&](int d, int4 r) {
+    TF c[BB], lv[BB], uv[BB];
+    read_blk(d, 0, c);
+    read_blk(d, 1, lv);
+    read_blk(d, 2, uv);
+    blk_msub<2>(c, lv, uv);
+    if (r.w >= 0) {
+      for (int q = r.w;; ++q) {
+        const int2 cq = __ldg(S.con + q);
+        if (cq.x < 0) break;
+        TF l2[BB], u2[BB];
+        blk_load<2>(gblk(cq.x), l2);
+        blk_load<2>(gblk(cq.y), u2);
+        blk_msub<2>(c, l2, u2);
+      }
+    }
+    blk_store<2>(gblk(r.x), c);
+  };
+  fetch_recs(S.fac_rec + S.fac_ptr[l0], count(S.fac_ptr[l0 + 1] - S.fac_ptr[l0]));
+  for (int l = l0; l < l1; ++l) {
+    const int f0 = S.fac_ptr[l], nf = S.fac_ptr[l + 1] - f0;
+    step(S.fac_rec + f0, count(nf), fetch1, work1);
+    const int t0 = S.tgt_ptr[l], nt = S.tgt_ptr[l + 1] - t0;
+    fetch_recs(S.tgt_rec + t0, count(nt));
+    __syncthreads();
+    if (nt > 0) {
+      step(S.tgt_rec + t0, count(nt), fetch2, work2);
+      if (l + 1 < l1) fetch_recs(S.fac_rec + S.fac_ptr[l + 1], count(S.fac_ptr[l + 2] - S.fac_ptr[l + 1]));
+      __syncthreads();
+    } else if (l + 1 < l1) {
+      cp_wait<0>();
+      fetch_recs(S.fac_rec + S.fac_ptr[l + 1], count(S.fac_ptr[l + 2] - S.fac_ptr[l + 1]));
+    }
+  }
+  cp_wait<0>();
+}
+
+template <int BS, typename TF, bool CL>
+__device__ __forceinline__ void factor_levels(const DevSys& S, const DevWork& w, const Team& tm,
+                                              int l0, int l1, unsigned char* ring) {
+  FactorArgs<TF> f;
+  f.lu = reinterpret_cast<TF*>(w.lu);
+  f.uinv = reinterpret_cast<TF*>(w.uinv);
+  f.flag = w.flag;
+  f.B = w.B;
+  f.fac_ptr = S.fac_ptr;
+  f.fac_rec = S.fac_rec;
+  f.tgt_ptr = S.tgt_ptr;
+  f.tgt_rec = S.tgt_rec;
+  f.con = S.con;
+  f.ring = ring;
+  if constexpr (BS == 2 && !CL) {
+    if (tm.S > 1 && ring) {
+      factor_pipe<TF>(f, tm, l0, l1);
+      return;
+    }
+  }
+  factor_run<BS, TF, CL>(f, tm, l0, l1);
+}
+
+// ---------------------------------------------------------------------------
+// Newton-Krylov: restarted GMRES(m), right-preconditioned by ILU(0)
+// ---------------------------------------------------------------------------
+
+
+// Team-wide sums of per-scenario partials.  part(j) is the calling thread's
+// partial of index j for its scenario slot; every thread must call (inactive
+// ones return 0).  Lanes of a slot are summed with shuffles, warps through
+// shared memory, and the CTAs of a cluster through per-rank global slots read
+// back after a cluster barrier -- a fixed order, so results are deterministic.
+// Results: rs[j * S + slot], valid for every thread of the CTA on return.
+template <bool CL, typename T, class Part>
+__device__ void team_sum(const Team& tm, int J, Part part, T* redw, T* rs, T* gred, int par,
+                         int csize, int crank, int B) {
+  const int S = tm.S;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < J; ++j) {
+    T v = part(j);
+    for (int off = 16; off >= S; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane < S) redw[(warp * J + j) * S + lane] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < J * S; t += blockDim.x) {
+    const int j = t / S, s = t - j * S;
+    T a = T(0);
+    for (int q = 0; q < nw; ++q) a += redw[(q * J + j) * S + s];
+    if constexpr (CL) {
+      if (s < tm.ns) gred[(((size_t)par * csize + crank) * B + tm.s0 + s) * kMaxJ + j] = a;
+    } else {
+      rs[j * S + s] = a;
+    }
+  }
+  if constexpr (CL) {
+    csync<CL>();
+    for (int t = threadIdx.x; t < J * S; t += blockDim.x) {
+      const int j = t / S, s = t - j * S;
+      T a = T(0);
+      if (s < tm.ns)
+        for (int r = 0; r < csize; ++r)
+          a += __ldcg(gred + (((size_t)par * csize + r) * B + tm.s0 + s) * kMaxJ + j);
+      rs[j * S + s] = a;
+    }
+  }
+  __syncthreads();
+}
+
+// Per-slot GMRES state kept by every CTA in shared memory (identical copies,
+// updated from identical reduction results): H column-major with leading
+// dimension m+1, Givens cosines / sines, the rotated right-hand side g and
+// the coefficients y.
+template <typename T>
+struct GmresState {
+  T* H;
+  T* cs;
+  T* sn;
+  T* g;
+  T* y;
+  __device__ static int words(int m) { return (m + 1) * m + 4 * m + 1; }
+  __device__ void bind(T* base, int m, int slot) {
+    H = base + (size_t)slot * words(m);
+    cs = H + (m + 1) * m;
+    sn = cs + m;
+    g = sn + m;
+    y = g + m + 1;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// per (row, scenario) steps shared by the persistent kernel and the batched
+// phase kernels
+// ---------------------------------------------------------------------------
+
+// Set-up of row i, scenario gs: specified injections, start voltage and
+// (row 0) the scenario's accumulators.
+template <bool THREE>
+__device__ __forceinline__ void setup_row(const DevSys& S, const DevWork& w, int i, int gs) {
+  const int B = w.B, n = S.n;
+  const size_t b = (size_t)i * B + gs;
+  const int oi = S.perm[i];
+  if (!THREE) {
+    const size_t src = (size_t)gs * n + oi;
+    w.spec[b * 3] = w.in_p_load ? w.in_p_load[src] : S.p_load0[i];
+    w.spec[b * 3 + 1] = w.in_q_load ? w.in_q_load[src] : S.q_load0[i];
+    w.spec[b * 3 + 2] = w.in_p_gen ? w.in_p_gen[src] : S.p_gen0[i];
+    double vm, va;
+    if (w.in_vm) {
+      vm = w.in_vm[oi];
+      va = w.in_va[oi];
+    } else if (w.warm_in) {
+      vm = w.warm_vm[oi];
+      va = w.warm_va[oi];
+    } else {
+      vm = (S.btype[i] == PF_PQ) ? 1.0 : S.v_set[i];
+      va = 0.0;
+    }
+    w.vm[b] = vm;
+    w.va[b] = va;
+    double sn, cs;
+    sincos_tab(S.trig, va, &sn, &cs);
+    w.U[b] = make_double2(cs, sn);
+    w.V[b] = make_double2(vm * cs, vm * sn);
+    w.uvm32[b] = make_float4((float)cs, (float)sn, (float)vm, 0.0f);
+  } else {
+    const int mask = S.btype[i] & 7;
+    for (int a = 0; a < 3; ++a) {
+      const size_t src = ((size_t)gs * n + oi) * 3 + a;
+      w.spec[b * 6 + a] = w.in_p_load ? w.in_p_load[src] : S.p_load0[(size_t)i * 3 + a];
+      w.spec[b * 6 + 3 + a] = w.in_q_load ? w.in_q_load[src] : S.q_load0[(size_t)i * 3 + a];
+      double2 v = make_double2(0.0, 0.0);
+      if ((mask >> a) & 1) {
+        if (w.in_vm) {
+          double sn, cs;
+          sincos(w.in_va[(size_t)oi * 3 + a], &sn, &cs);
+          v = make_double2(w.in_vm[(size_t)oi * 3 + a] * cs, w.in_vm[(size_t)oi * 3 + a] * sn);
+        } else if (w.warm_in) {
+          v = w.warm_V[(size_t)oi * 3 + a];
+        } else {
+          // balanced source angles 0, -120, +120 degrees
+          double sn, cs;
+          sincos(-2.0943951023931954923 * a, &sn, &cs);
+          v = make_double2(S.v_source * cs, S.v_source * sn);
+        }
+      }
+      w.V[b * 3 + a] = v;
+    }
+  }
+  if (i == 0) {
+    w.norm[gs] = 0ull;
+    w.norm[B + gs] = 0ull;
+    w.step[gs] = 0ull;
+    w.step[B + gs] = 0ull;
+    w.flag[gs] = 0;
+  }
+}
+
+// Voltage change of the current step (complex), for J dx evaluated from Y
+// and V in the FP64 refinement residual.
+template <bool THREE>
+__device__ __forceinline__ void dv_row(const DevSys& S, const DevWork& w, int i, int gs) {
+  const int B = w.B;
+  const size_t b = (size_t)i * B + gs;
+  if constexpr (THREE) {
+    for (int a = 0; a < 3; ++a)
+      w.dV[b * 3 + a] = make_double2(__ldcg(w.dx + b * 6 + a), __ldcg(w.dx + b * 6 + 3 + a));
+  } else {
+    // dV = j d_delta V + d|V| U
+    const double2 V = ldc(w.V + b), U = ldc(w.U + b);
+    const double dd = __ldcg(w.dx + b * 2), dm = __ldcg(w.dx + b * 2 + 1);
+    w.dV[b] = make_double2(-dd * V.y + dm * U.x, dd * V.x + dm * U.y);
+  }
+}
+
+// FP64 residual r = F - J dx of row i, matrix-free from Y, V and dV
+// (single phase: dS = dV conj(I) + V conj(Y dV) plus the load's slope).
+template <bool THREE>
+__device__ __forceinline__ void resid_row(const DevSys& S, const DevWork& w, int i, int gs) {
+  const int B = w.B;
+  const size_t b = (size_t)i * B + gs;
+  double* y = w.r;
+  const double2* Y = reinterpret_cast<const double2*>(S.y_val);
+  if constexpr (THREE) {
+    double2 YdV[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
+      const size_t bj = ((size_t)S.y_col[e] * B + gs) * 3;
+      for (int c = 0; c < 3; ++c) {
+        const double2 d = ldc(w.dV + bj + c);
+        for (int a = 0; a < 3; ++a) YdV[a] = cadd(YdV[a], cmul(Y[(size_t)e * 9 + a * 3 + c], d));
+      }
+    }
+    const int mask = S.btype[i] & 7;
+    const bool src = (S.btype[i] & 8) != 0;
+    for (int a = 0; a < 3; ++a) {
+      const bool fa = ((mask >> a) & 1) && !src;
+      const double dr = __ldcg(w.dx + b * 6 + a), di = __ldcg(w.dx + b * 6 + 3 + a);
+      double rim, rre;
+      if (fa) {
+        // J dV = [Im; Re](Y dV) - [a b; c d] dV   (Eq. 21-23)
+        const double* ad = w.abcd + b * 12;
+        const double jim = YdV[a].y - (ad[a] * dr + ad[3 + a] * di);
+        const double jre = YdV[a].x - (ad[6 + a] * dr + ad[9 + a] * di);
+        rim = __ldcg(w.F + b * 6 + a) - jim;
+        rre = __ldcg(w.F + b * 6 + 3 + a) - jre;
+      } else {
+        rim = -dr;
+        rre = -di;
+      }
+      y[b * 6 + a] = rim;
+      y[b * 6 + 3 + a] = rre;
+    }
+  } else {
+    double2 YdV = make_double2(0.0, 0.0);
+    for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e)
+      YdV = cadd(YdV, cmul(Y[e], ldc(w.dV + (size_t)S.y_col[e] * B + gs)));
+    const double2 V = ldc(w.V + b), I = ldc(w.I + b), dV = ldc(w.dV + b);
+    // dS = dV conj(I) + V conj(Y dV), plus the load's slope on |V|
+    const double2 dS = cadd(cmulc(dV, I), cmulc(V, YdV));
+    const double vmi = __ldcg(w.vm + b);
+    const double dshape = S.zip[3 * i + 1] + 2.0 * S.zip[3 * i + 2] * vmi;
+    const double dd = __ldcg(w.dx + b * 2), dm = __ldcg(w.dx + b * 2 + 1);
+    const int t = S.btype[i];
+    const double r0 = (t != PF_SLACK)
+                          ? __ldcg(w.F + b * 2) - (dS.x + __ldcg(w.spec + b * 3) * dshape * dm)
+                          : -dd;
+    const double r1 = (t == PF_PQ)
+                          ? __ldcg(w.F + b * 2 + 1) - (dS.y + __ldcg(w.spec + b * 3 + 1) * dshape * dm)
+                          : -dm;
+    y[b * 2] = r0;
+    y[b * 2 + 1] = r1;
+  }
+}
+
+// Voltage update of row i (Sec. II.A box: delta += Delta delta, |V| +=
+// Delta|V|; Sec. II.B box: V^c += Delta V^c).  Returns the largest step.
+template <bool THREE>
+__device__ __forceinline__ double update_row(const DevSys& S, const DevWork& w, int i, int gs) {
+  const int B = w.B;
+  constexpr int NSL = THREE ? 3 : 1;
+  const size_t b = (size_t)i * B + gs;
+  double stp = 0.0;
+  if constexpr (THREE) {
+    for (int a = 0; a < NSL; ++a) {
+      const double dr = __ldcg(w.dx + b * 6 + a), di = __ldcg(w.dx + b * 6 + 3 + a);
+      stp = fmax(stp, fmax(fabs(dr), fabs(di)));
+      const double2 v = ldc(w.V + b * 3 + a);
+      w.V[b * 3 + a] = make_double2(v.x + dr, v.y + di);
+    }
+  } else {
+    const double dd = __ldcg(w.dx + b * 2), dm = __ldcg(w.dx + b * 2 + 1);
+    stp = __longlong_as_double((long long)max(abs_bits(dd), abs_bits(dm)));
+    const double vm = __ldcg(w.vm + b) + dm, va = __ldcg(w.va + b) + dd;
+    w.vm[b] = vm;
+    w.va[b] = va;
+    double sn, cs;
+    sincos_tab(S.trig, va, &sn, &cs);
+    w.U[b] = make_double2(cs, sn);
+    w.V[b] = make_double2(vm * cs, vm * sn);
+    w.uvm32[b] = make_float4((float)cs, (float)sn, (float)vm, 0.0f);
+  }
+  return stp;
+}
+
+// Result of row i in the caller's numbering (and the warm start).
+template <bool THREE>
+__device__ __forceinline__ void output_row(const DevSys& S, const DevWork& w, int i, int gs, bool ok) {
+  const int B = w.B, n = S.n;
+  const size_t b = (size_t)i * B + gs;
+  const int oi = S.perm[i];
+  if constexpr (THREE) {
+    const int mask = S.btype[i] & 7;
+    for (int a = 0; a < 3; ++a) {
+      const double2 v = ldc(w.V + b * 3 + a);
+      const bool pres = (mask >> a) & 1;
+      const size_t dst = ((size_t)gs * n + oi) * 3 + a;
+      if (w.out_vm) w.out_vm[dst] = pres ? hypot(v.x, v.y) : 0.0;
+      if (w.out_va) w.out_va[dst] = pres ? atan2(v.y, v.x) : 0.0;
+      if (w.warm_out && gs == 0 && ok) w.warm_V[(size_t)oi * 3 + a] = v;
+    }
+  } else {
+    const size_t dst = (size_t)gs * n + oi;
+    const double vm = __ldcg(w.vm + b), va = __ldcg(w.va + b);
+    if (w.out_vm) w.out_vm[dst] = vm;
+    if (w.out_va) w.out_va[dst] = va;
+    if (w.warm_out && gs == 0 && ok) {
+      w.warm_vm[oi] = vm;
+      w.warm_va[oi] = va;
+    }
+  }
+}
+
+}  // namespace pf

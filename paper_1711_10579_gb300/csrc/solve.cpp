@@ -150,8 +150,31 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   // single solves keep the triangular-solve vector in shared memory when it fits
   const size_t tf = fp32 ? 4 : 8;
   d.y_in_smem = 0;
+  d.ring = 0;
   const size_t extra = dynamic_smem_bytes(bs, tf, nk, n, d, threads);
   d.y_in_smem = (B == 1 && (size_t)n * bs * tf + extra <= 200 * 1024) ? 1 : 0;
+  if (B > 1 && !nk && mode == RunMode::Solve) {
+    // a batch of Newton-Raphson solves: phase kernels; the factorisation of
+    // 2x2 blocks stages its gathers in shared memory
+    d.ring = (S > 1 && bs == 2) ? 1 : 0;
+    unsigned long long hprof[kProfPhases] = {};
+    cudaError_t e = launch_batch_nr(bs, fp32, sys, w, d, threads, st, prof ? hprof : nullptr);
+    if (e == cudaSuccess && prof) {
+      // the launches have finished (the profile waited for its last event)
+      unsigned long long cur[kProfPhases];
+      e = cudaMemcpy(cur, prof, sizeof(cur), cudaMemcpyDeviceToHost);
+      for (int k = 0; k < kProfPhases; ++k) cur[k] += hprof[k];
+      if (e == cudaSuccess) e = cudaMemcpy(prof, cur, sizeof(cur), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return cuda_error(e, "launching the batched Newton kernels");
+    return PF_OK;
+  }
+  // the persistent kernel: a batch of Newton-Krylov solves of 2x2 blocks
+  // stages the factorisation's gathers in shared memory when that fits
+  if (S > 1 && bs == 2) {
+    d.ring = 1;
+    if (dynamic_smem_bytes(bs, tf, nk, n, d, threads) > 200 * 1024) d.ring = 0;
+  }
   cudaError_t e = launch_newton(bs, fp32, nk, sys, w, d, grid, cluster, threads, st);
   if (e != cudaSuccess) return cuda_error(e, "launching the Newton kernel");
   return PF_OK;
