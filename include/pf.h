@@ -135,7 +135,9 @@ typedef struct {
 typedef struct {
   int status;            /* pf_status of this solve */
   int iterations;        /* Newton iterations performed (solves of Eq. 10 / 22) */
-  int linear_iterations; /* NK: total GMRES iterations */
+  int linear_iterations; /* NK: total GMRES iterations; NR batch (B >= 2):
+                            triangular-solve passes (one per Newton step
+                            plus one per FP64 refinement) */
   int reserved;
   double mismatch;       /* final infinity norm of the power mismatch (pu) */
   double max_step;       /* infinity norm of the last Newton correction */
@@ -325,13 +327,17 @@ int pf_solve_noalloc(pf_case c, const pf_opts* opts, const double* d_p_load,
 
 /*
  * Autotuner for batched solves (B >= 2): runs B copies of the case's own
- * scenario with each candidate launch shape (scenarios per CTA 1, 2, 4, 8;
- * threads per CTA 128, 256, 512), times them with CUDA events and stores the
- * fastest in the case for (B, method, precision).  Later batch solves of
- * that B with scen_per_cta == 0 and block_threads == 0 use it; *opts
- * (in: method, precision; out: the chosen shape) may be passed back.
- * Without tuning, a batch uses about one CTA per SM (at most 8 scenarios per
- * CTA).  Blocking; allocates the batch workspace.
+ * scenario with each candidate launch shape (scenarios per CTA 1, 2, 4, 8,
+ * and 16 for PF_NR when B >= 32; threads per CTA 128, 256, 512), times them
+ * with CUDA events and stores the fastest in the case for (B, method,
+ * precision).  A PF_NR batch runs its factorisation and its triangular
+ * sweeps as separate launches; each gets the shape with the least time of
+ * its own phase.  Later batch solves of that B with scen_per_cta == 0 and
+ * block_threads == 0 use the stored shapes; *opts (in: method, precision;
+ * out: the chosen shape, for PF_NR that of the factorisation, which alone
+ * also applies to the sweeps when passed back explicitly).  Without tuning,
+ * a batch uses about one CTA per SM (at most 8 scenarios per CTA).
+ * Blocking; allocates the batch workspace.
  */
 int pf_autotune(pf_case c, int B, pf_opts* opts);
 

@@ -241,7 +241,7 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
   t += (size_t)nnz_lu * B * bs * bs * 8;                // lu
   t += nb * bs * bs * 8;                                // uinv
   t += nb * bs * 8;                                     // y
-  t += (size_t)B * (2 * 8 + 2 * 8 + 4 + 8) + 8;         // norm, step, flag, status, t0
+  t += (size_t)B * (2 * 8 + 2 * 8 + 4 + 12) + 8 + 64;   // norm, step, flag, status, t0, call
   t += 3 * nb * nsl * 8;                                // staged inputs
   t += 2 * nb * nsl * 8 + (size_t)B * sizeof(pf_info);  // staged outputs
   if (m > 0) {                                          // Newton-Krylov (FP64 bound)
@@ -261,6 +261,7 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
     nnz_lu = std::max(nnz_lu, cap_nnz);
   }
   mem.release();
+  graph.reset();
   cap = 0;
   cap_m = -1;
   cap_kind = 0;
@@ -296,7 +297,9 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
   A((void**)&w.flag, (size_t)B * 4);
   A((void**)&w.status, (size_t)B * 4);
   A((void**)&w.refine, (size_t)B * 4);
+  A((void**)&w.iter, (size_t)B * 4);
   A((void**)&w.t0, 8);
+  A((void**)&w.call, sizeof(CallArgs));
   A((void**)&st_p_load, nb * nsl * 8);
   A((void**)&st_q_load, nb * nsl * 8);
   A((void**)&st_p_gen, nb * nsl * 8);

@@ -39,6 +39,28 @@ struct SysBuf {
 };
 
 // Per-solve device state for up to `cap` scenarios plus staging buffers.
+// A batched Newton-Raphson solve as one CUDA graph (batch.cu): its key is
+// the launch configuration and workspace it was built for.
+struct BatchGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::array<long long, 16> key{};
+  BatchGraph() = default;
+  BatchGraph(const BatchGraph&) {}  // a copy starts empty
+  BatchGraph& operator=(const BatchGraph&) {
+    reset();
+    return *this;
+  }
+  ~BatchGraph() { reset(); }
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    key = {};
+  }
+};
+
 struct Workspace {
   // capacity the buffers were sized for: scenarios, Krylov restart length,
   // case kind, rows and factor block entries
@@ -52,6 +74,7 @@ struct Workspace {
   double *st_p_load = nullptr, *st_q_load = nullptr, *st_p_gen = nullptr;
   double *st_vm = nullptr, *st_va = nullptr;
   pf_info* st_info = nullptr;
+  BatchGraph graph;  // batched Newton-Raphson launch sequence
   int ensure(int kind, int n, long long nnz_lu, int B, int m = 0);
   static size_t bytes_for(int kind, int n, long long nnz_lu, int B, int m = 0);
 };
@@ -83,8 +106,10 @@ struct pf_case_s {
   double2* warm_V = nullptr;
   bool warm_valid = false;
   std::mutex mu;
-  // autotuned batch shapes: (B, method, precision) -> (scenarios per CTA, threads)
-  std::map<std::array<int, 3>, std::array<int, 2>> tuned;
+  // autotuned batch shapes: (B, method, precision) -> (scenarios per CTA,
+  // threads) of the factorisation (Newton-Krylov: the whole launch), then of
+  // the triangular sweeps of a Newton-Raphson batch
+  std::map<std::array<int, 3>, std::array<int, 4>> tuned;
   std::mutex tuned_mu;
 };
 
@@ -117,8 +142,9 @@ cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const Dev
 int max_cluster(int bs, bool fp32, bool nk, int threads);
 // Batched Newton-Raphson as phase kernels (batch.cu); prof, if given, is a
 // host array of kProfPhases device times (ns) to add to.
-cudaError_t launch_batch_nr(int bs, bool fp32, const DevSys& S, const DevWork& w, const DevOpts& o,
-                            int threads, cudaStream_t st, unsigned long long* prof);
+cudaError_t launch_batch_nr(int bs, bool fp32, const DevSys& S, const DevWork& w,
+                            const DevOpts& of, int threads_f, const DevOpts& os, int threads_s,
+                            cudaStream_t st, BatchGraph* g, unsigned long long* prof);
 cudaError_t noalloc_scratch(void** ptr);
 int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const double* d_q_load,
                   const double* d_p_gen, double* d_vmag, double* d_vang, pf_info* d_info,

@@ -9,17 +9,25 @@
 //   which the 32 lanes of a warp serve 32 scenarios of one row, so every
 //   load of the [entry][scenario] arrays is one contiguous segment, and in
 //   which many small CTAs per SM hide the latency of the neighbour gathers;
-//   the stop test is one thread per scenario;
+//   the stop test is one CTA over all scenarios;
 //   the block LU refactorisation (Sec. III.A) and the triangular sweeps
 //   are level-synchronous: one CTA per S scenarios, as in the persistent
 //   kernel, with the registers and shared memory of the whole SM.
 //
 // Every launch reads the per-scenario status left by the previous ones and
-// skips finished scenarios, so the host issues the whole sequence up to the
-// iteration limit without waiting for the device.
+// skips finished scenarios.  The sequence is one CUDA graph: the set-up and
+// first stop test, then a conditional WHILE node whose body is one Newton
+// iteration and whose stop test sets the loop condition (any scenario still
+// running), then the results.  The device decides when to stop; the host
+// neither waits nor issues iterations that have nothing left to do.  The
+// graph is built once per launch shape and workspace; a call passes its own
+// inputs and outputs through a small record in device memory.
 
+#include "api_internal.h"
 #include "kernels.cuh"
 
+#include <array>
+#include <cstring>
 #include <vector>
 
 namespace pf {
@@ -53,39 +61,60 @@ __device__ __forceinline__ void commit_max(unsigned long long m, int sb, bool on
   if (on && (int)(threadIdx.x & 31) < sb && m != 0ull) atomicMax(dst, m);
 }
 
+// The workspace view of this call: its inputs and outputs from w.call.
+__device__ __forceinline__ DevWork with_call(DevWork w) {
+  const CallArgs* c = w.call;
+  w.in_p_load = c->p_load;
+  w.in_q_load = c->q_load;
+  w.in_p_gen = c->p_gen;
+  w.out_vm = c->vm;
+  w.out_va = c->va;
+  w.out_info = c->info;
+  return w;
+}
+
 __device__ __forceinline__ void put_info(const DevWork& w, int gs, int st, int it, double nrm,
                                          double step) {
-  if (!w.out_info) return;
+  pf_info* out = w.call->info;
+  if (!out) return;
   pf_info inf;
   inf.status = st;
   inf.iterations = it;
-  inf.linear_iterations = 0;
+  // triangular-solve passes: one per Newton step and one per refinement
+  inf.linear_iterations = it + (w.refine[gs] >> 1);
   inf.reserved = 0;
   inf.mismatch = nrm;
   inf.max_step = step;
   inf.solve_us = 0.0;
-  w.out_info[gs] = inf;
+  out[gs] = inf;
 }
+
+// This call's inputs and outputs (one thread; launched before the sequence).
+__global__ void k_args(CallArgs* dst, CallArgs a) { *dst = a; }
 
 template <int BS>
 __global__ void __launch_bounds__(kRowThreads) k_setup(DevSys S, DevWork w, int sb) {
   RowTile t;
   if (!row_tile(w.B, S.n, sb, t)) return;
-  for (int i = t.i; i < t.iend; i += t.di) setup_row<BS == 6>(S, w, i, t.gs);
+  const DevWork wc = with_call(w);
+  for (int i = t.i; i < t.iend; i += t.di) setup_row<BS == 6>(S, wc, i, t.gs);
   if (blockIdx.y == 0 && t.i == 0) {
     w.status[t.gs] = kRunning;
     w.refine[t.gs] = 0;
+    w.iter[t.gs] = 0;
   }
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *w.t0 = global_ns();
 }
 
-// Step A of iteration it: mismatch, its norm and the Jacobian.
+// Step A: mismatch, its norm and the Jacobian (iteration w.iter[gs]).
 template <int BS, typename TF>
-__global__ void __launch_bounds__(kRowThreads) k_mismatch(DevSys S, DevWork w, int sb, int it) {
+__global__ void __launch_bounds__(kRowThreads) k_mismatch(DevSys S, DevWork w, int sb) {
   RowTile t;
   const bool on = row_tile(w.B, S.n, sb, t) && w.status[t.gs] == kRunning;
   unsigned long long m = 0ull;
+  int it = 0;
   if (on) {
+    it = w.iter[t.gs];
     for (int i = t.i; i < t.iend; i += t.di) {
       double nrm;
       if constexpr (BS == 6) {
@@ -99,31 +128,44 @@ __global__ void __launch_bounds__(kRowThreads) k_mismatch(DevSys S, DevWork w, i
   commit_max(m, sb, on, w.norm + (size_t)(it & 1) * w.B + t.gs);
 }
 
-// Stop test of iteration it, one thread per scenario (the decisions of the
-// persistent kernel, with the refinement chosen per scenario).
-__global__ void k_stop(DevWork w, DevOpts o, int it) {
-  const int gs = blockIdx.x * blockDim.x + threadIdx.x;
+// Stop test (the decisions of the persistent kernel, with the refinement
+// chosen per scenario), one CTA over all scenarios.  A running scenario
+// advances its iteration index.  When a graph's loop condition is given, it
+// is set to whether any scenario still runs.
+__global__ void __launch_bounds__(1024) k_stop(DevWork w, DevOpts o, int has_cond,
+                                               cudaGraphConditionalHandle cond) {
   const int B = w.B;
-  if (gs >= B) return;
-  w.refine[gs] = 0;
-  if (w.status[gs] != kRunning) return;
-  const double nrm = __longlong_as_double((long long)__ldcg(w.norm + (size_t)(it & 1) * B + gs));
-  int st = kRunning;
-  if (!(nrm <= 1e12)) st = PF_ERR_DIVERGED;
-  else if (nrm <= o.tol) st = PF_OK;
-  else if (it >= o.max_iter) st = PF_ERR_MAXITER;
-  w.status[gs] = st;
-  if (st == kRunning) {
-    w.refine[gs] = (o.refine > 0 && nrm <= o.refine_below) ? 1 : 0;
-  } else {
-    const double step =
-        it > 0 ? __longlong_as_double((long long)__ldcg(w.step + (size_t)((it - 1) & 1) * B + gs))
-               : 0.0;
-    put_info(w, gs, st, it, nrm, step);
+  int running = 0;
+  for (int gs = threadIdx.x; gs < B; gs += blockDim.x) {
+    if (w.status[gs] != kRunning) continue;
+    const int it = w.iter[gs];
+    const double nrm =
+        __longlong_as_double((long long)__ldcg(w.norm + (size_t)(it & 1) * B + gs));
+    int st = kRunning;
+    if (!(nrm <= 1e12)) st = PF_ERR_DIVERGED;
+    else if (nrm <= o.tol) st = PF_OK;
+    else if (it >= o.max_iter) st = PF_ERR_MAXITER;
+    w.status[gs] = st;
+    int rf = w.refine[gs] & ~1;  // refinement count << 1
+    if (st == kRunning) {
+      if (o.refine > 0 && nrm <= o.refine_below) rf += 3;  // flag, and one more
+      w.refine[gs] = rf;
+      w.iter[gs] = it + 1;
+      ++running;
+    } else {
+      w.refine[gs] = rf;
+      const double step =
+          it > 0
+              ? __longlong_as_double((long long)__ldcg(w.step + (size_t)((it - 1) & 1) * B + gs))
+              : 0.0;
+      put_info(w, gs, st, it, nrm, step);
+    }
+    // the buffers of the next iteration (read last one iteration ago)
+    w.norm[(size_t)((it + 1) & 1) * B + gs] = 0ull;
+    w.step[(size_t)((it + 1) & 1) * B + gs] = 0ull;
   }
-  // the buffers of the next iteration (read last one iteration ago)
-  w.norm[(size_t)((it + 1) & 1) * B + gs] = 0ull;
-  w.step[(size_t)((it + 1) & 1) * B + gs] = 0ull;
+  running = __syncthreads_or(running);
+  if (has_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, running ? 1u : 0u);
 }
 
 // The team of one level-synchronous CTA: scenarios [blockIdx.x S, + S),
@@ -140,7 +182,7 @@ __device__ __forceinline__ bool level_team(const DevWork& w, const DevOpts& o, b
     unsigned act = 0;
     for (int s = 0; s < tm.ns; ++s) {
       const int gs = tm.s0 + s;
-      if (w.status[gs] == kRunning && (!refining || w.refine[gs])) act |= 1u << s;
+      if (w.status[gs] == kRunning && (!refining || (w.refine[gs] & 1))) act |= 1u << s;
     }
     sh_act = act;
   }
@@ -152,8 +194,7 @@ __device__ __forceinline__ bool level_team(const DevWork& w, const DevOpts& o, b
 // Step B: numeric block LU refactorisation; a singular pivot ends its
 // scenario.
 template <int BS, typename TF>
-__global__ void __launch_bounds__(BS == 2 ? 512 : 256) k_factor(DevSys S, DevWork w, DevOpts o,
-                                                                int it) {
+__global__ void __launch_bounds__(BS == 2 ? 512 : 256) k_factor(DevSys S, DevWork w, DevOpts o) {
   Team tm;
   if (!level_team(w, o, false, tm)) return;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -162,6 +203,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) k_factor(DevSys S, DevWor
   const int s = threadIdx.x;
   if (s < tm.ns && ((tm.act >> s) & 1u) && __ldcg(w.flag + tm.s0 + s)) {
     const int gs = tm.s0 + s;
+    const int it = w.iter[gs] - 1;  // the stop test advanced it
     w.status[gs] = PF_ERR_SINGULAR;
     put_info(w, gs, PF_ERR_SINGULAR, it,
              __longlong_as_double((long long)__ldcg(w.norm + (size_t)(it & 1) * w.B + gs)), 0.0);
@@ -205,24 +247,26 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) k_solve(DevSys S, DevWork
 template <int BS>
 __global__ void __launch_bounds__(kRowThreads) k_dv(DevSys S, DevWork w, int sb) {
   RowTile t;
-  if (!row_tile(w.B, S.n, sb, t) || w.status[t.gs] != kRunning || !w.refine[t.gs]) return;
+  if (!row_tile(w.B, S.n, sb, t) || w.status[t.gs] != kRunning || !(w.refine[t.gs] & 1)) return;
   for (int i = t.i; i < t.iend; i += t.di) dv_row<BS == 6>(S, w, i, t.gs);
 }
 
 template <int BS>
 __global__ void __launch_bounds__(kRowThreads) k_resid(DevSys S, DevWork w, int sb) {
   RowTile t;
-  if (!row_tile(w.B, S.n, sb, t) || w.status[t.gs] != kRunning || !w.refine[t.gs]) return;
+  if (!row_tile(w.B, S.n, sb, t) || w.status[t.gs] != kRunning || !(w.refine[t.gs] & 1)) return;
   for (int i = t.i; i < t.iend; i += t.di) resid_row<BS == 6>(S, w, i, t.gs);
 }
 
 // Step E: voltage update and the norm of the step.
 template <int BS>
-__global__ void __launch_bounds__(kRowThreads) k_update(DevSys S, DevWork w, int sb, int it) {
+__global__ void __launch_bounds__(kRowThreads) k_update(DevSys S, DevWork w, int sb) {
   RowTile t;
   const bool on = row_tile(w.B, S.n, sb, t) && w.status[t.gs] == kRunning;
   unsigned long long m = 0ull;
+  int it = 0;
   if (on) {
+    it = w.iter[t.gs] - 1;  // the stop test advanced it
     for (int i = t.i; i < t.iend; i += t.di) m = max(m, abs_bits(update_row<BS == 6>(S, w, i, t.gs)));
   }
   commit_max(m, sb, on, w.step + (size_t)(it & 1) * w.B + t.gs);
@@ -233,11 +277,72 @@ template <int BS>
 __global__ void __launch_bounds__(kRowThreads) k_output(DevSys S, DevWork w, int sb) {
   RowTile t;
   if (!row_tile(w.B, S.n, sb, t)) return;
+  const DevWork wc = with_call(w);
   const bool ok = w.status[t.gs] == PF_OK;
-  for (int i = t.i; i < t.iend; i += t.di) output_row<BS == 6>(S, w, i, t.gs, ok);
-  if (blockIdx.y == 0 && t.i == 0 && w.out_info)
-    w.out_info[t.gs].solve_us = (double)(global_ns() - __ldcg(w.t0)) * 1e-3;
+  for (int i = t.i; i < t.iend; i += t.di) output_row<BS == 6>(S, wc, i, t.gs, ok);
+  if (blockIdx.y == 0 && t.i == 0 && wc.out_info)
+    wc.out_info[t.gs].solve_us = (double)(global_ns() - __ldcg(w.t0)) * 1e-3;
 }
+
+// ---------------------------------------------------------------------------
+// host side: the launch sequence, direct or as one CUDA graph
+// ---------------------------------------------------------------------------
+
+// One kernel launch of the sequence: function, shape and arguments.
+struct Launch {
+  const void* fn;
+  dim3 grid, block;
+  size_t smem;
+  std::vector<void*> args;
+};
+
+// The sequence of one batched solve, as a list of launches: prologue
+// (set-up, first mismatch and stop test), the body of one Newton iteration
+// (factor, sweeps, refinement, update, next mismatch and stop test) and the
+// epilogue (results).  Argument storage lives in the Plan.
+template <int BS, typename TF>
+struct Plan {
+  DevSys S;
+  DevWork w;
+  DevOpts of, os;
+  int sb, pass0 = 0, pass1 = 1, has_cond = 0;
+  cudaGraphConditionalHandle cond = 0;
+  std::vector<Launch> pro, body, epi;
+  dim3 rows, blk;
+  int threads_f, threads_s;
+  size_t red, ring;
+
+  void build(int refine) {
+    const int B = w.B, n = S.n;
+    sb = 1;
+    while (sb < 32 && sb < B) sb <<= 1;
+    const int rb = kRowThreads / sb;
+    rows = dim3((B + sb - 1) / sb, (n + rb * kRowsPerThread - 1) / (rb * kRowsPerThread));
+    blk = dim3(kRowThreads);
+    const dim3 gf((B + of.S - 1) / of.S), gsv((B + os.S - 1) / os.S);
+    red = (size_t)threads_s * BS * sizeof(TF);
+    ring = of.ring ? (size_t)threads_f * FactorPipe<TF>::bytes : 0;
+    auto rowk = [&](const void* fn) {
+      return Launch{fn, rows, blk, 0, {&S, &w, &sb}};
+    };
+    const Launch stop{(const void*)k_stop, dim3(1), dim3(1024), 0, {&w, &of, &has_cond, &cond}};
+    pro = {rowk((const void*)k_setup<BS>), rowk((const void*)k_mismatch<BS, TF>), stop};
+    body.clear();
+    body.push_back(Launch{(const void*)k_factor<BS, TF>, gf, dim3(threads_f), ring, {&S, &w, &of}});
+    body.push_back(
+        Launch{(const void*)k_solve<BS, TF>, gsv, dim3(threads_s), red, {&S, &w, &os, &pass0}});
+    for (int p = 0; p < refine; ++p) {
+      body.push_back(rowk((const void*)k_dv<BS>));
+      body.push_back(rowk((const void*)k_resid<BS>));
+      body.push_back(
+          Launch{(const void*)k_solve<BS, TF>, gsv, dim3(threads_s), red, {&S, &w, &os, &pass1}});
+    }
+    body.push_back(rowk((const void*)k_update<BS>));
+    body.push_back(rowk((const void*)k_mismatch<BS, TF>));
+    body.push_back(stop);
+    epi = {rowk((const void*)k_output<BS>)};
+  }
+};
 
 // Optional per-phase device time: events between launches, summed per phase.
 struct PhaseClock {
@@ -271,69 +376,144 @@ struct PhaseClock {
 };
 
 template <int BS, typename TF>
-cudaError_t run_batch_t(const DevSys& S, const DevWork& w, const DevOpts& o, int threads,
-                        cudaStream_t st, unsigned long long* prof) {
-  const int B = w.B, n = S.n;
-  int sb = 1;
-  while (sb < 32 && sb < B) sb <<= 1;
-  const int rb = kRowThreads / sb;
-  const dim3 rows((B + sb - 1) / sb, (n + rb * kRowsPerThread - 1) / (rb * kRowsPerThread));
-  const dim3 blk(kRowThreads);
-  const int groups = (B + o.S - 1) / o.S;
-  const size_t red = (size_t)threads * BS * sizeof(TF);
-  const size_t ring = o.ring ? (size_t)threads * FactorPipe<TF>::bytes : 0;
+cudaError_t set_smem(const Plan<BS, TF>& p) {
   cudaError_t e = cudaSuccess;
-  if (ring > 48 * 1024)
+  if (p.ring > 48 * 1024)
     e = cudaFuncSetAttribute(k_factor<BS, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ring);
-  if (e == cudaSuccess && red > 48 * 1024)
+                             (int)p.ring);
+  if (e == cudaSuccess && p.red > 48 * 1024)
     e = cudaFuncSetAttribute(k_solve<BS, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)red);
-  if (e != cudaSuccess) return e;
+                             (int)p.red);
+  return e;
+}
+
+// Direct launches, max_iter bodies (finished scenarios make them no-ops),
+// with events between launches when a profile is asked for.
+template <int BS, typename TF>
+cudaError_t run_direct(Plan<BS, TF>& p, cudaStream_t st, unsigned long long* prof) {
   PhaseClock clk{st, prof, {}, {}};
-  auto check = [&](int ph) {
-    if (e == cudaSuccess) e = cudaGetLastError();
+  cudaError_t e = clk.mark(kProfSetup);
+  auto go = [&](const Launch& l, int ph) {
+    if (e == cudaSuccess)
+      e = cudaLaunchKernel(l.fn, l.grid, l.block, const_cast<void**>(l.args.data()), l.smem, st);
     if (e == cudaSuccess) e = clk.mark(ph);
   };
-  check(kProfSetup);
-  k_setup<BS><<<rows, blk, 0, st>>>(S, w, sb);
-  check(kProfSetup);
-  for (int it = 0; e == cudaSuccess; ++it) {
-    k_mismatch<BS, TF><<<rows, blk, 0, st>>>(S, w, sb, it);
-    check(kProfMismatch);
-    k_stop<<<(B + 127) / 128, 128, 0, st>>>(w, o, it);
-    check(kProfStop);
-    if (it >= o.max_iter) break;
-    k_factor<BS, TF><<<groups, threads, ring, st>>>(S, w, o, it);
-    check(kProfFactor);
-    for (int pass = 0; pass <= o.refine && e == cudaSuccess; ++pass) {
-      if (pass > 0) {
-        k_dv<BS><<<rows, blk, 0, st>>>(S, w, sb);
-        k_resid<BS><<<rows, blk, 0, st>>>(S, w, sb);
-        check(kProfResidual);
-      }
-      k_solve<BS, TF><<<groups, threads, red, st>>>(S, w, o, pass);
-      check(kProfSolve);
-    }
-    k_update<BS><<<rows, blk, 0, st>>>(S, w, sb, it);
-    check(kProfUpdate);
-  }
-  if (e == cudaSuccess) {
-    k_output<BS><<<rows, blk, 0, st>>>(S, w, sb);
-    check(kProfOutput);
-  }
+  const void* fsolve = (const void*)k_solve<BS, TF>;
+  const void* ffac = (const void*)k_factor<BS, TF>;
+  const void* fmis = (const void*)k_mismatch<BS, TF>;
+  auto phase = [&](const Launch& l) {
+    if (l.fn == fsolve) return (int)kProfSolve;
+    if (l.fn == ffac) return (int)kProfFactor;
+    if (l.fn == fmis) return (int)kProfMismatch;
+    if (l.fn == (const void*)k_stop) return (int)kProfStop;
+    if (l.fn == (const void*)k_update<BS>) return (int)kProfUpdate;
+    if (l.fn == (const void*)k_setup<BS>) return (int)kProfSetup;
+    if (l.fn == (const void*)k_output<BS>) return (int)kProfOutput;
+    return (int)kProfResidual;
+  };
+  for (const Launch& l : p.pro) go(l, phase(l));
+  for (int it = 0; it < p.of.max_iter && e == cudaSuccess; ++it)
+    for (const Launch& l : p.body) go(l, phase(l));
+  for (const Launch& l : p.epi) go(l, phase(l));
   const cudaError_t e2 = clk.finish();
   return e != cudaSuccess ? e : e2;
 }
 
+// Adds the launches as a chain of kernel nodes after `dep` (may be null).
+static cudaError_t add_chain(cudaGraph_t g, const std::vector<Launch>& ls, cudaGraphNode_t* dep) {
+  for (const Launch& l : ls) {
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void*>(l.fn);
+    kp.gridDim = l.grid;
+    kp.blockDim = l.block;
+    kp.sharedMemBytes = (unsigned)l.smem;
+    kp.kernelParams = const_cast<void**>(l.args.data());
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddKernelNode(&node, g, *dep ? dep : nullptr, *dep ? 1 : 0, &kp);
+    if (e != cudaSuccess) return e;
+    *dep = node;
+  }
+  return cudaSuccess;
+}
+
+// The whole solve as one graph: prologue, a WHILE node whose body is one
+// Newton iteration (its stop test sets the loop condition: any scenario
+// still running), epilogue.  Rebuilt when the key changes.
+template <int BS, typename TF>
+cudaError_t run_graph(Plan<BS, TF>& p, cudaStream_t st, BatchGraph* g, int refine) {
+  const DevOpts& o = p.of;
+  std::array<long long, 16> key = {
+      (long long)(uintptr_t)p.w.spec, (long long)(uintptr_t)p.S.lu_col, p.w.B, BS,
+      (long long)sizeof(TF), o.S, p.threads_f, p.os.S, p.threads_s, o.max_iter, refine, o.ring,
+      (long long)(uintptr_t)p.S.g_fwd, 0, 0, 0};
+  std::memcpy(&key[13], &o.tol, 8);
+  std::memcpy(&key[14], &o.refine_below, 8);
+  if (!g->exec || g->key != key) {
+    g->reset();
+    cudaError_t e = cudaGraphCreate(&g->graph, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphConditionalHandleCreate(&p.cond, g->graph, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    p.has_cond = 1;
+    cudaGraphNode_t dep = nullptr;
+    e = add_chain(g->graph, p.pro, &dep);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = p.cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    e = cudaGraphAddNode(&loop, g->graph, &dep, nullptr, 1, &cp);
+    if (e != cudaSuccess) return e;
+    cudaGraphNode_t bdep = nullptr;
+    e = add_chain(cp.conditional.phGraph_out[0], p.body, &bdep);
+    if (e != cudaSuccess) return e;
+    dep = loop;
+    e = add_chain(g->graph, p.epi, &dep);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+      g->reset();
+      return e;
+    }
+    g->key = key;
+  }
+  return cudaGraphLaunch(g->exec, st);
+}
+
+template <int BS, typename TF>
+cudaError_t run_batch_t(const DevSys& S, const DevWork& w, const DevOpts& of, int threads_f,
+                        const DevOpts& os, int threads_s, cudaStream_t st, BatchGraph* g,
+                        unsigned long long* prof) {
+  Plan<BS, TF> p;
+  p.S = S;
+  p.w = w;
+  p.of = of;
+  p.os = os;
+  p.threads_f = threads_f;
+  p.threads_s = threads_s;
+  p.build(of.refine);
+  cudaError_t e = set_smem(p);
+  if (e != cudaSuccess) return e;
+  // this call's inputs and outputs
+  CallArgs a{w.in_p_load, w.in_q_load, w.in_p_gen, w.out_vm, w.out_va, w.out_info};
+  k_args<<<1, 1, 0, st>>>(w.call, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (g && !prof) return run_graph(p, st, g, of.refine);
+  return run_direct(p, st, prof);
+}
+
 }  // namespace
 
-cudaError_t launch_batch_nr(int bs, bool fp32, const DevSys& S, const DevWork& w, const DevOpts& o,
-                            int threads, cudaStream_t st, unsigned long long* prof) {
-  if (bs == 2) return fp32 ? run_batch_t<2, float>(S, w, o, threads, st, prof)
-                           : run_batch_t<2, double>(S, w, o, threads, st, prof);
-  return fp32 ? run_batch_t<6, float>(S, w, o, threads, st, prof)
-              : run_batch_t<6, double>(S, w, o, threads, st, prof);
+cudaError_t launch_batch_nr(int bs, bool fp32, const DevSys& S, const DevWork& w,
+                            const DevOpts& of, int threads_f, const DevOpts& os, int threads_s,
+                            cudaStream_t st, BatchGraph* g, unsigned long long* prof) {
+  if (bs == 2) return fp32 ? run_batch_t<2, float>(S, w, of, threads_f, os, threads_s, st, g, prof)
+                           : run_batch_t<2, double>(S, w, of, threads_f, os, threads_s, st, g, prof);
+  return fp32 ? run_batch_t<6, float>(S, w, of, threads_f, os, threads_s, st, g, prof)
+              : run_batch_t<6, double>(S, w, of, threads_f, os, threads_s, st, g, prof);
 }
 
 }  // namespace pf

@@ -122,7 +122,20 @@ struct DevWork {
   // batched phase kernels: per-scenario state between launches
   int* status;               // [B] kRunning or the final pf_status
   int* refine;               // [B] this iteration takes the FP64 refinement
+  int* iter;                 // [B] index of the scenario's latest mismatch
   unsigned long long* t0;    // start time of the launch sequence (ns)
+  struct CallArgs* call;     // this call's inputs and outputs
+};
+
+// Inputs and outputs of one batched call, read by the phase kernels from
+// device memory (so that a captured graph of them serves every call).
+struct CallArgs {
+  const double* p_load;
+  const double* q_load;
+  const double* p_gen;
+  double* vm;
+  double* va;
+  pf_info* info;
 };
 
 struct DevOpts {

@@ -113,8 +113,19 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   const bool fp32 = (o.precision == PF_MIXED) && mode != RunMode::Eval;
   int threads, cluster, S, grid;
   launch_shape(c, o, B, fp32, &grid, &cluster, &threads, &S);
+  // a batch of Newton-Raphson solves runs its sweeps in a shape of their own
+  const bool phased = B > 1 && !nk && mode == RunMode::Solve;
+  int S_s = S, threads_s = threads;
+  if (phased && !o.scen_per_cta && !o.block_threads) {
+    std::lock_guard<std::mutex> lk(c->tuned_mu);
+    auto it = c->tuned.find({B, o.method, o.precision});
+    if (it != c->tuned.end() && it->second[2] > 0) {
+      S_s = it->second[2];
+      threads_s = it->second[3];
+    }
+  }
   DevSys sys;
-  rc = sb.lanes_for(threads, S, sys);
+  rc = sb.lanes_for(threads_s, S_s, sys);
   if (rc != PF_OK) return rc;
   DevWork w = ws->w;
   w.B = B;
@@ -153,12 +164,15 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   d.ring = 0;
   const size_t extra = dynamic_smem_bytes(bs, tf, nk, n, d, threads);
   d.y_in_smem = (B == 1 && (size_t)n * bs * tf + extra <= 200 * 1024) ? 1 : 0;
-  if (B > 1 && !nk && mode == RunMode::Solve) {
+  if (phased) {
     // a batch of Newton-Raphson solves: phase kernels; the factorisation of
     // 2x2 blocks stages its gathers in shared memory
     d.ring = (S > 1 && bs == 2) ? 1 : 0;
+    DevOpts ds = d;
+    ds.S = S_s;
     unsigned long long hprof[kProfPhases] = {};
-    cudaError_t e = launch_batch_nr(bs, fp32, sys, w, d, threads, st, prof ? hprof : nullptr);
+    cudaError_t e = launch_batch_nr(bs, fp32, sys, w, d, threads, ds, threads_s, st, &ws->graph,
+                                    prof ? hprof : nullptr);
     if (e == cudaSuccess && prof) {
       // the launches have finished (the profile waited for its last event)
       unsigned long long cur[kProfPhases];
@@ -410,47 +424,77 @@ int autotune(pf_case c, int B, pf_opts* io) {
   cudaSetDevice(c->ctx->device);
   cudaStream_t st = c->ctx->stream;
   Workspace* ws = &c->wsB;
+  const bool nr = o.method == PF_NR;
   cudaEvent_t e0, e1;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) return cuda_error(e, "creating timing events");
-  const int max_threads = (c->bs == 2 && o.method != PF_NK) ? 512 : 256;
-  float best = 1e30f;
-  int bestS = 0, bestT = 0;
-  for (int S : {1, 2, 4, 8}) {
+  // Newton-Raphson batches: the factorisation and the sweeps are separate
+  // launches whose times (per-phase profile) do not depend on each other's
+  // shape, so each gets its own fastest shape
+  unsigned long long* d_prof = nullptr;
+  if (nr) e = cudaMalloc(&d_prof, kProfPhases * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cuda_error(e, "allocating the profile counters");
+  }
+  const int max_threads = (c->bs == 2 && nr) ? 512 : 256;
+  float best = 1e30f, best_f = 1e30f, best_s = 1e30f;
+  int bestS = 0, bestT = 0, bestS_s = 0, bestT_s = 0;
+  for (int S : {1, 2, 4, 8, 16}) {
+    if (S > 8 && (!nr || 2 * S > B)) continue;
     for (int T : {128, 256, 512}) {
       if (T > max_threads) continue;
       pf_opts t = o;
       t.scen_per_cta = S;
       t.block_threads = T;
       float ms = 1e30f;
+      unsigned long long h[kProfPhases] = {};
       for (int rep = 0; rep < 2 && rc == PF_OK; ++rep) {
-        e = cudaEventRecord(e0, st);
+        if (nr) e = cudaMemsetAsync(d_prof, 0, kProfPhases * sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
         if (e == cudaSuccess)
           rc = run_solve(c, t, B, nullptr, nullptr, nullptr, ws, st, RunMode::Solve, nullptr,
-                         nullptr);
+                         nullptr, nullptr, (nr && rep > 0) ? d_prof : nullptr);
         if (rc == PF_OK && e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (rc == PF_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
         float x = 0;
         if (rc == PF_OK && e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+        if (rc == PF_OK && e == cudaSuccess && nr && rep > 0)
+          e = cudaMemcpy(h, d_prof, sizeof(h), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = cuda_error(e, "timing a candidate shape");
         if (rep > 0) ms = x;  // the first run warms up
       }
       if (rc != PF_OK) break;
-      if (ms < best) {
+      if (!nr && ms < best) {
         best = ms;
         bestS = S;
         bestT = T;
+      }
+      if (nr) {
+        const float f = (float)h[kProfFactor], sv = (float)h[kProfSolve];
+        if (f < best_f) {
+          best_f = f;
+          bestS = S;
+          bestT = T;
+        }
+        if (sv < best_s) {
+          best_s = sv;
+          bestS_s = S;
+          bestT_s = T;
+        }
       }
     }
     if (rc != PF_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (d_prof) cudaFree(d_prof);
   if (rc != PF_OK) return rc;
   {
     std::lock_guard<std::mutex> lk(c->tuned_mu);
-    c->tuned[{B, o.method, o.precision}] = {bestS, bestT};
+    c->tuned[{B, o.method, o.precision}] = {bestS, bestT, bestS_s, bestT_s};
   }
   io->scen_per_cta = bestS;
   io->block_threads = bestT;
