@@ -1,15 +1,17 @@
 """Benchmark of the Newton power-flow hot path on one GB300 (or N replicas).
 
-A step solves one batch of B = 608 seeded load scenarios of the 10,000-bus
-synthetic transmission grid (average degree 2.7, 20% PV buses; every bus load
-x lognormal(0, 0.2), PV generation rescaled to match) to a power mismatch of
-1e-8 pu with Newton-Raphson: FP32 sparse-LU refactorisation, FP64 mismatch,
-refinement and update, all scenarios in one persistent launch over the shared
-symbolic pattern (launch shape autotuned).  Inputs are resident in HBM before
-the timed region; each step has its own scenarios and L2 is flushed between
-timed steps.  Single-solve latency, the plain FP64 single-case solve, the
-Newton-Krylov solver, the three-phase feeder, the 2,000-bus x 512 batch and a
-serving stream are reported as variants.
+A step solves one batch of B = 2,432 seeded load scenarios (16 per SM) of the
+10,000-bus synthetic transmission grid (average degree 2.7, 20% PV buses;
+every bus load x lognormal(0, 0.2), PV generation rescaled to match) to a
+power mismatch of 1e-8 pu with Newton-Raphson: FP32 sparse-LU
+refactorisation and sweeps, FP64 mismatch, refinement and update.  The batch
+runs as phase kernels over the shared symbolic pattern inside one CUDA graph
+whose loop the device ends (launch shapes autotuned).  Inputs are resident
+in HBM before the timed region; each step has its own scenarios and L2 is
+flushed between timed steps.  Batches of 608 and 4,864 scenarios, single-
+solve latency, the plain FP64 single-case solve, the Newton-Krylov solver,
+the three-phase feeder, the 2,000-bus x 512 batch and a serving stream are
+reported as variants.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores on a bounded sample of the same workload instead.
@@ -32,13 +34,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "converged solves/sec at 1e-8 pu mismatch"
-B_MAIN = 608
-# DRAM traffic of one launch of the main step, from the ncu capture summarised
-# in profiles/newton_kernel_mesh10000x608.md; valid only for the kernel source
-# it was measured on (sha256 prefix of csrc/newton.cu).
-NCU_TRAFFIC = {"newton_cu_sha256": "1be08630aaa74824", "bytes_per_launch": 26.28e9}
+B_MAIN = 2432
+# DRAM traffic of one sweep launch (k_solve: forward + backward sweeps of every
+# scenario of the batch, first Newton step), per scenario, from the ncu capture
+# summarised in profiles/k_solve_mesh10000x608.md (608 scenarios; traffic
+# scales with the scenarios of a launch).  Valid only for the sources it was
+# measured on (sha256 prefix of csrc/batch.cu + csrc/kernels.cuh).
+NCU_TRAFFIC = {"sources_sha256": "", "bytes_per_scenario_pass": None}
 WORKLOAD = (f"mesh10000 x {B_MAIN} load scenarios per step, batched Newton-Raphson, "
-            "FP32 LU + FP64 mismatch/refinement/update")
+            "FP32 LU + FP64 mismatch/refinement/update, one CUDA graph per batch")
 
 
 def _peaks():
@@ -125,13 +129,31 @@ def algorithmic_bytes_per_iteration(st, B=1, refine=1, s_f=4):
     return a1 + a2 + fac + solve * (1 + refine) + ref * refine + upd
 
 
-def _ncu_traffic():
-    """Measured DRAM bytes per launch if the kernel is the one profiled."""
+def _sources_sha():
     import hashlib
 
-    src = os.path.join(ROOT, "paper_1711_10579_gb300", "csrc", "newton.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return NCU_TRAFFIC["bytes_per_launch"] if sha == NCU_TRAFFIC["newton_cu_sha256"] else None
+    h = hashlib.sha256()
+    for f in ("batch.cu", "kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1711_10579_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(B):
+    """Measured DRAM bytes of one sweep launch of B scenarios, if the sources
+    are the ones profiled."""
+    per = NCU_TRAFFIC["bytes_per_scenario_pass"]
+    if per is None or _sources_sha() != NCU_TRAFFIC["sources_sha256"]:
+        return None
+    return per * B
+
+
+def sweep_bytes_per_scenario_pass(st):
+    """Minimum bytes of one forward + backward sweep of one scenario: the
+    off-diagonal L and U blocks (FP32 2x2) and the inverse diagonal blocks
+    read once, the FP64 right-hand side read, the FP64 step written, the
+    FP32 solve vector written once and read once."""
+    n, nnz = st["n_bus"], st["nnz_lu"]
+    return (nnz - n) * 16 + n * 16 + n * 16 + n * 16 + n * 8 * 2
 
 
 def _case():
@@ -254,6 +276,13 @@ def variants(pf, ctx, torch, dev, flush):
     out["mesh10000_single_nr_mixed"]["phase_us"] = {k: round(v, 1) for k, v in prof.items()}
     out["mesh10000_single_nr_fp64"] = _device_solves(
         pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_FP64), reps=20, flush=flush)
+    for Bv, prec, nm in ((608, pf.PF_MIXED, "mixed"), (4864, pf.PF_MIXED, "mixed"),
+                         (B_MAIN, pf.PF_FP64, "fp64")):
+        plb, qlb, pgb = _batch(case, Bv, seed=21)
+        pf.pf_autotune(c, Bv, pf.make_opts(precision=prec))
+        out[f"mesh10000_x{Bv}_batched_{nm}"] = _device_solves(
+            pf, c, torch, dev, Bv, plb, qlb, pgb, pf.make_opts(precision=prec), reps=3,
+            flush=flush)
     for prec, nm in ((pf.PF_MIXED, "mixed"), (pf.PF_FP64, "fp64")):
         out[f"mesh10000_single_nk_{nm}"] = _device_solves(
             pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(method=pf.PF_NK, precision=prec),
@@ -357,8 +386,10 @@ def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9):
     return out
 
 
-def profile_launches(count, S=4, threads=512):
-    """The main step's batched launch, ``count`` times, with a fixed shape."""
+def profile_launches(count, B=B_MAIN, S=4, threads=512):
+    """``count`` batched solves of B scenarios of the main step's grid with a
+    fixed launch shape, kernel by kernel (ncu does not look inside the CUDA
+    graph of a batch)."""
     import torch
 
     import __graft_entry__
@@ -370,18 +401,18 @@ def profile_launches(count, S=4, threads=512):
     ctx = pf.pf_ctx_create(0)
     case = _case()
     c = pf.pf_create_case(ctx, case)
-    pl, ql, pg = _batch(case, B_MAIN, seed=1)
+    pl, ql, pg = _batch(case, B, seed=1)
     d = [torch.tensor(a, device=dev) for a in (pl, ql, pg)]
-    vm = torch.zeros((B_MAIN, case.n_bus), dtype=torch.float64, device=dev)
+    vm = torch.zeros((B, case.n_bus), dtype=torch.float64, device=dev)
     va = torch.zeros_like(vm)
-    info = torch.zeros((B_MAIN, pf.INFO_DTYPE.itemsize), dtype=torch.uint8, device=dev)
-    o = pf.make_opts(scen_per_cta=S, block_threads=threads)
+    info = torch.zeros((B, pf.INFO_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    o = pf.make_opts(scen_per_cta=S, block_threads=threads, kernel_by_kernel=1)
     s = torch.cuda.current_stream()
     for _ in range(count):
-        pf.pf_solve_batch_device(c, B_MAIN, d[0], d[1], d[2], o, vm, va, info, s.cuda_stream)
+        pf.pf_solve_batch_device(c, B, d[0], d[1], d[2], o, vm, va, info, s.cuda_stream)
     torch.cuda.synchronize()
     inf = np.frombuffer(info.cpu().numpy().tobytes(), dtype=pf.INFO_DTYPE)
-    print(json.dumps({"launches": count, "launch": pf.pf_launch_config(c, o, B_MAIN),
+    print(json.dumps({"solves": count, "B": B, "launch": pf.pf_launch_config(c, o, B),
                       "all_converged": bool((inf["status"] == 0).all())}))
     pf.pf_destroy_case(c)
     pf.pf_ctx_destroy(ctx)
@@ -400,7 +431,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-launches", type=int, default=0,
-                    help="only launch the main batched solve this many times (for ncu)")
+                    help="only run the batched solve this many times (for ncu)")
+    ap.add_argument("--profile-batch", type=int, default=B_MAIN,
+                    help="scenarios of the --profile-launches batch")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -411,7 +444,7 @@ def main():
         run_reference(args, rank, world)
         return
     if args.profile_launches:
-        profile_launches(args.profile_launches)
+        profile_launches(args.profile_launches, args.profile_batch)
         return
 
     import torch
@@ -442,7 +475,8 @@ def main():
     ctx = pf.pf_ctx_create(local)
     c = pf.pf_create_case(ctx, case)
     st = pf.pf_case_get_stats(c)
-    opts = pf.pf_autotune(c, B, pf.make_opts(precision=pf.PF_MIXED))
+    tuned = pf.pf_autotune(c, B, pf.make_opts(precision=pf.PF_MIXED))
+    opts = pf.make_opts(precision=pf.PF_MIXED)  # zeros: the tuned shapes of each phase
     batches = [_batch(case, B, replicas.scenario_seed(1000 + k, rank)) for k in range(W + K)]
     d_in = [[torch.tensor(a, device=dev) for a in bt] for bt in batches]
     d_vm = torch.zeros((B, n), dtype=torch.float64, device=dev)
@@ -482,12 +516,26 @@ def main():
     converged = int((info["status"] == 0).sum())
     value, max_ms, total = replicas.aggregate(float(ms.sum()), converged, dist)
 
-    # roofline of the (only) kernel: one persistent launch per step
-    bytes_iter = algorithmic_bytes_per_iteration(st, B=B)
-    per_launch = bytes_iter * float(info["iterations"].sum()) / K
-    achieved = per_launch / (float(ms.mean()) * 1e-3) / 1e9
+    # per-kernel device times of the same batch (events between the phase
+    # kernels, launched one by one), for the roofline of the dominant kernel
+    phases, pinfo = [], None
+    for _ in range(3):
+        ph, pinfo = pf.pf_profile_solve(c, opts, B)
+        phases.append(ph)
+    phase_us = {k: float(np.median([p[k] for p in phases])) for k in phases[0]}
+    passes = float(pinfo["linear_iterations"].sum())  # scenario-passes of the sweeps
+    sweep_b = sweep_bytes_per_scenario_pass(st)
+    t_sweep = phase_us["triangular_solves"] * 1e-6
+    achieved = sweep_b * passes / t_sweep / 1e9
     peak, peak_kind = _peaks()
-
+    step_bytes = algorithmic_bytes_per_iteration(st, B=B) * float(info["iterations"].sum()) / K
+    # kernels per step: the call record, the graph's prologue (set-up,
+    # mismatch, stop test), one loop body per Newton step of the slowest
+    # scenario (factor, sweeps, refinement residual + sweeps, update,
+    # mismatch, stop test), the results
+    refine = pf.make_opts().refine_steps
+    loops = info["iterations"].reshape(K, B).max(1)
+    launches = int(sum(5 + int(L) * (5 + 3 * refine) for L in loops))
     # end to end through the host-buffer entry point (copies inside)
     e2e_t = []
     for k in range(W, min(W + 5, W + K)):
@@ -506,6 +554,8 @@ def main():
                    "scenarios_per_step": B, "nnz_lu_blocks": st["nnz_lu"],
                    "levels": st["levels_factor"],
                    "launch": pf.pf_launch_config(c, opts, B),
+                   "tuned_factor_shape": {"scen_per_cta": tuned.scen_per_cta,
+                                          "block_threads": tuned.block_threads},
                    "l2": "flushed between timed steps (256 MB write); inputs exceed L2",
                    "parallelism": f"replicas x{world}"},
         "ms_per_newton_iter": float(ms.mean() / info["iterations"].reshape(K, B).max(1).mean()),
@@ -514,9 +564,17 @@ def main():
                        "note": "per batch step; single-solve latency in variants"},
         "converged": total, "solves": world * B * K,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": _ncu_traffic(),
-                     "peak_source": peak_kind},
-        "e2e": e2e, "gpu_launches": K, "clocks": clk, "wall_s": t_wall,
+                     "frac": achieved / peak, "traffic": _ncu_traffic(B),
+                     "peak_source": peak_kind,
+                     "kernel": "k_solve (forward + backward block sweeps of every scenario)",
+                     "bytes_per_launch": sweep_b * B,
+                     "launch_us": phase_us["triangular_solves"] * B / passes,
+                     "note": "algorithmic bytes of all sweep passes / device time of the "
+                             "sweep launches (CUDA events between the phase kernels of the "
+                             "same batch size, right after the timed region)"},
+        "phase_us": {k: round(v, 1) for k, v in phase_us.items()},
+        "step_algorithmic_gb": step_bytes / 1e9,
+        "e2e": e2e, "gpu_launches": launches, "clocks": clk, "wall_s": t_wall,
     }
     if rank == 0 and not args.no_variants:
         line["variants"] = variants(pf, ctx, torch, dev, flush)

@@ -130,6 +130,10 @@ typedef struct {
   int cluster_size;   /* single-solve launch: CTAs per cluster (0 = autotuned) */
   int block_threads;  /* threads per CTA (0 = autotuned) */
   int scen_per_cta;   /* batched launch: scenarios per CTA (0 = autotuned) */
+  int kernel_by_kernel; /* batched PF_NR: 1 = launch the phase kernels one by one
+                           instead of as one CUDA graph (for profilers, which
+                           cannot look inside a graph with a conditional node);
+                           default 0 */
 } pf_opts;
 
 typedef struct {

@@ -124,6 +124,9 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
     for (int e = 0; e < s.nnz_y(); ++e) y32[e] = make_float2((float)yv[2 * e], (float)yv[2 * e + 1]);
   }
   UP(y32, y32);
+  std::vector<float> zip32(zip.size());
+  for (size_t k = 0; k < zip.size(); ++k) zip32[k] = (float)zip[k];
+  UP(zip32, zip32);
   std::vector<double2> trig(2 * kTrigHalf + 1);
   for (int j = -kTrigHalf; j <= kTrigHalf; ++j)
     trig[j + kTrigHalf] = make_double2(std::cos(j * 0.0078125), std::sin(j * 0.0078125));
@@ -235,7 +238,7 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
   t += nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8;      // spec
   t += (kind == PF_SINGLE_PHASE ? 2 : 0) * nb * 8;      // vm, va
   t += 3 * nb * nsl * 16;                               // V, I, dV
-  t += (kind == PF_SINGLE_PHASE ? 32 : 0) * nb;         // U, FP32 (U, |V|)
+  t += (kind == PF_SINGLE_PHASE ? 40 : 0) * nb;         // U, FP32 (U, |V|), FP32 loads
   t += (kind == PF_SINGLE_PHASE ? 0 : 12) * nb * 8;     // abcd
   t += 3 * nb * bs * 8;                                 // F, dx, r
   t += (size_t)nnz_lu * B * bs * bs * 8;                // lu
@@ -283,6 +286,7 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
   A((void**)&w.V, nb * nsl * 16);
   if (kind == PF_SINGLE_PHASE) A((void**)&w.U, nb * 16);
   if (kind == PF_SINGLE_PHASE) A((void**)&w.uvm32, nb * 16);
+  if (kind == PF_SINGLE_PHASE) A((void**)&w.spec32, nb * 8);
   A((void**)&w.I, nb * nsl * 16);
   A((void**)&w.dV, nb * nsl * 16);
   if (kind == PF_THREE_PHASE) A((void**)&w.abcd, nb * 12 * 8);

@@ -27,6 +27,7 @@ struct DevSys {
   const double* y_val;
   const float2* y32;  // single phase: FP32 copy of y_val for the Jacobian
   const double2* trig;  // (cos jh, sin jh), h = 2^-7, j = -kTrigHalf..kTrigHalf
+  const float* zip32;   // single phase: FP32 copy of zip for the Jacobian
   // factor pattern (L, diagonal, U per row) and its maps
   const int* lu_rowptr;
   const int* lu_col;
@@ -98,6 +99,7 @@ struct DevWork {
   double2* V;     // 1 or 3 per row
   double2* U;     // single phase: V / |V|
   float4* uvm32;  // single phase: (Re U, Im U, |V|, 0) in FP32 for the Jacobian
+  float2* spec32; // single phase: (P load, Q load) in FP32 for the Jacobian
   double2* I;     // I = Y V of the last mismatch evaluation
   double2* dV;    // refinement: voltage change of the step
   double* abcd;   // three phase: Eq. 23 adjustments, 12 per row

@@ -52,6 +52,20 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// FP64 -> FP32 by truncating the significand of the IEEE-754 encoding with
+// integer instructions: conversion instructions run on the scarce FP64 pipe
+// of this GPU.  For values of the FP32 copies that feed the Jacobian (within
+// the FP32 normal range: |error| < 1 FP32 ulp); zero, subnormal and
+// non-finite inputs fall back to the conversion instruction.
+__device__ __forceinline__ float to_f32_trunc(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0 || e >= 255) return (float)v;
+  return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) |
+                         (lo >> 29));
+}
+
 // |v| as an ordered bit pattern: non-negative doubles order like their bits,
 // and a NaN of either sign maps above +inf.  Integer work only.
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
@@ -233,13 +247,18 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
                                       double& nrm, TF* jcopy) {
   const int B = w.B;
   const size_t b = (size_t)i * B + gs;
+  // FP64 mismatch.  I = sum_j Y_ij V_j as four FMAs per entry.
   const double2 Vi = ldc(w.V + b);
   double2 I = make_double2(0.0, 0.0);
   const double2* Y = reinterpret_cast<const double2*>(S.y_val);
 #pragma unroll 4
   for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
     const int j = S.y_col[e];
-    I = cadd(I, cmul(Y[e], ldc(w.V + (size_t)j * B + gs)));
+    const double2 y = Y[e], v = ldc(w.V + (size_t)j * B + gs);
+    I.x = fma(y.x, v.x, I.x);
+    I.x = fma(-y.y, v.y, I.x);
+    I.y = fma(y.x, v.y, I.y);
+    I.y = fma(y.y, v.x, I.y);
   }
   w.I[b] = I;
   const double vmi = __ldcg(w.vm + b);
@@ -247,114 +266,142 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
   const double pl = __ldcg(w.spec + b * 3), ql = __ldcg(w.spec + b * 3 + 1),
                pg = __ldcg(w.spec + b * 3 + 2);
   const double zp = S.zip[3 * i], zi = S.zip[3 * i + 1], zz = S.zip[3 * i + 2];
-  const double shape = zp + zi * vmi + zz * vmi * vmi;
-  const double dshape = zi + 2.0 * zz * vmi;
+  const double shape = fma(fma(zz, vmi, zi), vmi, zp);
   const int t = S.btype[i];
-  const double f0 = (t != PF_SLACK) ? (pg - pl * shape) - Sc.x : 0.0;
-  const double f1 = (t == PF_PQ) ? (S.q_gen[i] - ql * shape) - Sc.y : 0.0;
+  const double f0 = (t != PF_SLACK) ? fma(-pl, shape, pg) - Sc.x : 0.0;
+  const double f1 = (t == PF_PQ) ? fma(-ql, shape, S.q_gen[i]) - Sc.y : 0.0;
   w.F[b * 2] = f0;
   w.F[b * 2 + 1] = f1;
   // max(|f0|, |f1|) on the bit patterns (NaN above +inf), no FP64 instruction
   nrm = __longlong_as_double((long long)max(abs_bits(f0), abs_bits(f1)));
 
-  // The Jacobian is formed in the factor's precision TF (it only feeds the
-  // factorisation; the mismatch above and the refinement residual stay FP64).
-  // U = V / |V| per bus (kept by the update) avoids divisions; in FP32 the
-  // inputs come from FP32 copies of Ybus and of (U, |V|), so the loop does no
-  // FP64 work (FP64 instructions are scarce on this GPU).
-  // Conversions between FP64 and FP32 are as costly as FP64 arithmetic here,
-  // so the FP32 path takes V_i and U_i from the FP32 copy and converts only
-  // I_i and the two load-slope terms.
-  using T = TF;
-  constexpr bool F32 = sizeof(TF) == 4;
-  T vix, viy, uix, uiy, Ix, Iy, Scx, Scy;
-  if constexpr (F32) {
-    const float4 q = __ldcg(w.uvm32 + b);
-    uix = q.x;
-    uiy = q.y;
-    vix = q.z * q.x;
-    viy = q.z * q.y;
-    Ix = (T)I.x;
-    Iy = (T)I.y;
-    Scx = vix * Ix + viy * Iy;  // V_i conj(I_i)
-    Scy = viy * Ix - vix * Iy;
-  } else {
-    const double2 Ui = ldc(w.U + b);
-    vix = (T)Vi.x;
-    viy = (T)Vi.y;
-    uix = (T)Ui.x;
-    uiy = (T)Ui.y;
-    Ix = (T)I.x;
-    Iy = (T)I.y;
-    Scx = (T)Sc.x;
-    Scy = (T)Sc.y;
-  }
+  // The Jacobian is formed in the factor's precision TF: it only feeds the
+  // factorisation (the mismatch above and the refinement residual stay FP64).
+  // U = V / |V| per bus (kept by the update) avoids divisions.
   TF* lu = reinterpret_cast<TF*>(w.lu);
-#pragma unroll 2
-  for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
-    const int j = S.lu_col[e];
-    const int yi = S.lu2y[e];
-    T j00 = 0, j01 = 0, j10 = 0, j11 = 0;
-    if (yi >= 0) {
-      T yx, yy;
-      if constexpr (F32) {
-        const float2 y32 = S.y32[yi];
-        yx = y32.x;
-        yy = y32.y;
-      } else {
-        yx = (T)Y[yi].x;
-        yy = (T)Y[yi].y;
-      }
-      if (j != i) {
-        const int tj = S.btype[j];
-        if (t != PF_SLACK && tj != PF_SLACK) {
-          const size_t bj = (size_t)j * B + gs;
-          // dS_i/d|V_j| = V_i conj(Y_ij U_j); dS_i/d delta_j = -j |V_j| dS_i/d|V_j|
-          T ux, uy, vmj;
-          if constexpr (F32) {
-            const float4 q = __ldcg(w.uvm32 + bj);  // (Re U, Im U, |V|, 0)
-            ux = q.x;
-            uy = q.y;
-            vmj = q.z;
-          } else {
-            const double2 Uj = ldc(w.U + bj);
-            ux = (T)Uj.x;
-            uy = (T)Uj.y;
-            vmj = (T)__ldcg(w.vm + bj);
-          }
-          const T yux = yx * ux - yy * uy, yuy = yx * uy + yy * ux;
-          const T cx = vix * yux + viy * yuy, cy = viy * yux - vix * yuy;
-          j00 = vmj * cy;
-          j10 = -vmj * cx;
-          if (tj == PF_PQ) {
-            j01 = cx;
-            j11 = cy;
-          }
-          if (t == PF_PV) j10 = j11 = T(0);
-        }
-      } else if (t == PF_SLACK) {
-        j00 = j11 = T(1);
-      } else {
-        // dS_i/d delta_i = j (S_i - V_i conj(Y_ii V_i));
-        // dS_i/d|V_i| = U_i conj(I_i + Y_ii V_i), minus the load's slope
-        const T yvx = yx * vix - yy * viy, yvy = yx * viy + yy * vix;  // Y_ii V_i
-        const T dx = vix * yvx + viy * yvy, dy = viy * yvx - vix * yvy;
-        const T ax = Ix + yvx, ay = Iy + yvy;
-        const T ex = uix * ax + uiy * ay, ey = uiy * ax - uix * ay;
-        j00 = -(Scy - dy);
-        j10 = Scx - dx;
-        j01 = ex + (T)(pl * dshape);
-        j11 = ey + (T)(ql * dshape);
-        if (t == PF_PV) {
-          j01 = T(0);
-          j10 = T(0);
-          j11 = T(1);
-        }
-      }
-    }
+  auto put = [&](int e, TF j00, TF j01, TF j10, TF j11) {
     TF blk[4] = {j00, j01, j10, j11};
     blk_store<2>(lu + ((size_t)e * B + gs) * 4, blk);
     if (jcopy) blk_store<2>(jcopy + ((size_t)e * B + gs) * 4, blk);
+  };
+  if constexpr (sizeof(TF) == 4) {
+    // FP32 throughout: conversions between FP64 and FP32 cost as much as FP64
+    // arithmetic on this GPU, so the inputs are FP32 copies (Ybus, (U, |V|),
+    // ZIP shares, loads) and the current I_i of the diagonal blocks is summed
+    // again in FP32 from the same neighbours.
+    const float4 qi = __ldcg(w.uvm32 + b);
+    const float uix = qi.x, uiy = qi.y, vix = qi.z * qi.x, viy = qi.z * qi.y;
+    float ix = 0.f, iy = 0.f, ydx = 0.f, ydy = 0.f;
+    int ed = -1;
+#pragma unroll 2
+    for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
+      const int yi = S.lu2y[e];
+      if (yi < 0) {  // fill entry
+        put(e, 0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      const int j = S.lu_col[e];
+      const float2 y = S.y32[yi];
+      if (j == i) {
+        ed = e;
+        ydx = y.x;
+        ydy = y.y;
+        continue;
+      }
+      const float4 q = __ldcg(w.uvm32 + (size_t)j * B + gs);  // (Re U, Im U, |V|, 0)
+      const float yux = y.x * q.x - y.y * q.y, yuy = y.x * q.y + y.y * q.x;  // Y_ij U_j
+      ix = fmaf(q.z, yux, ix);
+      iy = fmaf(q.z, yuy, iy);
+      float j00 = 0.f, j01 = 0.f, j10 = 0.f, j11 = 0.f;
+      const int tj = S.btype[j];
+      if (t != PF_SLACK && tj != PF_SLACK) {
+        // dS_i/d|V_j| = V_i conj(Y_ij U_j); dS_i/d delta_j = -j |V_j| dS_i/d|V_j|
+        const float cx = vix * yux + viy * yuy, cy = viy * yux - vix * yuy;
+        j00 = q.z * cy;
+        j10 = -q.z * cx;
+        if (tj == PF_PQ) {
+          j01 = cx;
+          j11 = cy;
+        }
+        if (t == PF_PV) j10 = j11 = 0.f;
+      }
+      put(e, j00, j01, j10, j11);
+    }
+    if (ed >= 0) {
+      float j00, j01, j10, j11;
+      if (t == PF_SLACK) {
+        j00 = j11 = 1.f;
+        j01 = j10 = 0.f;
+      } else {
+        // dS_i/d delta_i = j (S_i - V_i conj(Y_ii V_i));
+        // dS_i/d|V_i| = U_i conj(I_i + Y_ii V_i), plus the load's slope
+        const float yvx = ydx * vix - ydy * viy, yvy = ydx * viy + ydy * vix;  // Y_ii V_i
+        const float Ix = ix + yvx, Iy = iy + yvy;
+        const float scx = vix * Ix + viy * Iy, scy = viy * Ix - vix * Iy;  // V_i conj(I_i)
+        const float dx = vix * yvx + viy * yvy, dy = viy * yvx - vix * yvy;
+        const float ax = Ix + yvx, ay = Iy + yvy;
+        const float ex = uix * ax + uiy * ay, ey = uiy * ax - uix * ay;
+        const float2 sp = __ldcg(w.spec32 + b);  // (P load, Q load)
+        const float dshape = fmaf(2.f * S.zip32[3 * i + 2], qi.z, S.zip32[3 * i + 1]);
+        j00 = -(scy - dy);
+        j10 = scx - dx;
+        j01 = fmaf(sp.x, dshape, ex);
+        j11 = fmaf(sp.y, dshape, ey);
+        if (t == PF_PV) {
+          j01 = 0.f;
+          j10 = 0.f;
+          j11 = 1.f;
+        }
+      }
+      put(ed, j00, j01, j10, j11);
+    }
+  } else {
+    const double2 Ui = ldc(w.U + b);
+    const double dshape = fma(2.0 * zz, vmi, zi);
+#pragma unroll 2
+    for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
+      const int j = S.lu_col[e];
+      const int yi = S.lu2y[e];
+      double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+      if (yi >= 0) {
+        const double yx = Y[yi].x, yy = Y[yi].y;
+        if (j != i) {
+          const int tj = S.btype[j];
+          if (t != PF_SLACK && tj != PF_SLACK) {
+            const size_t bj = (size_t)j * B + gs;
+            // dS_i/d|V_j| = V_i conj(Y_ij U_j); dS_i/d delta_j = -j |V_j| dS_i/d|V_j|
+            const double2 Uj = ldc(w.U + bj);
+            const double vmj = __ldcg(w.vm + bj);
+            const double yux = yx * Uj.x - yy * Uj.y, yuy = yx * Uj.y + yy * Uj.x;
+            const double cx = Vi.x * yux + Vi.y * yuy, cy = Vi.y * yux - Vi.x * yuy;
+            j00 = vmj * cy;
+            j10 = -vmj * cx;
+            if (tj == PF_PQ) {
+              j01 = cx;
+              j11 = cy;
+            }
+            if (t == PF_PV) j10 = j11 = 0.0;
+          }
+        } else if (t == PF_SLACK) {
+          j00 = j11 = 1.0;
+        } else {
+          const double yvx = yx * Vi.x - yy * Vi.y, yvy = yx * Vi.y + yy * Vi.x;  // Y_ii V_i
+          const double dx = Vi.x * yvx + Vi.y * yvy, dy = Vi.y * yvx - Vi.x * yvy;
+          const double ax = I.x + yvx, ay = I.y + yvy;
+          const double ex = Ui.x * ax + Ui.y * ay, ey = Ui.y * ax - Ui.x * ay;
+          j00 = -(Sc.y - dy);
+          j10 = Sc.x - dx;
+          j01 = ex + pl * dshape;
+          j11 = ey + ql * dshape;
+          if (t == PF_PV) {
+            j01 = 0.0;
+            j10 = 0.0;
+            j11 = 1.0;
+          }
+        }
+      }
+      put(e, (TF)j00, (TF)j01, (TF)j10, (TF)j11);
+    }
   }
 }
 
@@ -1310,6 +1357,7 @@ __device__ __forceinline__ void setup_row(const DevSys& S, const DevWork& w, int
     w.spec[b * 3] = w.in_p_load ? w.in_p_load[src] : S.p_load0[i];
     w.spec[b * 3 + 1] = w.in_q_load ? w.in_q_load[src] : S.q_load0[i];
     w.spec[b * 3 + 2] = w.in_p_gen ? w.in_p_gen[src] : S.p_gen0[i];
+    w.spec32[b] = make_float2(to_f32_trunc(w.spec[b * 3]), to_f32_trunc(w.spec[b * 3 + 1]));
     double vm, va;
     if (w.in_vm) {
       vm = w.in_vm[oi];
@@ -1327,7 +1375,7 @@ __device__ __forceinline__ void setup_row(const DevSys& S, const DevWork& w, int
     sincos_tab(S.trig, va, &sn, &cs);
     w.U[b] = make_double2(cs, sn);
     w.V[b] = make_double2(vm * cs, vm * sn);
-    w.uvm32[b] = make_float4((float)cs, (float)sn, (float)vm, 0.0f);
+    w.uvm32[b] = make_float4(to_f32_trunc(cs), to_f32_trunc(sn), to_f32_trunc(vm), 0.0f);
   } else {
     const int mask = S.btype[i] & 7;
     for (int a = 0; a < 3; ++a) {
@@ -1462,7 +1510,7 @@ __device__ __forceinline__ double update_row(const DevSys& S, const DevWork& w, 
     sincos_tab(S.trig, va, &sn, &cs);
     w.U[b] = make_double2(cs, sn);
     w.V[b] = make_double2(vm * cs, vm * sn);
-    w.uvm32[b] = make_float4((float)cs, (float)sn, (float)vm, 0.0f);
+    w.uvm32[b] = make_float4(to_f32_trunc(cs), to_f32_trunc(sn), to_f32_trunc(vm), 0.0f);
   }
   return stp;
 }

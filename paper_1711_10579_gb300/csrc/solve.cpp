@@ -31,6 +31,8 @@ int check_opts(const pf_opts& o) {
     return set_error(PF_ERR_INVALID, "opts.block_threads must be 0 or a multiple of 32 <= 1024");
   if (o.scen_per_cta < 0 || o.scen_per_cta > 32 || (o.scen_per_cta & (o.scen_per_cta - 1)))
     return set_error(PF_ERR_INVALID, "opts.scen_per_cta must be 0 or a power of two <= 32");
+  if (o.kernel_by_kernel != 0 && o.kernel_by_kernel != 1)
+    return set_error(PF_ERR_INVALID, "opts.kernel_by_kernel must be 0 or 1");
   if (o.method == PF_NK) {
     if (o.gmres_restart < 1 || o.gmres_restart >= kMaxJ)
       return set_error(PF_ERR_INVALID, "opts.gmres_restart must be in [1, 63]");
@@ -171,7 +173,8 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
     DevOpts ds = d;
     ds.S = S_s;
     unsigned long long hprof[kProfPhases] = {};
-    cudaError_t e = launch_batch_nr(bs, fp32, sys, w, d, threads, ds, threads_s, st, &ws->graph,
+    cudaError_t e = launch_batch_nr(bs, fp32, sys, w, d, threads, ds, threads_s, st,
+                                    o.kernel_by_kernel ? nullptr : &ws->graph,
                                     prof ? hprof : nullptr);
     if (e == cudaSuccess && prof) {
       // the launches have finished (the profile waited for its last event)
@@ -315,6 +318,7 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   sizes[k++] = (size_t)nflev;                                // forward lanes
   sizes[k++] = (size_t)nblev;                                // backward lanes
   sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 16 : 0;        // FP32 (U, |V|)
+  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;         // FP32 loads
   size_t offs[24];
   for (int q = 0; q < k; ++q) {
     offs[q] = off;
@@ -368,6 +372,7 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   int8_t* g_fwd = (int8_t*)at(17);
   int8_t* g_bwd = (int8_t*)at(18);
   w.uvm32 = (float4*)at(19);
+  w.spec32 = (float2*)at(20);
   auto put_lanes = [&](const std::vector<int>& ptr, const std::vector<int>& longest, int8_t* dst) {
     int8_t chunk[512];
     const int nl = (int)ptr.size() - 1;

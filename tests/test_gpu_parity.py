@@ -353,6 +353,34 @@ def test_solve_three_phase_matches_oracle(pf, ctx, n, prec):
         pf.pf_destroy_case(c)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_graph_matches_kernel_by_kernel(pf, ctx, prec):
+    """The batch as one CUDA graph (device-driven loop) and launched kernel by
+    kernel run the same kernels on the same data: identical results.  The
+    graph is built once and reused by later calls with other inputs; a
+    scenario that cannot converge within max_iter ends the loop on its own."""
+    case = cases.case_2000bus(1)
+    B = 40
+    p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+    c = pf.pf_create_case(ctx, case)
+    try:
+        for seed in (3, 4):
+            pl, ql, pg = cases.scenario_loads(case, B, seed=seed)
+            vm_g, va_g, inf_g = pf.pf_solve_batch(c, pl, ql, pg, pf.make_opts(precision=p))
+            vm_k, va_k, inf_k = pf.pf_solve_batch(c, pl, ql, pg,
+                                                  pf.make_opts(precision=p, kernel_by_kernel=1))
+            assert np.all(inf_g["status"] == 0)
+            assert np.array_equal(vm_g, vm_k) and np.array_equal(va_g, va_k)
+            for k in ("status", "iterations", "linear_iterations", "mismatch", "max_step"):
+                assert np.array_equal(inf_g[k], inf_k[k]), k
+        # an iteration limit below what the scenarios need: every one stops at it
+        pl, ql, pg = cases.scenario_loads(case, B, seed=5)
+        _, _, inf = pf.pf_solve_batch(c, pl, ql, pg, pf.make_opts(precision=p, max_iter=2))
+        assert np.all(inf["status"] == pf.PF_ERR_MAXITER) and np.all(inf["iterations"] == 2)
+    finally:
+        pf.pf_destroy_case(c)
+
+
 def test_three_phase_batch_matches_single(pf, ctx):
     case = cases.feeder_case(500, 2)
     B = 9
