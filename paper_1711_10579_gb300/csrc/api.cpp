@@ -154,6 +154,9 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   UP(pl, p_load0);
   UP(ql, q_load0);
   UP(s.perm, perm);
+  std::vector<int> iperm(s.perm.size());
+  for (size_t k = 0; k < s.perm.size(); ++k) iperm[s.perm[k]] = (int)k;
+  UP(iperm, iperm);
   // packed per-item records (one 16-byte load each) for the kernels' prefetch
   std::vector<int4> fwd(n), bwd(n), fac(s.fac_items.size()), tgt(s.tgt_entry.size());
   std::vector<int2> con;

@@ -106,6 +106,41 @@ __global__ void __launch_bounds__(kRowThreads) k_setup(DevSys S, DevWork w, int 
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *w.t0 = global_ns();
 }
 
+// Single-phase set-up through 32 x 32 tiles (buses in the caller's order x
+// scenarios) staged in shared memory: the caller's [scenario][bus] inputs
+// are read along buses and the [bus][scenario] state written along
+// scenarios, both contiguous.
+__global__ void __launch_bounds__(256) k_setup_tile(DevSys S, DevWork w) {
+  __shared__ double tp[3][32][33];
+  const int n = S.n, B = w.B;
+  const int o0 = blockIdx.x * 32, g0 = blockIdx.y * 32, tx = threadIdx.x;
+  const CallArgs* c = w.call;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int gs = g0 + r, oi = o0 + tx;
+    if (gs < B && oi < n) {
+      const size_t src = (size_t)gs * n + oi;
+      const int i = S.iperm[oi];
+      tp[0][r][tx] = c->p_load ? c->p_load[src] : S.p_load0[i];
+      tp[1][r][tx] = c->q_load ? c->q_load[src] : S.q_load0[i];
+      tp[2][r][tx] = c->p_gen ? c->p_gen[src] : S.p_gen0[i];
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int oi = o0 + r, gs = g0 + tx;
+    if (oi >= n || gs >= B) continue;
+    const int i = S.iperm[oi];
+    setup_1ph(S, w, i, gs, tp[0][tx][r], tp[1][tx][r], tp[2][tx][r]);
+    if (i == 0) {
+      setup_scenario(w, gs);
+      w.status[gs] = kRunning;
+      w.refine[gs] = 0;
+      w.iter[gs] = 0;
+      if (gs == 0) *w.t0 = global_ns();
+    }
+  }
+}
+
 // Step A: mismatch, its norm and the Jacobian (iteration w.iter[gs]).
 template <int BS, typename TF>
 __global__ void __launch_bounds__(kRowThreads) k_mismatch(DevSys S, DevWork w, int sb) {
@@ -284,6 +319,32 @@ __global__ void __launch_bounds__(kRowThreads) k_output(DevSys S, DevWork w, int
     wc.out_info[t.gs].solve_us = (double)(global_ns() - __ldcg(w.t0)) * 1e-3;
 }
 
+// Single-phase results through 32 x 32 tiles (the transpose of the set-up):
+// |V| and angle in the caller's [scenario][bus] order, and the device time.
+__global__ void __launch_bounds__(256) k_output_tile(DevSys S, DevWork w) {
+  __shared__ double tv[2][32][33];
+  const int n = S.n, B = w.B;
+  const int o0 = blockIdx.x * 32, g0 = blockIdx.y * 32, tx = threadIdx.x;
+  const CallArgs* c = w.call;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int oi = o0 + r, gs = g0 + tx;
+    if (oi >= n || gs >= B) continue;
+    const int i = S.iperm[oi];
+    const size_t b = (size_t)i * B + gs;
+    tv[0][r][tx] = __ldcg(w.vm + b);
+    tv[1][r][tx] = __ldcg(w.va + b);
+    if (i == 0 && c->info) c->info[gs].solve_us = (double)(global_ns() - __ldcg(w.t0)) * 1e-3;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int gs = g0 + r, oi = o0 + tx;
+    if (gs >= B || oi >= n) continue;
+    const size_t dst = (size_t)gs * n + oi;
+    if (c->vm) c->vm[dst] = tv[0][tx][r];
+    if (c->va) c->va[dst] = tv[1][tx][r];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side: the launch sequence, direct or as one CUDA graph
 // ---------------------------------------------------------------------------
@@ -326,7 +387,16 @@ struct Plan {
       return Launch{fn, rows, blk, 0, {&S, &w, &sb}};
     };
     const Launch stop{(const void*)k_stop, dim3(1), dim3(1024), 0, {&w, &of, &has_cond, &cond}};
-    pro = {rowk((const void*)k_setup<BS>), rowk((const void*)k_mismatch<BS, TF>), stop};
+    const dim3 tiles((n + 31) / 32, (B + 31) / 32), tblk(32, 8);
+    Launch setup, output;
+    if constexpr (BS == 2) {
+      setup = Launch{(const void*)k_setup_tile, tiles, tblk, 0, {&S, &w}};
+      output = Launch{(const void*)k_output_tile, tiles, tblk, 0, {&S, &w}};
+    } else {
+      setup = rowk((const void*)k_setup<BS>);
+      output = rowk((const void*)k_output<BS>);
+    }
+    pro = {setup, rowk((const void*)k_mismatch<BS, TF>), stop};
     body.clear();
     body.push_back(Launch{(const void*)k_factor<BS, TF>, gf, dim3(threads_f), ring, {&S, &w, &of}});
     body.push_back(
@@ -340,7 +410,7 @@ struct Plan {
     body.push_back(rowk((const void*)k_update<BS>));
     body.push_back(rowk((const void*)k_mismatch<BS, TF>));
     body.push_back(stop);
-    epi = {rowk((const void*)k_output<BS>)};
+    epi = {output};
   }
 };
 
@@ -407,8 +477,10 @@ cudaError_t run_direct(Plan<BS, TF>& p, cudaStream_t st, unsigned long long* pro
     if (l.fn == fmis) return (int)kProfMismatch;
     if (l.fn == (const void*)k_stop) return (int)kProfStop;
     if (l.fn == (const void*)k_update<BS>) return (int)kProfUpdate;
-    if (l.fn == (const void*)k_setup<BS>) return (int)kProfSetup;
-    if (l.fn == (const void*)k_output<BS>) return (int)kProfOutput;
+    if (l.fn == (const void*)k_setup<BS> || l.fn == (const void*)k_setup_tile)
+      return (int)kProfSetup;
+    if (l.fn == (const void*)k_output<BS> || l.fn == (const void*)k_output_tile)
+      return (int)kProfOutput;
     return (int)kProfResidual;
   };
   for (const Launch& l : p.pro) go(l, phase(l));

@@ -70,6 +70,7 @@ struct DevSys {
   const double* p_load0; // case's own loads (per bus or per slot)
   const double* q_load0;
   const int* perm;       // new -> caller numbering
+  const int* iperm;      // caller -> new numbering
   double v_source;
 };
 

@@ -1345,6 +1345,45 @@ struct GmresState {
 // phase kernels
 // ---------------------------------------------------------------------------
 
+// Set-up of bus i (single phase), scenario gs, from its specified load and
+// generation: the injections and the start voltage.
+__device__ __forceinline__ void setup_1ph(const DevSys& S, const DevWork& w, int i, int gs,
+                                          double pl, double ql, double pg) {
+  const size_t b = (size_t)i * w.B + gs;
+  const int oi = S.perm[i];
+  w.spec[b * 3] = pl;
+  w.spec[b * 3 + 1] = ql;
+  w.spec[b * 3 + 2] = pg;
+  w.spec32[b] = make_float2(to_f32_trunc(pl), to_f32_trunc(ql));
+  double vm, va;
+  if (w.in_vm) {
+    vm = w.in_vm[oi];
+    va = w.in_va[oi];
+  } else if (w.warm_in) {
+    vm = w.warm_vm[oi];
+    va = w.warm_va[oi];
+  } else {
+    vm = (S.btype[i] == PF_PQ) ? 1.0 : S.v_set[i];
+    va = 0.0;
+  }
+  w.vm[b] = vm;
+  w.va[b] = va;
+  double sn, cs;
+  sincos_tab(S.trig, va, &sn, &cs);
+  w.U[b] = make_double2(cs, sn);
+  w.V[b] = make_double2(vm * cs, vm * sn);
+  w.uvm32[b] = make_float4(to_f32_trunc(cs), to_f32_trunc(sn), to_f32_trunc(vm), 0.0f);
+}
+
+// The accumulators of scenario gs (once per scenario, with bus 0).
+__device__ __forceinline__ void setup_scenario(const DevWork& w, int gs) {
+  w.norm[gs] = 0ull;
+  w.norm[w.B + gs] = 0ull;
+  w.step[gs] = 0ull;
+  w.step[w.B + gs] = 0ull;
+  w.flag[gs] = 0;
+}
+
 // Set-up of row i, scenario gs: specified injections, start voltage and
 // (row 0) the scenario's accumulators.
 template <bool THREE>
@@ -1354,28 +1393,9 @@ __device__ __forceinline__ void setup_row(const DevSys& S, const DevWork& w, int
   const int oi = S.perm[i];
   if (!THREE) {
     const size_t src = (size_t)gs * n + oi;
-    w.spec[b * 3] = w.in_p_load ? w.in_p_load[src] : S.p_load0[i];
-    w.spec[b * 3 + 1] = w.in_q_load ? w.in_q_load[src] : S.q_load0[i];
-    w.spec[b * 3 + 2] = w.in_p_gen ? w.in_p_gen[src] : S.p_gen0[i];
-    w.spec32[b] = make_float2(to_f32_trunc(w.spec[b * 3]), to_f32_trunc(w.spec[b * 3 + 1]));
-    double vm, va;
-    if (w.in_vm) {
-      vm = w.in_vm[oi];
-      va = w.in_va[oi];
-    } else if (w.warm_in) {
-      vm = w.warm_vm[oi];
-      va = w.warm_va[oi];
-    } else {
-      vm = (S.btype[i] == PF_PQ) ? 1.0 : S.v_set[i];
-      va = 0.0;
-    }
-    w.vm[b] = vm;
-    w.va[b] = va;
-    double sn, cs;
-    sincos_tab(S.trig, va, &sn, &cs);
-    w.U[b] = make_double2(cs, sn);
-    w.V[b] = make_double2(vm * cs, vm * sn);
-    w.uvm32[b] = make_float4(to_f32_trunc(cs), to_f32_trunc(sn), to_f32_trunc(vm), 0.0f);
+    setup_1ph(S, w, i, gs, w.in_p_load ? w.in_p_load[src] : S.p_load0[i],
+              w.in_q_load ? w.in_q_load[src] : S.q_load0[i],
+              w.in_p_gen ? w.in_p_gen[src] : S.p_gen0[i]);
   } else {
     const int mask = S.btype[i] & 7;
     for (int a = 0; a < 3; ++a) {
@@ -1400,13 +1420,7 @@ __device__ __forceinline__ void setup_row(const DevSys& S, const DevWork& w, int
       w.V[b * 3 + a] = v;
     }
   }
-  if (i == 0) {
-    w.norm[gs] = 0ull;
-    w.norm[B + gs] = 0ull;
-    w.step[gs] = 0ull;
-    w.step[B + gs] = 0ull;
-    w.flag[gs] = 0;
-  }
+  if (i == 0) setup_scenario(w, gs);
 }
 
 // Voltage change of the current step (complex), for J dx evaluated from Y
@@ -1465,8 +1479,14 @@ __device__ __forceinline__ void resid_row(const DevSys& S, const DevWork& w, int
     }
   } else {
     double2 YdV = make_double2(0.0, 0.0);
-    for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e)
-      YdV = cadd(YdV, cmul(Y[e], ldc(w.dV + (size_t)S.y_col[e] * B + gs)));
+#pragma unroll 4
+    for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
+      const double2 y = Y[e], d = ldc(w.dV + (size_t)S.y_col[e] * B + gs);
+      YdV.x = fma(y.x, d.x, YdV.x);
+      YdV.x = fma(-y.y, d.y, YdV.x);
+      YdV.y = fma(y.x, d.y, YdV.y);
+      YdV.y = fma(y.y, d.x, YdV.y);
+    }
     const double2 V = ldc(w.V + b), I = ldc(w.I + b), dV = ldc(w.dV + b);
     // dS = dV conj(I) + V conj(Y dV), plus the load's slope on |V|
     const double2 dS = cadd(cmulc(dV, I), cmulc(V, YdV));
