@@ -274,6 +274,15 @@ def variants(pf, ctx, torch, dev, flush):
     out["mesh10000_single_nr_mixed"]["launch"] = pf.pf_launch_config(c, pf.make_opts())
     prof, _ = pf.pf_profile_solve(c, pf.make_opts())
     out["mesh10000_single_nr_mixed"]["phase_us"] = {k: round(v, 1) for k, v in prof.items()}
+    # branch flows and losses (post-step) of a solved 608-scenario batch
+    plf, qlf, pgf = _batch(case, 608, seed=23)
+    vmf, vaf, _ = pf.pf_solve_batch(c, plf, qlf, pgf)
+    t0 = time.perf_counter()
+    fl = pf.pf_branch_flows(c, vmf, vaf, case.n_branch)
+    out["mesh10000_x608_branch_flows"] = {
+        "ms_host_call": 1e3 * (time.perf_counter() - t0), "B": 608, "branches": case.n_branch,
+        "mean_loss_p_pu": float(fl["loss"][:, 0].mean()),
+        "note": "pf_branch_flows with host buffers (copies inside)"}
     out["mesh10000_single_nr_fp64"] = _device_solves(
         pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_FP64), reps=20, flush=flush)
     for Bv, prec, nm in ((608, pf.PF_MIXED, "mixed"), (4864, pf.PF_MIXED, "mixed"),

@@ -330,6 +330,24 @@ int pf_solve_noalloc(pf_case c, const pf_opts* opts, const double* d_p_load,
                      double* d_vang, pf_info* d_info, void* stream);
 
 /*
+ * Branch power flows of given bus voltages (the problem statement of Sec. I
+ * asks for voltages and branch flows).  Branch models as in Ybus: Eq. 2-3
+ * (pi model: series y = 1/(r + jx), half the line charging j b/2 at each end)
+ * and Eq. 11 (three phase: y = inverse of the series impedance over the
+ * branch's phases).  For scenario b and branch k (the case's branch order),
+ * the power leaving the from bus into the branch, s_from = V_f conj(I_f),
+ * I_f = y (V_f - V_t) + j b/2 V_f, and leaving the to bus, s_to likewise;
+ * s_from + s_to is the branch loss.  vmag, vang: [B][n] (single phase) or
+ * [B][n][3] (three phase) as pf_solve_batch writes them.  Outputs [B][m]
+ * or [B][m][3] (p_from, q_from, p_to, q_to, pu) and loss[B][2] (total P and
+ * Q loss of the scenario, summed on the device in a fixed order).  Host
+ * arrays, caller-owned; blocking; PF_ERR_INVALID on null arguments.  Not
+ * in the Newton iteration: a post-step over solved voltages.
+ */
+int pf_branch_flows(pf_case c, int B, const double* vmag, const double* vang, double* p_from,
+                    double* q_from, double* p_to, double* q_to, double* loss);
+
+/*
  * Autotuner for batched solves (B >= 2): runs B copies of the case's own
  * scenario with each candidate launch shape (scenarios per CTA 1, 2, 4, 8,
  * and 16 for PF_NR when B >= 32; threads per CTA 128, 256, 512), times them

@@ -18,6 +18,10 @@ What it computes, in the paper's notation (arXiv 1711.10579):
 * ``newton_cim``         three-phase current-injection Newton (Sec. II.B box).
 * ``ilu0`` / ``gmres``   ILU(0) and restarted, right-preconditioned GMRES used
                          by the Newton-Krylov variant (Sec. III.B).
+* ``branch_flows``       power into each branch at both ends and the losses
+                         (the "power flows" output of the problem statement,
+                         Sec. I), single and three phase, from the branch
+                         models of Eq. 2-3 and Eq. 11.
 
 Readings of points the paper leaves open (the same list is kept with the
 design notes):
@@ -556,3 +560,47 @@ def newton_cim(case, tol=1e-8, max_iter=30, linear="splu", V0=None,
         steps.append(float(np.max(np.abs(dx))) if dx.size else 0.0)
     return dict(V=V, iterations=k, mismatch=history[-1], history=history,
                 steps=steps, converged=converged)
+
+
+# ---------------------------------------------------------------------------
+# branch flows (Sec. I problem statement: voltages and branch power flows)
+# ---------------------------------------------------------------------------
+
+def branch_flows(case, vm, va):
+    """Power leaving each end of each branch into it, and the total loss.
+
+    Single phase, branch k from f to t (pi model of Eq. 2): series current
+    i_s = (V_f - V_t) / (r + jx), charging current j (b/2) V at each end, so
+    the power leaving bus f is S_f = V_f conj(i_s + j (b/2) V_f) and leaving
+    bus t is S_t = V_t conj(-i_s + j (b/2) V_t).  Three phase (Eq. 11): the
+    series currents over the branch's phases are Z^-1 (V_f - V_t), with Z the
+    branch's impedance restricted to its phases, and no charging.  vm, va as
+    the solvers return them (three phase: [3 n], slot 3 i + s).  Returns
+    (p_from, q_from, p_to, q_to) per branch (three phase: [m, 3], zero on
+    absent phases) and the total loss (P, Q) = sum of S_f + S_t.
+    """
+    V = np.asarray(vm, dtype=float) * np.exp(1j * np.asarray(va, dtype=float))
+    m = case.n_branch
+    if hasattr(case, "n_bus"):
+        Sf = np.zeros(m, dtype=np.complex128)
+        St = np.zeros(m, dtype=np.complex128)
+        for k in range(m):
+            f, t = int(case.br_from[k]), int(case.br_to[k])
+            i_s = (V[f] - V[t]) / complex(case.br_r[k], case.br_x[k])
+            ch = 1j * case.br_b[k] / 2.0
+            Sf[k] = V[f] * np.conj(i_s + ch * V[f])
+            St[k] = V[t] * np.conj(-i_s + ch * V[t])
+    else:
+        Sf = np.zeros((m, 3), dtype=np.complex128)
+        St = np.zeros((m, 3), dtype=np.complex128)
+        for k in range(m):
+            f, t = int(case.br_from[k]), int(case.br_to[k])
+            ph = _phase_list(case.br_phases[k])
+            Z = case.br_z[k][np.ix_(ph, ph)]
+            dv = V[3 * f + np.asarray(ph)] - V[3 * t + np.asarray(ph)]
+            i_s = np.linalg.solve(Z, dv)
+            for a, s in enumerate(ph):
+                Sf[k, s] = V[3 * f + s] * np.conj(i_s[a])
+                St[k, s] = V[3 * t + s] * np.conj(-i_s[a])
+    loss = (Sf + St).sum()
+    return Sf.real, Sf.imag, St.real, St.imag, (loss.real, loss.imag)

@@ -644,6 +644,53 @@ int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag, const dou
   return inspect(c, InspectKind::Step, &o, vmag, vang, dx, info);
 }
 
+int pf_branch_flows(pf_case c, int B, const double* vmag, const double* vang, double* p_from,
+                    double* q_from, double* p_to, double* q_to, double* loss) {
+  if (!c || B < 1 || !vmag || !vang || !p_from || !q_from || !p_to || !q_to || !loss)
+    return set_error(PF_ERR_INVALID, "null argument or B < 1");
+  std::lock_guard<std::mutex> lk(c->mu);
+  const CaseData& d = c->data;
+  const int ph = d.kind == PF_SINGLE_PHASE ? 1 : 3, n = d.n, m = d.m;
+  std::vector<double> yb, sh;
+  std::string err;
+  int rc = branch_admittances(d, yb, sh, err);
+  if (rc != PF_OK) return set_error(rc, err);
+  std::vector<int2> ft(m);
+  for (int e = 0; e < m; ++e) ft[e] = make_int2(d.br_from[e], d.br_to[e]);
+  cudaSetDevice(c->ctx->device);
+  cudaStream_t st = c->ctx->stream;
+  DevBuffer buf;
+  const size_t nv = (size_t)B * n * ph, nf = (size_t)B * m * ph;
+  int2* d_ft = nullptr;
+  double *d_yb = nullptr, *d_sh = nullptr, *d_vm = nullptr, *d_va = nullptr, *d_out = nullptr;
+  cudaError_t e = buf.alloc((void**)&d_ft, sizeof(int2) * std::max(m, 1));
+  if (e == cudaSuccess) e = buf.alloc((void**)&d_yb, 8 * std::max<size_t>(yb.size(), 1));
+  if (e == cudaSuccess) e = buf.alloc((void**)&d_sh, 8 * std::max(m, 1));
+  if (e == cudaSuccess) e = buf.alloc((void**)&d_vm, 8 * nv);
+  if (e == cudaSuccess) e = buf.alloc((void**)&d_va, 8 * nv);
+  if (e == cudaSuccess) e = buf.alloc((void**)&d_out, 8 * (4 * nf + 2 * (size_t)B));
+  if (e == cudaSuccess && m > 0) {
+    e = cudaMemcpyAsync(d_ft, ft.data(), sizeof(int2) * m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_yb, yb.data(), 8 * yb.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_sh, sh.data(), 8 * m, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_vm, vmag, 8 * nv, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_va, vang, 8 * nv, cudaMemcpyHostToDevice, st);
+  double* o = d_out;
+  if (e == cudaSuccess)
+    e = launch_branch_flows(ph, d_ft, d_yb, d_sh, n, m, B, d_vm, d_va, o, o + nf, o + 2 * nf,
+                            o + 3 * nf, o + 4 * nf, st);
+  double* outs[4] = {p_from, q_from, p_to, q_to};
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    if (nf) e = cudaMemcpyAsync(outs[k], o + k * nf, 8 * nf, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(loss, o + 4 * nf, 16 * (size_t)B, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "computing branch flows");
+  return PF_OK;
+}
+
 int pf_autotune(pf_case c, int B, pf_opts* opts) {
   if (!c || !opts) return set_error(PF_ERR_INVALID, "null argument");
   std::lock_guard<std::mutex> lk(c->mu);

@@ -140,6 +140,11 @@ cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const Dev
                           const DevOpts& o, int grid, int cluster, int threads,
                           cudaStream_t st);
 int max_cluster(int bs, bool fp32, bool nk, int threads);
+// Branch flows and losses (flows.cu); device arrays, ph = 1 or 3.
+cudaError_t launch_branch_flows(int ph, const int2* ft, const double* yb, const double* sh, int n,
+                                int m, int B, const double* vm, const double* va, double* pf_,
+                                double* qf, double* pt, double* qt, double* loss,
+                                cudaStream_t st);
 // Batched Newton-Raphson as phase kernels (batch.cu); prof, if given, is a
 // host array of kProfPhases device times (ns) to add to.
 cudaError_t launch_batch_nr(int bs, bool fp32, const DevSys& S, const DevWork& w,

@@ -47,6 +47,10 @@ struct CaseData {
 int copy_case(const pf_case_desc* d, CaseData& out, std::string& err);
 // Eq. 2-3 (pi-model branches) or Eq. 11 (3x3 blocks).
 int build_ybus(const CaseData& c, Ybus& y, std::string& err);
+// Per-branch admittances of the same models (for branch flows): yb[m][18] as
+// 3x3 complex row-major, sh[m] the half line charging (single phase).
+int branch_admittances(const CaseData& c, std::vector<double>& yb, std::vector<double>& sh,
+                       std::string& err);
 
 // Ordering of the bus graph.
 enum class Ordering { MinDegree, RCM, Natural };

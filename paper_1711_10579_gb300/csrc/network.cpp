@@ -335,4 +335,43 @@ int build_ybus(const CaseData& c, Ybus& y, std::string& err) {
   return PF_OK;
 }
 
+// Per-branch admittances for the branch-flow kernel: yb[e] a 3x3 complex
+// matrix (row-major, (re, im) pairs; single phase: y = 1/(r + jx) at [0][0],
+// three phase: the inverse of the series impedance over the branch's phases,
+// zero elsewhere) and sh[e] = b/2 (single phase; 0 for three phase).
+int branch_admittances(const CaseData& c, std::vector<double>& yb, std::vector<double>& sh,
+                       std::string& err) {
+  yb.assign((size_t)c.m * 18, 0.0);
+  sh.assign(c.m, 0.0);
+  for (int e = 0; e < c.m; ++e) {
+    double* out = &yb[(size_t)e * 18];
+    if (c.kind == PF_SINGLE_PHASE) {
+      const cd y = 1.0 / cd(c.br_r[e], c.br_x[e]);
+      out[0] = y.real();
+      out[1] = y.imag();
+      sh[e] = c.br_b[e] / 2.0;
+      continue;
+    }
+    int ph[3], k = 0;
+    for (int s = 0; s < 3; ++s)
+      if (c.br_phases[e] >> s & 1) ph[k++] = s;
+    cd z[9], y[9];
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) {
+        const double* zz = &c.br_z[(size_t)e * 18 + 2 * (3 * ph[a] + ph[b])];
+        z[a * k + b] = cd(zz[0], zz[1]);
+      }
+    if (!invert_small(k, z, y)) {
+      err = "a branch has a singular impedance matrix";
+      return PF_ERR_INVALID;
+    }
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) {
+        out[2 * (3 * ph[a] + ph[b])] = y[a * k + b].real();
+        out[2 * (3 * ph[a] + ph[b]) + 1] = y[a * k + b].imag();
+      }
+  }
+  return PF_OK;
+}
+
 }  // namespace pf

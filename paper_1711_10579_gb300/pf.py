@@ -123,6 +123,7 @@ def lib():
             "pf_launch_config": (C.c_int, [vp, C.POINTER(pf_opts), C.c_int, _ip, _ip, _ip, _ip]),
             "pf_solve_noalloc": (C.c_int, [vp, C.POINTER(pf_opts), vp, vp, vp, vp, vp, vp, vp]),
             "pf_autotune": (C.c_int, [vp, C.c_int, C.POINTER(pf_opts)]),
+            "pf_branch_flows": (C.c_int, [vp, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -339,6 +340,25 @@ def pf_solve_batch(c: CaseHandle, p_load, q_load, p_gen=None, opts: pf_opts | No
                                 _ptr(vm, C.c_double), _ptr(va, C.c_double),
                                 info.ctypes.data_as(C.POINTER(pf_info))))
     return vm, va, info
+
+
+def pf_branch_flows(c: CaseHandle, vmag, vang, n_branch: int):
+    """Branch flows of voltages [B, slots] (or [slots]): dict of p_from,
+    q_from, p_to, q_to [B, n_branch * ph] and loss [B, 2] (P, Q)."""
+    vm = np.ascontiguousarray(vmag, dtype=np.float64)
+    va = np.ascontiguousarray(vang, dtype=np.float64)
+    B = vm.shape[0] if vm.ndim == 2 else 1
+    vm = vm.reshape(B, -1)
+    va = va.reshape(B, -1)
+    ph = 1 if c.kind == PF_SINGLE_PHASE else 3
+    out = {k: np.zeros((B, n_branch * ph)) for k in ("p_from", "q_from", "p_to", "q_to")}
+    loss = np.zeros((B, 2))
+    _check(lib().pf_branch_flows(c.handle, B, _ptr(vm, C.c_double), _ptr(va, C.c_double),
+                                 *[_ptr(out[k], C.c_double)
+                                   for k in ("p_from", "q_from", "p_to", "q_to")],
+                                 _ptr(loss, C.c_double)))
+    out["loss"] = loss
+    return out
 
 
 def pf_solve_batch_device(c: CaseHandle, B, d_p_load, d_q_load, d_p_gen, opts, d_vmag, d_vang,

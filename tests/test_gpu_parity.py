@@ -473,3 +473,50 @@ def test_newton_krylov_batch_matches_single(pf, ctx):
             assert np.max(np.abs(va[b] - ref["va"])) <= A_TOL
     finally:
         pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# branch flows (Sec. I outputs), a post-step over solved voltages
+# ----------------------------------------------------------------------------
+
+def test_branch_flows_match_oracle_single_phase(pf, ctx):
+    case = cases.case_2000bus(2)
+    B = 5
+    pl, ql, pg = cases.scenario_loads(case, B, seed=6)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve_batch(c, pl, ql, pg)
+        assert np.all(info["status"] == 0)
+        rng = np.random.default_rng(1)
+        vm[1] = rng.uniform(0.9, 1.1, case.n_bus)  # an arbitrary voltage too
+        va[1] = rng.uniform(-0.5, 0.5, case.n_bus)
+        got = pf.pf_branch_flows(c, vm, va, case.n_branch)
+        for b in range(B):
+            ref = O.branch_flows(case, vm[b], va[b])
+            scale = max(1.0, np.max(np.abs(ref[0])))
+            for k, key in enumerate(("p_from", "q_from", "p_to", "q_to")):
+                assert np.max(np.abs(got[key][b] - ref[k])) <= 1e-12 * scale, key
+            assert abs(got["loss"][b, 0] - ref[4][0]) <= 1e-10 * scale
+            assert abs(got["loss"][b, 1] - ref[4][1]) <= 1e-10 * scale
+        # at a solution the losses are the net specified injection plus slack
+        Y = O.ybus_single(case)
+        V = vm[0] * np.exp(1j * va[0])
+        assert abs(got["loss"][0, 0] - (V * np.conj(Y @ V)).real.sum()) < 1e-9
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_branch_flows_match_oracle_three_phase(pf, ctx):
+    case = cases.feeder_case(400, 3)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve(c)
+        assert info["status"] == 0
+        got = pf.pf_branch_flows(c, vm, va, case.n_branch)
+        ref = O.branch_flows(case, vm, va)
+        scale = max(1.0, np.max(np.abs(ref[0])))
+        for k, key in enumerate(("p_from", "q_from", "p_to", "q_to")):
+            assert np.max(np.abs(got[key][0] - ref[k].reshape(-1))) <= 1e-12 * scale, key
+        assert abs(got["loss"][0, 0] - ref[4][0]) <= 1e-10 * scale
+    finally:
+        pf.pf_destroy_case(c)

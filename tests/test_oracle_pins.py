@@ -398,3 +398,62 @@ def test_cim_solvers_agree_on_generated_feeder():
         assert r["converged"]
     for r in out[1:]:
         assert np.max(np.abs(r["V"] - out[0]["V"])) < 1e-9
+
+
+# -----------------------------------------------------------------------------
+# branch flows (Sec. I: voltages and branch power flows are the outputs)
+# -----------------------------------------------------------------------------
+
+def _bus_sums(case, pf_, qf, pt, qt, slots, width):
+    """Power leaving each bus (slot) into its branches."""
+    S = np.zeros(slots, dtype=np.complex128)
+    for k in range(case.n_branch):
+        f, t = int(case.br_from[k]), int(case.br_to[k])
+        for a in range(width):
+            S[width * f + a] += pf_[k] + 1j * qf[k] if width == 1 else pf_[k, a] + 1j * qf[k, a]
+            S[width * t + a] += pt[k] + 1j * qt[k] if width == 1 else pt[k, a] + 1j * qt[k, a]
+    return S
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_branch_flows_sum_to_nodal_injections(seed):
+    """Kirchhoff at every bus: the powers leaving a bus into its branches add
+    up to V_i conj((Y V)_i), with Y assembled independently (Eq. 2-3)."""
+    rng = np.random.default_rng(seed)
+    case = cases.case_14bus(seed)
+    Y = O.ybus_single(case)
+    for _ in range(3):
+        vm, va = _random_voltage(case.n_bus, rng)
+        pf_, qf, pt, qt, loss = O.branch_flows(case, vm, va)
+        V = vm * np.exp(1j * va)
+        S = _bus_sums(case, pf_, qf, pt, qt, case.n_bus, 1)
+        ref = V * np.conj(Y @ V)
+        assert np.max(np.abs(S - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+        assert abs(loss[0] + 1j * loss[1] - ref.sum()) < 1e-11
+
+
+def test_branch_flows_three_phase_sum_to_nodal_injections():
+    case = _cim_random_case(5, n=25)
+    Y = O.ybus_three_phase(case)
+    rng = np.random.default_rng(2)
+    V = O.cim_flat_start(case) * rng.uniform(0.9, 1.1, 3 * case.n_node) * np.exp(
+        1j * rng.uniform(-0.05, 0.05, 3 * case.n_node))
+    vm, va = np.abs(V), np.where(np.abs(V) > 0, np.angle(V), 0.0)
+    pf_, qf, pt, qt, loss = O.branch_flows(case, vm, va)
+    S = _bus_sums(case, pf_, qf, pt, qt, 3 * case.n_node, 3)
+    ref = V * np.conj(Y @ V)
+    assert np.max(np.abs(S - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_branch_flow_of_two_bus_closed_form():
+    """A load P + jQ at the end of one line: the line carries P_to = -P,
+    Q_to = -Q at the load end and loses r |S|^2 / |V2|^2 (with |V2| from the
+    closed form above)."""
+    P, Q, r, x = 0.6, 0.25, 0.03, 0.12
+    case = cases.two_bus_case(P, Q, r, x)
+    res = O.newton_polar(case, tol=1e-12)
+    pf_, qf, pt, qt, loss = O.branch_flows(case, res["vm"], res["va"])
+    v2, _ = two_bus_pq_closed_form(P, Q, r, x)
+    assert abs(pt[0] + P) < 1e-10 and abs(qt[0] + Q) < 1e-10
+    assert abs(loss[0] - r * (P * P + Q * Q) / v2 ** 2) < 1e-10
+    assert abs(loss[1] - x * (P * P + Q * Q) / v2 ** 2) < 1e-10
