@@ -130,6 +130,11 @@ typedef struct {
   int cluster_size;   /* single-solve launch: CTAs per cluster (0 = autotuned) */
   int block_threads;  /* threads per CTA (0 = autotuned) */
   int scen_per_cta;   /* batched launch: scenarios per CTA (0 = autotuned) */
+  int nk_fallback;    /* PF_NK through pf_solve / pf_solve_batch: redo every
+                         scenario that ends without convergence (max_iter,
+                         divergence, singular preconditioner) with PF_NR from
+                         a flat start, as Sec. III.B warns NK may fail;
+                         default 1 */
   int kernel_by_kernel; /* batched PF_NR: 1 = launch the phase kernels one by one
                            instead of as one CUDA graph (for profilers, which
                            cannot look inside a graph with a conditional node);
@@ -142,7 +147,8 @@ typedef struct {
   int linear_iterations; /* NK: total GMRES iterations; NR batch (B >= 2):
                             triangular-solve passes (one per Newton step
                             plus one per FP64 refinement) */
-  int reserved;
+  int fallback;          /* 1: a PF_NK solve that ended without convergence
+                            was redone with PF_NR (opts.nk_fallback) */
   double mismatch;       /* final infinity norm of the power mismatch (pu) */
   double max_step;       /* infinity norm of the last Newton correction */
   double solve_us;       /* device time of the solve, microseconds */

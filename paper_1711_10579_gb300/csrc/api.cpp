@@ -387,6 +387,7 @@ void pf_opts_default(pf_opts* o) {
   o->gmres_max_iter = 300;
   o->gmres_rtol = 1e-6;
   o->warm_start = 0;
+  o->nk_fallback = 1;
 }
 
 const char* pf_last_error(void) { return g_last_error.c_str(); }
@@ -489,6 +490,19 @@ int pf_case_get_stats(pf_case c, pf_case_stats* out) {
   return PF_OK;
 }
 
+// Options of the Newton-Raphson redo of Newton-Krylov solves that did not
+// converge: same precision and stopping rule, Newton-Raphson's own launch
+// shapes, flat start.
+static pf_opts fallback_opts(const pf_opts& o) {
+  pf_opts r = o;
+  r.method = PF_NR;
+  r.cluster_size = 0;
+  r.block_threads = 0;
+  r.scen_per_cta = 0;
+  r.warm_start = 0;
+  return r;
+}
+
 int pf_solve(pf_case c, const pf_opts* opts, double* vmag, double* vang, pf_info* info) {
   if (!c) return set_error(PF_ERR_INVALID, "null case");
   pf_opts o;
@@ -499,7 +513,18 @@ int pf_solve(pf_case c, const pf_opts* opts, double* vmag, double* vang, pf_info
   int rc = run_solve(c, o, 1, nullptr, nullptr, nullptr, &c->ws1, st, RunMode::Solve, nullptr,
                      nullptr);
   if (rc != PF_OK) return rc;
-  return fetch_results(c, &c->ws1, 1, vmag, vang, info, st);
+  pf_info inf;
+  rc = fetch_results(c, &c->ws1, 1, vmag, vang, &inf, st);
+  if (rc == PF_OK && o.method == PF_NK && o.nk_fallback && inf.status != PF_OK) {
+    const int lin = inf.linear_iterations;
+    rc = run_solve(c, fallback_opts(o), 1, nullptr, nullptr, nullptr, &c->ws1, st, RunMode::Solve,
+                   nullptr, nullptr);
+    if (rc == PF_OK) rc = fetch_results(c, &c->ws1, 1, vmag, vang, &inf, st);
+    inf.fallback = 1;
+    inf.linear_iterations = lin;  // the GMRES iterations spent before the redo
+  }
+  if (info) *info = inf;
+  return rc;
 }
 
 int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
@@ -528,7 +553,55 @@ int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
   rc = run_solve(c, o, B, p_load ? ws->st_p_load : nullptr, q_load ? ws->st_q_load : nullptr,
                  p_gen ? ws->st_p_gen : nullptr, ws, st, RunMode::Solve, nullptr, nullptr);
   if (rc != PF_OK) return rc;
-  return fetch_results(c, ws, B, vmag, vang, info, st);
+  std::vector<pf_info> inf(B);
+  rc = fetch_results(c, ws, B, vmag, vang, inf.data(), st);
+  if (rc == PF_OK && o.method == PF_NK && o.nk_fallback) {
+    // redo the scenarios that did not converge with Newton-Raphson, as one
+    // batch of their own inputs
+    std::vector<int> bad;
+    for (int b = 0; b < B; ++b)
+      if (inf[b].status != PF_OK) bad.push_back(b);
+    if (!bad.empty()) {
+      const int R = (int)bad.size();
+      auto gather = [&](const double* src) {
+        std::vector<double> v;
+        if (!src) return v;
+        v.resize(per * R);
+        for (int k = 0; k < R; ++k)
+          std::copy(src + per * bad[k], src + per * (bad[k] + 1), v.begin() + per * k);
+        return v;
+      };
+      std::vector<double> pl = gather(p_load), ql = gather(q_load), pg = gather(p_gen);
+      std::vector<double> vm(per * R), va(per * R);
+      std::vector<pf_info> ri(R);
+      Workspace* ws2 = (R == 1) ? &c->ws1 : &c->wsB;
+      const pf_opts fo = fallback_opts(o);
+      rc = ws2->ensure(c->data.kind, c->data.n,
+                       std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), R, 0);
+      if (rc != PF_OK) return rc;
+      e = cudaSuccess;
+      if (p_load) e = cudaMemcpyAsync(ws2->st_p_load, pl.data(), per * R * 8, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess && q_load)
+        e = cudaMemcpyAsync(ws2->st_q_load, ql.data(), per * R * 8, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess && p_gen)
+        e = cudaMemcpyAsync(ws2->st_p_gen, pg.data(), per * R * 8, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_error(e, "copying scenario inputs");
+      rc = run_solve(c, fo, R, p_load ? ws2->st_p_load : nullptr, q_load ? ws2->st_q_load : nullptr,
+                     p_gen ? ws2->st_p_gen : nullptr, ws2, st, RunMode::Solve, nullptr, nullptr);
+      if (rc == PF_OK) rc = fetch_results(c, ws2, R, vm.data(), va.data(), ri.data(), st);
+      if (rc != PF_OK) return rc;
+      for (int k = 0; k < R; ++k) {
+        const int b = bad[k];
+        if (vmag) std::copy(vm.begin() + per * k, vm.begin() + per * (k + 1), vmag + per * b);
+        if (vang) std::copy(va.begin() + per * k, va.begin() + per * (k + 1), vang + per * b);
+        ri[k].linear_iterations = inf[b].linear_iterations;
+        ri[k].fallback = 1;
+        inf[b] = ri[k];
+      }
+    }
+  }
+  if (info) std::copy(inf.begin(), inf.end(), info);
+  return rc;
 }
 
 int pf_solve_batch_device(pf_case c, int B, const double* d_p_load, const double* d_q_load,

@@ -82,7 +82,7 @@ __device__ __forceinline__ void put_info(const DevWork& w, int gs, int st, int i
   inf.iterations = it;
   // triangular-solve passes: one per Newton step and one per refinement
   inf.linear_iterations = it + (w.refine[gs] >> 1);
-  inf.reserved = 0;
+  inf.fallback = 0;
   inf.mismatch = nrm;
   inf.max_step = step;
   inf.solve_us = 0.0;

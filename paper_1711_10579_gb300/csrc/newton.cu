@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
             inf.status = st;
             inf.iterations = it;
             inf.linear_iterations = sh_lin[s];
-            inf.reserved = 0;
+            inf.fallback = 0;
             inf.mismatch = nrm;
             inf.max_step = it > 0 ? __longlong_as_double((long long)__ldcg(w.step + (size_t)((it - 1) & 1) * B + gs)) : 0.0;
             inf.solve_us = 0.0;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
             inf.status = PF_ERR_SINGULAR;
             inf.iterations = it;
             inf.linear_iterations = sh_lin[s];
-            inf.reserved = 0;
+            inf.fallback = 0;
             inf.mismatch = __longlong_as_double((long long)__ldcg(w.norm + (size_t)(it & 1) * B + gs));
             inf.max_step = 0.0;
             inf.solve_us = 0.0;

@@ -33,6 +33,8 @@ int check_opts(const pf_opts& o) {
     return set_error(PF_ERR_INVALID, "opts.scen_per_cta must be 0 or a power of two <= 32");
   if (o.kernel_by_kernel != 0 && o.kernel_by_kernel != 1)
     return set_error(PF_ERR_INVALID, "opts.kernel_by_kernel must be 0 or 1");
+  if (o.nk_fallback != 0 && o.nk_fallback != 1)
+    return set_error(PF_ERR_INVALID, "opts.nk_fallback must be 0 or 1");
   if (o.method == PF_NK) {
     if (o.gmres_restart < 1 || o.gmres_restart >= kMaxJ)
       return set_error(PF_ERR_INVALID, "opts.gmres_restart must be in [1, 63]");

@@ -49,17 +49,18 @@ class pf_opts(C.Structure):
                 ("gmres_restart", C.c_int), ("gmres_max_iter", C.c_int),
                 ("gmres_rtol", C.c_double), ("warm_start", C.c_int),
                 ("cluster_size", C.c_int), ("block_threads", C.c_int),
-                ("scen_per_cta", C.c_int), ("kernel_by_kernel", C.c_int)]
+                ("scen_per_cta", C.c_int), ("nk_fallback", C.c_int),
+                ("kernel_by_kernel", C.c_int)]
 
 
 class pf_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int),
-                ("linear_iterations", C.c_int), ("reserved", C.c_int),
+                ("linear_iterations", C.c_int), ("fallback", C.c_int),
                 ("mismatch", C.c_double), ("max_step", C.c_double),
                 ("solve_us", C.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class pf_case_stats(C.Structure):
@@ -75,7 +76,7 @@ class pf_case_stats(C.Structure):
 
 
 INFO_DTYPE = np.dtype([("status", np.int32), ("iterations", np.int32),
-                       ("linear_iterations", np.int32), ("reserved", np.int32),
+                       ("linear_iterations", np.int32), ("fallback", np.int32),
                        ("mismatch", np.float64), ("max_step", np.float64),
                        ("solve_us", np.float64)])
 assert INFO_DTYPE.itemsize == C.sizeof(pf_info)
@@ -449,7 +450,7 @@ def pf_profile_solve(c: CaseHandle, opts: pf_opts | None = None, B: int = 1):
                                   _ptr(ph, C.c_double), info.ctypes.data_as(C.c_void_p)))
     prof = dict(zip(PROFILE_PHASES, ph.tolist()))
     if B == 1:
-        return prof, {k: (info[k][0].item()) for k in info.dtype.names if k != "reserved"}
+        return prof, {k: (info[k][0].item()) for k in info.dtype.names}
     return prof, info
 
 

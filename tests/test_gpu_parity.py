@@ -520,3 +520,32 @@ def test_branch_flows_match_oracle_three_phase(pf, ctx):
         assert abs(got["loss"][0, 0] - ref[4][0]) <= 1e-10 * scale
     finally:
         pf.pf_destroy_case(c)
+
+
+def test_newton_krylov_falls_back_to_newton_raphson(pf, ctx):
+    """NK starved of inner iterations cannot converge; with nk_fallback (the
+    default) the scenarios are redone with NR and match the oracle, alone and
+    in a batch; without it they report the failure."""
+    case = cases.case_2000bus(5)
+    starve = dict(method=pf.PF_NK, gmres_max_iter=1, max_iter=8)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve(c, pf.make_opts(nk_fallback=0, **starve))
+        assert info["status"] != 0 and info["fallback"] == 0
+        vm, va, info = pf.pf_solve(c, pf.make_opts(**starve))
+        assert info["fallback"] == 1
+        _check_solve(case, vm, va, info, O.newton_polar(case))
+        B = 6
+        pl, ql, pg = cases.scenario_loads(case, B, seed=9)
+        vm, va, inf = pf.pf_solve_batch(c, pl, ql, pg, pf.make_opts(scen_per_cta=2, **starve))
+        assert np.all(inf["status"] == 0) and np.all(inf["fallback"] == 1)
+        for b in (0, B - 1):
+            ref = O.newton_polar(case.with_loads(pl[b], ql[b], pg[b]))
+            assert np.max(np.abs(vm[b] - ref["vm"])) <= V_TOL
+            assert np.max(np.abs(va[b] - ref["va"])) <= A_TOL
+        # a converging NK batch is left alone
+        vm, va, inf = pf.pf_solve_batch(c, pl, ql, pg, pf.make_opts(method=pf.PF_NK,
+                                                                    scen_per_cta=2))
+        assert np.all(inf["status"] == 0) and np.all(inf["fallback"] == 0)
+    finally:
+        pf.pf_destroy_case(c)
