@@ -296,6 +296,9 @@ def variants(pf, ctx, torch, dev, flush):
         out[f"mesh10000_single_nk_{nm}"] = _device_solves(
             pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(method=pf.PF_NK, precision=prec),
             reps=1)
+        out[f"mesh10000_single_nk_bicgstab_{nm}"] = _device_solves(
+            pf, c, torch, dev, 1, pl, ql, pg,
+            pf.make_opts(method=pf.PF_NK, krylov=1, precision=prec, gmres_max_iter=2000), reps=1)
     pf.pf_destroy_case(c)
 
     case = cases.case_2000bus(0)

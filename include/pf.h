@@ -139,6 +139,9 @@ typedef struct {
                            instead of as one CUDA graph (for profilers, which
                            cannot look inside a graph with a conditional node);
                            default 0 */
+  int krylov;         /* PF_NK inner solver: 0 = restarted GMRES(gmres_restart)
+                         (default), 1 = BiCGSTAB (the method of Sec. III.B;
+                         needs gmres_restart >= 7 for its work vectors) */
 } pf_opts;
 
 typedef struct {

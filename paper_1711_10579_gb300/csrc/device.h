@@ -153,6 +153,7 @@ struct DevOpts {
   int m;                     // Newton-Krylov: GMRES restart length
   int max_lin;               // ... inner iterations per Newton step
   double rtol;               // ... inner relative-residual floor
+  int krylov;                // Newton-Krylov inner solver: 0 GMRES, 1 BiCGSTAB
   int ring;                  // batches of 2x2 blocks: the factorisation stages
                              // its gathers in dynamic shared memory
 };

@@ -73,6 +73,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
   __shared__ int sh_kk[32];
   __shared__ unsigned sh_inner;
   __shared__ TF sh_bnorm[32], sh_eta[32], sh_hk1[32];
+  __shared__ TF sh_rho[32], sh_rho0[32], sh_alpha[32], sh_omega[32];  // BiCGSTAB
+  __shared__ unsigned sh_sdone;
   __shared__ int sh_status[32];
   __shared__ unsigned sh_act;
   __shared__ int sh_refine;
@@ -271,6 +273,174 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
         sh_eta[t] = (TF)eta;
       }
       __syncthreads();
+      if (o.krylov == 1) {
+        // BiCGSTAB (the Krylov method of Sec. III.B), right-preconditioned by
+        // ILU(0): solves J M^-1 u = F with x = M^-1 u from x = 0.  Work
+        // vectors borrow the first 8 GMRES basis slots.
+        TF* const R = V0;
+        TF* const RH = V0 + NV;
+        TF* const P = V0 + 2 * NV;
+        TF* const VV = V0 + 3 * NV;
+        TF* const SV = V0 + 4 * NV;
+        TF* const TV = V0 + 5 * NV;
+        TF* const PH = V0 + 6 * NV;
+        TF* const SH = V0 + 7 * NV;
+        auto q_of = [&](int i, int c) { return ((size_t)i * B + gs) * BS + c; };
+        if (slot_on(tm.act))
+          for (int i = first; i < n; i += stride)
+            for (int c = 0; c < BS; ++c) {
+              const size_t q = q_of(i, c);
+              const TF f = (TF)__ldcg(w.F + q);
+              R[q] = f;
+              RH[q] = f;
+              P[q] = TF(0);
+              VV[q] = TF(0);
+            }
+        if (threadIdx.x < tm.ns) {
+          const int t = threadIdx.x;
+          sh_rho[t] = sh_bnorm[t] * sh_bnorm[t];  // (r_hat, r) with r = r_hat = F
+          sh_rho0[t] = TF(1);
+          sh_alpha[t] = TF(1);
+          sh_omega[t] = TF(1);
+        }
+        if (threadIdx.x == 0) {
+          unsigned bits = 0;
+          for (int t = 0; t < tm.ns; ++t)
+            if (((tm.act >> t) & 1u) && sh_bnorm[t] > TF(0) && o.max_lin > 0) bits |= 1u << t;
+          sh_inner = bits;
+        }
+        csync<CL>();
+        unsigned inner = sh_inner;
+        while (inner != 0) {
+          // p = r + beta (p - omega v), beta = (rho / rho_prev)(alpha / omega)
+          if (slot_on(inner)) {
+            const TF beta = (sh_rho[slot] / sh_rho0[slot]) * (sh_alpha[slot] / sh_omega[slot]);
+            const TF om = sh_omega[slot];
+            for (int i = first; i < n; i += stride)
+              for (int c = 0; c < BS; ++c) {
+                const size_t q = q_of(i, c);
+                P[q] = R[q] + beta * (P[q] - om * VV[q]);
+              }
+          }
+          csync<CL>();
+          precond(P, PH, false, inner);
+          // v = J p_hat, alpha = rho / (r_hat, v)
+          tsum(1, [&](int) {
+            TF a = TF(0);
+            if (slot_on(inner))
+              for (int i = first; i < n; i += stride) {
+                TF jv[BS];
+                jrow(i, PH, jv);
+                for (int c = 0; c < BS; ++c) {
+                  const size_t q = q_of(i, c);
+                  VV[q] = jv[c];
+                  a += RH[q] * jv[c];
+                }
+              }
+            return a;
+          });
+          if (threadIdx.x < tm.ns && ((inner >> threadIdx.x) & 1u)) {
+            const TF d = nk_rs[threadIdx.x];
+            sh_alpha[threadIdx.x] = (d != TF(0)) ? sh_rho[threadIdx.x] / d : TF(0);
+          }
+          __syncthreads();
+          // s = r - alpha v
+          tsum(1, [&](int) {
+            TF a = TF(0);
+            if (slot_on(inner)) {
+              const TF al = sh_alpha[slot];
+              for (int i = first; i < n; i += stride)
+                for (int c = 0; c < BS; ++c) {
+                  const size_t q = q_of(i, c);
+                  const TF sv = R[q] - al * VV[q];
+                  SV[q] = sv;
+                  a += sv * sv;
+                }
+            }
+            return a;
+          });
+          // slots whose s already meets the tolerance finish with x += alpha p_hat
+          if (threadIdx.x == 0) {
+            unsigned done = 0;
+            for (int t = 0; t < tm.ns; ++t)
+              if (((inner >> t) & 1u) &&
+                  (sqrt(nk_rs[t]) <= sh_eta[t] * sh_bnorm[t] || sh_alpha[t] == TF(0)))
+                done |= 1u << t;
+            sh_sdone = done;
+          }
+          __syncthreads();
+          const unsigned sdone = sh_sdone, go = inner & ~sdone;
+          if (slot_on(sdone)) {
+            const TF al = sh_alpha[slot];
+            for (int i = first; i < n; i += stride)
+              for (int c = 0; c < BS; ++c) X[q_of(i, c)] += al * PH[q_of(i, c)];
+          }
+          csync<CL>();
+          if (go != 0) {
+            precond(SV, SH, false, go);
+            // t = J s_hat, omega = (t, s) / (t, t)
+            if (slot_on(go))
+              for (int i = first; i < n; i += stride) {
+                TF jt[BS];
+                jrow(i, SH, jt);
+                for (int c = 0; c < BS; ++c) TV[q_of(i, c)] = jt[c];
+              }
+            tsum(2, [&](int j) {
+              TF a = TF(0);
+              if (slot_on(go))
+                for (int i = first; i < n; i += stride)
+                  for (int c = 0; c < BS; ++c) {
+                    const size_t q = q_of(i, c);
+                    a += TV[q] * (j == 0 ? SV[q] : TV[q]);
+                  }
+              return a;
+            });
+            if (threadIdx.x < tm.ns && ((go >> threadIdx.x) & 1u)) {
+              const TF ts = nk_rs[threadIdx.x], tt = nk_rs[tm.S + threadIdx.x];
+              sh_omega[threadIdx.x] = (tt > TF(0)) ? ts / tt : TF(0);
+            }
+            __syncthreads();
+            // x += alpha p_hat + omega s_hat; r = s - omega t; ||r||^2, (r_hat, r)
+            tsum(2, [&](int j) {
+              TF a = TF(0);
+              if (slot_on(go)) {
+                const TF al = sh_alpha[slot], om = sh_omega[slot];
+                for (int i = first; i < n; i += stride)
+                  for (int c = 0; c < BS; ++c) {
+                    const size_t q = q_of(i, c);
+                    if (j == 0) {
+                      X[q] += al * PH[q] + om * SH[q];
+                      const TF r = SV[q] - om * TV[q];
+                      R[q] = r;
+                      a += r * r;
+                    } else {
+                      a += RH[q] * R[q];
+                    }
+                  }
+              }
+              return a;
+            });
+          }
+          if (threadIdx.x == 0) {
+            unsigned nxt = 0;
+            for (int t = 0; t < tm.ns; ++t) {
+              if (!((inner >> t) & 1u)) continue;
+              sh_lin[t] += 1;
+              sh_lin_step[t] += 1;
+              if ((sdone >> t) & 1u) continue;
+              const TF res = sqrt(nk_rs[t]), rho = nk_rs[tm.S + t];
+              sh_rho0[t] = sh_rho[t];
+              sh_rho[t] = rho;
+              if (!(res <= sh_eta[t] * sh_bnorm[t]) && sh_lin_step[t] < o.max_lin &&
+                  rho != TF(0) && sh_omega[t] != TF(0))
+                nxt |= 1u << t;
+            }
+            sh_inner = nxt;
+          }
+          __syncthreads();
+          inner = sh_inner;
+        }
+      } else
       for (int restart = 0;; ++restart) {
         // r = F - J x into V_0, and ||r||_2
         tsum(1, [&](int) {

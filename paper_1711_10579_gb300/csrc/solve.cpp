@@ -35,6 +35,10 @@ int check_opts(const pf_opts& o) {
     return set_error(PF_ERR_INVALID, "opts.kernel_by_kernel must be 0 or 1");
   if (o.nk_fallback != 0 && o.nk_fallback != 1)
     return set_error(PF_ERR_INVALID, "opts.nk_fallback must be 0 or 1");
+  if (o.krylov != 0 && o.krylov != 1)
+    return set_error(PF_ERR_INVALID, "opts.krylov must be 0 (GMRES) or 1 (BiCGSTAB)");
+  if (o.method == PF_NK && o.krylov == 1 && o.gmres_restart < 7)
+    return set_error(PF_ERR_INVALID, "BiCGSTAB needs opts.gmres_restart >= 7 (work vectors)");
   if (o.method == PF_NK) {
     if (o.gmres_restart < 1 || o.gmres_restart >= kMaxJ)
       return set_error(PF_ERR_INVALID, "opts.gmres_restart must be in [1, 63]");
@@ -162,6 +166,7 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   d.m = nk ? o.gmres_restart : 0;
   d.max_lin = o.gmres_max_iter;
   d.rtol = o.gmres_rtol;
+  d.krylov = o.krylov;
   // single solves keep the triangular-solve vector in shared memory when it fits
   const size_t tf = fp32 ? 4 : 8;
   d.y_in_smem = 0;

@@ -549,3 +549,75 @@ def test_newton_krylov_falls_back_to_newton_raphson(pf, ctx):
         assert np.all(inf["status"] == 0) and np.all(inf["fallback"] == 0)
     finally:
         pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# Newton-Krylov with BiCGSTAB (the paper's Krylov method, Sec. III.B)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["300zip", "2000", "10000"])
+def test_newton_krylov_bicgstab_matches_oracle(pf, ctx, name, prec):
+    case = {"300zip": _zip_case(cases.transmission_case(300, 405, 60, 2), 2),
+            "2000": cases.case_2000bus(0), "10000": cases.case_10000bus(0)}[name]
+    ref = O.newton_polar(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        vm, va, info = pf.pf_solve(c, pf.make_opts(method=pf.PF_NK, krylov=1, precision=p,
+                                                   nk_fallback=0, gmres_max_iter=2000))
+        _check_solve(case, vm, va, info, ref)
+        assert info["linear_iterations"] > 0 and info["fallback"] == 0
+    finally:
+        pf.pf_destroy_case(c)
+
+
+@pytest.mark.parametrize("prec,rtol,slack", [("fp64", 1e-10, 10.0), ("mixed", 1e-5, 50.0)])
+def test_bicgstab_step_meets_its_residual_bound(pf, ctx, prec, rtol, slack):
+    case = _zip_case(cases.transmission_case(300, 405, 60, 2), 2)
+    Y = O.ybus_single(case)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va = O.flat_start_polar(case)
+        vm = vm + np.where(case.bus_type == cases.PQ, 0.01 * np.sin(np.arange(case.n_bus)), 0)
+        va = va + np.where(case.bus_type != cases.SLACK, 0.02 * np.cos(np.arange(case.n_bus)), 0)
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        dx, _ = pf.pf_newton_step(c, vm, va, pf.make_opts(method=pf.PF_NK, krylov=1,
+                                                        precision=p, gmres_rtol=rtol,
+                                                        gmres_max_iter=2000))
+        F = O.mismatch_polar(case, Y, vm, va)
+        J = O.jacobian_polar(case, Y, vm, va)
+        got = _gpu_mis_to_oracle_order(case, dx)
+        # the recursively updated BiCGSTAB residual drifts from the true one
+        # by rounding; the bound allows for that
+        assert np.linalg.norm(F - J @ got) <= slack * rtol * np.linalg.norm(F)
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_newton_krylov_bicgstab_batch_matches_oracle(pf, ctx):
+    case = cases.case_2000bus(4)
+    B = 8
+    p_load, q_load, p_gen = cases.scenario_loads(case, B, seed=12)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve_batch(c, p_load, q_load, p_gen,
+                                         pf.make_opts(method=pf.PF_NK, krylov=1, scen_per_cta=4,
+                                                      nk_fallback=0, gmres_max_iter=2000))
+        assert np.all(info["status"] == 0), info
+        for b in (0, B - 1):
+            ref = O.newton_polar(case.with_loads(p_load[b], q_load[b], p_gen[b]))
+            assert np.max(np.abs(vm[b] - ref["vm"])) <= V_TOL
+            assert np.max(np.abs(va[b] - ref["va"])) <= A_TOL
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_bicgstab_needs_its_work_vectors(pf, ctx):
+    case = cases.case_14bus(0)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        with pytest.raises(pf.PfError):
+            pf.pf_solve(c, pf.make_opts(method=pf.PF_NK, krylov=1, gmres_restart=4))
+    finally:
+        pf.pf_destroy_case(c)

@@ -249,6 +249,39 @@ def test_gmres_with_full_restart_solves_exactly():
     assert it <= n
 
 
+def test_bicgstab_solves_like_a_direct_solver():
+    """BiCGSTAB (unpreconditioned and with ILU(0)) reaches the dense LU
+    solution of a nonsymmetric Jacobian; with M = A exactly (ILU(0) of a
+    matrix without fill) it converges in one iteration."""
+    case = cases.case_14bus(2)
+    Y = O.ybus_single(case)
+    vm, va = O.flat_start_polar(case)
+    J = O.jacobian_polar(case, Y, vm + 0.01, va + 0.02).tocsr()
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(J.shape[0])
+    ref = np.linalg.solve(J.toarray(), b)
+    x, it = O.bicgstab(J, b, tol=1e-13, max_iter=500)
+    assert np.max(np.abs(x - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+    L, U = O.ilu0(J)
+    x2, it2 = O.bicgstab(J, b, L, U, tol=1e-13, max_iter=500)
+    assert np.max(np.abs(x2 - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref)))
+    assert it2 <= it
+    T = sp.diags([np.full(30, 4.0), np.full(29, -1.0), np.full(29, -2.0)], [0, 1, -1]).tocsr()
+    Lt, Ut = O.ilu0(T)  # tridiagonal: no fill, ILU(0) = LU
+    bt = rng.standard_normal(30)
+    xt, itt = O.bicgstab(T, bt, Lt, Ut, tol=1e-12)
+    assert itt == 1 and np.max(np.abs(T @ xt - bt)) <= 1e-10
+
+
+def test_newton_with_bicgstab_matches_direct():
+    case = cases.transmission_case(300, 405, 60, 7)
+    a = O.newton_polar(case, linear="splu")
+    b = O.newton_polar(case, linear="bicgstab")
+    assert a["converged"] and b["converged"]
+    assert np.max(np.abs(a["vm"] - b["vm"])) <= 1e-9
+    assert np.max(np.abs(a["va"] - b["va"])) <= 1e-9
+
+
 def test_gmres_restarted_with_ilu0():
     rng = np.random.default_rng(3)
     n = 120
