@@ -548,15 +548,25 @@ def main():
     refine = pf.make_opts().refine_steps
     loops = info["iterations"].reshape(K, B).max(1)
     launches = int(sum(5 + int(L) * (5 + 3 * refine) for L in loops))
-    # end to end through the host-buffer entry point (copies inside)
+    # end to end through the host-buffer entry point: inputs and results in
+    # pinned host memory, their copies inside the timed call
+    def pinned(shape, dtype=torch.float64):
+        return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
+
+    h_in = [pinned((B, n)) for _ in range(3)]
+    h_vm, h_va = pinned((B, n)), pinned((B, n))
+    h_info = pinned((B * pf.INFO_DTYPE.itemsize,), torch.uint8).view(pf.INFO_DTYPE)
     e2e_t = []
     for k in range(W, min(W + 5, W + K)):
+        for a, src in zip(h_in, batches[k]):
+            a[...] = src  # the step's inputs, staged outside the timed call
         t0 = time.perf_counter()
-        pf.pf_solve_batch(c, batches[k][0], batches[k][1], batches[k][2], opts)
+        pf.pf_solve_batch(c, h_in[0], h_in[1], h_in[2], opts, out=(h_vm, h_va, h_info))
         e2e_t.append(time.perf_counter() - t0)
     e2e = {"value": B * len(e2e_t) / sum(e2e_t), "unit": "solves/s",
            "h2d_bytes_per_step": 3 * B * n * 8,
-           "d2h_bytes_per_step": 2 * B * n * 8 + B * pf.INFO_DTYPE.itemsize}
+           "d2h_bytes_per_step": 2 * B * n * 8 + B * pf.INFO_DTYPE.itemsize,
+           "host_buffers": "pinned"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,

@@ -325,17 +325,26 @@ def pf_solve(c: CaseHandle, opts: pf_opts | None = None):
     return vm, va, info.as_dict()
 
 
-def pf_solve_batch(c: CaseHandle, p_load, q_load, p_gen=None, opts: pf_opts | None = None):
-    """Batch of B scenarios: loads [B, slots]; returns vmag, vang [B, slots], info[B]."""
+def pf_solve_batch(c: CaseHandle, p_load, q_load, p_gen=None, opts: pf_opts | None = None,
+                   out=None):
+    """Batch of B scenarios: loads [B, slots]; returns vmag, vang [B, slots], info[B].
+
+    ``out`` = (vmag, vang, info) writes into caller buffers (e.g. pinned host
+    memory) instead of new arrays."""
     p_load = np.ascontiguousarray(p_load, dtype=np.float64)
     q_load = np.ascontiguousarray(q_load, dtype=np.float64)
     B = p_load.shape[0]
     p_load = p_load.reshape(B, -1)
     q_load = q_load.reshape(B, -1)
     pg = None if p_gen is None else np.ascontiguousarray(p_gen, dtype=np.float64).reshape(B, -1)
-    vm = np.zeros((B, c.slots))
-    va = np.zeros((B, c.slots))
-    info = np.zeros(B, INFO_DTYPE)
+    if out is None:
+        vm = np.zeros((B, c.slots))
+        va = np.zeros((B, c.slots))
+        info = np.zeros(B, INFO_DTYPE)
+    else:
+        vm, va, info = out
+        assert vm.flags.c_contiguous and va.flags.c_contiguous and info.dtype == INFO_DTYPE
+        assert vm.size == B * c.slots and va.size == B * c.slots and info.size == B
     _check(lib().pf_solve_batch(c.handle, B, _ptr(p_load, C.c_double), _ptr(q_load, C.c_double),
                                 _ptr(pg, C.c_double), C.byref(opts) if opts else None,
                                 _ptr(vm, C.c_double), _ptr(va, C.c_double),
