@@ -19,9 +19,10 @@
 //   E  voltage update (Sec. II.A box: delta += Delta delta, |V| += Delta|V|;
 //      Sec. II.B box: V^c += Delta V^c).
 //
-// Single solves run one cluster of up to 16 CTAs; batches of scenarios run
-// one CTA per S scenarios.  Values are interleaved as [entry][scenario] so
-// that neighbouring threads of a batch read neighbouring memory.
+// Single solves run one cluster of up to 16 CTAs; Newton-Krylov batches run
+// one CTA per S scenarios (Newton-Raphson batches run as the phase kernels
+// of batch.cu).  Values are interleaved as [entry][scenario] so that
+// neighbouring threads of a batch read neighbouring memory.
 #include "kernels.cuh"
 
 namespace pf {
@@ -638,32 +639,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
       tick(kProfResidual);
       // forward and backward sweeps: CTA 0 alone for a single solve
       solo.act = tm.act;
-      if (!CL && tm.S > 1) {
-        // a batch: the sweeps read the right-hand side and write dx themselves
-        BSweep<TF> a;
-        a.lu = reinterpret_cast<const TF*>(w.lu);
-        a.uinv = reinterpret_cast<const TF*>(w.uinv);
-        a.col = S.lu_col;
-        a.y = yv;
-        a.rhs = (pass == 0) ? w.F : w.r;
-        a.dx = nullptr;
-        a.accumulate = 0;
-        a.B = B;
-        a.lev_ptr = S.flev_ptr;
-        a.rec = S.fwd_rec;
-        a.nlev = S.nflev;
-        a.gsz = S.g_fwd;
-        a.red = sw_red;
-        sweep_batch<BS, TF, true>(a, solo);
-        a.rhs = nullptr;
-        a.dx = w.dx;
-        a.accumulate = (pass == 0) ? 0 : 1;
-        a.lev_ptr = S.blev_ptr;
-        a.rec = S.bwd_rec;
-        a.nlev = S.nblev;
-        a.gsz = S.g_bwd;
-        sweep_batch<BS, TF, false>(a, solo);
-      } else if (crank == 0) {
+      // (Newton-Raphson batches run as the phase kernels of batch.cu)
+      if (crank == 0) {
         const double* rhs = (pass == 0) ? w.F : w.r;
         run_rows<false>(solo, n, [&](int i, int gs) {
           const size_t b = ((size_t)i * B + gs) * BS;
