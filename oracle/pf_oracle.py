@@ -459,33 +459,51 @@ def cim_flat_start(case):
     return V
 
 
-def cim_specified_power(case, V):
-    """Eq. 12-15 per phase slot: S_sp = -(ZIP load at |V|); no generators."""
+def cim_pv_slots(case):
+    """Phase slots of PV nodes (present phases; the reading beyond the paper:
+    a PV node's generator injects P_g per phase and holds |V| at v_set)."""
+    mask = np.zeros(3 * case.n_node, dtype=bool)
+    pv = case.pv_mask() if hasattr(case, "pv_mask") else np.zeros(case.n_node, bool)
+    for i in np.flatnonzero(pv):
+        for s in _phase_list(case.phases[i]):
+            mask[3 * i + s] = True
+    return mask
+
+
+def cim_specified_power(case, V, Qg=None):
+    """Eq. 12-15 per phase slot: S_sp = generation - ZIP load at |V|; the
+    generation is P_g + j Qg on PV slots (Qg, [3 n], the reactive injection
+    of the iterate) and zero elsewhere."""
     vm = np.abs(V)
     zp = np.repeat(case.zip[:, 0], 3)
     zi = np.repeat(case.zip[:, 1], 3)
     zz = np.repeat(case.zip[:, 2], 3)
     shape = zp + zi * vm + zz * vm * vm
-    return -(case.p_load.reshape(-1) * shape) - 1j * (case.q_load.reshape(-1) * shape)
+    S = -(case.p_load.reshape(-1) * shape) - 1j * (case.q_load.reshape(-1) * shape)
+    pv = cim_pv_slots(case)
+    if pv.any():
+        q = np.zeros(3 * case.n_node) if Qg is None else np.asarray(Qg, dtype=float)
+        S = S + np.where(pv, case.p_gen.reshape(-1) + 1j * q, 0.0)
+    return S
 
 
-def cim_specified_current(case, V):
+def cim_specified_current(case, V, Qg=None):
     """Eq. 17: I_sp = conj(S_sp / V) on free slots, 0 elsewhere."""
     free = cim_free_slots(case)
-    S = cim_specified_power(case, V)
+    S = cim_specified_power(case, V, Qg)
     I = np.zeros_like(V)
     I[free] = np.conj(S[free] / V[free])
     return I
 
 
-def cim_mismatch(case, Y, V):
+def cim_mismatch(case, Y, V, Qg=None):
     """Eq. 16, 18, 19: Delta I = I_sp - Y V, per node as [Im a,b,c, Re a,b,c].
 
     Returns the full 6 n vector; entries of absent phases and of the source
     are zero.
     """
     free = cim_free_slots(case)
-    dI = cim_specified_current(case, V) - Y @ V
+    dI = cim_specified_current(case, V, Qg) - Y @ V
     dI = np.where(free, dI, 0.0)
     n = case.n_node
     out = np.empty((n, 6))
@@ -495,14 +513,14 @@ def cim_mismatch(case, Y, V):
     return out.reshape(-1)
 
 
-def cim_power_mismatch(case, Y, V):
+def cim_power_mismatch(case, Y, V, Qg=None):
     """Delta S = V conj(Delta I) = S_sp - V conj(Y V) on free slots."""
     free = cim_free_slots(case)
-    dS = cim_specified_power(case, V) - V * np.conj(Y @ V)
+    dS = cim_specified_power(case, V, Qg) - V * np.conj(Y @ V)
     return np.where(free, dS, 0.0)
 
 
-def cim_load_derivatives(case, V):
+def cim_load_derivatives(case, V, Qg=None):
     """a, b, c, d of Eq. 23 per phase slot.
 
     With S_sp = P + jQ a function of m = |V| (Eq. 14-15) and
@@ -520,6 +538,10 @@ def cim_load_derivatives(case, V):
     ql = case.q_load.reshape(-1)
     P = -pl * (zp + zi * m + zz * m * m)
     Q = -ql * (zp + zi * m + zz * m * m)
+    pv = cim_pv_slots(case)
+    if pv.any():  # a PV generator injects constant P_g + j Qg
+        P = P + np.where(pv, case.p_gen.reshape(-1), 0.0)
+        Q = Q + np.where(pv, 0.0 if Qg is None else np.asarray(Qg, dtype=float), 0.0)
     dP = -pl * (zi + 2.0 * zz * m)  # dP/dm
     dQ = -ql * (zi + 2.0 * zz * m)
     free = cim_free_slots(case)
@@ -540,7 +562,7 @@ def cim_load_derivatives(case, V):
     return a, b, c, d
 
 
-def cim_jacobian(case, Y, V) -> sp.csr_matrix:
+def cim_jacobian(case, Y, V, Qg=None) -> sp.csr_matrix:
     """Eq. 21-23 as a 6n x 6n real matrix.
 
     Node-pair block (rows [Im a,b,c; Re a,b,c], columns [Re a,b,c; Im a,b,c]):
@@ -556,7 +578,7 @@ def cim_jacobian(case, Y, V) -> sp.csr_matrix:
     rows = np.concatenate([6 * ni + si, 6 * ni + si, 6 * ni + 3 + si, 6 * ni + 3 + si])
     cols = np.concatenate([6 * nj + sj, 6 * nj + 3 + sj, 6 * nj + sj, 6 * nj + 3 + sj])
     vals = np.concatenate([B, G, G, -B])
-    a, b, c, d = cim_load_derivatives(case, V)
+    a, b, c, d = cim_load_derivatives(case, V, Qg)
     k = np.arange(3 * n)
     nk, sk = k // 3, k % 3
     rows = np.concatenate([rows, 6 * nk + sk, 6 * nk + sk, 6 * nk + 3 + sk, 6 * nk + 3 + sk])
@@ -584,6 +606,8 @@ def newton_cim(case, tol=1e-8, max_iter=30, linear="splu", V0=None,
     if Y is None:
         Y = ybus_three_phase(case)
     V = cim_flat_start(case) if V0 is None else np.array(V0, dtype=np.complex128)
+    if cim_pv_slots(case).any():
+        return _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol)
     idx = cim_unknowns(case)
     n = case.n_node
     history, steps = [], []
@@ -655,3 +679,67 @@ def branch_flows(case, vm, va):
                 St[k, s] = V[3 * t + s] * np.conj(-i_s[a])
     loss = (Sf + St).sum()
     return Sf.real, Sf.imag, St.real, St.imag, (loss.real, loss.imag)
+
+
+def _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol):
+    """CIM Newton with PV nodes, augmented form: the reactive injection Q_g of
+    every PV slot is an extra unknown and |V|^2 = v_set^2 an extra equation
+    per PV slot (linearised: 2 Vr dVr + 2 Vi dVi = v_set^2 - |V|^2).  The
+    Q_g column of the current equations is d(Y V - I_sp)/dQ_g = j V / |V|^2
+    (I_sp = conj(S_sp) V / |V|^2 with S_sp containing j Q_g).  The start
+    puts PV slots at v_set on the flat-start angles with Q_g = 0."""
+    n = case.n_node
+    pv = cim_pv_slots(case)
+    vset = np.repeat(np.asarray(case.v_set, dtype=float), 3)
+    V = np.where(pv, V / np.where(np.abs(V) > 0, np.abs(V), 1.0) * vset, V)
+    Qg = np.zeros(3 * n)
+    idx = cim_unknowns(case)
+    pvs = np.flatnonzero(pv)
+    npv = pvs.size
+    # positions of each PV slot's Re / Im unknowns inside idx
+    pos = {int(k): p for p, k in enumerate(idx)}
+    history, steps = [], []
+    k = 0
+    converged = False
+    while True:
+        dS = cim_power_mismatch(case, Y, V, Qg)
+        cons = np.abs(V[pvs]) ** 2 - vset[pvs] ** 2
+        norm = float(max(np.max(np.abs(dS.real)), np.max(np.abs(dS.imag)),
+                         np.max(np.abs(cons)) if npv else 0.0))
+        history.append(norm)
+        if not np.isfinite(norm):
+            break
+        if norm <= tol:
+            converged = True
+            break
+        if k >= max_iter:
+            break
+        k += 1
+        F = cim_mismatch(case, Y, V, Qg)[idx]
+        J = cim_jacobian(case, Y, V, Qg)[idx][:, idx].tocsr()
+        nu = idx.size
+        rows, cols, vals = [], [], []
+        for t, slot in enumerate(pvs):
+            node, ph = divmod(int(slot), 3)
+            v = V[slot]
+            m2 = abs(v) ** 2
+            w = 1j * v / m2  # d(Y V - I_sp)/dQ_g of this slot
+            r_im, r_re = pos[6 * node + ph], pos[6 * node + 3 + ph]
+            rows += [r_im, r_re]
+            cols += [nu + t, nu + t]
+            vals += [w.imag, w.real]
+            rows += [nu + t, nu + t]
+            cols += [pos[6 * node + ph], pos[6 * node + 3 + ph]]
+            vals += [2.0 * v.real, 2.0 * v.imag]
+        Jq = sp.coo_matrix((vals, (rows, cols)), shape=(nu + npv, nu + npv)).tocsr()
+        Ja = sp.bmat([[J, None], [None, sp.csr_matrix((npv, npv))]]).tocsr() + Jq
+        Fa = np.concatenate([F, -cons])
+        dx = solve_linear(Ja, Fa, linear, gmres_restart, gmres_tol)
+        full = np.zeros(6 * n)
+        full[idx] = dx[:nu]
+        full = full.reshape(n, 6)
+        V = V + (full[:, :3] + 1j * full[:, 3:]).reshape(-1)
+        Qg[pvs] += dx[nu:]
+        steps.append(float(np.max(np.abs(dx))) if dx.size else 0.0)
+    return dict(V=V, iterations=k, mismatch=history[-1], history=history,
+                steps=steps, converged=converged, Qg=Qg)

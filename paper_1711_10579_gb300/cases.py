@@ -108,10 +108,21 @@ class ThreePhaseCase:
     load_scale: float = 1.0
     name: str = ""
     seed: int = 0
+    # PV nodes (a reading beyond the paper, which defers them): generators
+    # holding |V| of each present phase at v_set with injection p_gen
+    node_type: np.ndarray | None = None  # int32 [n]: 1 PV, 2 PQ; None = all PQ
+    v_set: np.ndarray | None = None  # float64 [n]: |V| of a PV node's phases
+    p_gen: np.ndarray | None = None  # float64 [n, 3]: P injected per phase
 
     @property
     def n_branch(self) -> int:
         return int(self.br_from.shape[0])
+
+    def pv_mask(self) -> np.ndarray:
+        """bool [n]: PV nodes."""
+        if self.node_type is None:
+            return np.zeros(self.n_node, dtype=bool)
+        return np.asarray(self.node_type) == PV
 
     def with_loads(self, p_load, q_load) -> "ThreePhaseCase":
         return dataclasses.replace(
@@ -408,6 +419,24 @@ def feeder_case(n: int, seed: int, lateral_p: float = 0.2,
         n_node=n, source=0, phases=phases, p_load=pl * scale, q_load=ql * scale,
         zip=zipf, br_from=br_from, br_to=br_to, br_phases=br_ph, br_z=br_z,
         v_source=1.0, load_scale=scale, name=name or f"feeder{n}", seed=seed)
+
+
+def with_pv_nodes(case: ThreePhaseCase, count: int, seed: int, p_range=(0.005, 0.02),
+                  v_set: float = 1.0) -> ThreePhaseCase:
+    """The feeder with ``count`` three-phase nodes (not the source) turned
+    into PV generators: P per phase ~ U[p_range] (times the load scale),
+    |V| held at ``v_set`` on every phase."""
+    rng = np.random.default_rng(seed)
+    cand = np.flatnonzero((case.phases == 7) & (np.arange(case.n_node) != case.source))
+    pick = rng.choice(cand, size=min(count, cand.size), replace=False)
+    node_type = np.full(case.n_node, PQ, dtype=np.int32)
+    node_type[pick] = PV
+    vset = np.ones(case.n_node)
+    vset[pick] = v_set
+    pg = np.zeros((case.n_node, 3))
+    pg[pick] = rng.uniform(p_range[0], p_range[1], (pick.size, 3)) * case.load_scale * 20.0
+    return dataclasses.replace(case, node_type=node_type, v_set=vset, p_gen=pg,
+                               name=case.name + f"_pv{pick.size}")
 
 
 def case_feeder8000(seed: int = 0) -> ThreePhaseCase:

@@ -490,3 +490,59 @@ def test_branch_flow_of_two_bus_closed_form():
     assert abs(pt[0] + P) < 1e-10 and abs(qt[0] + Q) < 1e-10
     assert abs(loss[0] - r * (P * P + Q * Q) / v2 ** 2) < 1e-10
     assert abs(loss[1] - x * (P * P + Q * Q) / v2 ** 2) < 1e-10
+
+
+# -----------------------------------------------------------------------------
+# three phase with PV nodes (augmented CIM Newton)
+# -----------------------------------------------------------------------------
+
+def _pv_line(x, pg, vset, n=2):
+    import dataclasses as dc
+
+    case = _line_feeder(n, 1j * x, 0.0, 0.0, 0.0)
+    node_type = np.full(n, cases.PQ, dtype=np.int32)
+    node_type[n - 1] = cases.PV
+    v = np.ones(n)
+    v[n - 1] = vset
+    p_gen = np.zeros((n, 3))
+    p_gen[n - 1] = pg
+    return dc.replace(case, node_type=node_type, v_set=v, p_gen=p_gen)
+
+
+@pytest.mark.parametrize("pg,x,vset", [(0.3, 0.1, 1.02), (-0.2, 0.2, 0.97)])
+def test_cim_pv_node_is_two_bus_pv_closed_form(pg, x, vset):
+    """A lossless line (z = jx, no mutual coupling) from the balanced source
+    to a PV node: each phase is the two-bus PV problem, delta2 = asin(P x /
+    (V1 V2)) from the phase's source angle, and the generator's reactive
+    injection Q = (V2^2 - V1 V2 cos delta2) / x."""
+    case = _pv_line(x, pg, vset)
+    res = O.newton_cim(case, tol=1e-12)
+    assert res["converged"]
+    d = math.asin(pg * x / vset)
+    q = (vset * vset - vset * math.cos(d)) / x
+    for s in range(3):
+        v2 = res["V"][3 + s]
+        assert abs(abs(v2) - vset) < 1e-12
+        assert abs(np.angle(v2 / ROT[s]) - d) < 1e-10
+        assert abs(res["Qg"][3 + s] - q) < 1e-10
+
+
+def test_cim_pv_converges_quadratically_and_balances_power():
+    """The augmented Jacobian is exact: the mismatch falls quadratically, and
+    at the solution the generation (with the solved Q_g) minus the loads
+    equals the series losses of all branches."""
+    case = cases.with_pv_nodes(cases.feeder_case(120, 5), 3, 2)
+    res = O.newton_cim(case, tol=1e-13)
+    h = res["history"]
+    assert res["converged"]
+    for k in range(1, len(h) - 1):
+        if h[k] < 1e-3 and h[k + 1] > 1e-12:
+            assert h[k + 1] <= 50.0 * h[k] ** 2
+    Y = O.ybus_three_phase(case)
+    V, Qg = res["V"], res["Qg"]
+    S = V * np.conj(Y @ V)  # injected into the network
+    free = O.cim_free_slots(case)
+    Ssp = O.cim_specified_power(case, V, Qg)
+    assert np.max(np.abs((S - Ssp)[free])) < 1e-11
+    pv = O.cim_pv_slots(case)
+    assert np.max(np.abs(np.abs(V[pv]) - np.repeat(case.v_set, 3)[pv])) < 1e-12
