@@ -81,8 +81,13 @@ enum pf_kind { PF_SINGLE_PHASE = 1, PF_THREE_PHASE = 3 };
  *                 Specified injection = gen - load(|V|)  (Eq. 12-15).
  *   br_from/br_to[m], br_r/br_x/br_b[m]: pi-model branches, series r + jx,
  *                 total line charging b split b/2 per end (Eq. 2-3).
- * kind == PF_THREE_PHASE (no PV buses, as in Sec. II.B):
+ * kind == PF_THREE_PHASE (Sec. II.B; PV nodes are a reading beyond the
+ * paper, which defers them):
  *   phases[n]     uint8 bit mask of present phases (a=1, b=2, c=4).
+ *   bus_type[n]   optional: PF_PV marks a node whose generator holds |V| of
+ *                 every present phase at v_set[n] while injecting
+ *                 p_gen[n][3] per phase (its reactive injection is solved
+ *                 for); other nodes PF_PQ.  NULL = no PV nodes.
  *   source        index of the ideal balanced source node (slack).
  *   v_source      its magnitude; phase angles 0, -120, +120 degrees.
  *   p_load[3n], q_load[3n]  wye load per slot at |V| = 1 pu.

@@ -84,7 +84,8 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
               yv.begin() + (size_t)e * vb);
   std::vector<int8_t> bt(n);
   std::vector<double> vset(n, 1.0), qg(n, 0.0), zip(3 * (size_t)n), pg(n, 0.0);
-  std::vector<double> pl, ql;
+  std::vector<double> pl, ql, pg3;
+  if (c.kind != PF_SINGLE_PHASE) pg3.assign(3 * (size_t)n, 0.0);
   if (c.kind == PF_SINGLE_PHASE) {
     pl.assign(n, 0.0);
     ql.assign(n, 0.0);
@@ -103,11 +104,14 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
     ql.assign(3 * (size_t)n, 0.0);
     for (int i = 0; i < n; ++i) {
       int o = s.perm[i];
-      bt[i] = (int8_t)((c.phases[o] & 7) | (o == c.source ? 8 : 0));
+      const bool pv = !c.bus_type.empty() && c.bus_type[o] == PF_PV;
+      bt[i] = (int8_t)((c.phases[o] & 7) | (o == c.source ? 8 : 0) | (pv ? 16 : 0));
+      vset[i] = c.v_set.empty() ? 1.0 : c.v_set[o];
       for (int k = 0; k < 3; ++k) {
         zip[3 * (size_t)i + k] = c.zip[3 * (size_t)o + k];
         pl[3 * (size_t)i + k] = c.p_load3[3 * (size_t)o + k];
         ql[3 * (size_t)i + k] = c.q_load3[3 * (size_t)o + k];
+        pg3[3 * (size_t)i + k] = c.p_gen3.empty() ? 0.0 : c.p_gen3[3 * (size_t)o + k];
       }
     }
     d.v_source = c.v_source;
@@ -151,6 +155,7 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   UP(qg, q_gen);
   UP(zip, zip);
   UP(pg, p_gen0);
+  UP(pg3, p_gen3);
   UP(pl, p_load0);
   UP(ql, q_load0);
   UP(s.perm, perm);
@@ -242,7 +247,7 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
   t += (kind == PF_SINGLE_PHASE ? 2 : 0) * nb * 8;      // vm, va
   t += 3 * nb * nsl * 16;                               // V, I, dV
   t += (kind == PF_SINGLE_PHASE ? 40 : 0) * nb;         // U, FP32 (U, |V|), FP32 loads
-  t += (kind == PF_SINGLE_PHASE ? 0 : 12) * nb * 8;     // abcd
+  t += (kind == PF_SINGLE_PHASE ? 0 : 15) * nb * 8;     // abcd, PV reactive injection
   t += 3 * nb * bs * 8;                                 // F, dx, r
   t += (size_t)nnz_lu * B * bs * bs * 8;                // lu
   t += nb * bs * bs * 8;                                // uinv
@@ -293,6 +298,7 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
   A((void**)&w.I, nb * nsl * 16);
   A((void**)&w.dV, nb * nsl * 16);
   if (kind == PF_THREE_PHASE) A((void**)&w.abcd, nb * 12 * 8);
+  if (kind == PF_THREE_PHASE) A((void**)&w.qg, nb * 3 * 8);
   A((void**)&w.F, nb * bs * 8);
   A((void**)&w.dx, nb * bs * 8);
   A((void**)&w.r, nb * bs * 8);

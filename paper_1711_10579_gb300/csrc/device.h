@@ -61,12 +61,14 @@ struct DevSys {
   const int2* con;
   const int8_t* g_fwd;
   const int8_t* g_bwd;
-  // bus data: single phase type 0/1/2; three phase phase mask | 8 at source
+  // bus data: single phase type 0/1/2; three phase phase mask | 8 at the
+  // source | 16 at a PV node (v_set its |V|, p_gen3 its generation)
   const int8_t* btype;
   const double* v_set;
   const double* q_gen;
   const double* zip;     // 3 per bus / node
   const double* p_gen0;  // case's own generation (single phase)
+  const double* p_gen3;  // three phase: generation per slot of PV nodes (btype & 16)
   const double* p_load0; // case's own loads (per bus or per slot)
   const double* q_load0;
   const int* perm;       // new -> caller numbering
@@ -107,6 +109,7 @@ struct DevWork {
   double* F;      // mismatch, bs per row
   double* dx;     // Newton step, bs per row
   double* r;      // refinement residual, bs per row
+  double* qg;     // three phase: reactive injection of PV slots, 3 per row
   void* lu;       // factor values, bs*bs per entry
   void* uinv;     // inverse diagonal blocks, bs*bs per row
   void* y;        // triangular-solve vector, bs per row

@@ -36,6 +36,7 @@ struct CaseData {
   int source = 0;
   double v_source = 1.0;
   std::vector<double> p_load3, q_load3;  // 3n
+  std::vector<double> p_gen3;            // 3n: generation of PV nodes (bus_type, v_set)
   // branches
   std::vector<int> br_from, br_to;
   std::vector<double> br_r, br_x, br_b;

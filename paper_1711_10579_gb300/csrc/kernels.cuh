@@ -438,6 +438,7 @@ __device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, 
   const size_t b = (size_t)i * B + gs;
   const int mask = S.btype[i] & 7;
   const bool src = (S.btype[i] & 8) != 0;
+  const bool pv = (S.btype[i] & 16) != 0;
   double2 Vi[3], I[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -468,6 +469,15 @@ __device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, 
       const double pl = __ldcg(w.spec + b * 6 + a), ql = __ldcg(w.spec + b * 6 + 3 + a);
       double2 Isp, dr, di;
       load_slope(Vi[a], pl, ql, zp, zi, zz, Isp, dr, di);
+      if (pv) {
+        // the generator of a PV node: constant P_g + j Q_g (Q_g solved for)
+        double2 Ig, gr, gi;
+        load_slope(Vi[a], -S.p_gen3[(size_t)i * 3 + a], -__ldcg(w.qg + b * 3 + a), 1.0, 0.0,
+                   0.0, Ig, gr, gi);
+        Isp = cadd(Isp, Ig);
+        dr = cadd(dr, gr);
+        di = cadd(di, gi);
+      }
       const double2 dI = csub(Isp, I[a]);
       fim = dI.y;
       fre = dI.x;
@@ -524,6 +534,29 @@ __device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, 
           } else {
             blk[a * 6 + a] = TF(1);
             blk[(3 + a) * 6 + 3 + a] = TF(1);
+          }
+        }
+      }
+      if ((S.btype[j] & 16) && !srcj) {
+        // PV column node: its phase c keeps |V| by dVr = -(Vi/Vr) dVi, so
+        // the unknowns are (dQ_c, dVi_c): column 3 + c becomes col(Vi) -
+        // (Vi/Vr) col(Vr), and column c carries d(Y V - I_sp)/dQ_c = j V / |V|^2,
+        // nonzero only in the node's own rows of phase c
+        const size_t bj3 = ((size_t)j * B + gs) * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          if (!((maskj >> c) & 1)) continue;
+          const double2 v = (j == i) ? Vi[c] : ldc(w.V + bj3 + c);
+          const TF rho = (TF)(v.y / v.x);
+#pragma unroll
+          for (int r = 0; r < 6; ++r) {
+            blk[r * 6 + 3 + c] -= rho * blk[r * 6 + c];
+            blk[r * 6 + c] = TF(0);
+          }
+          if (j == i) {
+            const double m2 = v.x * v.x + v.y * v.y;
+            blk[c * 6 + c] = (TF)(v.x / m2);
+            blk[(3 + c) * 6 + c] = (TF)(-v.y / m2);
           }
         }
       }
@@ -1411,13 +1444,15 @@ __device__ __forceinline__ void setup_row(const DevSys& S, const DevWork& w, int
         } else if (w.warm_in) {
           v = w.warm_V[(size_t)oi * 3 + a];
         } else {
-          // balanced source angles 0, -120, +120 degrees
+          // balanced source angles 0, -120, +120 degrees; PV nodes at v_set
           double sn, cs;
           sincos(-2.0943951023931954923 * a, &sn, &cs);
-          v = make_double2(S.v_source * cs, S.v_source * sn);
+          const double m0 = (S.btype[i] & 16) ? S.v_set[i] : S.v_source;
+          v = make_double2(m0 * cs, m0 * sn);
         }
       }
       w.V[b * 3 + a] = v;
+      w.qg[b * 3 + a] = 0.0;
     }
   }
   if (i == 0) setup_scenario(w, gs);
@@ -1430,8 +1465,16 @@ __device__ __forceinline__ void dv_row(const DevSys& S, const DevWork& w, int i,
   const int B = w.B;
   const size_t b = (size_t)i * B + gs;
   if constexpr (THREE) {
-    for (int a = 0; a < 3; ++a)
-      w.dV[b * 3 + a] = make_double2(__ldcg(w.dx + b * 6 + a), __ldcg(w.dx + b * 6 + 3 + a));
+    const bool pv = (S.btype[i] & 16) != 0 && !(S.btype[i] & 8);
+    for (int a = 0; a < 3; ++a) {
+      const double di = __ldcg(w.dx + b * 6 + 3 + a);
+      double dr = __ldcg(w.dx + b * 6 + a);
+      if (pv && ((S.btype[i] >> a) & 1)) {  // (dQ, dVi): dVr = -(Vi/Vr) dVi
+        const double2 v = ldc(w.V + b * 3 + a);
+        dr = -(v.y / v.x) * di;
+      }
+      w.dV[b * 3 + a] = make_double2(dr, di);
+    }
   } else {
     // dV = j d_delta V + d|V| U
     const double2 V = ldc(w.V + b), U = ldc(w.U + b);
@@ -1459,15 +1502,23 @@ __device__ __forceinline__ void resid_row(const DevSys& S, const DevWork& w, int
     }
     const int mask = S.btype[i] & 7;
     const bool src = (S.btype[i] & 8) != 0;
+    const bool pv = (S.btype[i] & 16) != 0;
     for (int a = 0; a < 3; ++a) {
       const bool fa = ((mask >> a) & 1) && !src;
-      const double dr = __ldcg(w.dx + b * 6 + a), di = __ldcg(w.dx + b * 6 + 3 + a);
+      const double2 dv = ldc(w.dV + b * 3 + a);  // the step as a voltage change
+      const double dr = dv.x, di = dv.y;
       double rim, rre;
       if (fa) {
         // J dV = [Im; Re](Y dV) - [a b; c d] dV   (Eq. 21-23)
         const double* ad = w.abcd + b * 12;
-        const double jim = YdV[a].y - (ad[a] * dr + ad[3 + a] * di);
-        const double jre = YdV[a].x - (ad[6 + a] * dr + ad[9 + a] * di);
+        double jim = YdV[a].y - (ad[a] * dr + ad[3 + a] * di);
+        double jre = YdV[a].x - (ad[6 + a] * dr + ad[9 + a] * di);
+        if (pv) {  // plus the dQ column j V / |V|^2
+          const double2 v = ldc(w.V + b * 3 + a);
+          const double dq = __ldcg(w.dx + b * 6 + a), m2 = v.x * v.x + v.y * v.y;
+          jim += v.x / m2 * dq;
+          jre -= v.y / m2 * dq;
+        }
         rim = __ldcg(w.F + b * 6 + a) - jim;
         rre = __ldcg(w.F + b * 6 + 3 + a) - jre;
       } else {
@@ -1514,11 +1565,23 @@ __device__ __forceinline__ double update_row(const DevSys& S, const DevWork& w, 
   const size_t b = (size_t)i * B + gs;
   double stp = 0.0;
   if constexpr (THREE) {
+    const bool pv = (S.btype[i] & 16) != 0 && !(S.btype[i] & 8);
     for (int a = 0; a < NSL; ++a) {
-      const double dr = __ldcg(w.dx + b * 6 + a), di = __ldcg(w.dx + b * 6 + 3 + a);
+      double dr = __ldcg(w.dx + b * 6 + a);
+      const double di = __ldcg(w.dx + b * 6 + 3 + a);
       stp = fmax(stp, fmax(fabs(dr), fabs(di)));
       const double2 v = ldc(w.V + b * 3 + a);
-      w.V[b * 3 + a] = make_double2(v.x + dr, v.y + di);
+      if (pv && ((S.btype[i] >> a) & 1)) {
+        // PV slot: the step is (dQ, dVi) with dVr = -(Vi/Vr) dVi; the new
+        // voltage is put back on |V| = v_set
+        w.qg[b * 3 + a] += dr;
+        dr = -(v.y / v.x) * di;
+        const double2 u = make_double2(v.x + dr, v.y + di);
+        const double sc = S.v_set[i] / sqrt(u.x * u.x + u.y * u.y);
+        w.V[b * 3 + a] = make_double2(u.x * sc, u.y * sc);
+      } else {
+        w.V[b * 3 + a] = make_double2(v.x + dr, v.y + di);
+      }
     }
   } else {
     const double dd = __ldcg(w.dx + b * 2), dm = __ldcg(w.dx + b * 2 + 1);

@@ -198,17 +198,49 @@ int copy_case(const pf_case_desc* d, CaseData& c, std::string& err) {
       err = "phases, br_phases and br_z are required for a three-phase case";
       return PF_ERR_INVALID;
     }
-    if (d->bus_type) {
-      for (int i = 0; i < n; ++i)
-        if (d->bus_type[i] == PF_PV) {
-          err = "PV buses are not part of the three-phase formulation";
-          return PF_ERR_INVALID;
-        }
-    }
     if (d->source < 0 || d->source >= n) {
       err = "source node out of range";
       return PF_ERR_INVALID;
     }
+    // PV nodes (optional): bus_type PF_PV, |V| set point v_set[n], generation
+    // p_gen[n][3] per phase
+    c.bus_type.assign(n, (int8_t)PF_PQ);
+    bool any_pv = false;
+    if (d->bus_type) {
+      for (int i = 0; i < n; ++i) {
+        const int t = d->bus_type[i];
+        if (t != PF_PV && t != PF_PQ && t != PF_SLACK) {
+          msg << "node " << i << " has an unknown type " << t;
+          err = msg.str();
+          return PF_ERR_INVALID;
+        }
+        if (t == PF_PV) {
+          if (i == d->source) {
+            err = "the source node cannot be a PV node";
+            return PF_ERR_INVALID;
+          }
+          c.bus_type[i] = (int8_t)PF_PV;
+          any_pv = true;
+        }
+      }
+    }
+    if (any_pv && (!d->v_set || !d->p_gen)) {
+      err = "PV nodes need v_set[n] and p_gen[n][3]";
+      return PF_ERR_INVALID;
+    }
+    c.v_set = copy_or<double>(any_pv ? d->v_set : nullptr, n, 1.0);
+    c.p_gen3 = copy_or<double>(any_pv ? d->p_gen : nullptr, (size_t)3 * n, 0.0);
+    if (!finite_all(c.v_set.data(), c.v_set.size()) ||
+        !finite_all(c.p_gen3.data(), c.p_gen3.size())) {
+      err = "v_set or p_gen contain non-finite values";
+      return PF_ERR_INVALID;
+    }
+    for (int i = 0; i < n; ++i)
+      if (c.bus_type[i] == PF_PV && !(c.v_set[i] > 0.0)) {
+        msg << "PV node " << i << " needs a positive |V| set point";
+        err = msg.str();
+        return PF_ERR_INVALID;
+      }
     c.source = d->source;
     c.v_source = d->v_source > 0 ? d->v_source : 1.0;
     if (!std::isfinite(c.v_source)) {

@@ -326,6 +326,7 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   sizes[k++] = (size_t)nblev;                                // backward lanes
   sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 16 : 0;        // FP32 (U, |V|)
   sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;         // FP32 loads
+  sizes[k++] = kind == PF_THREE_PHASE ? nb * 3 * 8 : 0;      // PV reactive injection
   size_t offs[24];
   for (int q = 0; q < k; ++q) {
     offs[q] = off;
@@ -380,6 +381,7 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   int8_t* g_bwd = (int8_t*)at(18);
   w.uvm32 = (float4*)at(19);
   w.spec32 = (float2*)at(20);
+  w.qg = (double*)at(21);
   auto put_lanes = [&](const std::vector<int>& ptr, const std::vector<int>& longest, int8_t* dst) {
     int8_t chunk[512];
     const int nl = (int)ptr.size() - 1;

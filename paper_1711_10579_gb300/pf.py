@@ -206,6 +206,10 @@ def make_desc(case) -> _Desc:
         d.br_phases = u8(case.br_phases)
         z = np.ascontiguousarray(case.br_z, dtype=np.complex128)
         d.br_z = f64(np.stack([z.real, z.imag], axis=-1).reshape(-1))
+        if case.node_type is not None:  # PV nodes
+            d.bus_type = i32(case.node_type)
+            d.v_set = f64(case.v_set)
+            d.p_gen = f64(np.asarray(case.p_gen).reshape(-1))
     else:
         raise TypeError("expected a SinglePhaseCase or ThreePhaseCase")
     return _Desc(d, keep)

@@ -621,3 +621,80 @@ def test_bicgstab_needs_its_work_vectors(pf, ctx):
             pf.pf_solve(c, pf.make_opts(method=pf.PF_NK, krylov=1, gmres_restart=4))
     finally:
         pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# three phase with PV nodes (dVr = -(Vi/Vr) dVi substitution on the GPU,
+# augmented system in the oracle)
+# ----------------------------------------------------------------------------
+
+def _check_cim_solve(case, vm, va, info, ref):
+    assert info["status"] == 0, info
+    assert info["mismatch"] <= 1e-8
+    Vref = ref["V"]
+    assert np.max(np.abs(vm - np.abs(Vref))) <= V_TOL
+    present = np.abs(Vref) > 0
+    dang = np.angle(np.exp(1j * (va - np.angle(Vref))))
+    assert np.max(np.abs(dang[present])) <= A_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_three_phase_pv_solve_matches_oracle(pf, ctx, prec):
+    case = cases.with_pv_nodes(cases.feeder_case(600, 4), 8, 3)
+    ref = O.newton_cim(case)
+    assert ref["converged"]
+    c = pf.pf_create_case(ctx, case)
+    try:
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        vm, va, info = pf.pf_solve(c, pf.make_opts(precision=p))
+        _check_cim_solve(case, vm, va, info, ref)
+        pv = O.cim_pv_slots(case)
+        assert np.max(np.abs(vm[pv] - np.repeat(case.v_set, 3)[pv])) <= 1e-12
+        # Newton-Krylov on the same system
+        vm, va, info = pf.pf_solve(c, pf.make_opts(method=pf.PF_NK, precision=p, nk_fallback=0,
+                                                   gmres_max_iter=2000))
+        _check_cim_solve(case, vm, va, info, ref)
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_three_phase_pv_batch_matches_oracle(pf, ctx):
+    case = cases.with_pv_nodes(cases.feeder_case(500, 6), 6, 1)
+    B = 6
+    pl, ql = cases.feeder_scenario_loads(case, B, seed=5, sigma=0.1)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve_batch(c, pl, ql, None, pf.make_opts(scen_per_cta=2))
+        assert np.all(info["status"] == 0), info
+        for b in (0, B - 1):
+            ref = O.newton_cim(case.with_loads(pl[b], ql[b]))
+            _check_cim_solve(case, vm[b], va[b], info[b], ref)
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_three_phase_pv_two_node_closed_form(pf, ctx):
+    """A PV node behind a lossless line from the balanced source: each phase
+    is the two-bus PV problem (delta2 = asin(P x / (V1 V2)))."""
+    import dataclasses as dc
+
+    pg, x, vset = 0.3, 0.1, 1.02
+    base = np.zeros((3, 3), dtype=np.complex128)
+    np.fill_diagonal(base, 1j * x)
+    case = cases.ThreePhaseCase(
+        n_node=2, source=0, phases=np.array([7, 7], np.uint8), p_load=np.zeros((2, 3)),
+        q_load=np.zeros((2, 3)), zip=np.tile([1.0, 0.0, 0.0], (2, 1)),
+        br_from=np.array([0], np.int32), br_to=np.array([1], np.int32),
+        br_phases=np.array([7], np.uint8), br_z=base[None])
+    case = dc.replace(case, node_type=np.array([cases.PQ, cases.PV], np.int32),
+                      v_set=np.array([1.0, vset]), p_gen=np.array([[0, 0, 0], [pg, pg, pg]], float))
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve(c, pf.make_opts(precision=pf.PF_FP64))
+        assert info["status"] == 0
+        d = np.arcsin(pg * x / vset)
+        rot = np.angle(np.exp(-2j * np.pi / 3 * np.arange(3)))
+        assert np.max(np.abs(vm[3:] - vset)) <= 1e-12
+        assert np.max(np.abs(np.angle(np.exp(1j * (va[3:] - rot - d))))) <= 1e-9
+    finally:
+        pf.pf_destroy_case(c)
