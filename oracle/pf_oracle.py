@@ -681,6 +681,38 @@ def branch_flows(case, vm, va):
     return Sf.real, Sf.imag, St.real, St.imag, (loss.real, loss.imag)
 
 
+def cim_pv_system(case, Y, V, Qg):
+    """Right-hand side and Jacobian of the augmented CIM system with PV slots.
+    Unknowns: the CIM unknowns (cim_unknowns order) then Q_g of every PV slot
+    (cim_pv_slots order).  Equations: the current mismatch rows, then
+    |V|^2 - v_set^2 per PV slot.  Returns (Fa, Ja) with Ja the derivative of
+    G = [Y V - I_sp, |V|^2 - v_set^2] and Fa = -G, so that Ja dx = Fa is the
+    Newton step.  The Q_g column of the current rows is
+    d(Y V - I_sp)/dQ_g = j V / |V|^2 (I_sp = conj(S_sp) V / |V|^2 with S_sp
+    containing j Q_g); the magnitude row is (2 Re V, 2 Im V)."""
+    idx = cim_unknowns(case)
+    pvs = np.flatnonzero(cim_pv_slots(case))
+    npv = pvs.size
+    vset = np.repeat(np.asarray(case.v_set, dtype=float), 3)
+    pos = {int(k): p for p, k in enumerate(idx)}
+    F = cim_mismatch(case, Y, V, Qg)[idx]
+    J = cim_jacobian(case, Y, V, Qg)[idx][:, idx].tocsr()
+    nu = idx.size
+    rows, cols, vals = [], [], []
+    for t, slot in enumerate(pvs):
+        node, ph = divmod(int(slot), 3)
+        v = V[slot]
+        w = 1j * v / abs(v) ** 2
+        r_im, r_re = pos[6 * node + ph], pos[6 * node + 3 + ph]
+        rows += [r_im, r_re, nu + t, nu + t]
+        cols += [nu + t, nu + t, r_im, r_re]
+        vals += [w.imag, w.real, 2.0 * v.real, 2.0 * v.imag]
+    Jq = sp.coo_matrix((vals, (rows, cols)), shape=(nu + npv, nu + npv)).tocsr()
+    Ja = sp.bmat([[J, None], [None, sp.csr_matrix((npv, npv))]]).tocsr() + Jq
+    cons = np.abs(V[pvs]) ** 2 - vset[pvs] ** 2
+    return np.concatenate([F, -cons]), Ja
+
+
 def _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol):
     """CIM Newton with PV nodes, augmented form: the reactive injection Q_g of
     every PV slot is an extra unknown and |V|^2 = v_set^2 an extra equation
@@ -696,8 +728,6 @@ def _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol):
     idx = cim_unknowns(case)
     pvs = np.flatnonzero(pv)
     npv = pvs.size
-    # positions of each PV slot's Re / Im unknowns inside idx
-    pos = {int(k): p for p, k in enumerate(idx)}
     history, steps = [], []
     k = 0
     converged = False
@@ -715,25 +745,8 @@ def _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol):
         if k >= max_iter:
             break
         k += 1
-        F = cim_mismatch(case, Y, V, Qg)[idx]
-        J = cim_jacobian(case, Y, V, Qg)[idx][:, idx].tocsr()
+        Fa, Ja = cim_pv_system(case, Y, V, Qg)
         nu = idx.size
-        rows, cols, vals = [], [], []
-        for t, slot in enumerate(pvs):
-            node, ph = divmod(int(slot), 3)
-            v = V[slot]
-            m2 = abs(v) ** 2
-            w = 1j * v / m2  # d(Y V - I_sp)/dQ_g of this slot
-            r_im, r_re = pos[6 * node + ph], pos[6 * node + 3 + ph]
-            rows += [r_im, r_re]
-            cols += [nu + t, nu + t]
-            vals += [w.imag, w.real]
-            rows += [nu + t, nu + t]
-            cols += [pos[6 * node + ph], pos[6 * node + 3 + ph]]
-            vals += [2.0 * v.real, 2.0 * v.imag]
-        Jq = sp.coo_matrix((vals, (rows, cols)), shape=(nu + npv, nu + npv)).tocsr()
-        Ja = sp.bmat([[J, None], [None, sp.csr_matrix((npv, npv))]]).tocsr() + Jq
-        Fa = np.concatenate([F, -cons])
         dx = solve_linear(Ja, Fa, linear, gmres_restart, gmres_tol)
         full = np.zeros(6 * n)
         full[idx] = dx[:nu]

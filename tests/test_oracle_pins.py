@@ -546,3 +546,44 @@ def test_cim_pv_converges_quadratically_and_balances_power():
     assert np.max(np.abs((S - Ssp)[free])) < 1e-11
     pv = O.cim_pv_slots(case)
     assert np.max(np.abs(np.abs(V[pv]) - np.repeat(case.v_set, 3)[pv])) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_cim_pv_augmented_jacobian_matches_central_differences(seed):
+    """Every column of the augmented system (Re V, Im V and Q_g unknowns;
+    current and magnitude rows) against central differences of
+    G = [Y V - I_sp, |V|^2 - v_set^2], at a point with non-zero Q_g."""
+    case = cases.with_pv_nodes(cases.feeder_case(40, 7 + seed), 4, seed)
+    Y = O.ybus_three_phase(case)
+    rng = np.random.default_rng(seed)
+    V = O.cim_flat_start(case)
+    V = V * rng.uniform(0.92, 1.05, V.size) * np.exp(1j * rng.uniform(-0.1, 0.1, V.size))
+    pvs = np.flatnonzero(O.cim_pv_slots(case))
+    assert pvs.size > 0
+    Qg = np.zeros(3 * case.n_node)
+    Qg[pvs] = rng.uniform(-0.2, 0.2, pvs.size)
+    Fa, Ja = O.cim_pv_system(case, Y, V, Qg)
+    Ja = Ja.toarray()
+    idx = O.cim_unknowns(case)
+    n = case.n_node
+    h = 1e-6
+
+    def G(V_, Q_):
+        return -O.cim_pv_system(case, Y, V_, Q_)[0]
+
+    cols = []
+    for k in idx:
+        node, slot = divmod(int(k), 6)
+        dv = np.zeros(3 * n, dtype=np.complex128)
+        dv[3 * node + slot % 3] = h if slot < 3 else 1j * h
+        cols.append((G(V + dv, Qg) - G(V - dv, Qg)) / (2 * h))
+    for s in pvs:
+        dq = np.zeros(3 * n)
+        dq[s] = h
+        cols.append((G(V, Qg + dq) - G(V, Qg - dq)) / (2 * h))
+    Jfd = np.array(cols).T
+    assert Ja.shape == Jfd.shape
+    assert np.max(np.abs(Ja - Jfd)) <= 1e-6 * max(1.0, np.max(np.abs(Ja)))
+    # the Q_g columns are non-zero only in the PV node's own two rows
+    qcols = Ja[:, idx.size:]
+    assert np.all(np.count_nonzero(qcols, axis=0) <= 2)
