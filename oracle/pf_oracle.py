@@ -12,10 +12,14 @@ What it computes, in the paper's notation (arXiv 1711.10579):
 * ``mismatch_polar``     Delta P, Delta Q, Eq. 8-9 (with ZIP loads, Eq. 14-15).
 * ``jacobian_polar``     [J1 J2; J3 J4] of Eq. 10, first derivatives of Eq. 6-7.
 * ``newton_polar``       single-phase Newton-Raphson (Sec. II.A algorithm box).
+* ``generator_q`` / ``newton_polar_qlim``  reactive output of PV generators and
+                         the rounds of PV -> PQ switching at their limits.
 * ``ybus_three_phase``   3x3 complex block admittance matrix, Eq. 11.
 * ``cim_mismatch``       current mismatch Delta I, Eq. 12-19.
 * ``cim_jacobian``       6x6 real blocks of Eq. 21-23.
-* ``newton_cim``         three-phase current-injection Newton (Sec. II.B box).
+* ``newton_cim``         three-phase current-injection Newton (Sec. II.B box),
+                         with PV nodes through ``cim_pv_system`` (augmented
+                         with reactive injections and |V| equations).
 * ``ilu0`` / ``gmres``   ILU(0) and restarted, right-preconditioned GMRES used
                          by the Newton-Krylov variant (Sec. III.B).
 * ``bicgstab``           right-preconditioned BiCGSTAB, the Krylov method the
@@ -40,7 +44,12 @@ design notes):
   (constant power, constant current, constant impedance), Eq. 14-15;
 * three-phase: every node has three phase slots; absent phases and the
   source node carry no unknowns; the source is an ideal balanced source;
-  loads are wye-connected; no PV buses (Sec. II.B);
+  loads are wye-connected; a PV node (deferred by Sec. II.B) injects a given
+  P and a free Q per phase and holds |V| = v_set on every phase present;
+* reactive limits of PV buses (single phase): after a converged solve every
+  PV bus whose generator Q is outside [q_min, q_max] becomes PQ at that
+  limit and the solve is repeated from the last voltages, until no bus
+  violates; switched buses stay PQ;
 * the diagonal adjustments a, b, c, d of Eq. 23 are the derivatives of the
   specified current (Eq. 17) with respect to the real and imaginary voltage,
   so that J is the exact Jacobian of Y V - I_sp in the ordering of Eq. 19-20;
@@ -50,6 +59,7 @@ design notes):
 from __future__ import annotations
 
 import math
+from dataclasses import replace
 
 import numpy as np
 import scipy.sparse as sp
@@ -232,6 +242,58 @@ def newton_polar(case, tol=1e-8, max_iter=30, linear="splu", vm0=None,
         steps.append(float(np.max(np.abs(dx))) if dx.size else 0.0)
     return dict(vm=vm, va=va, iterations=k, mismatch=history[-1],
                 history=history, steps=steps, converged=converged)
+
+
+def generator_q(case, Y, vm, va):
+    """Reactive output of the generator at every bus: the injection Q_i of
+    Eq. 7 plus the bus's own reactive load at |V_i| (Eq. 12-15)."""
+    _, Q = power_polar(Y, vm, va)
+    zp, zi, zz = case.zip[:, 0], case.zip[:, 1], case.zip[:, 2]
+    return Q + case.q_load * (zp + zi * vm + zz * vm * vm)
+
+
+def newton_polar_qlim(case, tol=1e-8, max_iter=30, linear="splu", max_rounds=50,
+                      gmres_restart=30, gmres_tol=1e-10):
+    """Newton-Raphson with the reactive limits [q_min, q_max] of PV buses
+    enforced by type switching (the PV rule of Sec. II.A holds |V| by free
+    reactive output; a generator at its limit can no longer do so).
+
+    Rounds: solve (newton_polar) from the last voltages; take the reactive
+    output of every PV bus (generator_q); every PV bus outside its limits
+    becomes a PQ bus whose generation is the limit it crossed; stop after a
+    round with no violation.  A switched bus stays PQ.  Returns
+    newton_polar's dict with the iterations of all rounds summed, plus
+    ``switched`` (bool per bus), ``rounds``, ``qg`` (reactive generation at
+    the solution) and ``case`` (the switched case)."""
+    Y = ybus_single(case)
+    cur = case
+    switched = np.zeros(case.n_bus, dtype=bool)
+    vm0 = va0 = None
+    total = 0
+    rounds = 0
+    while True:
+        rounds += 1
+        res = newton_polar(cur, tol, max_iter, linear, vm0, va0, gmres_restart, gmres_tol, Y=Y)
+        total += res["iterations"]
+        qg = generator_q(cur, Y, res["vm"], res["va"])
+        if not res["converged"] or case.q_max is None or rounds >= max_rounds:
+            break
+        pv = cur.bus_type == PV
+        hi = pv & (qg > case.q_max)
+        lo = pv & (qg < case.q_min)
+        if not (hi | lo).any():
+            break
+        bt = cur.bus_type.copy()
+        bt[hi | lo] = PQ
+        q_gen = cur.q_gen.copy()
+        q_gen[hi] = case.q_max[hi]
+        q_gen[lo] = case.q_min[lo]
+        cur = replace(cur, bus_type=bt, q_gen=q_gen)
+        switched |= hi | lo
+        vm0, va0 = res["vm"], res["va"]
+    res = dict(res)
+    res.update(iterations=total, switched=switched, rounds=rounds, qg=qg, case=cur)
+    return res
 
 
 def solve_linear(J, F, linear="splu", restart=30, tol=1e-10):

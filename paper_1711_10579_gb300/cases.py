@@ -53,6 +53,8 @@ class SinglePhaseCase:
     name: str = ""
     seed: int = 0
     load_scale: float = 1.0
+    q_min: np.ndarray | None = None  # float64 [n]: reactive generation limits
+    q_max: np.ndarray | None = None  # of PV buses (pu); None = no limits
 
     @property
     def n_branch(self) -> int:
@@ -78,6 +80,8 @@ class SinglePhaseCase:
             p_gen=self.p_gen[perm].copy(), q_gen=self.q_gen[perm].copy(),
             p_load=self.p_load[perm].copy(), q_load=self.q_load[perm].copy(),
             zip=self.zip[perm].copy(),
+            q_min=None if self.q_min is None else self.q_min[perm].copy(),
+            q_max=None if self.q_max is None else self.q_max[perm].copy(),
             br_from=inv[self.br_from].astype(np.int32),
             br_to=inv[self.br_to].astype(np.int32))
 
@@ -437,6 +441,16 @@ def with_pv_nodes(case: ThreePhaseCase, count: int, seed: int, p_range=(0.005, 0
     pg[pick] = rng.uniform(p_range[0], p_range[1], (pick.size, 3)) * case.load_scale * 20.0
     return dataclasses.replace(case, node_type=node_type, v_set=vset, p_gen=pg,
                                name=case.name + f"_pv{pick.size}")
+
+
+def with_q_limits(case: SinglePhaseCase, seed: int, q_range=(0.5, 3.0)) -> SinglePhaseCase:
+    """The grid with reactive generation limits at every bus (read at PV
+    buses only): q_max ~ U[q_range] and q_min = -U[q_range] pu, drawn
+    independently."""
+    rng = np.random.default_rng(seed)
+    qmax = rng.uniform(q_range[0], q_range[1], case.n_bus)
+    qmin = -rng.uniform(q_range[0], q_range[1], case.n_bus)
+    return dataclasses.replace(case, q_min=qmin, q_max=qmax, name=case.name + "_qlim")
 
 
 def case_feeder8000(seed: int = 0) -> ThreePhaseCase:

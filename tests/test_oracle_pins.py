@@ -59,6 +59,89 @@ def test_two_bus_lossless_pv_closed_form(P, x, v2):
     assert res["vm"][1] == v2
 
 
+def _two_bus_pv_with_load(pg, x, vset, pl, ql, qmin, qmax):
+    import dataclasses as dc
+
+    case = cases.two_bus_case(pg, 0.0, 0.0, x, pv=True, v2=vset)
+    return dc.replace(case, p_load=np.array([0.0, pl]), q_load=np.array([0.0, ql]),
+                      q_min=np.array([-9.0, qmin]), q_max=np.array([9.0, qmax]))
+
+
+@pytest.mark.parametrize("vset,qmin,qmax,side", [(1.02, -1.0, 0.15, "max"),
+                                                 (0.98, -0.1, 1.0, "min"),
+                                                 (1.02, -1.0, 1.0, None)])
+def test_two_bus_pv_reactive_limit_closed_form(vset, qmin, qmax, side):
+    """A generator with a local load behind a lossless line: held at v_set
+    its reactive output is (v^2 - v cos delta)/x + q_load with
+    v sin delta = (p_gen - p_load) x; past a limit the bus is PQ with net
+    injection (p_gen - p_load) + j (limit - q_load), the PQ closed form."""
+    pg, x, pl, ql = 0.3, 0.1, 0.1, 0.05
+    case = _two_bus_pv_with_load(pg, x, vset, pl, ql, qmin, qmax)
+    res = O.newton_polar_qlim(case, tol=1e-12)
+    assert res["converged"]
+    d = math.asin((pg - pl) * x / vset)
+    q_free = (vset * vset - vset * math.cos(d)) / x + ql
+    if side is None:
+        assert not res["switched"].any() and res["rounds"] == 1
+        assert abs(res["qg"][1] - q_free) < 1e-10
+        assert abs(res["va"][1] - d) < 1e-11 and res["vm"][1] == vset
+        return
+    lim = qmax if side == "max" else qmin
+    assert (q_free > qmax) if side == "max" else (q_free < qmin)
+    assert res["switched"][1] and res["rounds"] == 2
+    vm2, va2 = two_bus_pq_closed_form(-(pg - pl), -(lim - ql), 0.0, x)
+    assert abs(res["vm"][1] - vm2) < 1e-10
+    assert abs(res["va"][1] - va2) < 1e-10
+    assert abs(res["qg"][1] - lim) < 1e-10
+
+
+@pytest.mark.parametrize("zip_frac", [(0.2, 0.3, 0.5), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0)])
+def test_generator_q_with_zip_load_closed_form(zip_frac):
+    """Two-bus PV with a ZIP load at the generator's bus: at |V| = v_set the
+    load is (p, q) x (zp + zi v + zz v^2), so the generator's reactive output
+    is (v^2 - v cos delta)/x + q (zp + zi v + zz v^2) with
+    v sin delta = (p_gen - p shape) x."""
+    import dataclasses as dc
+
+    pg, x, v, pl, ql = 0.3, 0.1, 1.04, 0.1, 0.05
+    case = _two_bus_pv_with_load(pg, x, v, pl, ql, -9.0, 9.0)
+    case = dc.replace(case, zip=np.array([[1.0, 0.0, 0.0], list(zip_frac)]))
+    res = O.newton_polar_qlim(case, tol=1e-12)
+    shape = zip_frac[0] + zip_frac[1] * v + zip_frac[2] * v * v
+    d = math.asin((pg - pl * shape) * x / v)
+    assert abs(res["va"][1] - d) < 1e-11
+    assert abs(res["qg"][1] - ((v * v - v * math.cos(d)) / x + ql * shape)) < 1e-10
+
+
+@pytest.mark.parametrize("name,seed", [("300", 1), ("2000", 2)])
+def test_reactive_limits_hold_at_the_solution(name, seed):
+    """After the rounds: the mismatch of the switched system is below tol,
+    every remaining PV bus is inside its limits, every switched bus was PV
+    and sits exactly at the limit it crossed with |V| off its set point;
+    wide limits give the plain solve."""
+    base = {"300": cases.transmission_case(300, 405, 60, 2), "2000": cases.case_2000bus(0)}[name]
+    case = cases.with_q_limits(base, seed)
+    res = O.newton_polar_qlim(case)
+    assert res["converged"] and res["switched"].any()
+    Y = O.ybus_single(case)
+    sw = res["switched"]
+    assert np.all(case.bus_type[sw] == cases.PV)
+    assert np.all(res["case"].bus_type[sw] == cases.PQ)
+    F = O.mismatch_polar(res["case"], Y, res["vm"], res["va"])
+    assert np.max(np.abs(F)) <= 1e-8
+    qg = O.generator_q(case, Y, res["vm"], res["va"])
+    at = np.where(qg[sw] > 0, case.q_max[sw], case.q_min[sw])
+    assert np.max(np.abs(qg[sw] - at)) <= 1e-8
+    assert np.min(np.abs(res["vm"][sw] - case.v_set[sw])) > 1e-6
+    pv = res["case"].bus_type == cases.PV
+    assert np.all(qg[pv] <= case.q_max[pv] + 1e-9) and np.all(qg[pv] >= case.q_min[pv] - 1e-9)
+    wide = cases.with_q_limits(base, seed, q_range=(50.0, 60.0))
+    r2 = O.newton_polar_qlim(wide)
+    r0 = O.newton_polar(base)
+    assert r2["rounds"] == 1 and not r2["switched"].any()
+    assert np.array_equal(r2["vm"], r0["vm"]) and np.array_equal(r2["va"], r0["va"])
+
+
 def _random_voltage(n, rng):
     return rng.uniform(0.9, 1.1, n), rng.uniform(-0.3, 0.3, n)
 
