@@ -158,6 +158,16 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   UP(pg3, p_gen3);
   UP(pl, p_load0);
   UP(ql, q_load0);
+  d.q_min = d.q_max = nullptr;
+  if (c.kind == PF_SINGLE_PHASE && !c.q_max.empty()) {
+    std::vector<double> qmin(n), qmax(n);
+    for (int i = 0; i < n; ++i) {
+      qmin[i] = c.q_min[s.perm[i]];
+      qmax[i] = c.q_max[s.perm[i]];
+    }
+    UP(qmin, q_min);
+    UP(qmax, q_max);
+  }
   UP(s.perm, perm);
   std::vector<int> iperm(s.perm.size());
   for (size_t k = 0; k < s.perm.size(); ++k) iperm[s.perm[k]] = (int)k;
@@ -255,6 +265,8 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
   t += (size_t)B * (2 * 8 + 2 * 8 + 4 + 12) + 8 + 64;   // norm, step, flag, status, t0, call
   t += 3 * nb * nsl * 8;                                // staged inputs
   t += 2 * nb * nsl * 8 + (size_t)B * sizeof(pf_info);  // staged outputs
+  if (kind == PF_SINGLE_PHASE)                          // reactive-limit rounds
+    t += nb * 9 + (size_t)B * (5 * 4 + 8 + sizeof(pf_info)) + 4;
   if (m > 0) {                                          // Newton-Krylov (FP64 bound)
     t += (size_t)nnz_lu * B * bs * bs * 8;              // Jacobian copy
     t += (size_t)(m + 1 + 3) * nb * bs * 8;             // basis, w, z, x
@@ -319,6 +331,16 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
   A((void**)&st_vm, nb * nsl * 8);
   A((void**)&st_va, nb * nsl * 8);
   A((void**)&st_info, (size_t)B * sizeof(pf_info));
+  if (kind == PF_SINGLE_PHASE) {
+    A((void**)&w.bt, nb);
+    A((void**)&w.qsw, nb * 8);
+    A((void**)&w.qdone, (size_t)B * 4);
+    A((void**)&w.qcnt, (size_t)B * 4);
+    A((void**)&w.qit, (size_t)3 * B * 4);
+    A((void**)&w.qus, (size_t)B * 8);
+    A((void**)&w.qinfo, (size_t)B * sizeof(pf_info));
+    A((void**)&w.nsw, 4);
+  }
   if (m > 0) {
     A(&w.jm, (size_t)nnz_lu * B * bs * bs * 8);
     A(&w.vb, (size_t)(m + 1) * nb * bs * 8);
@@ -516,15 +538,15 @@ int pf_solve(pf_case c, const pf_opts* opts, double* vmag, double* vang, pf_info
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->ctx->device);
   cudaStream_t st = c->ctx->stream;
-  int rc = run_solve(c, o, 1, nullptr, nullptr, nullptr, &c->ws1, st, RunMode::Solve, nullptr,
-                     nullptr);
+  int rc = run_solve_q(c, o, 1, nullptr, nullptr, nullptr, &c->ws1, st, nullptr, nullptr,
+                       nullptr);
   if (rc != PF_OK) return rc;
   pf_info inf;
   rc = fetch_results(c, &c->ws1, 1, vmag, vang, &inf, st);
   if (rc == PF_OK && o.method == PF_NK && o.nk_fallback && inf.status != PF_OK) {
     const int lin = inf.linear_iterations;
-    rc = run_solve(c, fallback_opts(o), 1, nullptr, nullptr, nullptr, &c->ws1, st, RunMode::Solve,
-                   nullptr, nullptr);
+    rc = run_solve_q(c, fallback_opts(o), 1, nullptr, nullptr, nullptr, &c->ws1, st, nullptr,
+                     nullptr, nullptr);
     if (rc == PF_OK) rc = fetch_results(c, &c->ws1, 1, vmag, vang, &inf, st);
     inf.fallback = 1;
     inf.linear_iterations = lin;  // the GMRES iterations spent before the redo
@@ -556,8 +578,8 @@ int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
   if (e == cudaSuccess && p_gen)
     e = cudaMemcpyAsync(ws->st_p_gen, p_gen, per * B * 8, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_error(e, "copying scenario inputs");
-  rc = run_solve(c, o, B, p_load ? ws->st_p_load : nullptr, q_load ? ws->st_q_load : nullptr,
-                 p_gen ? ws->st_p_gen : nullptr, ws, st, RunMode::Solve, nullptr, nullptr);
+  rc = run_solve_q(c, o, B, p_load ? ws->st_p_load : nullptr, q_load ? ws->st_q_load : nullptr,
+                 p_gen ? ws->st_p_gen : nullptr, ws, st, nullptr, nullptr, nullptr);
   if (rc != PF_OK) return rc;
   std::vector<pf_info> inf(B);
   rc = fetch_results(c, ws, B, vmag, vang, inf.data(), st);
@@ -592,8 +614,8 @@ int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
       if (e == cudaSuccess && p_gen)
         e = cudaMemcpyAsync(ws2->st_p_gen, pg.data(), per * R * 8, cudaMemcpyHostToDevice, st);
       if (e != cudaSuccess) return cuda_error(e, "copying scenario inputs");
-      rc = run_solve(c, fo, R, p_load ? ws2->st_p_load : nullptr, q_load ? ws2->st_q_load : nullptr,
-                     p_gen ? ws2->st_p_gen : nullptr, ws2, st, RunMode::Solve, nullptr, nullptr);
+      rc = run_solve_q(c, fo, R, p_load ? ws2->st_p_load : nullptr, q_load ? ws2->st_q_load : nullptr,
+                     p_gen ? ws2->st_p_gen : nullptr, ws2, st, nullptr, nullptr, nullptr);
       if (rc == PF_OK) rc = fetch_results(c, ws2, R, vm.data(), va.data(), ri.data(), st);
       if (rc != PF_OK) return rc;
       for (int k = 0; k < R; ++k) {
@@ -621,8 +643,8 @@ int pf_solve_batch_device(pf_case c, int B, const double* d_p_load, const double
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->ctx->device);
   Workspace* ws = (B == 1) ? &c->ws1 : &c->wsB;
-  return run_solve(c, o, B, d_p_load, d_q_load, d_p_gen, ws, (cudaStream_t)stream,
-                   RunMode::Solve, d_vmag, d_vang, d_info);
+  return run_solve_q(c, o, B, d_p_load, d_q_load, d_p_gen, ws, (cudaStream_t)stream, d_vmag,
+                     d_vang, d_info);
 }
 
 int pf_analyze(const pf_case_desc* desc, pf_case_stats* out) {

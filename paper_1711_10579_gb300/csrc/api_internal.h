@@ -124,7 +124,20 @@ enum class InspectKind { Mismatch, Jacobian, Step };
 int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load,
               const double* d_q_load, const double* d_p_gen, Workspace* ws,
               cudaStream_t st, RunMode mode, double* out_vm, double* out_va,
-              pf_info* out_info = nullptr, unsigned long long* prof = nullptr);
+              pf_info* out_info = nullptr, unsigned long long* prof = nullptr,
+              const double* d_vm0 = nullptr, const double* d_va0 = nullptr, bool qlim = false);
+// run_solve of a Solve with the reactive limits of PV buses enforced when
+// o.q_limits is set and the case has them (rounds of solves, waiting for the
+// device between rounds); otherwise run_solve.
+int run_solve_q(pf_case c, const pf_opts& o, int B, const double* d_p_load,
+                const double* d_q_load, const double* d_p_gen, Workspace* ws, cudaStream_t st,
+                double* out_vm, double* out_va, pf_info* out_info);
+// Reactive-limit checks (qlim.cu).
+cudaError_t launch_qlim_init(const DevSys& S, const DevWork& w, cudaStream_t st);
+cudaError_t launch_qlim_check(const DevSys& S, const DevWork& w, const pf_info* info, int round,
+                              cudaStream_t st);
+cudaError_t launch_qlim_final(const DevWork& w, pf_info* info, int round, int capped,
+                              cudaStream_t st);
 void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int* cluster,
                   int* threads, int* S);
 int profile_solve(pf_case c, int B, const pf_opts& o, double* phase_us, pf_info* info);

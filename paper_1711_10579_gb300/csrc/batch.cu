@@ -67,6 +67,8 @@ __device__ __forceinline__ DevWork with_call(DevWork w) {
   w.in_p_load = c->p_load;
   w.in_q_load = c->q_load;
   w.in_p_gen = c->p_gen;
+  w.in_vm = c->vm0;
+  w.in_va = c->va0;
   w.out_vm = c->vm;
   w.out_va = c->va;
   w.out_info = c->info;
@@ -86,6 +88,8 @@ __device__ __forceinline__ void put_info(const DevWork& w, int gs, int st, int i
   inf.mismatch = nrm;
   inf.max_step = step;
   inf.solve_us = 0.0;
+  inf.q_switched = 0;
+  inf.q_rounds = 1;
   out[gs] = inf;
 }
 
@@ -115,6 +119,7 @@ __global__ void __launch_bounds__(256) k_setup_tile(DevSys S, DevWork w) {
   const int n = S.n, B = w.B;
   const int o0 = blockIdx.x * 32, g0 = blockIdx.y * 32, tx = threadIdx.x;
   const CallArgs* c = w.call;
+  const DevWork wc = with_call(w);
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int gs = g0 + r, oi = o0 + tx;
     if (gs < B && oi < n) {
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(256) k_setup_tile(DevSys S, DevWork w) {
     const int oi = o0 + r, gs = g0 + tx;
     if (oi >= n || gs >= B) continue;
     const int i = S.iperm[oi];
-    setup_1ph(S, w, i, gs, tp[0][tx][r], tp[1][tx][r], tp[2][tx][r]);
+    setup_1ph(S, wc, i, gs, tp[0][tx][r], tp[1][tx][r], tp[2][tx][r]);
     if (i == 0) {
       setup_scenario(w, gs);
       w.status[gs] = kRunning;
@@ -517,7 +522,7 @@ cudaError_t run_graph(Plan<BS, TF>& p, cudaStream_t st, BatchGraph* g, int refin
   std::array<long long, 16> key = {
       (long long)(uintptr_t)p.w.spec, (long long)(uintptr_t)p.S.lu_col, p.w.B, BS,
       (long long)sizeof(TF), o.S, p.threads_f, p.os.S, p.threads_s, o.max_iter, refine, o.ring,
-      (long long)(uintptr_t)p.S.g_fwd, 0, 0, 0};
+      (long long)(uintptr_t)p.S.g_fwd, 0, 0, (long long)(uintptr_t)p.w.bt};
   std::memcpy(&key[13], &o.tol, 8);
   std::memcpy(&key[14], &o.refine_below, 8);
   if (!g->exec || g->key != key) {
@@ -569,7 +574,7 @@ cudaError_t run_batch_t(const DevSys& S, const DevWork& w, const DevOpts& of, in
   cudaError_t e = set_smem(p);
   if (e != cudaSuccess) return e;
   // this call's inputs and outputs
-  CallArgs a{w.in_p_load, w.in_q_load, w.in_p_gen, w.out_vm, w.out_va, w.out_info};
+  CallArgs a{w.in_p_load, w.in_q_load, w.in_p_gen, w.in_vm, w.in_va, w.out_vm, w.out_va, w.out_info};
   k_args<<<1, 1, 0, st>>>(w.call, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

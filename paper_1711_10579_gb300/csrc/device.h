@@ -9,6 +9,8 @@ namespace pf {
 
 // Running status of a scenario inside a solve.
 constexpr int kRunning = PF_PENDING;
+// Scenario bus type of a PV bus switched to PQ at a reactive limit.
+constexpr int kPQLimit = 3;
 // Krylov basis vectors per GMRES cycle (restart m <= kMaxJ - 1).
 constexpr int kMaxJ = 64;
 // Half width of the sine / cosine table: angles j 2^-7 for |j| <= kTrigHalf.
@@ -69,6 +71,8 @@ struct DevSys {
   const double* zip;     // 3 per bus / node
   const double* p_gen0;  // case's own generation (single phase)
   const double* p_gen3;  // three phase: generation per slot of PV nodes (btype & 16)
+  const double* q_min;   // single phase, optional: reactive limits of PV buses
+  const double* q_max;
   const double* p_load0; // case's own loads (per bus or per slot)
   const double* q_load0;
   const int* perm;       // new -> caller numbering
@@ -131,6 +135,16 @@ struct DevWork {
   int* iter;                 // [B] index of the scenario's latest mismatch
   unsigned long long* t0;    // start time of the launch sequence (ns)
   struct CallArgs* call;     // this call's inputs and outputs
+  // reactive limits of PV buses (single phase; null when not enforced)
+  int8_t* bt;                // [row][B] bus type of the scenario (kPQLimit:
+                             // PQ at a limit, generation qsw)
+  double* qsw;               // [row][B] reactive generation of a switched bus
+  int* qdone;                // [B] 1: the scenario failed in an earlier round
+  int* qcnt;                 // [B] switched buses
+  int* qit;                  // [2][B] Newton and linear iterations of the rounds
+  double* qus;               // [B] device time of the rounds
+  pf_info* qinfo;            // [B] result of a scenario that failed
+  int* nsw;                  // buses switched by the last check (one counter)
 };
 
 // Inputs and outputs of one batched call, read by the phase kernels from
@@ -139,6 +153,8 @@ struct CallArgs {
   const double* p_load;
   const double* q_load;
   const double* p_gen;
+  const double* vm0;  // optional start voltages, the caller's [scenario][bus] order
+  const double* va0;
   double* vm;
   double* va;
   pf_info* info;

@@ -31,6 +31,7 @@ struct CaseData {
   // single phase, per bus
   std::vector<int8_t> bus_type;
   std::vector<double> v_set, p_gen, q_gen, p_load, q_load, zip;  // zip: n*3
+  std::vector<double> q_min, q_max;  // optional reactive limits (empty = none)
   // three phase: per node / per slot
   std::vector<uint8_t> phases;
   int source = 0;

@@ -241,12 +241,16 @@ __device__ __forceinline__ T group_sum(T v, int G, unsigned gmask) {
 
 // Rows: (P, Q) equations of bus i; columns: (delta, |V|) of bus j.  The slack
 // has no unknown and PV buses no |V| unknown: their rows become identity rows
-// and their columns zero, which keeps the system of Eq. 10 unchanged.
+// and their columns zero, which keeps the system of Eq. 10 unchanged.  With
+// reactive limits enforced the types are the scenario's (w.bt): a PV bus at
+// its limit is PQ with generation w.qsw.
 template <typename TF>
 __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, int gs,
                                       double& nrm, TF* jcopy) {
   const int B = w.B;
   const size_t b = (size_t)i * B + gs;
+  const int8_t* tp = w.bt ? w.bt + gs : S.btype;
+  const size_t ts = w.bt ? (size_t)B : 1;
   // FP64 mismatch.  I = sum_j Y_ij V_j as four FMAs per entry.
   const double2 Vi = ldc(w.V + b);
   double2 I = make_double2(0.0, 0.0);
@@ -267,9 +271,10 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
                pg = __ldcg(w.spec + b * 3 + 2);
   const double zp = S.zip[3 * i], zi = S.zip[3 * i + 1], zz = S.zip[3 * i + 2];
   const double shape = fma(fma(zz, vmi, zi), vmi, zp);
-  const int t = S.btype[i];
+  const int t = tp[i * ts];
   const double f0 = (t != PF_SLACK) ? fma(-pl, shape, pg) - Sc.x : 0.0;
-  const double f1 = (t == PF_PQ) ? fma(-ql, shape, S.q_gen[i]) - Sc.y : 0.0;
+  const double qgen = (t == kPQLimit) ? __ldcg(w.qsw + b) : S.q_gen[i];
+  const double f1 = (t >= PF_PQ) ? fma(-ql, shape, qgen) - Sc.y : 0.0;
   w.F[b * 2] = f0;
   w.F[b * 2 + 1] = f1;
   // max(|f0|, |f1|) on the bit patterns (NaN above +inf), no FP64 instruction
@@ -313,13 +318,13 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
       ix = fmaf(q.z, yux, ix);
       iy = fmaf(q.z, yuy, iy);
       float j00 = 0.f, j01 = 0.f, j10 = 0.f, j11 = 0.f;
-      const int tj = S.btype[j];
+      const int tj = tp[j * ts];
       if (t != PF_SLACK && tj != PF_SLACK) {
         // dS_i/d|V_j| = V_i conj(Y_ij U_j); dS_i/d delta_j = -j |V_j| dS_i/d|V_j|
         const float cx = vix * yux + viy * yuy, cy = viy * yux - vix * yuy;
         j00 = q.z * cy;
         j10 = -q.z * cx;
-        if (tj == PF_PQ) {
+        if (tj >= PF_PQ) {
           j01 = cx;
           j11 = cy;
         }
@@ -366,7 +371,7 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
       if (yi >= 0) {
         const double yx = Y[yi].x, yy = Y[yi].y;
         if (j != i) {
-          const int tj = S.btype[j];
+          const int tj = tp[j * ts];
           if (t != PF_SLACK && tj != PF_SLACK) {
             const size_t bj = (size_t)j * B + gs;
             // dS_i/d|V_j| = V_i conj(Y_ij U_j); dS_i/d delta_j = -j |V_j| dS_i/d|V_j|
@@ -376,7 +381,7 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
             const double cx = Vi.x * yux + Vi.y * yuy, cy = Vi.y * yux - Vi.x * yuy;
             j00 = vmj * cy;
             j10 = -vmj * cx;
-            if (tj == PF_PQ) {
+            if (tj >= PF_PQ) {
               j01 = cx;
               j11 = cy;
             }
@@ -1390,8 +1395,8 @@ __device__ __forceinline__ void setup_1ph(const DevSys& S, const DevWork& w, int
   w.spec32[b] = make_float2(to_f32_trunc(pl), to_f32_trunc(ql));
   double vm, va;
   if (w.in_vm) {
-    vm = w.in_vm[oi];
-    va = w.in_va[oi];
+    vm = w.in_vm[(size_t)gs * S.n + oi];
+    va = w.in_va[(size_t)gs * S.n + oi];
   } else if (w.warm_in) {
     vm = w.warm_vm[oi];
     va = w.warm_va[oi];
@@ -1439,8 +1444,8 @@ __device__ __forceinline__ void setup_row(const DevSys& S, const DevWork& w, int
       if ((mask >> a) & 1) {
         if (w.in_vm) {
           double sn, cs;
-          sincos(w.in_va[(size_t)oi * 3 + a], &sn, &cs);
-          v = make_double2(w.in_vm[(size_t)oi * 3 + a] * cs, w.in_vm[(size_t)oi * 3 + a] * sn);
+          sincos(w.in_va[src], &sn, &cs);
+          v = make_double2(w.in_vm[src] * cs, w.in_vm[src] * sn);
         } else if (w.warm_in) {
           v = w.warm_V[(size_t)oi * 3 + a];
         } else {
@@ -1544,11 +1549,11 @@ __device__ __forceinline__ void resid_row(const DevSys& S, const DevWork& w, int
     const double vmi = __ldcg(w.vm + b);
     const double dshape = S.zip[3 * i + 1] + 2.0 * S.zip[3 * i + 2] * vmi;
     const double dd = __ldcg(w.dx + b * 2), dm = __ldcg(w.dx + b * 2 + 1);
-    const int t = S.btype[i];
+    const int t = w.bt ? w.bt[b] : S.btype[i];
     const double r0 = (t != PF_SLACK)
                           ? __ldcg(w.F + b * 2) - (dS.x + __ldcg(w.spec + b * 3) * dshape * dm)
                           : -dd;
-    const double r1 = (t == PF_PQ)
+    const double r1 = (t >= PF_PQ)
                           ? __ldcg(w.F + b * 2 + 1) - (dS.y + __ldcg(w.spec + b * 3 + 1) * dshape * dm)
                           : -dm;
     y[b * 2] = r0;

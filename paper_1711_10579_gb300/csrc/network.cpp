@@ -177,6 +177,20 @@ int copy_case(const pf_case_desc* d, CaseData& c, std::string& err) {
         err = "case data contain non-finite values";
         return PF_ERR_INVALID;
       }
+    if ((d->q_min != nullptr) != (d->q_max != nullptr)) {
+      err = "q_min and q_max go together";
+      return PF_ERR_INVALID;
+    }
+    if (d->q_min) {
+      c.q_min.assign(d->q_min, d->q_min + n);
+      c.q_max.assign(d->q_max, d->q_max + n);
+      for (int i = 0; i < n; ++i)
+        if (std::isnan(c.q_min[i]) || std::isnan(c.q_max[i]) || c.q_min[i] > c.q_max[i]) {
+          msg << "bus " << i << " has reactive limits that are not an interval";
+          err = msg.str();
+          return PF_ERR_INVALID;
+        }
+    }
     for (int i = 0; i < n; ++i)
       if (c.bus_type[i] != PF_PQ && !(c.v_set[i] > 0.0)) {
         msg << "bus " << i << " needs a positive |V| set point";

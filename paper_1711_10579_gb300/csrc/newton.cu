@@ -148,6 +148,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
             inf.mismatch = nrm;
             inf.max_step = it > 0 ? __longlong_as_double((long long)__ldcg(w.step + (size_t)((it - 1) & 1) * B + gs)) : 0.0;
             inf.solve_us = 0.0;
+            inf.q_switched = 0;
+            inf.q_rounds = 1;
             w.out_info[gs] = inf;
           }
           // the buffers of the next iteration (read last one iteration ago)
@@ -189,6 +191,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
             inf.mismatch = __longlong_as_double((long long)__ldcg(w.norm + (size_t)(it & 1) * B + gs));
             inf.max_step = 0.0;
             inf.solve_us = 0.0;
+            inf.q_switched = 0;
+            inf.q_rounds = 1;
             w.out_info[gs] = inf;
           }
         }

@@ -119,8 +119,7 @@ struct Server {
     if (!c->warm_valid) o.warm_start = 0;
     // served solves run on 8-CTA clusters so that every slot fits on the GPU
     if (!o.cluster_size) o.cluster_size = 8;
-    rc = run_solve(c, o, 1, d_in[0], d_in[1], d_in[2], &ws, s.st, RunMode::Solve, nullptr,
-                   nullptr);
+    rc = run_solve_q(c, o, 1, d_in[0], d_in[1], d_in[2], &ws, s.st, nullptr, nullptr, nullptr);
     if (rc != PF_OK) return rc;
     cudaError_t e = cudaMemcpyAsync(s.h_out, ws.st_vm, per * sizeof(double),
                                     cudaMemcpyDeviceToHost, s.st);

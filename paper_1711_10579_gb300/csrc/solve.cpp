@@ -37,6 +37,8 @@ int check_opts(const pf_opts& o) {
     return set_error(PF_ERR_INVALID, "opts.nk_fallback must be 0 or 1");
   if (o.krylov != 0 && o.krylov != 1)
     return set_error(PF_ERR_INVALID, "opts.krylov must be 0 (GMRES) or 1 (BiCGSTAB)");
+  if (o.q_limits != 0 && o.q_limits != 1)
+    return set_error(PF_ERR_INVALID, "opts.q_limits must be 0 or 1");
   if (o.method == PF_NK && o.krylov == 1 && o.gmres_restart < 7)
     return set_error(PF_ERR_INVALID, "BiCGSTAB needs opts.gmres_restart >= 7 (work vectors)");
   if (o.method == PF_NK) {
@@ -108,7 +110,8 @@ void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int*
 
 int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const double* d_q_load,
               const double* d_p_gen, Workspace* ws, cudaStream_t st, RunMode mode, double* out_vm,
-              double* out_va, pf_info* out_info, unsigned long long* prof) {
+              double* out_va, pf_info* out_info, unsigned long long* prof, const double* d_vm0,
+              const double* d_va0, bool qlim) {
   int rc = check_opts(o);
   if (rc != PF_OK) return rc;
   const bool nk = o.method == PF_NK;
@@ -154,7 +157,12 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
     w.in_vm = ws->st_p_load;  // staged start voltage of an inspection call
     w.in_va = ws->st_q_load;
     w.in_p_load = w.in_q_load = w.in_p_gen = nullptr;
+  } else if (d_vm0) {
+    w.in_vm = d_vm0;  // the rounds of reactive limits restart from the last voltages
+    w.in_va = d_va0;
+    w.warm_in = 0;
   }
+  if (!qlim || mode != RunMode::Solve) w.bt = nullptr;
   DevOpts d;
   d.tol = o.tol;
   d.max_iter = o.max_iter;
@@ -201,6 +209,55 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   }
   cudaError_t e = launch_newton(bs, fp32, nk, sys, w, d, grid, cluster, threads, st);
   if (e != cudaSuccess) return cuda_error(e, "launching the Newton kernel");
+  return PF_OK;
+}
+
+// Reactive limits of PV buses: rounds of solves.  Each round solves every
+// scenario (the first from the usual start, the later ones from the last
+// voltages, so that a scenario with nothing switched stops at once), then
+// one check switches every PV bus whose generator Q is outside its limits
+// to PQ at that limit, in that scenario only.  The rounds end when a check
+// switches nothing; a bus switches at most once, so at most nPV + 1 rounds
+// are needed (capped at 64).
+int run_solve_q(pf_case c, const pf_opts& o, int B, const double* d_p_load, const double* d_q_load,
+                const double* d_p_gen, Workspace* ws, cudaStream_t st, double* out_vm,
+                double* out_va, pf_info* out_info) {
+  const CaseData& cd = c->data;
+  if (!o.q_limits || cd.kind != PF_SINGLE_PHASE || cd.q_max.empty())
+    return run_solve(c, o, B, d_p_load, d_q_load, d_p_gen, ws, st, RunMode::Solve, out_vm,
+                     out_va, out_info);
+  int rc = check_opts(o);
+  if (rc != PF_OK) return rc;
+  const bool nk = o.method == PF_NK;
+  rc = ws->ensure(cd.kind, cd.n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), B,
+                  nk ? o.gmres_restart : 0);
+  if (rc != PF_OK) return rc;
+  double* vm = out_vm ? out_vm : ws->st_vm;
+  double* va = out_va ? out_va : ws->st_va;
+  pf_info* info = out_info ? out_info : ws->st_info;
+  const DevSys& sys = (nk ? c->nk : c->nr).view;
+  DevWork w = ws->w;
+  w.B = B;
+  int npv = 0;
+  for (int8_t t : cd.bus_type) npv += (t == PF_PV);
+  const int cap = std::min(npv + 1, 64);
+  cudaError_t e = launch_qlim_init(sys, w, st);
+  if (e != cudaSuccess) return cuda_error(e, "launching the reactive-limit set-up");
+  int round = 0, pending = 0;
+  for (;;) {
+    ++round;
+    rc = run_solve(c, o, B, d_p_load, d_q_load, d_p_gen, ws, st, RunMode::Solve, vm, va, info,
+                   nullptr, round > 1 ? vm : nullptr, round > 1 ? va : nullptr, true);
+    if (rc != PF_OK) return rc;
+    e = cudaMemsetAsync(w.nsw, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_qlim_check(sys, w, info, round, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&pending, w.nsw, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "checking reactive limits");
+    if (pending == 0 || round >= cap) break;
+  }
+  e = launch_qlim_final(w, info, round, pending > 0 ? 1 : 0, st);
+  if (e != cudaSuccess) return cuda_error(e, "launching the reactive-limit summary");
   return PF_OK;
 }
 

@@ -39,7 +39,8 @@ class pf_case_desc(C.Structure):
                 ("p_load", _dp), ("q_load", _dp), ("zip", _dp),
                 ("br_from", _ip), ("br_to", _ip), ("br_r", _dp), ("br_x", _dp),
                 ("br_b", _dp), ("phases", _u8p), ("source", C.c_int),
-                ("v_source", C.c_double), ("br_phases", _u8p), ("br_z", _dp)]
+                ("v_source", C.c_double), ("br_phases", _u8p), ("br_z", _dp),
+                ("q_min", _dp), ("q_max", _dp)]
 
 
 class pf_opts(C.Structure):
@@ -50,14 +51,14 @@ class pf_opts(C.Structure):
                 ("gmres_rtol", C.c_double), ("warm_start", C.c_int),
                 ("cluster_size", C.c_int), ("block_threads", C.c_int),
                 ("scen_per_cta", C.c_int), ("nk_fallback", C.c_int),
-                ("kernel_by_kernel", C.c_int), ("krylov", C.c_int)]
+                ("kernel_by_kernel", C.c_int), ("krylov", C.c_int), ("q_limits", C.c_int)]
 
 
 class pf_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int),
                 ("linear_iterations", C.c_int), ("fallback", C.c_int),
                 ("mismatch", C.c_double), ("max_step", C.c_double),
-                ("solve_us", C.c_double)]
+                ("solve_us", C.c_double), ("q_switched", C.c_int), ("q_rounds", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,7 +79,8 @@ class pf_case_stats(C.Structure):
 INFO_DTYPE = np.dtype([("status", np.int32), ("iterations", np.int32),
                        ("linear_iterations", np.int32), ("fallback", np.int32),
                        ("mismatch", np.float64), ("max_step", np.float64),
-                       ("solve_us", np.float64)])
+                       ("solve_us", np.float64), ("q_switched", np.int32),
+                       ("q_rounds", np.int32)])
 assert INFO_DTYPE.itemsize == C.sizeof(pf_info)
 
 _lib = None
@@ -196,6 +198,8 @@ def make_desc(case) -> _Desc:
         d.p_load, d.q_load, d.zip = f64(case.p_load), f64(case.q_load), f64(case.zip)
         d.br_from, d.br_to = i32(case.br_from), i32(case.br_to)
         d.br_r, d.br_x, d.br_b = f64(case.br_r), f64(case.br_x), f64(case.br_b)
+        if case.q_max is not None:  # reactive limits of PV buses
+            d.q_min, d.q_max = f64(case.q_min), f64(case.q_max)
     elif isinstance(case, _cases.ThreePhaseCase):
         d.kind, d.n_bus, d.n_branch = PF_THREE_PHASE, case.n_node, case.n_branch
         d.phases = u8(case.phases)

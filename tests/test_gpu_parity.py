@@ -698,3 +698,111 @@ def test_three_phase_pv_two_node_closed_form(pf, ctx):
         assert np.max(np.abs(np.angle(np.exp(1j * (va[3:] - rot - d))))) <= 1e-9
     finally:
         pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# reactive limits of PV buses (rounds of PV -> PQ switching)
+# ----------------------------------------------------------------------------
+
+def _gpu_switched(case, vm):
+    """PV buses the GPU switched: a PV bus keeps |V| = v_set exactly (its |V|
+    is no unknown), a switched one does not."""
+    pv = case.bus_type == cases.PV
+    return pv & (vm != case.v_set)
+
+
+def _check_qlim(case, vm, va, info, ref):
+    assert info["status"] == 0, info
+    assert info["mismatch"] <= 1e-8
+    assert np.array_equal(_gpu_switched(case, vm), ref["switched"])
+    assert info["q_switched"] == int(ref["switched"].sum())
+    assert info["q_rounds"] == ref["rounds"]
+    assert np.max(np.abs(vm - ref["vm"])) <= V_TOL
+    assert np.max(np.abs(va - ref["va"])) <= A_TOL
+
+
+@pytest.mark.parametrize("method", ["nr", "nk"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name,seed", [("300", 1), ("2000", 2), ("10000", 1)])
+def test_q_limits_single_matches_oracle(pf, ctx, name, seed, prec, method):
+    base = {"300": cases.transmission_case(300, 405, 60, 2), "2000": cases.case_2000bus(0),
+            "10000": cases.case_10000bus(0)}[name]
+    case = cases.with_q_limits(base, seed)
+    ref = O.newton_polar_qlim(case)
+    assert ref["converged"] and ref["switched"].any()
+    c = pf.pf_create_case(ctx, case)
+    try:
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        m = pf.PF_NR if method == "nr" else pf.PF_NK
+        vm, va, info = pf.pf_solve(c, pf.make_opts(precision=p, method=m, q_limits=1,
+                                                   nk_fallback=0))
+        _check_qlim(case, vm, va, info, ref)
+        assert info["iterations"] >= ref["rounds"] - 1
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_q_limits_batch_matches_oracle(pf, ctx):
+    base = cases.case_2000bus(1)
+    case = cases.with_q_limits(base, 3)
+    B = 40
+    p_load, q_load, p_gen = cases.scenario_loads(case, B, seed=21)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        for opts in (pf.make_opts(q_limits=1), pf.make_opts(q_limits=1, kernel_by_kernel=1),
+                     pf.make_opts(q_limits=1, method=pf.PF_NK, nk_fallback=0)):
+            vm, va, info = pf.pf_solve_batch(c, p_load, q_load, p_gen, opts)
+            counts = set()
+            for b in (0, 7, 19, B - 1):
+                ref = O.newton_polar_qlim(case.with_loads(p_load[b], q_load[b], p_gen[b]))
+                assert ref["converged"]
+                _check_qlim(case, vm[b], va[b], info[b], ref)
+                counts.add(int(info[b]["q_switched"]))
+            assert np.all(info["status"] == 0)
+            # the rounds are per scenario: a scenario with nothing left to
+            # switch stops at once
+            assert len(counts) > 1 or max(counts) > 0
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_q_limits_two_bus_closed_form(pf, ctx):
+    """Two-bus PV past q_max becomes PQ at q_max: the PQ closed form."""
+    import dataclasses as dc
+    import math
+
+    pg, x, vset, pl, ql, qmax = 0.3, 0.1, 1.02, 0.1, 0.05, 0.15
+    case = cases.two_bus_case(pg, 0.0, 0.0, x, pv=True, v2=vset)
+    case = dc.replace(case, p_load=np.array([0.0, pl]), q_load=np.array([0.0, ql]),
+                      q_min=np.array([-9.0, -1.0]), q_max=np.array([9.0, qmax]))
+    # PQ closed form: u = |V2|^2 solves u^2 - (2 Q x + 1) u + (P^2 + Q^2) x^2 = 0
+    # for the net injection P + jQ through a lossless line x (larger root)
+    P, Q = pg - pl, qmax - ql
+    u = ((2 * Q * x + 1) + math.sqrt((2 * Q * x + 1) ** 2 - 4 * (P * P + Q * Q) * x * x)) / 2
+    v2 = math.sqrt(u)
+    d2 = math.asin(P * x / v2)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve(c, pf.make_opts(precision=pf.PF_FP64, q_limits=1, tol=1e-12))
+        assert info["status"] == 0 and info["q_switched"] == 1 and info["q_rounds"] == 2
+        assert abs(vm[1] - v2) < 1e-10 and abs(va[1] - d2) < 1e-10
+        vm0, _, info0 = pf.pf_solve(c, pf.make_opts(precision=pf.PF_FP64, tol=1e-12))
+        assert info0["q_switched"] == 0 and vm0[1] == vset
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_q_limits_wide_limits_change_nothing(pf, ctx):
+    base = cases.case_2000bus(0)
+    case = cases.with_q_limits(base, 1, q_range=(50.0, 60.0))
+    B = 16
+    p_load, q_load, p_gen = cases.scenario_loads(case, B, seed=4)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm0, va0, i0 = pf.pf_solve_batch(c, p_load, q_load, p_gen)
+        vm1, va1, i1 = pf.pf_solve_batch(c, p_load, q_load, p_gen, pf.make_opts(q_limits=1))
+        assert np.all(i1["q_switched"] == 0) and np.all(i1["q_rounds"] == 1)
+        assert np.array_equal(vm0, vm1) and np.array_equal(va0, va1)
+        assert np.array_equal(i0["iterations"], i1["iterations"])
+    finally:
+        pf.pf_destroy_case(c)

@@ -196,3 +196,32 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cpp", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"(import\s+oracle|from\s+oracle|pf_oracle)", src), f
+
+
+def test_reactive_limit_validation(pf):
+    import dataclasses as dc
+
+    base = cases.with_q_limits(cases.case_14bus(0), 1)
+    pf.pf_analyze(base)  # valid
+    qmin = base.q_min.copy()
+    qmin[3] = base.q_max[3] + 0.1
+    _invalid(pf, dc.replace(base, q_min=qmin), "not an interval")
+    qmin[3] = np.nan
+    _invalid(pf, dc.replace(base, q_min=qmin), "not an interval")
+    # infinite limits are an interval
+    pf.pf_analyze(dc.replace(base, q_min=np.full(base.n_bus, -np.inf),
+                             q_max=np.full(base.n_bus, np.inf)))
+    d = pf.make_desc(base)
+    d.desc.q_max = None  # one without the other
+    with pytest.raises(pf.PfError) as e:
+        st = pf.pf_case_stats()
+        pf._check(pf.lib().pf_analyze(pf.C.byref(d.desc), pf.C.byref(st)))
+    assert "go together" in str(e.value)
+
+
+def test_info_and_opts_layout(pf):
+    """The Python mirrors of pf_info / pf_opts end with the reactive-limit
+    fields, and the defaults leave the limits off."""
+    assert [f for f, _ in pf.pf_info._fields_][-2:] == ["q_switched", "q_rounds"]
+    assert pf.INFO_DTYPE.itemsize == pf.C.sizeof(pf.pf_info) == 48
+    assert pf.make_opts().q_limits == 0
