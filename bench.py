@@ -301,6 +301,18 @@ def variants(pf, ctx, torch, dev, flush):
             pf.make_opts(method=pf.PF_NK, krylov=1, precision=prec, gmres_max_iter=2000), reps=1)
     pf.pf_destroy_case(c)
 
+    # reactive limits of PV buses enforced (rounds of PV -> PQ switching)
+    qcase = cases.with_q_limits(case, 1)
+    c = pf.pf_create_case(ctx, qcase)
+    plq, qlq, pgq = _batch(qcase, 608, seed=21)
+    r = _device_solves(pf, c, torch, dev, 608, plq, qlq, pgq, pf.make_opts(q_limits=1), reps=3,
+                       flush=flush)
+    _, _, iq = pf.pf_solve_batch(c, plq, qlq, pgq, pf.make_opts(q_limits=1))
+    r["q_switched_mean"] = float(iq["q_switched"].mean())
+    r["q_rounds_max"] = int(iq["q_rounds"].max())
+    out["mesh10000_x608_batched_mixed_qlimits"] = r
+    pf.pf_destroy_case(c)
+
     case = cases.case_2000bus(0)
     c = pf.pf_create_case(ctx, case)
     pl, ql, pg = cases.scenario_loads(case, 512, seed=11)
