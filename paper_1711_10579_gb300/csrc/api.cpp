@@ -131,9 +131,13 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   std::vector<float> zip32(zip.size());
   for (size_t k = 0; k < zip.size(); ++k) zip32[k] = (float)zip[k];
   UP(zip32, zip32);
-  std::vector<double2> trig(2 * kTrigHalf + 1);
-  for (int j = -kTrigHalf; j <= kTrigHalf; ++j)
-    trig[j + kTrigHalf] = make_double2(std::cos(j * 0.0078125), std::sin(j * 0.0078125));
+  // cos and sin of j 2^-7 as 2^62 fixed point (long double on the host)
+  std::vector<long long> trig(2 * (2 * kTrigHalf + 1));
+  for (int j = -kTrigHalf; j <= kTrigHalf; ++j) {
+    const long double a = (long double)j / 128.0L;
+    trig[2 * (j + kTrigHalf)] = llroundl(cosl(a) * 4611686018427387904.0L);
+    trig[2 * (j + kTrigHalf) + 1] = llroundl(sinl(a) * 4611686018427387904.0L);
+  }
   UP(trig, trig);
   UP(s.lu_rowptr, lu_rowptr);
   UP(s.lu_col, lu_col);

@@ -14,7 +14,7 @@ constexpr int kPQLimit = 3;
 // Krylov basis vectors per GMRES cycle (restart m <= kMaxJ - 1).
 constexpr int kMaxJ = 64;
 // Half width of the sine / cosine table: angles j 2^-7 for |j| <= kTrigHalf.
-constexpr int kTrigHalf = 512;
+constexpr int kTrigHalf = 512;  // = fx::kHalf (fixtrig.h)
 // Size of the fixed scratch array used by pf_solve_noalloc.
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
 
@@ -28,7 +28,7 @@ struct DevSys {
   const int* y_col;
   const double* y_val;
   const float2* y32;  // single phase: FP32 copy of y_val for the Jacobian
-  const double2* trig;  // (cos jh, sin jh), h = 2^-7, j = -kTrigHalf..kTrigHalf
+  const long long* trig;  // (cos jh, sin jh) x 2^62, h = 2^-7, j = -kTrigHalf..kTrigHalf
   const float* zip32;   // single phase: FP32 copy of zip for the Jacobian
   // factor pattern (L, diagonal, U per row) and its maps
   const int* lu_rowptr;

@@ -13,6 +13,9 @@
 #include <mutex>
 
 #include "device.h"
+#include "fixtrig.h"
+
+static_assert(pf::kTrigHalf == pf::fx::kHalf, "one sine / cosine table size");
 
 namespace cg = cooperative_groups;
 
@@ -72,31 +75,11 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
 }
 
-// sin a and cos a in FP64 by table lookup and angle addition (the
-// table-driven method of P. T. P. Tang, 1990): a = j h + r with h = 2^-7,
-// (cos jh, sin jh) from a table built on the host for |j| <= kTrigHalf, and
-// |r| <= 2^-8, where the Taylor series sin r = r - r^3/6 + r^5/120 and
-// cos r = 1 - r^2/2 + r^4/24 are exact to FP64 rounding (the next terms are
-// below 1e-17).  About fifteen FP64 operations; outside the table's range it
-// uses sincos().
-__device__ __forceinline__ void sincos_tab(const double2* tab, double a, double* s, double* c) {
-  if (!(fabs(a) <= kTrigHalf * 0.0078125)) {
-    sincos(a, s, c);
-    return;
-  }
-  // j = nearest integer to 128 a: adding 1.5 * 2^52 rounds it into the low
-  // bits of the sum (no conversion instruction, which is slow in FP64)
-  const double big = a * 128.0 + 6755399441055744.0;
-  const int k = __double2loint(big);
-  const double j = big - 6755399441055744.0;
-  const double r = fma(j, -0.0078125, a);  // exact
-  const double r2 = r * r;
-  const double q = (r2 * (1.0 / 6.0)) * fma(r2, -0.05, 1.0);
-  const double sr = fma(-r, q, r);
-  const double cr = fma(-0.5 * r2, fma(r2, -1.0 / 12.0, 1.0), 1.0);
-  const double2 t = __ldg(tab + k + kTrigHalf);  // (cos jh, sin jh)
-  *c = fma(t.x, cr, -(t.y * sr));
-  *s = fma(t.y, cr, t.x * sr);
+// sin a and cos a: the table method in 64-bit fixed point on the integer
+// pipes (fixtrig.h; four FP64-free conversions and a dozen 64-bit integer
+// products), sincos() beyond |a| <= 4.
+__device__ __forceinline__ void sincos_tab(const long long* tab, double a, double* s, double* c) {
+  if (!fx::sincos_q(tab, a, s, c)) sincos(a, s, c);
 }
 
 template <bool CL>
