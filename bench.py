@@ -555,11 +555,14 @@ def main():
     step_bytes = algorithmic_bytes_per_iteration(st, B=B) * float(info["iterations"].sum()) / K
     # kernels per step: the call record, the graph's prologue (set-up,
     # mismatch, stop test), one loop body per Newton step of the slowest
-    # scenario (factor, sweeps, refinement residual + sweeps, update,
-    # mismatch, stop test), the results
+    # scenario (refinement flag, factor, sweeps, update, mismatch, stop
+    # test), the refinement launches (voltage change, residual, sweeps) of
+    # the steps where a scenario refines (at least the most any scenario
+    # took), the results
     refine = pf.make_opts().refine_steps
     loops = info["iterations"].reshape(K, B).max(1)
-    launches = int(sum(5 + int(L) * (5 + 3 * refine) for L in loops))
+    refs = (info["linear_iterations"] - info["iterations"]).reshape(K, B).max(1)
+    launches = int(sum(5 + int(L) * 6 + 3 * refine * int(R) for L, R in zip(loops, refs)))
     # end to end through the host-buffer entry point: inputs and results in
     # pinned host memory, their copies inside the timed call
     def pinned(shape, dtype=torch.float64):

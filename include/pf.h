@@ -162,6 +162,12 @@ typedef struct {
                          for PV and PQ buses, so no symbolic step is repeated.
                          The call waits for the device between rounds.
                          Default 0 (limits ignored) */
+  double refine_stall; /* NR + PF_MIXED: the FP64 refinement of a step is taken
+                          only where the FP32 factors hold convergence back:
+                          the mismatch is <= refine_below and the last Newton
+                          step cut it by less than 1 / refine_stall (norm_k >
+                          refine_stall x norm_(k-1)).  0 = whenever the
+                          mismatch is <= refine_below.  Default 0.1 */
 } pf_opts;
 
 typedef struct {

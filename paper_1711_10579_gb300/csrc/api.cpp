@@ -266,7 +266,7 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
   t += (size_t)nnz_lu * B * bs * bs * 8;                // lu
   t += nb * bs * bs * 8;                                // uinv
   t += nb * bs * 8;                                     // y
-  t += (size_t)B * (2 * 8 + 2 * 8 + 4 + 12) + 8 + 64;   // norm, step, flag, status, t0, call
+  t += (size_t)B * (2 * 8 + 2 * 8 + 4 + 12) + 16 + 64;  // norm, step, flag, status, t0, call
   t += 3 * nb * nsl * 8;                                // staged inputs
   t += 2 * nb * nsl * 8 + (size_t)B * sizeof(pf_info);  // staged outputs
   if (kind == PF_SINGLE_PHASE)                          // reactive-limit rounds
@@ -328,6 +328,7 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
   A((void**)&w.refine, (size_t)B * 4);
   A((void**)&w.iter, (size_t)B * 4);
   A((void**)&w.t0, 8);
+  A((void**)&w.anyref, 8);
   A((void**)&w.call, sizeof(CallArgs));
   A((void**)&st_p_load, nb * nsl * 8);
   A((void**)&st_q_load, nb * nsl * 8);
@@ -415,6 +416,7 @@ void pf_opts_default(pf_opts* o) {
   o->max_iter = 30;
   o->refine_steps = 1;
   o->refine_below = 1e-3;
+  o->refine_stall = 0.1;
   o->gmres_restart = 30;
   o->gmres_max_iter = 300;
   o->gmres_rtol = 1e-6;

@@ -44,7 +44,7 @@ struct SysBuf {
 struct BatchGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::array<long long, 16> key{};
+  std::array<long long, 17> key{};
   BatchGraph() = default;
   BatchGraph(const BatchGraph&) {}  // a copy starts empty
   BatchGraph& operator=(const BatchGraph&) {

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kRowThreads) k_mismatch(DevSys S, DevWork w, i
 __global__ void __launch_bounds__(1024) k_stop(DevWork w, DevOpts o, int has_cond,
                                                cudaGraphConditionalHandle cond) {
   const int B = w.B;
-  int running = 0;
+  int running = 0, refining = 0;
   for (int gs = threadIdx.x; gs < B; gs += blockDim.x) {
     if (w.status[gs] != kRunning) continue;
     const int it = w.iter[gs];
@@ -188,7 +188,13 @@ __global__ void __launch_bounds__(1024) k_stop(DevWork w, DevOpts o, int has_con
     w.status[gs] = st;
     int rf = w.refine[gs] & ~1;  // refinement count << 1
     if (st == kRunning) {
-      if (o.refine > 0 && nrm <= o.refine_below) rf += 3;  // flag, and one more
+      // the previous iteration's norm (its buffer is cleared below)
+      const double prev =
+          __longlong_as_double((long long)__ldcg(w.norm + (size_t)((it + 1) & 1) * B + gs));
+      if (o.refine > 0 && refine_now(o, it, nrm, prev)) {
+        rf += 3;  // flag, and one more
+        refining = 1;
+      }
       w.refine[gs] = rf;
       w.iter[gs] = it + 1;
       ++running;
@@ -205,7 +211,14 @@ __global__ void __launch_bounds__(1024) k_stop(DevWork w, DevOpts o, int has_con
     w.step[(size_t)((it + 1) & 1) * B + gs] = 0ull;
   }
   running = __syncthreads_or(running);
+  refining = __syncthreads_or(refining);
+  if (threadIdx.x == 0) *w.anyref = refining;
   if (has_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, running ? 1u : 0u);
+}
+
+// Inside a graph: whether this iteration's refinement launches run at all.
+__global__ void k_rflag(const int* anyref, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, *anyref ? 1u : 0u);
 }
 
 // The team of one level-synchronous CTA: scenarios [blockIdx.x S, + S),
@@ -372,8 +385,10 @@ struct Plan {
   DevWork w;
   DevOpts of, os;
   int sb, pass0 = 0, pass1 = 1, has_cond = 0;
-  cudaGraphConditionalHandle cond = 0;
-  std::vector<Launch> pro, body, epi;
+  cudaGraphConditionalHandle cond = 0, rcond = 0;
+  const int* anyref = nullptr;
+  // the loop body: pre, refinement, post (body = all three, in order)
+  std::vector<Launch> pro, body, pre, ref, post, epi;
   dim3 rows, blk;
   int threads_f, threads_s;
   size_t red, ring;
@@ -402,19 +417,20 @@ struct Plan {
       output = rowk((const void*)k_output<BS>);
     }
     pro = {setup, rowk((const void*)k_mismatch<BS, TF>), stop};
-    body.clear();
-    body.push_back(Launch{(const void*)k_factor<BS, TF>, gf, dim3(threads_f), ring, {&S, &w, &of}});
-    body.push_back(
-        Launch{(const void*)k_solve<BS, TF>, gsv, dim3(threads_s), red, {&S, &w, &os, &pass0}});
+    pre = {Launch{(const void*)k_factor<BS, TF>, gf, dim3(threads_f), ring, {&S, &w, &of}},
+           Launch{(const void*)k_solve<BS, TF>, gsv, dim3(threads_s), red, {&S, &w, &os, &pass0}}};
+    ref.clear();
     for (int p = 0; p < refine; ++p) {
-      body.push_back(rowk((const void*)k_dv<BS>));
-      body.push_back(rowk((const void*)k_resid<BS>));
-      body.push_back(
+      ref.push_back(rowk((const void*)k_dv<BS>));
+      ref.push_back(rowk((const void*)k_resid<BS>));
+      ref.push_back(
           Launch{(const void*)k_solve<BS, TF>, gsv, dim3(threads_s), red, {&S, &w, &os, &pass1}});
     }
-    body.push_back(rowk((const void*)k_update<BS>));
-    body.push_back(rowk((const void*)k_mismatch<BS, TF>));
-    body.push_back(stop);
+    post = {rowk((const void*)k_update<BS>), rowk((const void*)k_mismatch<BS, TF>), stop};
+    body = pre;
+    body.insert(body.end(), ref.begin(), ref.end());
+    body.insert(body.end(), post.begin(), post.end());
+    anyref = w.anyref;
     epi = {output};
   }
 };
@@ -519,12 +535,13 @@ static cudaError_t add_chain(cudaGraph_t g, const std::vector<Launch>& ls, cudaG
 template <int BS, typename TF>
 cudaError_t run_graph(Plan<BS, TF>& p, cudaStream_t st, BatchGraph* g, int refine) {
   const DevOpts& o = p.of;
-  std::array<long long, 16> key = {
+  std::array<long long, 17> key = {
       (long long)(uintptr_t)p.w.spec, (long long)(uintptr_t)p.S.lu_col, p.w.B, BS,
       (long long)sizeof(TF), o.S, p.threads_f, p.os.S, p.threads_s, o.max_iter, refine, o.ring,
-      (long long)(uintptr_t)p.S.g_fwd, 0, 0, (long long)(uintptr_t)p.w.bt};
+      (long long)(uintptr_t)p.S.g_fwd, 0, 0, (long long)(uintptr_t)p.w.bt, 0};
   std::memcpy(&key[13], &o.tol, 8);
   std::memcpy(&key[14], &o.refine_below, 8);
+  std::memcpy(&key[16], &o.refine_stall, 8);
   if (!g->exec || g->key != key) {
     g->reset();
     cudaError_t e = cudaGraphCreate(&g->graph, 0);
@@ -543,8 +560,35 @@ cudaError_t run_graph(Plan<BS, TF>& p, cudaStream_t st, BatchGraph* g, int refin
     cudaGraphNode_t loop;
     e = cudaGraphAddNode(&loop, g->graph, &dep, nullptr, 1, &cp);
     if (e != cudaSuccess) return e;
+    cudaGraph_t bg = cp.conditional.phGraph_out[0];
     cudaGraphNode_t bdep = nullptr;
-    e = add_chain(cp.conditional.phGraph_out[0], p.body, &bdep);
+    // the refinement launches sit in an IF node, skipped in the iterations
+    // where no scenario refines (its flag is set inside the body)
+    const bool nested =
+        !p.ref.empty() && cudaGraphConditionalHandleCreate(&p.rcond, bg, 0, 0) == cudaSuccess;
+    cudaGetLastError();
+    if (nested) {
+      std::vector<Launch> flag = {
+          Launch{(const void*)k_rflag, dim3(1), dim3(1), 0, {&p.anyref, &p.rcond}}};
+      e = add_chain(bg, flag, &bdep);
+      if (e == cudaSuccess) e = add_chain(bg, p.pre, &bdep);
+      if (e != cudaSuccess) return e;
+      cudaGraphNodeParams ip = {};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = p.rcond;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t ifn;
+      e = cudaGraphAddNode(&ifn, bg, &bdep, nullptr, 1, &ip);
+      if (e != cudaSuccess) return e;
+      cudaGraphNode_t rdep = nullptr;
+      e = add_chain(ip.conditional.phGraph_out[0], p.ref, &rdep);
+      if (e != cudaSuccess) return e;
+      bdep = ifn;
+      e = add_chain(bg, p.post, &bdep);
+    } else {
+      e = add_chain(bg, p.body, &bdep);
+    }
     if (e != cudaSuccess) return e;
     dep = loop;
     e = add_chain(g->graph, p.epi, &dep);

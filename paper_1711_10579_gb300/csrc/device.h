@@ -134,6 +134,7 @@ struct DevWork {
   int* refine;               // [B] this iteration takes the FP64 refinement
   int* iter;                 // [B] index of the scenario's latest mismatch
   unsigned long long* t0;    // start time of the launch sequence (ns)
+  int* anyref;               // the last stop test left a scenario refining
   struct CallArgs* call;     // this call's inputs and outputs
   // reactive limits of PV buses (single phase; null when not enforced)
   int8_t* bt;                // [row][B] bus type of the scenario (kPQLimit:
@@ -165,6 +166,7 @@ struct DevOpts {
   int max_iter;
   int refine;   // FP64 refinement steps (mixed NR)
   double refine_below;  // ... taken once the mismatch norm is at most this
+  double refine_stall;  // ... and the last step cut it by less than 1 / this (0: always)
   int S;        // scenarios per cluster
   int mode;     // 0 solve, 1 evaluate mismatch + Jacobian, 2 one Newton step
   unsigned long long* prof;  // optional per-phase device time (ns), kProfPhases

@@ -82,6 +82,15 @@ __device__ __forceinline__ void sincos_tab(const long long* tab, double a, doubl
   if (!fx::sincos_q(tab, a, s, c)) sincos(a, s, c);
 }
 
+// The FP64 refinement of a mixed-precision Newton-Raphson step is taken
+// where the FP32 factors hold convergence back: the mismatch norm is at
+// most refine_below and (refine_stall > 0) the last step cut it by less
+// than 1 / refine_stall.
+__device__ __forceinline__ bool refine_now(const DevOpts& o, int it, double nrm, double prev) {
+  if (!(nrm <= o.refine_below)) return false;
+  return o.refine_stall <= 0.0 || it == 0 || !(prev > 0.0) || nrm > o.refine_stall * prev;
+}
+
 template <bool CL>
 __device__ __forceinline__ void csync() {
   if constexpr (CL) {

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
   __shared__ TF sh_rho[32], sh_rho0[32], sh_alpha[32], sh_omega[32];  // BiCGSTAB
   __shared__ unsigned sh_sdone;
   __shared__ int sh_status[32];
+  __shared__ double sh_prev[32];  // mismatch norm of the previous iteration
   __shared__ unsigned sh_act;
   __shared__ int sh_refine;
   __shared__ unsigned long long sh_t0;
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
     for (int s = 0; s < 32; ++s) {
       sh_status[s] = kRunning;
       sh_lin[s] = 0;
+      sh_prev[s] = 0.0;
     }
     sh_act = (tm.ns >= 32) ? 0xffffffffu : ((1u << tm.ns) - 1u);
   }
@@ -137,7 +139,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
         else if (o.mode == 0 && it >= o.max_iter) st = PF_ERR_MAXITER;
         sh_status[s] = st;
         if (st == kRunning) act |= 1u << s;
-        if (st == kRunning && nrm <= o.refine_below) refine = 1;
+        if (st == kRunning && refine_now(o, it, nrm, sh_prev[s])) refine = 1;
+        sh_prev[s] = nrm;
         if (crank == 0) {
           if (st != kRunning && w.out_info) {
             pf_info inf;

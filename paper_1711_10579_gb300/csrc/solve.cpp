@@ -23,6 +23,8 @@ int check_opts(const pf_opts& o) {
     return set_error(PF_ERR_INVALID, "opts.max_iter must be in [0, 1000]");
   if (!(o.refine_below >= 0.0))
     return set_error(PF_ERR_INVALID, "opts.refine_below must be >= 0");
+  if (!(o.refine_stall >= 0.0))
+    return set_error(PF_ERR_INVALID, "opts.refine_stall must be >= 0");
   if (o.refine_steps < 0 || o.refine_steps > 10)
     return set_error(PF_ERR_INVALID, "opts.refine_steps must be in [0, 10]");
   if (o.cluster_size < 0 || o.cluster_size > 16 || (o.cluster_size & (o.cluster_size - 1)))
@@ -168,6 +170,7 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   d.max_iter = o.max_iter;
   d.refine = fp32 && o.method == PF_NR ? o.refine_steps : 0;
   d.refine_below = o.refine_below;
+  d.refine_stall = o.refine_stall;
   d.S = S;
   d.mode = mode == RunMode::Solve ? 0 : (mode == RunMode::Eval ? 1 : 2);
   d.prof = prof;
@@ -475,6 +478,7 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   d.max_iter = o.max_iter;
   d.refine = fp32 ? o.refine_steps : 0;
   d.refine_below = o.refine_below;
+  d.refine_stall = o.refine_stall;
   d.S = 1;
   d.mode = 0;
   d.prof = nullptr;

@@ -51,7 +51,8 @@ class pf_opts(C.Structure):
                 ("gmres_rtol", C.c_double), ("warm_start", C.c_int),
                 ("cluster_size", C.c_int), ("block_threads", C.c_int),
                 ("scen_per_cta", C.c_int), ("nk_fallback", C.c_int),
-                ("kernel_by_kernel", C.c_int), ("krylov", C.c_int), ("q_limits", C.c_int)]
+                ("kernel_by_kernel", C.c_int), ("krylov", C.c_int), ("q_limits", C.c_int),
+                ("refine_stall", C.c_double)]
 
 
 class pf_info(C.Structure):

@@ -806,3 +806,39 @@ def test_q_limits_wide_limits_change_nothing(pf, ctx):
         assert np.array_equal(i0["iterations"], i1["iterations"])
     finally:
         pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# FP64 refinement on demand (mixed Newton-Raphson)
+# ----------------------------------------------------------------------------
+
+def test_refinement_on_demand(pf, ctx):
+    """refine_stall = 0 refines every step below refine_below; a tiny
+    refine_stall refines the same steps (any reduction counts as a stall);
+    the default refines only steps that cut the mismatch by less than 10x.
+    All reach the oracle's solution."""
+    case = cases.case_2000bus(3)
+    ref = O.newton_polar(case)
+    B = 24
+    p_load, q_load, p_gen = cases.scenario_loads(case, B, seed=31)
+    refs = [O.newton_polar(case.with_loads(p_load[b], q_load[b], p_gen[b])) for b in (0, B - 1)]
+    c = pf.pf_create_case(ctx, case)
+    try:
+        res = {}
+        for name, rs in (("always", 0.0), ("tiny", 1e-12), ("default", None)):
+            o = pf.make_opts() if rs is None else pf.make_opts(refine_stall=rs)
+            vm, va, info = pf.pf_solve(c, o)
+            _check_solve(case, vm, va, info, ref)
+            vmb, vab, ib = pf.pf_solve_batch(c, p_load, q_load, p_gen, o)
+            assert np.all(ib["status"] == 0)
+            for k, b in enumerate((0, B - 1)):
+                _check_solve(case, vmb[b], vab[b], ib[b], refs[k])
+            res[name] = (info, ib)
+        # refinement passes are the linear iterations beyond one per step
+        extra = lambda i: np.asarray(i["linear_iterations"]) - np.asarray(i["iterations"])
+        assert np.all(extra(res["always"][1]) > 0)
+        assert np.array_equal(extra(res["always"][1]), extra(res["tiny"][1]))
+        assert np.all(extra(res["default"][1]) <= extra(res["always"][1]))
+        assert pf.make_opts().refine_stall == 0.1
+    finally:
+        pf.pf_destroy_case(c)
