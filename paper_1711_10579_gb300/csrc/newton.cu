@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
   __shared__ unsigned sh_inner;
   __shared__ TF sh_bnorm[32], sh_eta[32], sh_hk1[32];
   __shared__ TF sh_rho[32], sh_rho0[32], sh_alpha[32], sh_omega[32];  // BiCGSTAB
-  __shared__ unsigned sh_sdone;
+  __shared__ unsigned sh_sdone, sh_restart;
   __shared__ int sh_status[32];
   __shared__ double sh_prev[32];  // mismatch norm of the previous iteration
   __shared__ unsigned sh_act;
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
             });
           }
           if (threadIdx.x == 0) {
-            unsigned nxt = 0;
+            unsigned nxt = 0, rst = 0;
             for (int t = 0; t < tm.ns; ++t) {
               if (!((inner >> t) & 1u)) continue;
               sh_lin[t] += 1;
@@ -440,13 +440,38 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
               sh_rho0[t] = sh_rho[t];
               sh_rho[t] = rho;
               if (!(res <= sh_eta[t] * sh_bnorm[t]) && sh_lin_step[t] < o.max_lin &&
-                  rho != TF(0) && sh_omega[t] != TF(0))
+                  res > TF(0) && sh_omega[t] != TF(0)) {
                 nxt |= 1u << t;
+                // near breakdown, (r_hat, r) << |r_hat| |r| (r_hat = F, |F| =
+                // bnorm; 1e-5 in FP32, 1e-10 in FP64): restart from the
+                // current x with r_hat = r
+                const TF brk = sizeof(TF) == 4 ? TF(1e-5) : TF(1e-10);
+                if (!(fabs(rho) > brk * sh_bnorm[t] * res)) {
+                  rst |= 1u << t;
+                  sh_rho[t] = res * res;
+                  sh_rho0[t] = TF(1);
+                  sh_alpha[t] = TF(1);
+                  sh_omega[t] = TF(1);
+                }
+              }
             }
             sh_inner = nxt;
+            sh_restart = rst;
           }
           __syncthreads();
           inner = sh_inner;
+          if (sh_restart != 0) {
+            const unsigned rst = sh_restart;
+            if (slot_on(rst))
+              for (int i = first; i < n; i += stride)
+                for (int c = 0; c < BS; ++c) {
+                  const size_t q = q_of(i, c);
+                  RH[q] = R[q];
+                  P[q] = TF(0);
+                  VV[q] = TF(0);
+                }
+            csync<CL>();
+          }
         }
       } else
       for (int restart = 0;; ++restart) {
