@@ -20,6 +20,8 @@ What it computes, in the paper's notation (arXiv 1711.10579):
 * ``newton_cim``         three-phase current-injection Newton (Sec. II.B box),
                          with PV nodes through ``cim_pv_system`` (augmented
                          with reactive injections and |V| equations).
+* ``newton_cim_qlim``    the same with the reactive limits of PV phase slots
+                         enforced by rounds of switching.
 * ``ilu0`` / ``gmres``   ILU(0) and restarted, right-preconditioned GMRES used
                          by the Newton-Krylov variant (Sec. III.B).
 * ``bicgstab``           right-preconditioned BiCGSTAB, the Krylov method the
@@ -46,10 +48,10 @@ design notes):
   source node carry no unknowns; the source is an ideal balanced source;
   loads are wye-connected; a PV node (deferred by Sec. II.B) injects a given
   P and a free Q per phase and holds |V| = v_set on every phase present;
-* reactive limits of PV buses (single phase): after a converged solve every
-  PV bus whose generator Q is outside [q_min, q_max] becomes PQ at that
-  limit and the solve is repeated from the last voltages, until no bus
-  violates; switched buses stay PQ;
+* reactive limits of PV buses: after a converged solve every PV bus (three
+  phase: every PV phase slot) whose generator Q is outside [q_min, q_max]
+  is held at that limit (|V| free) and the solve is repeated from the last
+  voltages, until nothing violates; a held bus or slot stays held;
 * the diagonal adjustments a, b, c, d of Eq. 23 are the derivatives of the
   specified current (Eq. 17) with respect to the real and imaginary voltage,
   so that J is the exact Jacobian of Y V - I_sp in the ordering of Eq. 19-20;
@@ -699,6 +701,48 @@ def newton_cim(case, tol=1e-8, max_iter=30, linear="splu", V0=None,
                 steps=steps, converged=converged)
 
 
+def newton_cim_qlim(case, tol=1e-8, max_iter=30, linear="splu", max_rounds=50,
+                    gmres_restart=30, gmres_tol=1e-10):
+    """Three-phase Newton with the reactive limits [q_min, q_max] of every
+    PV phase slot enforced by switching, the rounds of newton_polar_qlim per
+    slot: after a converged solve every PV slot whose reactive injection Q_g
+    is outside its limits is held at the limit it crossed (a given
+    injection, |V| free) and the solve repeats from the last voltages; stop
+    after a round with no violation.  Returns newton_cim's dict with the
+    iterations summed, ``switched`` (bool [3 n]) and ``rounds``."""
+    Y = ybus_three_phase(case)
+    n = case.n_node
+    V = cim_flat_start(case)
+    pv = cim_pv_slots(case)
+    switched = np.zeros(3 * n, dtype=bool)
+    Qg = np.zeros(3 * n)
+    total = 0
+    rounds = 0
+    while True:
+        rounds += 1
+        res = _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol,
+                             switched, Qg)
+        total += res["iterations"]
+        if not res["converged"] or case.q_max is None or rounds >= max_rounds:
+            break
+        qg = res["Qg"]
+        qmax = np.asarray(case.q_max, dtype=float).reshape(-1)
+        qmin = np.asarray(case.q_min, dtype=float).reshape(-1)
+        act = pv & ~switched
+        hi = act & (qg > qmax)
+        lo = act & (qg < qmin)
+        if not (hi | lo).any():
+            break
+        Qg = qg.copy()
+        Qg[hi] = qmax[hi]
+        Qg[lo] = qmin[lo]
+        switched |= hi | lo
+        V = res["V"]
+    res = dict(res)
+    res.update(iterations=total, switched=switched, rounds=rounds)
+    return res
+
+
 # ---------------------------------------------------------------------------
 # branch flows (Sec. I problem statement: voltages and branch power flows)
 # ---------------------------------------------------------------------------
@@ -743,7 +787,7 @@ def branch_flows(case, vm, va):
     return Sf.real, Sf.imag, St.real, St.imag, (loss.real, loss.imag)
 
 
-def cim_pv_system(case, Y, V, Qg):
+def cim_pv_system(case, Y, V, Qg, switched=None):
     """Right-hand side and Jacobian of the augmented CIM system with PV slots.
     Unknowns: the CIM unknowns (cim_unknowns order) then Q_g of every PV slot
     (cim_pv_slots order).  Equations: the current mismatch rows, then
@@ -751,9 +795,14 @@ def cim_pv_system(case, Y, V, Qg):
     G = [Y V - I_sp, |V|^2 - v_set^2] and Fa = -G, so that Ja dx = Fa is the
     Newton step.  The Q_g column of the current rows is
     d(Y V - I_sp)/dQ_g = j V / |V|^2 (I_sp = conj(S_sp) V / |V|^2 with S_sp
-    containing j Q_g); the magnitude row is (2 Re V, 2 Im V)."""
+    containing j Q_g); the magnitude row is (2 Re V, 2 Im V).  Slots in
+    ``switched`` (held at a reactive limit) keep their Q_g as a given
+    injection and have neither unknown nor magnitude equation."""
     idx = cim_unknowns(case)
-    pvs = np.flatnonzero(cim_pv_slots(case))
+    act = cim_pv_slots(case)
+    if switched is not None:
+        act = act & ~switched
+    pvs = np.flatnonzero(act)
     npv = pvs.size
     vset = np.repeat(np.asarray(case.v_set, dtype=float), 3)
     pos = {int(k): p for p, k in enumerate(idx)}
@@ -775,7 +824,8 @@ def cim_pv_system(case, Y, V, Qg):
     return np.concatenate([F, -cons]), Ja
 
 
-def _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol):
+def _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol,
+                   switched=None, Qg0=None):
     """CIM Newton with PV nodes, augmented form: the reactive injection Q_g of
     every PV slot is an extra unknown and |V|^2 = v_set^2 an extra equation
     per PV slot (linearised: 2 Vr dVr + 2 Vi dVi = v_set^2 - |V|^2).  The
@@ -784,9 +834,11 @@ def _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol):
     puts PV slots at v_set on the flat-start angles with Q_g = 0."""
     n = case.n_node
     pv = cim_pv_slots(case)
+    if switched is not None:
+        pv = pv & ~switched
     vset = np.repeat(np.asarray(case.v_set, dtype=float), 3)
     V = np.where(pv, V / np.where(np.abs(V) > 0, np.abs(V), 1.0) * vset, V)
-    Qg = np.zeros(3 * n)
+    Qg = np.zeros(3 * n) if Qg0 is None else np.array(Qg0, dtype=float)
     idx = cim_unknowns(case)
     pvs = np.flatnonzero(pv)
     npv = pvs.size
@@ -807,7 +859,7 @@ def _newton_cim_pv(case, Y, V, tol, max_iter, linear, gmres_restart, gmres_tol):
         if k >= max_iter:
             break
         k += 1
-        Fa, Ja = cim_pv_system(case, Y, V, Qg)
+        Fa, Ja = cim_pv_system(case, Y, V, Qg, switched)
         nu = idx.size
         dx = solve_linear(Ja, Fa, linear, gmres_restart, gmres_tol)
         full = np.zeros(6 * n)

@@ -117,6 +117,8 @@ class ThreePhaseCase:
     node_type: np.ndarray | None = None  # int32 [n]: 1 PV, 2 PQ; None = all PQ
     v_set: np.ndarray | None = None  # float64 [n]: |V| of a PV node's phases
     p_gen: np.ndarray | None = None  # float64 [n, 3]: P injected per phase
+    q_min: np.ndarray | None = None  # float64 [n, 3]: reactive limits of PV
+    q_max: np.ndarray | None = None  # nodes' phases (pu); None = no limits
 
     @property
     def n_branch(self) -> int:
@@ -450,6 +452,19 @@ def with_q_limits(case: SinglePhaseCase, seed: int, q_range=(0.5, 3.0)) -> Singl
     rng = np.random.default_rng(seed)
     qmax = rng.uniform(q_range[0], q_range[1], case.n_bus)
     qmin = -rng.uniform(q_range[0], q_range[1], case.n_bus)
+    return dataclasses.replace(case, q_min=qmin, q_max=qmax, name=case.name + "_qlim")
+
+
+def with_phase_q_limits(case: ThreePhaseCase, seed: int, q_max_range=(0.01, 0.08),
+                        q_min_range=(0.0, 0.004)) -> ThreePhaseCase:
+    """The feeder with reactive limits on every phase slot (read at PV
+    nodes only), in units of the load scale x 20 (the scale of the PV
+    generation of with_pv_nodes): q_max ~ U[q_max_range], q_min ~
+    -U[q_min_range], drawn independently."""
+    rng = np.random.default_rng(seed)
+    unit = case.load_scale * 20.0
+    qmax = rng.uniform(q_max_range[0], q_max_range[1], (case.n_node, 3)) * unit
+    qmin = -rng.uniform(q_min_range[0], q_min_range[1], (case.n_node, 3)) * unit
     return dataclasses.replace(case, q_min=qmin, q_max=qmax, name=case.name + "_qlim")
 
 

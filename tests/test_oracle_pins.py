@@ -670,3 +670,61 @@ def test_cim_pv_augmented_jacobian_matches_central_differences(seed):
     # the Q_g columns are non-zero only in the PV node's own two rows
     qcols = Ja[:, idx.size:]
     assert np.all(np.count_nonzero(qcols, axis=0) <= 2)
+
+
+# three phase: reactive limits of PV phase slots (rounds of switching)
+
+@pytest.mark.parametrize("pg,x,vset,qmax", [(0.3, 0.1, 1.02, 0.1), (0.1, 0.2, 1.03, 0.05)])
+def test_cim_reactive_limit_two_node_closed_form(pg, x, vset, qmax):
+    """The lossless two-node line of the PV closed form with q_max below the
+    reactive injection that holds v_set: every phase is held at q_max, a
+    two-bus PQ problem with injection pg + j q_max per phase."""
+    import dataclasses as dc
+
+    case = _pv_line(x, pg, vset)
+    d = math.asin(pg * x / vset)
+    q_free = (vset * vset - vset * math.cos(d)) / x
+    assert q_free > qmax
+    case = dc.replace(case, q_min=np.full((2, 3), -1.0), q_max=np.full((2, 3), qmax))
+    res = O.newton_cim_qlim(case, tol=1e-12)
+    assert res["converged"] and res["rounds"] == 2
+    assert res["switched"][3:].all() and not res["switched"][:3].any()
+    vm2, va2 = two_bus_pq_closed_form(-pg, -qmax, 0.0, x)
+    for s in range(3):
+        v2 = res["V"][3 + s]
+        assert abs(abs(v2) - vm2) < 1e-10
+        assert abs(np.angle(v2 / ROT[s]) - va2) < 1e-10
+        assert abs(res["Qg"][3 + s] - qmax) < 1e-12
+
+
+@pytest.mark.parametrize("n,seed", [(400, 3), (600, 4)])
+def test_cim_reactive_limits_hold_at_the_solution(n, seed):
+    """After the rounds: the power mismatch is below tol, every PV slot still
+    free is inside its limits at |V| = v_set, every held slot sits at the
+    limit it crossed with |V| off v_set; wide limits give the plain solve."""
+    import dataclasses as dc
+
+    base = cases.with_pv_nodes(cases.feeder_case(n, seed), 8, 3)
+    case = cases.with_phase_q_limits(base, 1)
+    res = O.newton_cim_qlim(case)
+    assert res["converged"] and res["switched"].any() and res["rounds"] >= 2
+    Y = O.ybus_three_phase(case)
+    V, Qg, sw = res["V"], res["Qg"], res["switched"]
+    dS = O.cim_power_mismatch(case, Y, V, Qg)
+    assert max(np.max(np.abs(dS.real)), np.max(np.abs(dS.imag))) <= 1e-8
+    pv = O.cim_pv_slots(case)
+    assert not (sw & ~pv).any()
+    qmin, qmax = case.q_min.reshape(-1), case.q_max.reshape(-1)
+    free = pv & ~sw
+    assert np.all(Qg[free] <= qmax[free] + 1e-12) and np.all(Qg[free] >= qmin[free] - 1e-12)
+    vset = np.repeat(case.v_set, 3)
+    assert np.max(np.abs(np.abs(V[free]) - vset[free])) < 1e-12
+    at = np.minimum(np.abs(Qg[sw] - qmax[sw]), np.abs(Qg[sw] - qmin[sw]))
+    assert np.max(at) == 0.0
+    assert np.min(np.abs(np.abs(V[sw]) - vset[sw])) > 1e-7
+    wide = dc.replace(case, q_min=np.full((case.n_node, 3), -10.0),
+                      q_max=np.full((case.n_node, 3), 10.0))
+    r2 = O.newton_cim_qlim(wide)
+    r0 = O.newton_cim(base)
+    assert r2["rounds"] == 1 and not r2["switched"].any()
+    assert np.array_equal(r2["V"], r0["V"])
