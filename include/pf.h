@@ -119,8 +119,9 @@ typedef struct {
   double v_source;
   const uint8_t* br_phases;
   const double* br_z;
-  /* single phase, optional: reactive generation limits per bus (pu, read at
-     PV buses when pf_opts.q_limits is set; both or neither; q_min <= q_max) */
+  /* optional reactive generation limits (pu; both or neither; q_min <= q_max;
+     read when pf_opts.q_limits is set): single phase per bus [n], read at
+     PV buses; three phase per node and phase [n][3], read at PV nodes */
   const double* q_min;
   const double* q_max;
 } pf_case_desc;
@@ -151,15 +152,16 @@ typedef struct {
   int krylov;         /* PF_NK inner solver: 0 = restarted GMRES(gmres_restart)
                          (default), 1 = BiCGSTAB (the method of Sec. III.B;
                          needs gmres_restart >= 7 for its work vectors) */
-  int q_limits;       /* single phase with q_min/q_max: 1 = enforce the reactive
-                         limits of PV buses.  After a converged solve every PV
-                         bus whose generator Q (Q_i of Eq. 7 plus its own
-                         reactive load) is outside [q_min, q_max] becomes PQ at
-                         the limit it crossed, and the scenario is solved again
-                         from its last voltages; rounds end when no PV bus
-                         violates (switched buses stay PQ; at most 64 rounds,
-                         then PF_ERR_MAXITER).  The block pattern is the same
-                         for PV and PQ buses, so no symbolic step is repeated.
+  int q_limits;       /* cases with q_min/q_max: 1 = enforce the reactive limits.
+                         After a converged solve every PV bus whose generator Q
+                         (Q_i of Eq. 7 plus its own reactive load) -- three
+                         phase: every PV phase slot whose reactive injection
+                         Q_g -- is outside [q_min, q_max] is held at the limit
+                         it crossed (|V| free), and the scenario is solved again
+                         from its last voltages; rounds end when nothing
+                         violates (held buses and slots stay held; at most 64
+                         rounds, then PF_ERR_MAXITER).  The block pattern is the
+                         same either way, so no symbolic step is repeated.
                          The call waits for the device between rounds.
                          Default 0 (limits ignored) */
   double refine_stall; /* NR + PF_MIXED: the FP64 refinement of a step is taken
@@ -181,7 +183,8 @@ typedef struct {
   double mismatch;       /* final infinity norm of the power mismatch (pu) */
   double max_step;       /* infinity norm of the last Newton correction */
   double solve_us;       /* device time of the solve, microseconds */
-  int q_switched;        /* opts.q_limits: PV buses held at a reactive limit */
+  int q_switched;        /* opts.q_limits: PV buses (three phase: PV phase
+                            slots) held at a reactive limit */
   int q_rounds;          /* opts.q_limits: solves the scenario needed (1 + the
                             last round that switched one of its buses) */
 } pf_info;

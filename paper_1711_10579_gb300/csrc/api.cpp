@@ -163,12 +163,14 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   UP(pl, p_load0);
   UP(ql, q_load0);
   d.q_min = d.q_max = nullptr;
-  if (c.kind == PF_SINGLE_PHASE && !c.q_max.empty()) {
-    std::vector<double> qmin(n), qmax(n);
-    for (int i = 0; i < n; ++i) {
-      qmin[i] = c.q_min[s.perm[i]];
-      qmax[i] = c.q_max[s.perm[i]];
-    }
+  if (!c.q_max.empty()) {  // per bus, or per node and phase
+    const int per = c.kind == PF_SINGLE_PHASE ? 1 : 3;
+    std::vector<double> qmin((size_t)per * n), qmax((size_t)per * n);
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < per; ++a) {
+        qmin[(size_t)i * per + a] = c.q_min[(size_t)s.perm[i] * per + a];
+        qmax[(size_t)i * per + a] = c.q_max[(size_t)s.perm[i] * per + a];
+      }
     UP(qmin, q_min);
     UP(qmax, q_max);
   }
@@ -269,8 +271,8 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
   t += (size_t)B * (2 * 8 + 2 * 8 + 4 + 12) + 16 + 64;  // norm, step, flag, status, t0, call
   t += 3 * nb * nsl * 8;                                // staged inputs
   t += 2 * nb * nsl * 8 + (size_t)B * sizeof(pf_info);  // staged outputs
-  if (kind == PF_SINGLE_PHASE)                          // reactive-limit rounds
-    t += nb * 9 + (size_t)B * (5 * 4 + 8 + sizeof(pf_info)) + 4;
+  t += nb * (kind == PF_SINGLE_PHASE ? 9 : 1)          // reactive-limit rounds
+       + (size_t)B * (5 * 4 + 8 + sizeof(pf_info)) + 4;
   if (m > 0) {                                          // Newton-Krylov (FP64 bound)
     t += (size_t)nnz_lu * B * bs * bs * 8;              // Jacobian copy
     t += (size_t)(m + 1 + 3) * nb * bs * 8;             // basis, w, z, x
@@ -336,9 +338,9 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
   A((void**)&st_vm, nb * nsl * 8);
   A((void**)&st_va, nb * nsl * 8);
   A((void**)&st_info, (size_t)B * sizeof(pf_info));
-  if (kind == PF_SINGLE_PHASE) {
+  {  // reactive-limit rounds (three phase: held phases in bt, values in qg)
     A((void**)&w.bt, nb);
-    A((void**)&w.qsw, nb * 8);
+    if (kind == PF_SINGLE_PHASE) A((void**)&w.qsw, nb * 8);
     A((void**)&w.qdone, (size_t)B * 4);
     A((void**)&w.qcnt, (size_t)B * 4);
     A((void**)&w.qit, (size_t)3 * B * 4);

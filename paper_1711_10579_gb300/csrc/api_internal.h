@@ -133,9 +133,9 @@ int run_solve_q(pf_case c, const pf_opts& o, int B, const double* d_p_load,
                 const double* d_q_load, const double* d_p_gen, Workspace* ws, cudaStream_t st,
                 double* out_vm, double* out_va, pf_info* out_info);
 // Reactive-limit checks (qlim.cu).
-cudaError_t launch_qlim_init(const DevSys& S, const DevWork& w, cudaStream_t st);
+cudaError_t launch_qlim_init(const DevSys& S, const DevWork& w, bool three, cudaStream_t st);
 cudaError_t launch_qlim_check(const DevSys& S, const DevWork& w, const pf_info* info, int round,
-                              cudaStream_t st);
+                              bool three, cudaStream_t st);
 cudaError_t launch_qlim_final(const DevWork& w, pf_info* info, int round, int capped,
                               cudaStream_t st);
 void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int* cluster,

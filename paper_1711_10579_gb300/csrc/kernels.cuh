@@ -538,11 +538,13 @@ __device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, 
         // PV column node: its phase c keeps |V| by dVr = -(Vi/Vr) dVi, so
         // the unknowns are (dQ_c, dVi_c): column 3 + c becomes col(Vi) -
         // (Vi/Vr) col(Vr), and column c carries d(Y V - I_sp)/dQ_c = j V / |V|^2,
-        // nonzero only in the node's own rows of phase c
+        // nonzero only in the node's own rows of phase c.  A phase held at a
+        // reactive limit (w.bt) keeps its plain columns.
         const size_t bj3 = ((size_t)j * B + gs) * 3;
+        const int heldj = w.bt ? w.bt[(size_t)j * B + gs] : 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          if (!((maskj >> c) & 1)) continue;
+          if (!((maskj >> c) & 1) || ((heldj >> c) & 1)) continue;
           const double2 v = (j == i) ? Vi[c] : ldc(w.V + bj3 + c);
           const TF rho = (TF)(v.y / v.x);
 #pragma unroll
@@ -1449,7 +1451,8 @@ __device__ __forceinline__ void setup_row(const DevSys& S, const DevWork& w, int
         }
       }
       w.V[b * 3 + a] = v;
-      w.qg[b * 3 + a] = 0.0;
+      // the reactive injections carry over between rounds of reactive limits
+      if (!(w.bt && w.in_vm)) w.qg[b * 3 + a] = 0.0;
     }
   }
   if (i == 0) setup_scenario(w, gs);
@@ -1463,10 +1466,11 @@ __device__ __forceinline__ void dv_row(const DevSys& S, const DevWork& w, int i,
   const size_t b = (size_t)i * B + gs;
   if constexpr (THREE) {
     const bool pv = (S.btype[i] & 16) != 0 && !(S.btype[i] & 8);
+    const int held = w.bt ? w.bt[b] : 0;
     for (int a = 0; a < 3; ++a) {
       const double di = __ldcg(w.dx + b * 6 + 3 + a);
       double dr = __ldcg(w.dx + b * 6 + a);
-      if (pv && ((S.btype[i] >> a) & 1)) {  // (dQ, dVi): dVr = -(Vi/Vr) dVi
+      if (pv && ((S.btype[i] >> a) & 1) && !((held >> a) & 1)) {  // (dQ, dVi): dVr = -(Vi/Vr) dVi
         const double2 v = ldc(w.V + b * 3 + a);
         dr = -(v.y / v.x) * di;
       }
@@ -1500,6 +1504,7 @@ __device__ __forceinline__ void resid_row(const DevSys& S, const DevWork& w, int
     const int mask = S.btype[i] & 7;
     const bool src = (S.btype[i] & 8) != 0;
     const bool pv = (S.btype[i] & 16) != 0;
+    const int held = w.bt ? w.bt[b] : 0;
     for (int a = 0; a < 3; ++a) {
       const bool fa = ((mask >> a) & 1) && !src;
       const double2 dv = ldc(w.dV + b * 3 + a);  // the step as a voltage change
@@ -1510,7 +1515,7 @@ __device__ __forceinline__ void resid_row(const DevSys& S, const DevWork& w, int
         const double* ad = w.abcd + b * 12;
         double jim = YdV[a].y - (ad[a] * dr + ad[3 + a] * di);
         double jre = YdV[a].x - (ad[6 + a] * dr + ad[9 + a] * di);
-        if (pv) {  // plus the dQ column j V / |V|^2
+        if (pv && !((held >> a) & 1)) {  // plus the dQ column j V / |V|^2
           const double2 v = ldc(w.V + b * 3 + a);
           const double dq = __ldcg(w.dx + b * 6 + a), m2 = v.x * v.x + v.y * v.y;
           jim += v.x / m2 * dq;
@@ -1563,12 +1568,13 @@ __device__ __forceinline__ double update_row(const DevSys& S, const DevWork& w, 
   double stp = 0.0;
   if constexpr (THREE) {
     const bool pv = (S.btype[i] & 16) != 0 && !(S.btype[i] & 8);
+    const int held = w.bt ? w.bt[b] : 0;
     for (int a = 0; a < NSL; ++a) {
       double dr = __ldcg(w.dx + b * 6 + a);
       const double di = __ldcg(w.dx + b * 6 + 3 + a);
       stp = fmax(stp, fmax(fabs(dr), fabs(di)));
       const double2 v = ldc(w.V + b * 3 + a);
-      if (pv && ((S.btype[i] >> a) & 1)) {
+      if (pv && ((S.btype[i] >> a) & 1) && !((held >> a) & 1)) {
         // PV slot: the step is (dQ, dVi) with dVr = -(Vi/Vr) dVi; the new
         // voltage is put back on |V| = v_set
         w.qg[b * 3 + a] += dr;

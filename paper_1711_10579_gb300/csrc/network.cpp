@@ -91,6 +91,26 @@ bool invert_small(int k, cd* a, cd* inv) {
 
 }  // namespace
 
+// Optional reactive limits (per bus, or per node and phase): both or
+// neither, each an interval (infinite ends allowed).
+static int copy_q_limits(const pf_case_desc* d, size_t cnt, CaseData& c, std::string& err) {
+  if ((d->q_min != nullptr) != (d->q_max != nullptr)) {
+    err = "q_min and q_max go together";
+    return PF_ERR_INVALID;
+  }
+  if (!d->q_min) return PF_OK;
+  c.q_min.assign(d->q_min, d->q_min + cnt);
+  c.q_max.assign(d->q_max, d->q_max + cnt);
+  for (size_t k = 0; k < cnt; ++k)
+    if (std::isnan(c.q_min[k]) || std::isnan(c.q_max[k]) || c.q_min[k] > c.q_max[k]) {
+      std::ostringstream msg;
+      msg << "slot " << k << " has reactive limits that are not an interval";
+      err = msg.str();
+      return PF_ERR_INVALID;
+    }
+  return PF_OK;
+}
+
 int copy_case(const pf_case_desc* d, CaseData& c, std::string& err) {
   std::ostringstream msg;
   if (!d) {
@@ -177,20 +197,7 @@ int copy_case(const pf_case_desc* d, CaseData& c, std::string& err) {
         err = "case data contain non-finite values";
         return PF_ERR_INVALID;
       }
-    if ((d->q_min != nullptr) != (d->q_max != nullptr)) {
-      err = "q_min and q_max go together";
-      return PF_ERR_INVALID;
-    }
-    if (d->q_min) {
-      c.q_min.assign(d->q_min, d->q_min + n);
-      c.q_max.assign(d->q_max, d->q_max + n);
-      for (int i = 0; i < n; ++i)
-        if (std::isnan(c.q_min[i]) || std::isnan(c.q_max[i]) || c.q_min[i] > c.q_max[i]) {
-          msg << "bus " << i << " has reactive limits that are not an interval";
-          err = msg.str();
-          return PF_ERR_INVALID;
-        }
-    }
+    if (copy_q_limits(d, (size_t)n, c, err) != PF_OK) return PF_ERR_INVALID;
     for (int i = 0; i < n; ++i)
       if (c.bus_type[i] != PF_PQ && !(c.v_set[i] > 0.0)) {
         msg << "bus " << i << " needs a positive |V| set point";
@@ -255,6 +262,7 @@ int copy_case(const pf_case_desc* d, CaseData& c, std::string& err) {
         err = msg.str();
         return PF_ERR_INVALID;
       }
+    if (copy_q_limits(d, (size_t)3 * n, c, err) != PF_OK) return PF_ERR_INVALID;
     c.source = d->source;
     c.v_source = d->v_source > 0 ? d->v_source : 1.0;
     if (!std::isfinite(c.v_source)) {

@@ -1,5 +1,5 @@
-// Reactive limits of PV buses (single phase): the checks between the rounds
-// of solves.
+// Reactive limits of PV buses and of the phases of three-phase PV nodes:
+// the checks between the rounds of solves.
 //
 // Sec. II.A holds the magnitude of a PV bus by letting its generator supply
 // whatever reactive power that takes.  A real generator has limits
@@ -10,6 +10,10 @@
 // bus's own reactive load at |V_i| (Eq. 12-15); a bus outside its limits
 // gets the scenario bus type kPQLimit and its limit as generation, which
 // the mismatch (Eq. 8-9) and Jacobian (Eq. 10) read in the next round.
+// Three phase: the reactive injection Q_g of a PV phase slot is an unknown
+// of the current-injection Newton (w.qg); a slot outside [q_min, q_max] is
+// held at the limit it crossed (w.qg fixed, its bit set in w.bt, |V| free)
+// and keeps the plain columns of Eq. 21-23 in the next round.
 // Rows are in the numbering of the solve's ordering; w.bt is [row][B].
 
 #include <cuda_runtime.h>
@@ -22,13 +26,17 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(kThreads) k_qlim_init(DevSys S, DevWork w) {
+__global__ void __launch_bounds__(kThreads) k_qlim_init(DevSys S, DevWork w, int three) {
   const size_t k = (size_t)blockIdx.x * kThreads + threadIdx.x;
   const int B = w.B;
   if (k >= (size_t)S.n * B) return;
   const int i = (int)(k / B), gs = (int)(k % B);
-  w.bt[k] = S.btype[i];
-  w.qsw[k] = 0.0;
+  if (three) {
+    w.bt[k] = 0;  // no phase held
+  } else {
+    w.bt[k] = S.btype[i];
+    w.qsw[k] = 0.0;
+  }
   if (i == 0) {
     w.qdone[gs] = 0;
     w.qcnt[gs] = 0;
@@ -43,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_qlim_init(DevSys S, DevWork w) {
 // round's counters to the scenario's totals and keeps the result of a
 // scenario that failed (it takes no further part in the rounds).
 __global__ void __launch_bounds__(kThreads) k_qlim_check(DevSys S, DevWork w, const pf_info* info,
-                                                         int round) {
+                                                         int round, int three) {
   const size_t k = (size_t)blockIdx.x * kThreads + threadIdx.x;
   const int B = w.B;
   if (k >= (size_t)S.n * B) return;
@@ -64,7 +72,31 @@ __global__ void __launch_bounds__(kThreads) k_qlim_check(DevSys S, DevWork w, co
       w.qdone[gs] = 1;
     }
   }
-  if (status != PF_OK || w.bt[k] != PF_PV) return;
+  if (status != PF_OK) return;
+  if (three) {
+    const int t = S.btype[i];
+    if (!(t & 16) || (t & 8)) return;  // not a PV node, or the source
+    int held = w.bt[k], add = 0;
+    for (int a = 0; a < 3; ++a) {
+      if (!((t >> a) & 1) || ((held >> a) & 1)) continue;
+      const double q = w.qg[k * 3 + a], qmax = S.q_max[i * 3 + a], qmin = S.q_min[i * 3 + a];
+      double lim;
+      if (q > qmax) lim = qmax;
+      else if (q < qmin) lim = qmin;
+      else continue;
+      w.qg[k * 3 + a] = lim;
+      held |= 1 << a;
+      ++add;
+    }
+    if (add) {
+      w.bt[k] = (int8_t)held;
+      atomicAdd(w.qcnt + gs, add);
+      atomicAdd(w.nsw, add);
+      w.qit[2 * B + gs] = round;
+    }
+    return;
+  }
+  if (w.bt[k] != PF_PV) return;
   // Q_i = Im(V_i conj(I_i)), I = Y V (Eq. 1, 7)
   const double2* Y = reinterpret_cast<const double2*>(S.y_val);
   double2 I = make_double2(0.0, 0.0);
@@ -112,17 +144,17 @@ __global__ void __launch_bounds__(kThreads) k_qlim_final(DevWork w, pf_info* inf
 
 }  // namespace
 
-cudaError_t launch_qlim_init(const DevSys& S, const DevWork& w, cudaStream_t st) {
+cudaError_t launch_qlim_init(const DevSys& S, const DevWork& w, bool three, cudaStream_t st) {
   const size_t tot = (size_t)S.n * w.B;
-  k_qlim_init<<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, st>>>(S, w);
+  k_qlim_init<<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, st>>>(S, w, three);
   return cudaGetLastError();
 }
 
 cudaError_t launch_qlim_check(const DevSys& S, const DevWork& w, const pf_info* info, int round,
-                              cudaStream_t st) {
+                              bool three, cudaStream_t st) {
   const size_t tot = (size_t)S.n * w.B;
   k_qlim_check<<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, st>>>(S, w, info,
-                                                                                  round);
+                                                                                  round, three);
   return cudaGetLastError();
 }
 

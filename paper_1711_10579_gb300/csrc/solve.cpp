@@ -226,7 +226,7 @@ int run_solve_q(pf_case c, const pf_opts& o, int B, const double* d_p_load, cons
                 const double* d_p_gen, Workspace* ws, cudaStream_t st, double* out_vm,
                 double* out_va, pf_info* out_info) {
   const CaseData& cd = c->data;
-  if (!o.q_limits || cd.kind != PF_SINGLE_PHASE || cd.q_max.empty())
+  if (!o.q_limits || cd.q_max.empty())
     return run_solve(c, o, B, d_p_load, d_q_load, d_p_gen, ws, st, RunMode::Solve, out_vm,
                      out_va, out_info);
   int rc = check_opts(o);
@@ -241,10 +241,14 @@ int run_solve_q(pf_case c, const pf_opts& o, int B, const double* d_p_load, cons
   const DevSys& sys = (nk ? c->nk : c->nr).view;
   DevWork w = ws->w;
   w.B = B;
-  int npv = 0;
-  for (int8_t t : cd.bus_type) npv += (t == PF_PV);
+  const bool three = cd.kind != PF_SINGLE_PHASE;
+  int npv = 0;  // buses, or phase slots, that can switch
+  for (size_t i = 0; i < cd.bus_type.size(); ++i)
+    if (cd.bus_type[i] == PF_PV)
+      npv += three ? ((cd.phases[i] & 1) + ((cd.phases[i] >> 1) & 1) + ((cd.phases[i] >> 2) & 1))
+                   : 1;
   const int cap = std::min(npv + 1, 64);
-  cudaError_t e = launch_qlim_init(sys, w, st);
+  cudaError_t e = launch_qlim_init(sys, w, three, st);
   if (e != cudaSuccess) return cuda_error(e, "launching the reactive-limit set-up");
   int round = 0, pending = 0;
   for (;;) {
@@ -253,7 +257,7 @@ int run_solve_q(pf_case c, const pf_opts& o, int B, const double* d_p_load, cons
                    nullptr, round > 1 ? vm : nullptr, round > 1 ? va : nullptr, true);
     if (rc != PF_OK) return rc;
     e = cudaMemsetAsync(w.nsw, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = launch_qlim_check(sys, w, info, round, st);
+    if (e == cudaSuccess) e = launch_qlim_check(sys, w, info, round, three, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&pending, w.nsw, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_error(e, "checking reactive limits");

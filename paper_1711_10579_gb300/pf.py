@@ -215,6 +215,9 @@ def make_desc(case) -> _Desc:
             d.bus_type = i32(case.node_type)
             d.v_set = f64(case.v_set)
             d.p_gen = f64(np.asarray(case.p_gen).reshape(-1))
+        if case.q_max is not None:  # reactive limits per node and phase
+            d.q_min = f64(np.asarray(case.q_min).reshape(-1))
+            d.q_max = f64(np.asarray(case.q_max).reshape(-1))
     else:
         raise TypeError("expected a SinglePhaseCase or ThreePhaseCase")
     return _Desc(d, keep)

@@ -842,3 +842,84 @@ def test_refinement_on_demand(pf, ctx):
         assert pf.make_opts().refine_stall == 0.1
     finally:
         pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# reactive limits of three-phase PV slots
+# ----------------------------------------------------------------------------
+
+def _check_cim_qlim(case, vm, va, info, ref):
+    _check_cim_solve(case, vm, va, info, ref)
+    pv = O.cim_pv_slots(case)
+    vset = np.repeat(case.v_set, 3)
+    held = pv & (np.abs(vm - vset) > 1e-9)
+    assert np.array_equal(held, ref["switched"])
+    assert info["q_switched"] == int(ref["switched"].sum())
+    assert info["q_rounds"] == ref["rounds"]
+
+
+@pytest.mark.parametrize("method", ["nr", "nk"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_three_phase_q_limits_match_oracle(pf, ctx, prec, method):
+    base = cases.with_pv_nodes(cases.feeder_case(600, 4), 8, 3)
+    case = cases.with_phase_q_limits(base, 1)
+    ref = O.newton_cim_qlim(case)
+    assert ref["converged"] and ref["switched"].any()
+    c = pf.pf_create_case(ctx, case)
+    try:
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        m = pf.PF_NR if method == "nr" else pf.PF_NK
+        vm, va, info = pf.pf_solve(c, pf.make_opts(precision=p, method=m, q_limits=1,
+                                                   nk_fallback=0, gmres_max_iter=2000))
+        _check_cim_qlim(case, vm, va, info, ref)
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_three_phase_q_limits_batch_matches_oracle(pf, ctx):
+    base = cases.with_pv_nodes(cases.feeder_case(500, 6), 8, 1)
+    case = cases.with_phase_q_limits(base, 2)
+    B = 8
+    pl, ql = cases.feeder_scenario_loads(case, B, seed=5, sigma=0.1)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        for opts in (pf.make_opts(q_limits=1), pf.make_opts(q_limits=1, kernel_by_kernel=1)):
+            vm, va, info = pf.pf_solve_batch(c, pl, ql, None, opts)
+            assert np.all(info["status"] == 0), info
+            for b in (0, 3, B - 1):
+                ref = O.newton_cim_qlim(case.with_loads(pl[b], ql[b]))
+                _check_cim_qlim(case, vm[b], va[b], info[b], ref)
+    finally:
+        pf.pf_destroy_case(c)
+
+
+def test_three_phase_q_limit_two_node_closed_form(pf, ctx):
+    """The lossless two-node line with q_max below the injection that holds
+    v_set: every phase is held at q_max, the two-bus PQ closed form."""
+    import dataclasses as dc
+    import math
+
+    pg, x, vset, qmax = 0.3, 0.1, 1.02, 0.1
+    base = np.zeros((3, 3), dtype=np.complex128)
+    np.fill_diagonal(base, 1j * x)
+    case = cases.ThreePhaseCase(
+        n_node=2, source=0, phases=np.array([7, 7], np.uint8), p_load=np.zeros((2, 3)),
+        q_load=np.zeros((2, 3)), zip=np.tile([1.0, 0.0, 0.0], (2, 1)),
+        br_from=np.array([0], np.int32), br_to=np.array([1], np.int32),
+        br_phases=np.array([7], np.uint8), br_z=base[None])
+    case = dc.replace(case, node_type=np.array([cases.PQ, cases.PV], np.int32),
+                      v_set=np.array([1.0, vset]), p_gen=np.array([[0, 0, 0], [pg, pg, pg]], float),
+                      q_min=np.full((2, 3), -1.0), q_max=np.full((2, 3), qmax))
+    P, Q = pg, qmax
+    u = ((2 * Q * x + 1) + math.sqrt((2 * Q * x + 1) ** 2 - 4 * (P * P + Q * Q) * x * x)) / 2
+    v2 = math.sqrt(u)
+    d2 = math.asin(P * x / v2)
+    rot = np.angle(np.exp(-2j * np.pi / 3 * np.arange(3)))
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve(c, pf.make_opts(precision=pf.PF_FP64, q_limits=1, tol=1e-12))
+        assert info["status"] == 0 and info["q_switched"] == 3 and info["q_rounds"] == 2
+        assert np.max(np.abs(vm[3:] - v2)) <= 1e-10
+        assert np.max(np.abs(np.angle(np.exp(1j * (va[3:] - rot - d2))))) <= 1e-10
+    finally:
+        pf.pf_destroy_case(c)
