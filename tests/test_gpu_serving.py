@@ -162,3 +162,39 @@ def test_serving_errors_are_reported_on_the_host(pf):
         pf.pf_destroy_case(h)
     finally:
         pf.pf_ctx_destroy(ctx)
+
+
+def test_served_solves_enforce_reactive_limits(pf):
+    """Requests with opts.q_limits on cases with limits (single phase and a
+    three-phase feeder with PV nodes) give the oracle's switched solutions."""
+    ctx = pf.pf_ctx_create(0)
+    try:
+        c1 = cases.with_q_limits(cases.transmission_case(300, 405, 60, 2), 1)
+        c3 = cases.with_phase_q_limits(cases.with_pv_nodes(cases.feeder_case(400, 3), 8, 3), 1)
+        h1, h3 = pf.pf_create_case(ctx, c1), pf.pf_create_case(ctx, c3)
+        o = pf.make_opts(q_limits=1)
+        tickets, slots = [], {}
+        for k in range(3):
+            t = pf.pf_submit(ctx, h1, c1.p_load, c1.q_load, c1.p_gen, o)
+            tickets.append(t)
+            slots[t] = h1.slots
+            t = pf.pf_submit(ctx, h3, c3.p_load.reshape(-1), c3.q_load.reshape(-1), None, o)
+            tickets.append(t)
+            slots[t] = h3.slots
+        out = _wait(pf, ctx, tickets, slots)
+        r1 = O.newton_polar_qlim(c1)
+        r3 = O.newton_cim_qlim(c3)
+        for t in tickets:
+            vm, va, info = out[t]
+            assert info["status"] == 0 and info["q_switched"] > 0
+            if slots[t] == h1.slots:
+                assert info["q_switched"] == int(r1["switched"].sum())
+                assert np.max(np.abs(vm - r1["vm"])) <= 1e-6
+                assert np.max(np.abs(va - r1["va"])) <= 1e-6
+            else:
+                assert info["q_switched"] == int(r3["switched"].sum())
+                assert np.max(np.abs(vm - np.abs(r3["V"]))) <= 1e-6
+        pf.pf_destroy_case(h1)
+        pf.pf_destroy_case(h3)
+    finally:
+        pf.pf_ctx_destroy(ctx)
