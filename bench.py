@@ -552,7 +552,10 @@ def main():
     t_sweep = phase_us["triangular_solves"] * 1e-6
     achieved = sweep_b * passes / t_sweep / 1e9
     peak, peak_kind = _peaks()
-    step_bytes = algorithmic_bytes_per_iteration(st, B=B) * float(info["iterations"].sum()) / K
+    # refinement passes taken (on demand), per Newton iteration
+    its = float(info["iterations"].sum())
+    ref_per_it = float((info["linear_iterations"] - info["iterations"]).sum()) / max(its, 1.0)
+    step_bytes = algorithmic_bytes_per_iteration(st, B=B, refine=ref_per_it) * its / K
     # kernels per step: the call record, the graph's prologue (set-up,
     # mismatch, stop test), one loop body per Newton step of the slowest
     # scenario (refinement flag, factor, sweeps, update, mismatch, stop
