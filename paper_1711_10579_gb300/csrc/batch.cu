@@ -285,6 +285,8 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) k_solve(DevSys S, DevWork
   a.nlev = S.nflev;
   a.gsz = S.g_fwd;
   a.red = reinterpret_cast<TF*>(dsm);
+  // the staged records after the lanes' partial sums (16-byte aligned)
+  a.srec = reinterpret_cast<int4*>(dsm + (((size_t)blockDim.x * BS * sizeof(TF) + 15) & ~(size_t)15));
   sweep_batch<BS, TF, true>(a, tm);
   a.rhs = nullptr;
   a.dx = w.dx;
@@ -401,7 +403,7 @@ struct Plan {
     rows = dim3((B + sb - 1) / sb, (n + rb * kRowsPerThread - 1) / (rb * kRowsPerThread));
     blk = dim3(kRowThreads);
     const dim3 gf((B + of.S - 1) / of.S), gsv((B + os.S - 1) / os.S);
-    red = (size_t)threads_s * BS * sizeof(TF);
+    red = (((size_t)threads_s * BS * sizeof(TF) + 15) & ~(size_t)15) + (size_t)kSweepStage * 16;
     ring = of.ring ? (size_t)threads_f * FactorPipe<TF>::bytes : 0;
     auto rowk = [&](const void* fn) {
       return Launch{fn, rows, blk, 0, {&S, &w, &sb}};

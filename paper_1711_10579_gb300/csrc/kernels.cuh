@@ -746,15 +746,16 @@ struct BSweep {
   int nlev;
   const int8_t* gsz;   // lanes per row for each level
   TF* red;             // shared memory for the partial sums of lanes
+  int4* srec;          // shared memory for kSweepStage row records, or null
 };
 
+// Rows of a wide level whose records one batched sweep stages in shared
+// memory at a time (16 bytes each).
+constexpr int kSweepStage = 1024;
+
 template <int BS, typename TF, bool FWD>
-__device__ __forceinline__ void brow_load(BRow<BS, TF>& P, const BSweep<TF>& a, int pos, bool have,
-                                          int lane, int gs) {
-  P.i = -1;
-  P.p = P.pe = 0;
-  if (!have) return;
-  const int4 q = __ldg(a.rec + pos);
+__device__ __forceinline__ void brow_from(BRow<BS, TF>& P, const BSweep<TF>& a, int4 q, int lane,
+                                          int gs) {
   P.i = q.x;
   P.p = q.y + lane;
   P.pe = q.z;
@@ -768,6 +769,15 @@ __device__ __forceinline__ void brow_load(BRow<BS, TF>& P, const BSweep<TF>& a, 
     for (int c = 0; c < BS; ++c) P.own[c] = (FWD && a.rhs) ? (TF)__ldcg(a.rhs + bi + c) : a.y[bi + c];
     if constexpr (!FWD && BS == 2) blk_load<2>(a.uinv + ((size_t)P.i * a.B + gs) * 4, P.d);
   }
+}
+
+template <int BS, typename TF, bool FWD>
+__device__ __forceinline__ void brow_load(BRow<BS, TF>& P, const BSweep<TF>& a, int pos, bool have,
+                                          int lane, int gs) {
+  P.i = -1;
+  P.p = P.pe = 0;
+  if (!have) return;
+  brow_from<BS, TF, FWD>(P, a, __ldg(a.rec + pos), lane, gs);
 }
 
 // Entry p of a row: its column and block (from the row's prefetch when p is
@@ -833,9 +843,8 @@ __device__ __forceinline__ void brow_finish(const BRow<BS, TF>& P, const BSweep<
 template <int BS, typename TF, bool FWD>
 __device__ __noinline__ void sweep_batch(const BSweep<TF> a, const Team tm) {
   constexpr int BB = BS * BS;
-  // rows in flight per thread: more than one measured no faster (the extra
+  // one row in flight per thread (more measured no faster: the extra
   // registers spill)
-  constexpr int R = 1;
   const int NS = tm.S;
   const int slot = tm.tid & (NS - 1);
   const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
@@ -852,46 +861,44 @@ __device__ __noinline__ void sweep_batch(const BSweep<TF> a, const Team tm) {
     const int G = a.gsz[l], base = a.lev_ptr[l], width = a.lev_ptr[l + 1] - base;
     if (l + 1 < a.nlev) pref(l + 1, nxt);
     if (G == 1) {
-      if (on) {
-        for (int r0 = q; r0 < width; r0 += R * nq) {
-          BRow<BS, TF> P[R];
+      // one lane per row: row r goes to row slot r % nq
+      auto row = [&](const BRow<BS, TF>& P) {
+        TF acc[BS];
 #pragma unroll
-          for (int u = 0; u < R; ++u) {
-            const int r = r0 + u * nq;
-            if (u == 0 && r0 == q) P[0] = cur;
-            else brow_load<BS, TF, FWD>(P[u], a, base + r, r < width, 0, gs);
-          }
-          TF acc[R][BS];
+        for (int c = 0; c < BS; ++c) acc[c] = TF(0);
+        for (int p = P.p; p < P.pe; ++p) {
+          int k;
+          TF L[BB];
+          brow_entry<BS, TF>(P, a, p, gs, k, L);
+          const size_t bk = ((size_t)k * a.B + gs) * BS;
 #pragma unroll
-          for (int u = 0; u < R; ++u)
+          for (int rr = 0; rr < BS; ++rr)
 #pragma unroll
-            for (int c = 0; c < BS; ++c) acc[u][c] = TF(0);
-          for (int e = 0;; ++e) {
-            bool any = false;
-            int k[R];
-            TF L[R][BB];
-#pragma unroll
-            for (int u = 0; u < R; ++u) {
-              if (P[u].p + e < P[u].pe) {
-                any = true;
-                brow_entry<BS, TF>(P[u], a, P[u].p + e, gs, k[u], L[u]);
-              }
+            for (int c = 0; c < BS; ++c) acc[rr] += L[rr * BS + c] * a.y[bk + c];
+        }
+        if (P.i >= 0) brow_finish<BS, TF, FWD>(P, a, gs, acc);
+      };
+      if (on && q < width) row(cur);  // its record came during the last level
+      if (a.srec && width > nq) {
+        // the other rows' records staged in shared memory, kSweepStage at a
+        // time, so that a row's loads start one round trip earlier
+        for (int c0 = nq; c0 < width; c0 += kSweepStage) {
+          const int c1 = min(c0 + kSweepStage, width);
+          __syncthreads();  // the last chunk's readers are done
+          for (int t = tm.tid; t < c1 - c0; t += tm.nthr) a.srec[t] = __ldg(a.rec + base + c0 + t);
+          __syncthreads();
+          if (on)
+            for (int r = c0 + q; r < c1; r += nq) {
+              BRow<BS, TF> P;
+              brow_from<BS, TF, FWD>(P, a, a.srec[r - c0], 0, gs);
+              row(P);
             }
-            if (!any) break;
-#pragma unroll
-            for (int u = 0; u < R; ++u) {
-              if (P[u].p + e < P[u].pe) {
-                const size_t bk = ((size_t)k[u] * a.B + gs) * BS;
-#pragma unroll
-                for (int rr = 0; rr < BS; ++rr)
-#pragma unroll
-                  for (int c = 0; c < BS; ++c) acc[u][rr] += L[u][rr * BS + c] * a.y[bk + c];
-              }
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < R; ++u)
-            if (P[u].i >= 0) brow_finish<BS, TF, FWD>(P[u], a, gs, acc[u]);
+        }
+      } else if (on) {
+        for (int r = q + nq; r < width; r += nq) {
+          BRow<BS, TF> P;
+          brow_load<BS, TF, FWD>(P, a, base + r, true, 0, gs);
+          row(P);
         }
       }
     } else {
@@ -963,6 +970,7 @@ __device__ void sweep(const DevSys& S, const DevWork& w, TF* y, const Team& tm,
       a.nlev = nlev;
       a.gsz = gsz;
       a.red = red;
+      a.srec = nullptr;
       sweep_batch<BS, TF, FWD>(a, tm);
       return;
     }
