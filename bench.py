@@ -40,7 +40,7 @@ B_MAIN = 2432
 # summarised in profiles/k_solve_mesh10000x608.md (608 scenarios; traffic
 # scales with the scenarios of a launch).  Valid only for the sources it was
 # measured on (sha256 prefix of csrc/batch.cu + csrc/kernels.cuh).
-NCU_TRAFFIC = {"sources_sha256": "db4bfda7f04cb8ec", "bytes_per_scenario_pass": 831.98e6 / 608}
+NCU_TRAFFIC = {"sources_sha256": "22df78494f6b7caa", "bytes_per_scenario_pass": 831.92e6 / 608}
 WORKLOAD = (f"mesh10000 x {B_MAIN} load scenarios per step, batched Newton-Raphson, "
             "FP32 LU + FP64 mismatch/refinement/update, one CUDA graph per batch")
 
