@@ -923,3 +923,40 @@ def test_three_phase_q_limit_two_node_closed_form(pf, ctx):
         assert np.max(np.abs(np.angle(np.exp(1j * (va[3:] - rot - d2))))) <= 1e-10
     finally:
         pf.pf_destroy_case(c)
+
+
+# ----------------------------------------------------------------------------
+# the benchmark's own workload at full size
+# ----------------------------------------------------------------------------
+
+def test_full_size_batch_in_the_benchmark_launch_shape(pf, ctx):
+    """The 10,000-bus grid x 2,432 scenarios, autotuned as the benchmark runs
+    it (mixed NR, graph): every scenario converges with its PV magnitudes and
+    the slack untouched; sampled scenarios match the oracle; and a random
+    scenario's power mismatch, recomputed by the oracle from the GPU's
+    voltages, is below the tolerance."""
+    case = cases.case_10000bus(0)
+    B = 2432
+    pl, ql, pg = cases.scenario_loads(case, B, seed=21, sigma=0.2)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        pf.pf_autotune(c, B, pf.make_opts())
+        vm, va, info = pf.pf_solve_batch(c, pl, ql, pg)
+        assert np.all(info["status"] == 0)
+        assert np.all(info["mismatch"] <= 1e-8)
+        pv = case.bus_type == cases.PV
+        slack = case.bus_type == cases.SLACK
+        assert np.all(vm[:, pv] == case.v_set[pv]) and np.all(vm[:, slack] == case.v_set[slack])
+        assert np.all(va[:, slack] == 0.0)
+        Y = O.ybus_single(case)
+        rng = np.random.default_rng(2)
+        for b in [0, B - 1] + list(rng.integers(1, B - 1, 2)):
+            sc = case.with_loads(pl[b], ql[b], pg[b])
+            ref = O.newton_polar(sc)
+            assert np.max(np.abs(vm[b] - ref["vm"])) <= V_TOL
+            assert np.max(np.abs(va[b] - ref["va"])) <= A_TOL
+            F = O.mismatch_polar(sc, Y, vm[b], va[b])
+            assert np.max(np.abs(F)) <= 1e-8
+    finally:
+        pf.pf_destroy_case(c)
+
