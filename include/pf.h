@@ -81,6 +81,8 @@ enum pf_kind { PF_SINGLE_PHASE = 1, PF_THREE_PHASE = 3 };
  *                 Specified injection = gen - load(|V|)  (Eq. 12-15).
  *   br_from/br_to[m], br_r/br_x/br_b[m]: pi-model branches, series r + jx,
  *                 total line charging b split b/2 per end (Eq. 2-3).
+ *   q_min[n], q_max[n]  optional reactive generation limits of PV buses
+ *                 (enforced with pf_opts.q_limits).
  * kind == PF_THREE_PHASE (Sec. II.B; PV nodes are a reading beyond the
  * paper, which defers them):
  *   phases[n]     uint8 bit mask of present phases (a=1, b=2, c=4).
@@ -96,6 +98,8 @@ enum pf_kind { PF_SINGLE_PHASE = 1, PF_THREE_PHASE = 3 };
  *                 of both end nodes' phases), br_z[m][3][3][2] the series
  *                 impedance matrix (re, im); the branch admittance is the
  *                 inverse of its submatrix over the branch's phases (Eq. 11).
+ *   q_min[3n], q_max[3n]  optional reactive limits per phase slot of PV
+ *                 nodes (enforced with pf_opts.q_limits).
  * Unused fields may be NULL.
  */
 typedef struct {
