@@ -359,7 +359,9 @@ int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag,
  * Arguments as pf_solve_batch_device with B = 1: d_p_load, d_q_load,
  * d_p_gen (NULL = the case's own), d_vmag, d_vang, d_info are device
  * pointers; the call is asynchronous on `stream`.  opts->method must be
- * PF_NR and block_threads / scen_per_cta 0.  A case whose workspace does not
+ * PF_NR and block_threads / scen_per_cta 0; opts->q_limits on a case with
+ * reactive limits is PF_ERR_UNSUPPORTED (the rounds wait for the device and
+ * keep per-scenario state).  A case whose workspace does not
  * fit the array is rejected with PF_ERR_INVALID and a message giving both
  * sizes (about 370 bytes per bus plus the LU values: single-phase grids of a
  * few tens of thousands of buses fit).

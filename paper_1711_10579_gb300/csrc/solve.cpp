@@ -352,6 +352,8 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   if (rc != PF_OK) return rc;
   if (o.method != PF_NR)
     return set_error(PF_ERR_UNSUPPORTED, "pf_solve_noalloc runs Newton-Raphson only");
+  if (o.q_limits && !c->data.q_max.empty())
+    return set_error(PF_ERR_UNSUPPORTED, "pf_solve_noalloc does not enforce reactive limits");
   if (o.block_threads || o.scen_per_cta)
     return set_error(PF_ERR_INVALID, "pf_solve_noalloc uses the default CTA shape");
   const int kind = c->data.kind, n = c->data.n, bs = c->bs;

@@ -91,3 +91,17 @@ def test_noalloc_rejects_a_case_beyond_its_scratch(env):
         assert e.value.code == pf.PF_ERR_INVALID and "scratch" in str(e.value)
     finally:
         pf.pf_destroy_case(c)
+
+
+def test_noalloc_refuses_reactive_limits(env):
+    pf, torch, ctx = env
+    case = cases.with_q_limits(cases.case_14bus(0), 1)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = _buffers(pf, torch, case, c.slots)
+        with pytest.raises(pf.PfError) as e:
+            pf.pf_solve_noalloc(c, pf.make_opts(q_limits=1), None, None, None, vm, va, info,
+                                torch.cuda.current_stream().cuda_stream)
+        assert e.value.code == pf.PF_ERR_UNSUPPORTED and "reactive" in str(e.value)
+    finally:
+        pf.pf_destroy_case(c)
