@@ -321,6 +321,10 @@ def variants(pf, ctx, torch, dev, flush):
                                                         pf.make_opts(), flush=flush)
     out["mesh2000_x512_batched_mixed"]["tuned"] = {"scen_per_cta": tuned.scen_per_cta,
                                                    "block_threads": tuned.block_threads}
+    # a batch of Newton-Krylov solves (one persistent launch)
+    out["mesh2000_x64_batched_nk_mixed"] = _device_solves(
+        pf, c, torch, dev, 64, pl[:64], ql[:64], pg[:64], pf.make_opts(method=pf.PF_NK), reps=1,
+        flush=flush)
     pf.pf_destroy_case(c)
 
     case = cases.case_feeder8000(0)
