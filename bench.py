@@ -342,9 +342,9 @@ def variants(pf, ctx, torch, dev, flush):
 def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9):
     """Poisson arrivals, 70% transmission (500-70,000 buses) / 30% feeders
     (1,000-20,000 nodes) from pools of resident cases, mixed precision with
-    warm starts.  The offered rate runs first; if it exceeds capacity the
-    sustained rate is reported and a second stream at 70% of it gives the
-    latency percentiles."""
+    warm starts.  The offered rate runs first (its sustained rate and
+    latencies); a second stream at 70% of the sustained rate gives the
+    latency percentiles below saturation."""
     from paper_1711_10579_gb300 import cases
 
     t_setup = time.perf_counter()
@@ -404,8 +404,8 @@ def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9):
 
     first = run(rate, seed)
     out = {"offered": first}
-    if first["solves_per_s"] < 0.9 * rate:
-        out["at_70pct_of_sustained"] = run(0.7 * first["solves_per_s"], seed + 100)
+    # latency below saturation: a second stream at 70% of the sustained rate
+    out["at_70pct_of_sustained"] = run(0.7 * first["solves_per_s"], seed + 100)
     for h in handles.values():
         pf.pf_destroy_case(h)
     out["pool"] = {"transmission_buses": [p.n_bus for p in pools["transmission"]],
