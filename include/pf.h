@@ -270,11 +270,13 @@ int pf_solve(pf_case c, const pf_opts* opts, double* vmag, double* vang,
              pf_info* info);
 
 /*
- * B scenarios of one topology solved together (one persistent launch over
- * the shared symbolic pattern).  Scenario b uses p_load[b][*], q_load[b][*]
- * (per bus or per slot) and, single phase only, p_gen[b][n] (NULL = the
- * case's own generation).  Outputs vmag[b][*], vang[b][*], info[b].
- * Host arrays; the call blocks until done.
+ * B scenarios of one topology solved together over the shared symbolic
+ * pattern (Newton-Raphson: phase kernels in one CUDA graph whose loop ends on
+ * the device when no scenario runs; Newton-Krylov: one persistent launch).
+ * Scenario b uses p_load[b][*], q_load[b][*] (per bus or per slot; a load
+ * scale per bus and scenario is these arrays scaled) and, single phase
+ * only, p_gen[b][n]; NULL = the case's own values.  Outputs vmag[b][*],
+ * vang[b][*], info[b].  Host arrays; the call blocks until done.
  */
 int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
                    const double* p_gen, const pf_opts* opts, double* vmag,
