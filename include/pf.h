@@ -59,7 +59,7 @@ enum pf_status {
   PF_ERR_TIMEOUT = -6,    /* a bounded wait ran out */
   PF_ERR_BUSY = -7,       /* serving queue full; retry later */
   PF_ERR_CUDA = -8,       /* a CUDA runtime call failed */
-  PF_ERR_UNSUPPORTED = -9 /* valid request this build does not implement */
+  PF_ERR_UNSUPPORTED = -9 /* valid request the library does not implement */
 };
 
 enum pf_bus_type { PF_SLACK = 0, PF_PV = 1, PF_PQ = 2 };
