@@ -225,3 +225,34 @@ def test_info_and_opts_layout(pf):
     assert [f for f, _ in pf.pf_info._fields_][-2:] == ["q_switched", "q_rounds"]
     assert pf.INFO_DTYPE.itemsize == pf.C.sizeof(pf.pf_info) == 48
     assert pf.make_opts().q_limits == 0
+
+
+def _c_struct_fields(header, name):
+    """Field names of `typedef struct { ... } name;` in a C header, in order."""
+    import re as _re
+
+    end = _re.search(r"\}\s*" + name + r";", header).start()
+    body = header[header.rfind("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = _re.sub(r"/\*.*?\*/", "", body, flags=_re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "int a, b" or "const double* x"
+        head, *rest = decl.split(",")
+        fields.append(_re.findall(r"[A-Za-z_]\w*", head)[-1])
+        fields += [_re.findall(r"[A-Za-z_]\w*", r)[-1] for r in rest]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("pf_opts", "pf_opts"), ("pf_info", "pf_info"),
+                                          ("pf_case_desc", "pf_case_desc"),
+                                          ("pf_case_stats", "pf_case_stats")])
+def test_binding_structs_mirror_the_header(pf, cname, pyname):
+    """The ctypes mirrors list the header's fields in the header's order (a
+    field added to one side only, or reordered, shifts every later field)."""
+    import os
+
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "pf.h")).read()
+    assert [f for f, _ in getattr(pf, pyname)._fields_] == _c_struct_fields(hdr, cname)
