@@ -1,6 +1,6 @@
 """Benchmark of the Newton power-flow hot path on one GB300 (or N replicas).
 
-A step solves one batch of B = 2,432 seeded load scenarios (16 per SM) of the
+A step solves one batch of B = 4,864 seeded load scenarios (32 per SM) of the
 10,000-bus synthetic transmission grid (average degree 2.7, 20% PV buses;
 every bus load x lognormal(0, 0.2), PV generation rescaled to match) to a
 power mismatch of 1e-8 pu with Newton-Raphson: FP32 sparse-LU
@@ -8,7 +8,7 @@ refactorisation and sweeps, FP64 mismatch, refinement and update.  The batch
 runs as phase kernels over the shared symbolic pattern inside one CUDA graph
 whose loop the device ends (launch shapes autotuned).  Inputs are resident
 in HBM before the timed region; each step has its own scenarios and L2 is
-flushed between timed steps.  Batches of 608 and 4,864 scenarios, single-
+flushed between timed steps.  Batches of 608 and 2,432 scenarios, single-
 solve latency, the plain FP64 single-case solve, the Newton-Krylov solver,
 the three-phase feeder, the 2,000-bus x 512 batch and a serving stream are
 reported as variants.
@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "converged solves/sec at 1e-8 pu mismatch"
-B_MAIN = 2432
+B_MAIN = 4864
 # DRAM traffic of one sweep launch (k_solve: forward + backward sweeps of every
 # scenario of the batch, first Newton step), per scenario, from the ncu capture
 # summarised in profiles/k_solve_mesh10000x608.md (608 scenarios; traffic
@@ -344,7 +344,7 @@ def variants(pf, ctx, torch, dev, flush):
         "note": "pf_branch_flows with host buffers (copies inside)"}
     out["mesh10000_single_nr_fp64"] = _device_solves(
         pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_FP64), reps=20, flush=flush)
-    for Bv, prec, nm in ((608, pf.PF_MIXED, "mixed"), (4864, pf.PF_MIXED, "mixed"),
+    for Bv, prec, nm in ((608, pf.PF_MIXED, "mixed"), (2432, pf.PF_MIXED, "mixed"),
                          (B_MAIN, pf.PF_FP64, "fp64")):
         plb, qlb, pgb = _batch(case, Bv, seed=21)
         pf.pf_autotune(c, Bv, pf.make_opts(precision=prec))
@@ -473,7 +473,7 @@ def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9):
     return out
 
 
-def profile_launches(count, B=B_MAIN, S=4, threads=512):
+def profile_launches(count, B=608, S=4, threads=512):
     """``count`` batched solves of B scenarios of the main step's grid with a
     fixed launch shape, kernel by kernel (ncu does not look inside the CUDA
     graph of a batch)."""
@@ -519,7 +519,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-launches", type=int, default=0,
                     help="only run the batched solve this many times (for ncu)")
-    ap.add_argument("--profile-batch", type=int, default=B_MAIN,
+    ap.add_argument("--profile-batch", type=int, default=608,
                     help="scenarios of the --profile-launches batch")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
