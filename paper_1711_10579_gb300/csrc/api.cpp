@@ -192,16 +192,21 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   }
   // a target carries its first contribution; the others (rare: most targets
   // receive one per level) follow in `con`, each list ended by (-1, -1)
+  // the first update of a fill entry (levels in order) starts from zero
   con.clear();
+  std::vector<char> touched(s.nnz_lu(), 0);
   for (size_t t = 0; t < tgt.size(); ++t) {
     const int c0 = s.tgt_cptr[t], c1 = s.tgt_cptr[t + 1];
+    const int te = s.tgt_entry[t];
+    const bool fill_first = s.lu2y[te] < 0 && !touched[te];
+    touched[te] = 1;
     int rest = -1;
     if (c1 - c0 > 1) {
       rest = (int)con.size();
       for (int c = c0 + 1; c < c1; ++c) con.push_back(make_int2(s.con_l[c], s.con_u[c]));
       con.push_back(make_int2(-1, -1));
     }
-    tgt[t] = make_int4(s.tgt_entry[t], s.con_l[c0], s.con_u[c0], rest);
+    tgt[t] = make_int4(te | (fill_first ? kFillFirst : 0), s.con_l[c0], s.con_u[c0], rest);
   }
   if (con.empty()) con.push_back(make_int2(-1, -1));
   UP(fwd, fwd_rec);

@@ -404,7 +404,9 @@ struct Plan {
     blk = dim3(kRowThreads);
     const dim3 gf((B + of.S - 1) / of.S), gsv((B + os.S - 1) / os.S);
     red = (((size_t)threads_s * BS * sizeof(TF) + 15) & ~(size_t)15) + (size_t)kSweepStage * 16;
-    ring = of.ring ? (size_t)threads_f * FactorPipe<TF>::bytes : 0;
+    ring = !of.ring ? 0
+                    : (size_t)threads_f * (of.S == 32 && BS == 2 ? FactorWarp<TF>::bytes
+                                                                  : FactorPipe<TF>::bytes);
     auto rowk = [&](const void* fn) {
       return Launch{fn, rows, blk, 0, {&S, &w, &sb}};
     };

@@ -14,6 +14,10 @@ constexpr int kPQLimit = 3;
 // Krylov basis vectors per GMRES cycle (restart m <= kMaxJ - 1).
 constexpr int kMaxJ = 64;
 // Half width of the sine / cosine table: angles j 2^-7 for |j| <= kTrigHalf.
+// A target record whose entry index carries this bit is the first update of
+// a fill entry of the factor: it starts from zero (no Jacobian value is
+// written there and none is read).
+constexpr int kFillFirst = 1 << 30;
 constexpr int kTrigHalf = 512;  // = fx::kHalf (fixtrig.h)
 // Size of the fixed scratch array used by pf_solve_noalloc.
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;

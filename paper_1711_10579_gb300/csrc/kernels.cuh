@@ -293,10 +293,7 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
 #pragma unroll 2
     for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
       const int yi = S.lu2y[e];
-      if (yi < 0) {  // fill entry
-        put(e, 0.f, 0.f, 0.f, 0.f);
-        continue;
-      }
+      if (yi < 0) continue;  // fill entry: the factor starts it from zero
       const int j = S.lu_col[e];
       const float2 y = S.y32[yi];
       if (j == i) {
@@ -359,8 +356,9 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
     for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
       const int j = S.lu_col[e];
       const int yi = S.lu2y[e];
+      if (yi < 0) continue;  // fill entry: the factor starts it from zero
       double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
-      if (yi >= 0) {
+      {
         const double yx = Y[yi].x, yy = Y[yi].y;
         if (j != i) {
           const int tj = tp[j * ts];
@@ -497,10 +495,11 @@ __device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, 
   for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
     const int j = S.lu_col[e];
     const int yi = S.lu2y[e];
+    if (yi < 0) continue;  // fill entry: the factor starts it from zero
     TF blk[36];
 #pragma unroll
     for (int k = 0; k < 36; ++k) blk[k] = TF(0);
-    if (yi >= 0) {
+    {
       const int maskj = S.btype[j] & 7;
       const bool srcj = (S.btype[j] & 8) != 0;
 #pragma unroll
@@ -1124,7 +1123,13 @@ __device__ __noinline__ void factor_run(const FactorArgs<TF> S, const Team tm, i
 #pragma unroll
           for (int u = 0; u < R; ++u) {
             if (r[u].x >= 0) {
-              blk_load<BS>(blk(r[u].x), c[u]);
+              if (r[u].x & kFillFirst) {
+                r[u].x &= ~kFillFirst;
+#pragma unroll
+                for (int q = 0; q < BB; ++q) c[u][q] = TF(0);
+              } else {
+                blk_load<BS>(blk(r[u].x), c[u]);
+              }
               blk_load<BS>(blk(r[u].y), lv[u]);
               blk_load<BS>(blk(r[u].z), uv[u]);
             }
@@ -1249,13 +1254,18 @@ __device__ __noinline__ void factor_pipe(const FactorArgs<TF> S, const Team tm, 
   };
   // step 2: r = {e, L entry, U entry, rest}: A_e -= L U, then the rest
   auto fetch2 = [&](int d, int4 r) {
-    fetch_blk(d, 0, r.x);
+    if (!(r.x & kFillFirst)) fetch_blk(d, 0, r.x);
     fetch_blk(d, 1, r.y);
     fetch_blk(d, 2, r.z);
   };
   auto work2 = [&](int d, int4 r) {
     TF c[BB], lv[BB], uv[BB];
-    read_blk(d, 0, c);
+    if (r.x & kFillFirst) {
+#pragma unroll
+      for (int q = 0; q < BB; ++q) c[q] = TF(0);
+    } else {
+      read_blk(d, 0, c);
+    }
     read_blk(d, 1, lv);
     read_blk(d, 2, uv);
     blk_msub<2>(c, lv, uv);
@@ -1269,7 +1279,7 @@ __device__ __noinline__ void factor_pipe(const FactorArgs<TF> S, const Team tm, 
         blk_msub<2>(c, l2, u2);
       }
     }
-    blk_store<2>(gblk(r.x), c);
+    blk_store<2>(gblk(r.x & ~kFillFirst), c);
   };
   fetch_recs(S.fac_rec + S.fac_ptr[l0], count(S.fac_ptr[l0 + 1] - S.fac_ptr[l0]));
   for (int l = l0; l < l1; ++l) {
@@ -1290,6 +1300,166 @@ __device__ __noinline__ void factor_pipe(const FactorArgs<TF> S, const Team tm, 
   cp_wait<0>();
 }
 
+// Depth of factor_warp's per-thread ring of items (2x2 blocks) and its
+// shared memory per thread: D slots of three blocks, no records.
+template <typename TF>
+struct FactorWarp {
+  static constexpr int D = sizeof(TF) == 4 ? 8 : 4;    // items in flight per warp
+  static constexpr int NV = 4 * (int)sizeof(TF) / 16;  // 16-byte pieces per block
+  static constexpr int bytes = D * 3 * NV * 16;
+};
+
+// The factorisation of factor_pipe with the 32 lanes of a warp on 32
+// scenarios of the same item (S = 32): every block load is one contiguous
+// 32-scenario segment and the item records are the same for the whole warp.
+// A warp takes the items w, w + W, ... of a step (W warps); lane j loads the
+// record of the warp's item 32 b + j, and the record of any item in flight is
+// broadcast from the two batches held in registers, so the shared-memory ring
+// holds block data only and keeps D items per warp in flight.  The 2x2
+// pivot block is inverted in closed form (adjugate over the determinant); a
+// zero or non-finite determinant or inverse marks the scenario singular.
+template <typename TF>
+__device__ __noinline__ void factor_warp(const FactorArgs<TF> S, const Team tm, int l0, int l1) {
+  if (l0 >= l1) return;
+  using P = FactorWarp<TF>;
+  constexpr int D = P::D, NV = P::NV, BB = 4;
+  static_assert(D < 32, "an item in flight lies in one of two record batches");
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool on = lane < tm.ns && ((tm.act >> lane) & 1u);
+  const int gs = tm.s0 + lane;
+  const int T = blockDim.x;
+  uint4* R = reinterpret_cast<uint4*>(S.ring);
+  auto at = [&](int d, int c, int v) { return R + ((d * 3 + c) * NV + v) * T + threadIdx.x; };
+  auto gblk = [&](int e) { return S.lu + ((size_t)e * S.B + gs) * BB; };
+  auto fetch_blk = [&](int d, int c, int e) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cp16(at(d, c, v), gblk(e) + v * (16 / sizeof(TF)));
+  };
+  auto read_blk = [&](int d, int c, TF (&a)[BB]) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const uint4 q = *at(d, c, v);
+      const TF* t = reinterpret_cast<const TF*>(&q);
+#pragma unroll
+      for (int k = 0; k < 16 / (int)sizeof(TF); ++k) a[v * (16 / sizeof(TF)) + k] = t[k];
+    }
+  };
+  const int4 none = make_int4(-1, 0, 0, -1);
+  // items of a step for this warp, and lane's record of batch b
+  auto count = [&](int n) { return n > wid ? (n - wid + nw - 1) / nw : 0; };
+  auto batch = [&](const int4* rec, int K, int b) {
+    const int k = 32 * b + lane;
+    return k < K ? __ldg(rec + wid + (size_t)k * nw) : none;
+  };
+  auto bcast = [&](int4 x, int src) {
+    return make_int4(__shfl_sync(0xffffffffu, x.x, src), __shfl_sync(0xffffffffu, x.y, src),
+                     __shfl_sync(0xffffffffu, x.z, src), __shfl_sync(0xffffffffu, x.w, src));
+  };
+  // one step: fetch(d, r) requests the blocks of record r into slot d,
+  // work(d, r) computes the item and stores its result; first = the
+  // warp's first record batch, loaded before the barrier that precedes it
+  auto step = [&](const int4* rec, int K, int4 first, auto fetch, auto work) {
+    int4 ra = first, rb = K > 32 ? batch(rec, K, 1) : none;
+    int base = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (k < K) {
+        const int4 r = bcast(ra, k);
+        if (on) fetch(k, r);
+      }
+      cp_commit();
+    }
+    for (int k = 0; k < K; ++k) {
+      cp_wait<D - 1>();
+      const int4 r = bcast(ra, k - base);
+      if (on) work(k % D, r);
+      const int k2 = k + D;
+      if (k2 < K) {
+        const int o = k2 - base;
+        const int4 r2 = bcast(o < 32 ? ra : rb, o & 31);
+        if (on) fetch(k % D, r2);
+      }
+      cp_commit();
+      if (k + 1 - base == 32) {
+        ra = rb;
+        base += 32;
+        rb = base + 32 < K ? batch(rec, K, base / 32 + 1) : none;
+      }
+    }
+  };
+  // step 1: r = {e, k, diag(k)}: U_kk^-1 for the diagonal, else L_ik = A_ik U_kk^-1
+  auto fetch1 = [&](int d, int4 r) {
+    fetch_blk(d, 0, r.z);
+    if (r.x != r.z) fetch_blk(d, 1, r.x);
+  };
+  auto work1 = [&](int d, int4 r) {
+    TF a[BB];
+    read_blk(d, 0, a);
+    const TF det = a[0] * a[3] - a[1] * a[2];
+    const TF rd = TF(1) / det;
+    TF di[BB] = {a[3] * rd, -a[1] * rd, -a[2] * rd, a[0] * rd};
+    if (r.x == r.z) {
+      if (!(det != TF(0)) || !isfinite(di[0]) || !isfinite(di[1]) || !isfinite(di[2]) ||
+          !isfinite(di[3]))
+        S.flag[gs] = 1;
+      blk_store<2>(S.uinv + ((size_t)r.y * S.B + gs) * BB, di);
+    } else {
+      TF x[BB], lk[BB];
+      read_blk(d, 1, x);
+      blk_mul<2>(x, di, lk);
+      blk_store<2>(gblk(r.x), lk);
+    }
+  };
+  // step 2: r = {e, L entry, U entry, rest}: A_e -= L U, then the rest
+  auto fetch2 = [&](int d, int4 r) {
+    if (!(r.x & kFillFirst)) fetch_blk(d, 0, r.x);
+    fetch_blk(d, 1, r.y);
+    fetch_blk(d, 2, r.z);
+  };
+  auto work2 = [&](int d, int4 r) {
+    TF c[BB], lv[BB], uv[BB];
+    if (r.x & kFillFirst) {
+#pragma unroll
+      for (int q = 0; q < BB; ++q) c[q] = TF(0);
+    } else {
+      read_blk(d, 0, c);
+    }
+    read_blk(d, 1, lv);
+    read_blk(d, 2, uv);
+    blk_msub<2>(c, lv, uv);
+    if (r.w >= 0) {
+      for (int q = r.w;; ++q) {
+        const int2 cq = __ldg(S.con + q);
+        if (cq.x < 0) break;
+        TF l2[BB], u2[BB];
+        blk_load<2>(gblk(cq.x), l2);
+        blk_load<2>(gblk(cq.y), u2);
+        blk_msub<2>(c, l2, u2);
+      }
+    }
+    blk_store<2>(gblk(r.x & ~kFillFirst), c);
+  };
+  int f0 = S.fac_ptr[l0], nf = S.fac_ptr[l0 + 1] - f0;
+  int4 first = batch(S.fac_rec + f0, count(nf), 0);
+  for (int l = l0; l < l1; ++l) {
+    step(S.fac_rec + f0, count(nf), first, fetch1, work1);
+    const int t0 = S.tgt_ptr[l], nt = S.tgt_ptr[l + 1] - t0;
+    first = batch(S.tgt_rec + t0, count(nt), 0);
+    cp_wait<0>();
+    __syncthreads();
+    if (nt > 0) {
+      step(S.tgt_rec + t0, count(nt), first, fetch2, work2);
+      cp_wait<0>();
+    }
+    if (l + 1 < l1) {
+      f0 = S.fac_ptr[l + 1];
+      nf = S.fac_ptr[l + 2] - f0;
+      first = batch(S.fac_rec + f0, count(nf), 0);
+    }
+    if (nt > 0) __syncthreads();
+  }
+}
+
 template <int BS, typename TF, bool CL>
 __device__ __forceinline__ void factor_levels(const DevSys& S, const DevWork& w, const Team& tm,
                                               int l0, int l1, unsigned char* ring) {
@@ -1305,6 +1475,10 @@ __device__ __forceinline__ void factor_levels(const DevSys& S, const DevWork& w,
   f.con = S.con;
   f.ring = ring;
   if constexpr (BS == 2 && !CL) {
+    if (tm.S == 32 && ring) {
+      factor_warp<TF>(f, tm, l0, l1);
+      return;
+    }
     if (tm.S > 1 && ring) {
       factor_pipe<TF>(f, tm, l0, l1);
       return;

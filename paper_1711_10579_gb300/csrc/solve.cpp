@@ -523,7 +523,7 @@ int autotune(pf_case c, int B, pf_opts* io) {
   const int max_threads = (c->bs == 2 && nr) ? 512 : 256;
   float best = 1e30f, best_f = 1e30f, best_s = 1e30f;
   int bestS = 0, bestT = 0, bestS_s = 0, bestT_s = 0;
-  for (int S : {1, 2, 4, 8, 16}) {
+  for (int S : {1, 2, 4, 8, 16, 32}) {
     if (S > 8 && (!nr || 2 * S > B)) continue;
     for (int T : {128, 256, 512}) {
       if (T > max_threads) continue;

@@ -219,7 +219,7 @@ def test_edge_cases(pf, ctx):
 # batches of scenarios
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("B,S", [(37, 2), (64, 4), (512, 0)])
+@pytest.mark.parametrize("B,S", [(37, 2), (64, 4), (100, 32), (512, 0)])
 def test_batch_matches_oracle_and_single(pf, ctx, B, S):
     case = cases.case_2000bus(0)
     p_load, q_load, p_gen = cases.scenario_loads(case, B, seed=11)
