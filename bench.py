@@ -35,12 +35,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "converged solves/sec at 1e-8 pu mismatch"
 B_MAIN = 4864
-# DRAM traffic of one sweep launch (k_solve: forward + backward sweeps of every
-# scenario of the batch, first Newton step), per scenario, from the ncu capture
-# summarised in profiles/k_solve_mesh10000x608.md (608 scenarios; traffic
-# scales with the scenarios of a launch).  Valid only for the sources it was
-# measured on (sha256 prefix of csrc/batch.cu + csrc/kernels.cuh).
-NCU_TRAFFIC = {"sources_sha256": "22df78494f6b7caa", "bytes_per_scenario_pass": 831.92e6 / 608}
+ORACLE_SAMPLE = 16  # results of the timed step checked against the oracle
+# DRAM traffic per scenario-unit of each phase kernel, from ncu captures of
+# the 608-scenario batch (traffic scales with the scenarios of a launch).
+# Valid only for the kernel sources each was measured on (sha256 prefix of
+# csrc/batch.cu + csrc/kernels.cuh); otherwise the traffic is reported as null.
+NCU_TRAFFIC = {
+    "k_solve": {"sources_sha256": "22df78494f6b7caa", "bytes_per_unit": 831.92e6 / 608},
+    "k_factor": {"sources_sha256": "22df78494f6b7caa", "bytes_per_unit": 1245.2e6 / 608},
+}
 WORKLOAD = (f"mesh10000 x {B_MAIN} load scenarios per step, batched Newton-Raphson, "
             "FP32 LU + FP64 mismatch/refinement/update, one CUDA graph per batch")
 
@@ -106,27 +109,41 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes_per_iteration(st, B=1, refine=1, s_f=4):
-    """Minimum bytes one mixed-precision NR iteration of one scenario moves.
+def jacobian_nnz(case):
+    """Scalar non-zeros of the polar Jacobian of Eq. 10 (J1..J4 blocks): one
+    per Ybus entry (i, j) with i, j not the slack for dP/d delta, plus one
+    for dP/d|V| where j is PQ, dQ/d delta where i is PQ, dQ/d|V| where both
+    are PQ.  Counted from the branch list and bus types."""
+    t = np.asarray(case.bus_type)
+    f, g = np.asarray(case.br_from), np.asarray(case.br_to)
+    pairs = np.unique(np.concatenate([np.stack([f, g], 1), np.stack([g, f], 1),
+                                      np.stack([np.arange(case.n_bus)] * 2, 1)]), axis=0)
+    i, j = pairs[:, 0], pairs[:, 1]
+    ns = (t[i] != 0) & (t[j] != 0)
+    pi, pj = t[i] == 2, t[j] == 2
+    return int((ns * (1 + pj + pi + (pi & pj))).sum())
 
-    Single phase, with the per-scenario share of the shared Ybus (values and
-    indices divided by B).  mismatch: Ybus + row pointers, V, specified S,
-    mismatch; assembly: Jacobian values written once; factor: L+U values
-    read and written once; each triangular-solve pass: L+U values and 3
-    vectors; each refinement: Ybus, V and step for J dx, L+U again, 4 FP64
-    vectors; update: |V|, angle, V.
+
+def scope_bytes(case, st, B):
+    """Algorithmic bytes per unit of each phase kernel of a mixed-precision
+    Newton-Raphson step, as the hot-path scope table counts them (Ybus and
+    its indices are shared by the B scenarios):
+
+    k_mismatch (a1 + a2), per scenario-iteration: Ybus values and column
+      indices, row pointers; V, specified S and the mismatch per bus (16 B
+      each); the Jacobian's scalar non-zeros written in FP32;
+    k_factor, per scenario-factorisation: the factor's values read and
+      written once (nnz_LU scalars of the 2x2 blocks, FP32);
+    k_solve, per scenario-pass: the factor's values once and three FP32
+      vectors of the N unknowns;
+    k_update (a4), per scenario-iteration: 40 B per bus.
     """
     n, nnz_y, N = st["n_bus"], st["nnz_y"], st["n_unknowns"]
-    nnz_lu = st["nnz_lu"] * 4  # scalar values of the 2x2 blocks
-    nnz_j = nnz_y * 4
-    ybus = nnz_y * (16 + 4) / B + 4 * (n + 1) / B
-    a1 = ybus + n * (16 + 16 + 16)
-    a2 = nnz_j * s_f
-    fac = nnz_lu * 2 * s_f
-    solve = nnz_lu * s_f + 3 * N * s_f
-    ref = ybus + n * 16 * 2 + nnz_lu * s_f + 4 * N * 8
-    upd = n * (16 + 16 + 8)
-    return a1 + a2 + fac + solve * (1 + refine) + ref * refine + upd
+    nnz_lu = st["nnz_lu"] * 4
+    a1 = nnz_y * (16 + 4) / B + 4 * (n + 1) / B + n * (16 + 16 + 16)
+    a2 = jacobian_nnz(case) * 4
+    return {"k_mismatch": a1 + a2, "k_factor": nnz_lu * 2 * 4,
+            "k_solve": nnz_lu * 4 + 3 * N * 4, "k_update": n * (16 + 16 + 8)}
 
 
 def _sources_sha():
@@ -138,22 +155,46 @@ def _sources_sha():
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(B):
-    """Measured DRAM bytes of one sweep launch of B scenarios, if the sources
-    are the ones profiled."""
-    per = NCU_TRAFFIC["bytes_per_scenario_pass"]
-    if per is None or _sources_sha() != NCU_TRAFFIC["sources_sha256"]:
+def _ncu_traffic(kernel, units):
+    """Measured DRAM bytes of a launch of `kernel` over `units` scenario-units,
+    if the sources are the ones profiled (else None)."""
+    rec = NCU_TRAFFIC.get(kernel)
+    if rec is None or _sources_sha() != rec["sources_sha256"]:
         return None
-    return per * B
+    return rec["bytes_per_unit"] * units
 
 
-def sweep_bytes_per_scenario_pass(st):
-    """Minimum bytes of one forward + backward sweep of one scenario: the
-    off-diagonal L and U blocks (FP32 2x2) and the inverse diagonal blocks
-    read once, the FP64 right-hand side read, the FP64 step written, the
-    FP32 solve vector written once and read once."""
-    n, nnz = st["n_bus"], st["nnz_lu"]
-    return (nnz - n) * 16 + n * 16 + n * 16 + n * 16 + n * 8 * 2
+# phase of pf_profile_solve -> (kernel, unit counted per scenario)
+PHASE_KERNELS = {"mismatch_jacobian": ("k_mismatch", "iterations+1"),
+                 "factor": ("k_factor", "iterations"),
+                 "triangular_solves": ("k_solve", "linear_iterations"),
+                 "update": ("k_update", "iterations")}
+
+
+def kernel_rooflines(case, st, B, phase_us, pinfo, peak):
+    """Per-kernel roofline of one batch: algorithmic bytes of every unit the
+    batch processed / the kernel's device time (CUDA events between the phase
+    kernels), against the measured copy bandwidth."""
+    per = scope_bytes(case, st, B)
+    it = pinfo["iterations"].astype(float)
+    units = {"iterations": float(it.sum()), "iterations+1": float((it + 1).sum()),
+             "linear_iterations": float(pinfo["linear_iterations"].sum())}
+    launches = {"iterations": float(it.max()), "iterations+1": float(it.max() + 1),
+                "linear_iterations": float(it.max())}
+    out = {}
+    for ph, (kern, u) in PHASE_KERNELS.items():
+        t = phase_us[ph] * 1e-6
+        if t <= 0 or units[u] <= 0:
+            continue
+        ach = per[kern] * units[u] / t / 1e9
+        out[kern] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "bytes_per_unit": per[kern], "unit_of_work":
+                     "scenario-" + {"iterations": "iteration", "iterations+1": "iteration",
+                                    "linear_iterations": "pass"}[u],
+                     "units": units[u], "device_us": phase_us[ph],
+                     "launch_us": phase_us[ph] / launches[u],
+                     "share_of_phases": phase_us[ph] / sum(phase_us.values())}
+    return out
 
 
 def _case():
@@ -184,6 +225,7 @@ def _oracle_init():
     _W["O"] = O
     _W["case"] = _case()
     _W["Y"] = O.ybus_single(_W["case"])
+    _W["named"] = {}
 
 
 def _oracle_solve(loads):
@@ -191,6 +233,68 @@ def _oracle_solve(loads):
     r = O.newton_polar(case.with_loads(*loads), Y=_W["Y"])
     assert r["converged"]
     return r["iterations"]
+
+
+def named_case(key):
+    """The seeded grids the benchmark and its variants solve, by name."""
+    from paper_1711_10579_gb300 import cases
+
+    name, seed = key
+    return {"mesh14": cases.case_14bus, "mesh10000": cases.case_10000bus,
+            "mesh2000": cases.case_2000bus, "feeder8000": cases.case_feeder8000,
+            "mesh10000_heavy": heavy_case,
+            "mesh10000_qlim": lambda s: cases.with_q_limits(cases.case_10000bus(s), 1),
+            }[name](seed)
+
+
+def heavy_case(seed=0):
+    """The 10,000-bus grid loaded 5.3 times as heavily (DC angle target 1.6
+    rad instead of 0.3; lowest |V| about 0.36 pu, near the nose of the
+    loading curve), with 8 Newton steps instead of 5."""
+    from paper_1711_10579_gb300 import cases
+
+    return cases.transmission_case(10_000, 13_500, 2_000, seed, name="mesh10000_heavy",
+                                   max_angle=HEAVY_ANGLE)
+
+
+HEAVY_ANGLE = 1.6
+HEAVY_SIGMA = 0.1  # lognormal spread of its scenarios' loads (0.2 puts some past the nose)
+
+
+def _oracle_result(job):
+    """FP64 oracle solution of one result to check: job = (case name and seed,
+    or a case object; loads; reactive limits on).  Returns (|V|, angle) per
+    bus (per node and phase for a feeder, absent phases 0)."""
+    O = _W["O"]
+    key, loads, qlim = job
+    if isinstance(key, tuple):
+        if key not in _W["named"]:
+            _W["named"][key] = named_case(key)
+        case = _W["named"][key]
+    else:
+        case = key
+    if hasattr(case, "n_node"):
+        r = O.newton_cim(case.with_loads(np.reshape(loads[0], (-1, 3)),
+                                         np.reshape(loads[1], (-1, 3))))
+        V = r["V"]
+        return r["converged"], np.abs(V).reshape(-1), np.where(np.abs(V) > 0, np.angle(V), 0.0).reshape(-1)
+    c = case.with_loads(*loads)
+    r = O.newton_polar_qlim(c) if qlim else O.newton_polar(c)
+    return r["converged"], r["vm"], r["va"]
+
+
+def oracle_errors(pool, jobs, results):
+    """Largest |dV| (pu) and |d theta| (rad) of GPU results against the FP64
+    oracle's solutions of the same inputs, per result and overall."""
+    refs = pool.map(_oracle_result, jobs, chunksize=1)
+    per = []
+    for (ok, rvm, rva), (vm, va) in zip(refs, results):
+        vm, va = np.asarray(vm).reshape(-1), np.asarray(va).reshape(-1)
+        dv = float(np.max(np.abs(vm - rvm)))
+        dth = float(np.max(np.abs(np.angle(np.exp(1j * (va - rva))))))
+        per.append([round(dv, 12), round(dth, 12), bool(ok)])
+    return {"max_dv_pu": max(p[0] for p in per), "max_dtheta_rad": max(p[1] for p in per),
+            "all_oracle_converged": all(p[2] for p in per), "per_result": per}
 
 
 def _host_cores():
@@ -266,22 +370,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline():
+def cpu_baseline(pool, cores):
     """The oracle as it stands on a bounded sample of the same workload,
-    one process per host core: 4 scenarios per core (about 0.15 s of one
+    one process per host core: 4 scenarios per core (about 0.3 s of one
     core each on this grid)."""
     case = _case()
-    pool, cores = _oracle_pool()
-    try:
-        n = 4 * cores
-        pl, ql, pg = _batch(case, n, seed=77)
-        work = [(pl[b], ql[b], pg[b]) for b in range(n)]
-        t0 = time.perf_counter()
-        pool.map(_oracle_solve, work, chunksize=1)
-        dt = time.perf_counter() - t0
-    finally:
-        pool.close()
-        pool.join()
+    n = 4 * cores
+    pl, ql, pg = _batch(case, n, seed=77)
+    work = [(pl[b], ql[b], pg[b]) for b in range(n)]
+    t0 = time.perf_counter()
+    pool.map(_oracle_solve, work, chunksize=1)
+    dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": f"{n} scenarios of the 10,000-bus grid in {dt:.2f} s on {cores} "
                       "processes (one per host core; start-up not timed)"}
@@ -291,7 +390,10 @@ def cpu_baseline():
 # variants
 # ----------------------------------------------------------------------------
 
-def _device_solves(pf, c, torch, dev, B, pl, ql, pg, opts, reps=5, flush=None):
+def _device_solves(pf, c, torch, dev, B, pl, ql, pg, opts, reps=5, flush=None, check=None):
+    """Times `reps` device-buffer batch solves; with check = (pool, case key)
+    the FP64 oracle's error of up to 4 of the results (evenly spaced) is
+    added as oracle_err."""
     d = [None if a is None else torch.tensor(a, device=dev) for a in (pl, ql, pg)]
     slots = pl.shape[1]
     vm = torch.zeros((B, slots), dtype=torch.float64, device=dev)
@@ -313,23 +415,47 @@ def _device_solves(pf, c, torch, dev, B, pl, ql, pg, opts, reps=5, flush=None):
     ms = float(np.median(times))
     ok = int((inf["status"] == 0).sum())
     its = float(inf["iterations"].mean())
-    return {"solves_per_s": ok / (ms * 1e-3), "ms_per_launch": ms,
-            "latency_ms": {"p50": float(np.percentile(times, 50)),
-                           "p99": float(np.percentile(times, 99))},
-            "ms_per_newton_iter": ms / max(1.0, its), "newton_iters_mean": its,
-            "linear_iters_mean": float(inf["linear_iterations"].mean()),
-            "all_converged": bool(ok == B), "B": B}
+    out = {"solves_per_s": ok / (ms * 1e-3), "ms_per_launch": ms,
+           "latency_ms": {"p50": float(np.percentile(times, 50)),
+                          "p99": float(np.percentile(times, 99))},
+           "ms_per_newton_iter": ms / max(1.0, its), "newton_iters_mean": its,
+           "linear_iters_mean": float(inf["linear_iterations"].mean()),
+           "all_converged": bool(ok == B), "B": B}
+    if check is not None:
+        pool, key, qlim = check
+        idx = np.unique(np.linspace(0, B - 1, min(B, 4)).astype(int))
+        jobs = [(key, tuple(None if a is None else a[b] for a in (pl, ql, pg)), qlim)
+                for b in idx]
+        res = list(zip(vm[idx].cpu().numpy(), va[idx].cpu().numpy()))
+        out["oracle_err"] = dict(oracle_errors(pool, jobs, res), scenarios=idx.tolist())
+    return out
 
 
-def variants(pf, ctx, torch, dev, flush):
+def variants(pf, ctx, torch, dev, flush, pool):
     from paper_1711_10579_gb300 import cases
 
     out = {}
+    # the 14-bus mesh: one batch of 4,864 load scenarios, and single solves
+    case = named_case(("mesh14", 0))
+    c = pf.pf_create_case(ctx, case)
+    pl, ql, pg = _batch(case, B_MAIN, seed=5)
+    pf.pf_autotune(c, B_MAIN, pf.make_opts())
+    out[f"mesh14_x{B_MAIN}_batched_mixed"] = _device_solves(
+        pf, c, torch, dev, B_MAIN, pl, ql, pg, pf.make_opts(), reps=10, flush=flush,
+        check=(pool, ("mesh14", 0), False))
+    for prec, nm in ((pf.PF_FP64, "fp64"), (pf.PF_MIXED, "mixed")):
+        out[f"mesh14_single_nr_{nm}"] = _device_solves(
+            pf, c, torch, dev, 1, pl[:1], ql[:1], pg[:1], pf.make_opts(precision=prec), reps=20,
+            flush=flush, check=(pool, ("mesh14", 0), False))
+    pf.pf_destroy_case(c)
+
     case = _case()
+    key = ("mesh10000", 0)
     c = pf.pf_create_case(ctx, case)
     pl, ql, pg = _batch(case, 1, seed=7)
     out["mesh10000_single_nr_mixed"] = _device_solves(
-        pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_MIXED), reps=20, flush=flush)
+        pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_MIXED), reps=20, flush=flush,
+        check=(pool, key, False))
     out["mesh10000_single_nr_mixed"]["launch"] = pf.pf_launch_config(c, pf.make_opts())
     prof, _ = pf.pf_profile_solve(c, pf.make_opts())
     out["mesh10000_single_nr_mixed"]["phase_us"] = {k: round(v, 1) for k, v in prof.items()}
@@ -343,29 +469,51 @@ def variants(pf, ctx, torch, dev, flush):
         "mean_loss_p_pu": float(fl["loss"][:, 0].mean()),
         "note": "pf_branch_flows with host buffers (copies inside)"}
     out["mesh10000_single_nr_fp64"] = _device_solves(
-        pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_FP64), reps=20, flush=flush)
+        pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_FP64), reps=20, flush=flush,
+        check=(pool, key, False))
     for Bv, prec, nm in ((608, pf.PF_MIXED, "mixed"), (2432, pf.PF_MIXED, "mixed"),
                          (B_MAIN, pf.PF_FP64, "fp64")):
         plb, qlb, pgb = _batch(case, Bv, seed=21)
         pf.pf_autotune(c, Bv, pf.make_opts(precision=prec))
         out[f"mesh10000_x{Bv}_batched_{nm}"] = _device_solves(
             pf, c, torch, dev, Bv, plb, qlb, pgb, pf.make_opts(precision=prec), reps=3,
-            flush=flush)
+            flush=flush, check=(pool, key, False))
     for prec, nm in ((pf.PF_MIXED, "mixed"), (pf.PF_FP64, "fp64")):
         out[f"mesh10000_single_nk_{nm}"] = _device_solves(
             pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(method=pf.PF_NK, precision=prec),
-            reps=1)
+            reps=1, check=(pool, key, False))
         out[f"mesh10000_single_nk_bicgstab_{nm}"] = _device_solves(
             pf, c, torch, dev, 1, pl, ql, pg,
-            pf.make_opts(method=pf.PF_NK, krylov=1, precision=prec, gmres_max_iter=2000), reps=1)
+            pf.make_opts(method=pf.PF_NK, krylov=1, precision=prec, gmres_max_iter=2000), reps=1,
+            check=(pool, key, False))
+    pf.pf_destroy_case(c)
+
+    # heavier loading: the mixed-precision steps slow down and the on-demand
+    # FP64 refinement is taken
+    case = named_case(("mesh10000_heavy", 0))
+    c = pf.pf_create_case(ctx, case)
+    plh, qlh, pgh = cases.scenario_loads(case, 2432, seed=31, sigma=HEAVY_SIGMA)
+    pf.pf_autotune(c, 2432, pf.make_opts())
+    r = _device_solves(pf, c, torch, dev, 2432, plh, qlh, pgh, pf.make_opts(), reps=3,
+                       flush=flush, check=(pool, ("mesh10000_heavy", 0), False))
+    r["max_angle_rad"] = HEAVY_ANGLE
+    r["load_sigma"] = HEAVY_SIGMA
+    r["load_scale"] = case.load_scale
+    out["mesh10000_heavy_x2432_batched_mixed"] = r
+    # the same with the FP64 refinement of every step below refine_below
+    r = _device_solves(pf, c, torch, dev, 2432, plh, qlh, pgh, pf.make_opts(refine_stall=0.0),
+                       reps=3, flush=flush, check=(pool, ("mesh10000_heavy", 0), False))
+    r["refine_stall"] = 0.0
+    out["mesh10000_heavy_x2432_batched_mixed_refine_always"] = r
     pf.pf_destroy_case(c)
 
     # reactive limits of PV buses enforced (rounds of PV -> PQ switching)
-    qcase = cases.with_q_limits(case, 1)
+    qkey = ("mesh10000_qlim", 0)
+    qcase = named_case(qkey)
     c = pf.pf_create_case(ctx, qcase)
     plq, qlq, pgq = _batch(qcase, 608, seed=21)
     r = _device_solves(pf, c, torch, dev, 608, plq, qlq, pgq, pf.make_opts(q_limits=1), reps=3,
-                       flush=flush)
+                       flush=flush, check=(pool, qkey, True))
     _, _, iq = pf.pf_solve_batch(c, plq, qlq, pgq, pf.make_opts(q_limits=1))
     r["q_switched_mean"] = float(iq["q_switched"].mean())
     r["q_rounds_max"] = int(iq["q_rounds"].max())
@@ -373,17 +521,19 @@ def variants(pf, ctx, torch, dev, flush):
     pf.pf_destroy_case(c)
 
     case = cases.case_2000bus(0)
+    key = ("mesh2000", 0)
     c = pf.pf_create_case(ctx, case)
     pl, ql, pg = cases.scenario_loads(case, 512, seed=11)
     tuned = pf.pf_autotune(c, 512, pf.make_opts())
     out["mesh2000_x512_batched_mixed"] = _device_solves(pf, c, torch, dev, 512, pl, ql, pg,
-                                                        pf.make_opts(), flush=flush)
+                                                        pf.make_opts(), flush=flush,
+                                                        check=(pool, key, False))
     out["mesh2000_x512_batched_mixed"]["tuned"] = {"scen_per_cta": tuned.scen_per_cta,
                                                    "block_threads": tuned.block_threads}
     # a batch of Newton-Krylov solves (one persistent launch)
     out["mesh2000_x64_batched_nk_mixed"] = _device_solves(
         pf, c, torch, dev, 64, pl[:64], ql[:64], pg[:64], pf.make_opts(method=pf.PF_NK), reps=1,
-        flush=flush)
+        flush=flush, check=(pool, key, False))
     pf.pf_destroy_case(c)
 
     case = cases.case_feeder8000(0)
@@ -392,13 +542,14 @@ def variants(pf, ctx, torch, dev, flush):
     for prec, nm in ((pf.PF_FP64, "fp64"), (pf.PF_MIXED, "mixed")):
         out[f"feeder8000_cim_{nm}"] = _device_solves(
             pf, c, torch, dev, 1, pl3.reshape(1, -1), ql3.reshape(1, -1), None,
-            pf.make_opts(precision=prec), reps=10, flush=flush)
+            pf.make_opts(precision=prec), reps=10, flush=flush,
+            check=(pool, ("feeder8000", 0), False))
     pf.pf_destroy_case(c)
-    out["serving"] = serving_stream(pf, ctx)
+    out["serving"] = serving_stream(pf, ctx, pool=pool)
     return out
 
 
-def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9):
+def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9, pool=None):
     """Poisson arrivals, 70% transmission (500-70,000 buses) / 30% feeders
     (1,000-20,000 nodes) from pools of resident cases, mixed precision with
     warm starts.  The offered rate runs first (its sustained rate and
@@ -534,6 +685,10 @@ def main():
         profile_launches(args.profile_launches, args.profile_batch)
         return
 
+    # the oracle's worker processes (spawned), for the error check of the
+    # results and the CPU baseline
+    pool, cores = _oracle_pool() if rank == 0 else (None, 0)
+
     import torch
 
     from paper_1711_10579_gb300 import replicas
@@ -604,21 +759,24 @@ def main():
     value, max_ms, total = replicas.aggregate(float(ms.sum()), converged, dist)
 
     # per-kernel device times of the same batch (events between the phase
-    # kernels, launched one by one), for the roofline of the dominant kernel
+    # kernels, launched one by one, on the library's stream), for the
+    # roofline of every phase kernel; the dominant one heads the line
     phases, pinfo = [], None
     for _ in range(3):
         ph, pinfo = pf.pf_profile_solve(c, opts, B)
         phases.append(ph)
     phase_us = {k: float(np.median([p[k] for p in phases])) for k in phases[0]}
-    passes = float(pinfo["linear_iterations"].sum())  # scenario-passes of the sweeps
-    sweep_b = sweep_bytes_per_scenario_pass(st)
-    t_sweep = phase_us["triangular_solves"] * 1e-6
-    achieved = sweep_b * passes / t_sweep / 1e9
     peak, peak_kind = _peaks()
-    # refinement passes taken (on demand), per Newton iteration
-    its = float(info["iterations"].sum())
-    ref_per_it = float((info["linear_iterations"] - info["iterations"]).sum()) / max(its, 1.0)
-    step_bytes = algorithmic_bytes_per_iteration(st, B=B, refine=ref_per_it) * its / K
+    kr = kernel_rooflines(case, st, B, phase_us, pinfo, peak)
+    dom = max(kr, key=lambda k: kr[k]["device_us"])
+    # algorithmic bytes of the timed steps: every phase kernel's units, plus
+    # the FP64 residuals of the refinements taken (on demand)
+    per = scope_bytes(case, st, B)
+    its = info["iterations"].astype(float)
+    nref = float((info["linear_iterations"] - info["iterations"]).sum())
+    step_bytes = (per["k_mismatch"] * (its + 1).sum() + (per["k_factor"] + per["k_update"]) * its.sum()
+                  + per["k_solve"] * float(info["linear_iterations"].sum())
+                  + nref * (st["nnz_y"] * 20 / B + n * 32 + 4 * st["n_unknowns"] * 8)) / K
     # kernels per step: the call record, the graph's prologue (set-up,
     # mismatch, stop test), one loop body per Newton step of the slowest
     # scenario (refinement flag, factor, sweeps, update, mismatch, stop
@@ -666,23 +824,35 @@ def main():
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                        "note": "per batch step; single-solve latency in variants"},
         "converged": total, "solves": world * B * K,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": _ncu_traffic(B),
-                     "peak_source": peak_kind,
-                     "kernel": "k_solve (forward + backward block sweeps of every scenario)",
-                     "bytes_per_launch": sweep_b * B,
-                     "launch_us": phase_us["triangular_solves"] * B / passes,
-                     "note": "algorithmic bytes of all sweep passes / device time of the "
-                             "sweep launches (CUDA events between the phase kernels of the "
-                             "same batch size, right after the timed region)"},
+        "roofline": dict(kr[dom], kernel=dom, peak_source=peak_kind,
+                         traffic=_ncu_traffic(dom, B),
+                         note="achieved = algorithmic bytes per scenario-unit (hot-path scope "
+                              "table) x units the batch processed / device time of the "
+                              "kernel's launches (CUDA events between the phase kernels of a "
+                              "batch of the same size, right after the timed region); traffic "
+                              "= ncu DRAM bytes per launch of B scenarios"),
+        "kernel_rooflines": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                                 for kk, vv in v.items()} for k, v in kr.items()},
         "phase_us": {k: round(v, 1) for k, v in phase_us.items()},
         "step_algorithmic_gb": step_bytes / 1e9,
         "e2e": e2e, "gpu_launches": launches, "clocks": clk, "wall_s": t_wall,
     }
+    if rank == 0:
+        # the FP64 oracle's error of a sample of the last timed step's results
+        idx = np.unique(np.linspace(0, B - 1, ORACLE_SAMPLE).astype(int))
+        last = batches[W + K - 1]
+        jobs = [(("mesh10000", 0), tuple(a[b] for a in last), False) for b in idx]
+        res = list(zip(d_vm[idx].cpu().numpy(), d_va[idx].cpu().numpy()))
+        line["oracle_err"] = dict(oracle_errors(pool, jobs, res), scenarios=idx.tolist(),
+                                  sample=f"{len(idx)} of the {B} scenarios of the last timed "
+                                         "step, evenly spaced")
     if rank == 0 and not args.no_variants:
-        line["variants"] = variants(pf, ctx, torch, dev, flush)
+        line["variants"] = variants(pf, ctx, torch, dev, flush, pool)
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(pool, cores)
+    if pool is not None:
+        pool.close()
+        pool.join()
     if rank == 0:
         print(json.dumps(line), flush=True)
     pf.pf_destroy_case(c)

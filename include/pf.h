@@ -365,8 +365,16 @@ int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag,
  * reactive limits is PF_ERR_UNSUPPORTED (the rounds wait for the device and
  * keep per-scenario state).  A case whose workspace does not
  * fit the array is rejected with PF_ERR_INVALID and a message giving both
- * sizes (about 370 bytes per bus plus the LU values: single-phase grids of a
- * few tens of thousands of buses fit).
+ * sizes (with the LU values, about 230 bytes per bus in mixed precision and
+ * 350 in FP64 on grids as dense as the 10,000-bus test grid).  The lane
+ * tables of the launch are uploaded by pf_create_case, so a call makes no
+ * host-to-device copy.
+ *
+ * Like pf_solve, a converged call stores its voltages in the case as the warm
+ * start that later calls with opts->warm_start read.  That state is shared
+ * with pf_solve and with served requests of the same case: warm-started
+ * solves of one case that overlap on the GPU may start from a mix of two
+ * solutions, so a caller that warm-starts must not let them overlap.
  *
  * The first call on a device looks up the array's device address; make that
  * first call before any stream capture.  Every call shares the array and the

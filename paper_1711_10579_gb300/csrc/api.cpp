@@ -227,7 +227,6 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
 // (summed across warps through shared memory).
 int SysBuf::lanes_for(int threads, int S, DevSys& out) {
   std::lock_guard<std::mutex> lk(g_mu);
-  out = view;
   const int rows = S > 1 ? threads / S : threads;
   const int key = 2 * rows + (S > 1 ? 1 : 0);
   auto it = g_cache.find(key);
@@ -241,8 +240,24 @@ int SysBuf::lanes_for(int threads, int S, DevSys& out) {
     if (e != cudaSuccess) return cuda_error(e, "uploading lane tables");
     it = g_cache.emplace(key, arr).first;
   }
-  out.g_fwd = it->second[0];
-  out.g_bwd = it->second[1];
+  finish_view(it->second, threads, out);
+  return PF_OK;
+}
+
+int SysBuf::lanes_cached(int threads, int S, DevSys& out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  const int rows = S > 1 ? threads / S : threads;
+  auto it = g_cache.find(2 * rows + (S > 1 ? 1 : 0));
+  if (it == g_cache.end())
+    return set_error(PF_ERR_INVALID, "no lane tables were uploaded for this launch shape");
+  finish_view(it->second, threads, out);
+  return PF_OK;
+}
+
+void SysBuf::finish_view(const std::array<const int8_t*, 2>& g, int threads, DevSys& out) const {
+  out = view;
+  out.g_fwd = g[0];
+  out.g_bwd = g[1];
   // the suffix of factor levels narrow enough for one CTA of `threads`
   int solo = (int)sym.flev_ptr.size() - 1;
   while (solo > 0) {
@@ -252,7 +267,6 @@ int SysBuf::lanes_for(int threads, int S, DevSys& out) {
     --solo;
   }
   out.fac_solo_from = solo;
-  return PF_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -316,9 +330,6 @@ int Workspace::ensure(int kind, int n, long long nnz_lu, int B, int m) {
   }
   A((void**)&w.V, nb * nsl * 16);
   if (kind == PF_SINGLE_PHASE) A((void**)&w.U, nb * 16);
-  if (kind == PF_SINGLE_PHASE) A((void**)&w.uvm32, nb * 16);
-  if (kind == PF_SINGLE_PHASE) A((void**)&w.spec32, nb * 8);
-  A((void**)&w.I, nb * nsl * 16);
   A((void**)&w.dV, nb * nsl * 16);
   if (kind == PF_THREE_PHASE) A((void**)&w.abcd, nb * 12 * 8);
   if (kind == PF_THREE_PHASE) A((void**)&w.qg, nb * 3 * 8);
@@ -503,6 +514,12 @@ int pf_create_case(pf_ctx ctx, const pf_case_desc* desc, pf_case* out) {
   c->bs = c->data.kind == PF_SINGLE_PHASE ? 2 : 6;
   rc = c->nr.build(c->data, c->y, Ordering::MinDegree, true);
   if (rc != PF_OK) return rc;
+  {
+    // the lane tables of the entry point without allocation, uploaded now
+    DevSys unused;
+    rc = c->nr.lanes_for(pf::noalloc_threads(c->bs), 1, unused);
+    if (rc != PF_OK) return rc;
+  }
   rc = c->nk.build(c->data, c->y, Ordering::RCM, false);
   if (rc != PF_OK) return rc;
   // warm-start storage (new numbering of the NR ordering)

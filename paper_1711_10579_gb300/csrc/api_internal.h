@@ -35,8 +35,18 @@ struct SysBuf {
   std::map<int, std::array<const int8_t*, 2>> g_cache;
   std::mutex g_mu;  // the serving thread and callers share g_cache
   int build(const CaseData& c, const Ybus& y, Ordering ord, bool fill);
+  // The view with the lane tables of a launch shape (uploaded on first use
+  // and cached); lanes_cached only looks them up and fails if absent.
   int lanes_for(int threads, int S, DevSys& out);
+  int lanes_cached(int threads, int S, DevSys& out);
+
+ private:
+  void finish_view(const std::array<const int8_t*, 2>& g, int threads, DevSys& out) const;
 };
+
+// Threads per CTA of the entry point without allocation (its lane tables are
+// uploaded when the case is created).
+inline int noalloc_threads(int bs) { return bs == 2 ? 512 : 256; }
 
 // Per-solve device state for up to `cap` scenarios plus staging buffers.
 // A batched Newton-Raphson solve as one CUDA graph (batch.cu): its key is

@@ -108,10 +108,7 @@ struct DevWork {
   double* vm;     // single phase
   double* va;
   double2* V;     // 1 or 3 per row
-  double2* U;     // single phase: V / |V|
-  float4* uvm32;  // single phase: (Re U, Im U, |V|, 0) in FP32 for the Jacobian
-  float2* spec32; // single phase: (P load, Q load) in FP32 for the Jacobian
-  double2* I;     // I = Y V of the last mismatch evaluation
+  double2* U;     // single phase, FP64 solves: V / |V| (null in mixed precision)
   double2* dV;    // refinement: voltage change of the step
   double* abcd;   // three phase: Eq. 23 adjustments, 12 per row
   double* F;      // mismatch, bs per row

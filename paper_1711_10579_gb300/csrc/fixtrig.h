@@ -77,6 +77,31 @@ PF_FX_HD double double_of(uint64_t u) {
 #endif
 }
 
+// FP64 -> FP32 by truncating the significand of the IEEE-754 encoding with
+// integer instructions only (a conversion instruction would run on the FP64
+// pipe).  Within the FP32 normal range the result is v rounded toward zero
+// (|error| < 1 FP32 ulp); magnitudes below 2^-126, zero included, become a
+// zero of the same sign; magnitudes beyond the FP32 range an infinity of the
+// same sign; NaN stays NaN.
+PF_FX_HD float to_f32_trunc(double v) {
+  const uint64_t u = bits_of(v);
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const uint32_t sign = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu;
+  const int e = (int)ex - 1023 + 127;
+  const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const bool nan = ex == 0x7ffu && ((hi & 0xfffffu) | lo) != 0u;
+  uint32_t bits = sign | ((uint32_t)e << 23) | mant;
+  bits = e <= 0 ? sign : bits;
+  bits = e >= 255 ? (sign | 0x7f800000u | (nan ? 0x400000u : 0u)) : bits;
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(bits);
+#else
+  float f;
+  memcpy(&f, &bits, 4);
+  return f;
+#endif
+}
+
 // a as a signed Q60 number (a 2^60 rounded); false when |a| > 4 or a is not
 // finite.
 PF_FX_HD bool to_q60(double a, int64_t* q) {

@@ -55,19 +55,8 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// FP64 -> FP32 by truncating the significand of the IEEE-754 encoding with
-// integer instructions: conversion instructions run on the scarce FP64 pipe
-// of this GPU.  For values of the FP32 copies that feed the Jacobian (within
-// the FP32 normal range: |error| < 1 FP32 ulp); zero, subnormal and
-// non-finite inputs fall back to the conversion instruction.
-__device__ __forceinline__ float to_f32_trunc(double v) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (e <= 0 || e >= 255) return (float)v;
-  return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) |
-                         (lo >> 29));
-}
+// FP64 -> FP32 rounded toward zero by integer instructions (fixtrig.h).
+__device__ __forceinline__ float to_f32_trunc(double v) { return fx::to_f32_trunc(v); }
 
 // |v| as an ordered bit pattern: non-negative doubles order like their bits,
 // and a NaN of either sign maps above +inf.  Integer work only.
@@ -243,79 +232,82 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
   const size_t b = (size_t)i * B + gs;
   const int8_t* tp = w.bt ? w.bt + gs : S.btype;
   const size_t ts = w.bt ? (size_t)B : 1;
-  // FP64 mismatch.  I = sum_j Y_ij V_j as four FMAs per entry.
   const double2 Vi = ldc(w.V + b);
-  double2 I = make_double2(0.0, 0.0);
-  const double2* Y = reinterpret_cast<const double2*>(S.y_val);
-#pragma unroll 4
-  for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
-    const int j = S.y_col[e];
-    const double2 y = Y[e], v = ldc(w.V + (size_t)j * B + gs);
-    I.x = fma(y.x, v.x, I.x);
-    I.x = fma(-y.y, v.y, I.x);
-    I.y = fma(y.x, v.y, I.y);
-    I.y = fma(y.y, v.x, I.y);
-  }
-  w.I[b] = I;
   const double vmi = __ldcg(w.vm + b);
-  const double2 Sc = cmulc(Vi, I);
   const double pl = __ldcg(w.spec + b * 3), ql = __ldcg(w.spec + b * 3 + 1),
                pg = __ldcg(w.spec + b * 3 + 2);
   const double zp = S.zip[3 * i], zi = S.zip[3 * i + 1], zz = S.zip[3 * i + 2];
-  const double shape = fma(fma(zz, vmi, zi), vmi, zp);
   const int t = tp[i * ts];
-  const double f0 = (t != PF_SLACK) ? fma(-pl, shape, pg) - Sc.x : 0.0;
-  const double qgen = (t == kPQLimit) ? __ldcg(w.qsw + b) : S.q_gen[i];
-  const double f1 = (t >= PF_PQ) ? fma(-ql, shape, qgen) - Sc.y : 0.0;
-  w.F[b * 2] = f0;
-  w.F[b * 2 + 1] = f1;
-  // max(|f0|, |f1|) on the bit patterns (NaN above +inf), no FP64 instruction
-  nrm = __longlong_as_double((long long)max(abs_bits(f0), abs_bits(f1)));
-
+  const double2* Y = reinterpret_cast<const double2*>(S.y_val);
   // The Jacobian is formed in the factor's precision TF: it only feeds the
-  // factorisation (the mismatch above and the refinement residual stay FP64).
-  // U = V / |V| per bus (kept by the update) avoids divisions.
+  // factorisation (the mismatch and the refinement residual stay FP64).
   TF* lu = reinterpret_cast<TF*>(w.lu);
   auto put = [&](int e, TF j00, TF j01, TF j10, TF j11) {
     TF blk[4] = {j00, j01, j10, j11};
     blk_store<2>(lu + ((size_t)e * B + gs) * 4, blk);
     if (jcopy) blk_store<2>(jcopy + ((size_t)e * B + gs) * 4, blk);
   };
+  // FP64 mismatch of Eq. 8-9 from the current I = sum_j Y_ij V_j (four FMAs
+  // per entry) and S = V conj(I)
+  double2 I = make_double2(0.0, 0.0);
+  auto mismatch = [&]() {
+    const double2 Sc = cmulc(Vi, I);
+    const double shape = fma(fma(zz, vmi, zi), vmi, zp);
+    const double f0 = (t != PF_SLACK) ? fma(-pl, shape, pg) - Sc.x : 0.0;
+    const double qgen = (t == kPQLimit) ? __ldcg(w.qsw + b) : S.q_gen[i];
+    const double f1 = (t >= PF_PQ) ? fma(-ql, shape, qgen) - Sc.y : 0.0;
+    w.F[b * 2] = f0;
+    w.F[b * 2 + 1] = f1;
+    // max(|f0|, |f1|) on the bit patterns (NaN above +inf), no FP64 instruction
+    nrm = __longlong_as_double((long long)max(abs_bits(f0), abs_bits(f1)));
+    return Sc;
+  };
   if constexpr (sizeof(TF) == 4) {
-    // FP32 throughout: conversions between FP64 and FP32 cost as much as FP64
-    // arithmetic on this GPU, so the inputs are FP32 copies (Ybus, (U, |V|),
-    // ZIP shares, loads) and the current I_i of the diagonal blocks is summed
-    // again in FP32 from the same neighbours.
-    const float4 qi = __ldcg(w.uvm32 + b);
-    const float uix = qi.x, uiy = qi.y, vix = qi.z * qi.x, viy = qi.z * qi.y;
-    float ix = 0.f, iy = 0.f, ydx = 0.f, ydy = 0.f;
+#pragma unroll 4
+    for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
+      const int j = S.y_col[e];
+      const double2 y = Y[e], v = ldc(w.V + (size_t)j * B + gs);
+      I.x = fma(y.x, v.x, I.x);
+      I.x = fma(-y.y, v.y, I.x);
+      I.y = fma(y.x, v.y, I.y);
+      I.y = fma(y.y, v.x, I.y);
+    }
+    mismatch();
+    // The FP32 Jacobian over the factor's row, from the same neighbour
+    // voltages (now in L1): the FP32 operands are cut from the FP64 values by
+    // integer bit operations (conversion instructions would occupy the FP64
+    // pipe of this GPU), so the assembly executes no FP64 instruction.
+    const float vix = to_f32_trunc(Vi.x), viy = to_f32_trunc(Vi.y);
+    const float Ix = to_f32_trunc(I.x), Iy = to_f32_trunc(I.y);
+    const float pl32 = to_f32_trunc(pl), ql32 = to_f32_trunc(ql), vm32 = to_f32_trunc(vmi);
+    float ydx = 0.f, ydy = 0.f;
     int ed = -1;
-#pragma unroll 2
+#pragma unroll 1
     for (int e = S.lu_rowptr[i]; e < S.lu_rowptr[i + 1]; ++e) {
       const int yi = S.lu2y[e];
       if (yi < 0) continue;  // fill entry: the factor starts it from zero
       const int j = S.lu_col[e];
-      const float2 y = S.y32[yi];
+      const float2 y32 = S.y32[yi];
       if (j == i) {
         ed = e;
-        ydx = y.x;
-        ydy = y.y;
+        ydx = y32.x;
+        ydy = y32.y;
         continue;
       }
-      const float4 q = __ldcg(w.uvm32 + (size_t)j * B + gs);  // (Re U, Im U, |V|, 0)
-      const float yux = y.x * q.x - y.y * q.y, yuy = y.x * q.y + y.y * q.x;  // Y_ij U_j
-      ix = fmaf(q.z, yux, ix);
-      iy = fmaf(q.z, yuy, iy);
       float j00 = 0.f, j01 = 0.f, j10 = 0.f, j11 = 0.f;
       const int tj = tp[j * ts];
       if (t != PF_SLACK && tj != PF_SLACK) {
-        // dS_i/d|V_j| = V_i conj(Y_ij U_j); dS_i/d delta_j = -j |V_j| dS_i/d|V_j|
-        const float cx = vix * yux + viy * yuy, cy = viy * yux - vix * yuy;
-        j00 = q.z * cy;
-        j10 = -q.z * cx;
+        // c = V_i conj(Y_ij V_j): dS_i/d delta_j = -j c, dS_i/d|V_j| = c / |V_j|
+        const double2 v = ldc(w.V + (size_t)j * B + gs);
+        const float vjx = to_f32_trunc(v.x), vjy = to_f32_trunc(v.y);
+        const float yvx = y32.x * vjx - y32.y * vjy, yvy = y32.x * vjy + y32.y * vjx;
+        const float cx = vix * yvx + viy * yvy, cy = viy * yvx - vix * yvy;
+        j00 = cy;
+        j10 = -cx;
         if (tj >= PF_PQ) {
-          j01 = cx;
-          j11 = cy;
+          const float rv = rsqrtf(fmaf(vjx, vjx, vjy * vjy));
+          j01 = cx * rv;
+          j11 = cy * rv;
         }
         if (t == PF_PV) j10 = j11 = 0.f;
       }
@@ -329,18 +321,18 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
       } else {
         // dS_i/d delta_i = j (S_i - V_i conj(Y_ii V_i));
         // dS_i/d|V_i| = U_i conj(I_i + Y_ii V_i), plus the load's slope
+        const float rvi = rsqrtf(fmaf(vix, vix, viy * viy));
+        const float uix = vix * rvi, uiy = viy * rvi;
         const float yvx = ydx * vix - ydy * viy, yvy = ydx * viy + ydy * vix;  // Y_ii V_i
-        const float Ix = ix + yvx, Iy = iy + yvy;
         const float scx = vix * Ix + viy * Iy, scy = viy * Ix - vix * Iy;  // V_i conj(I_i)
         const float dx = vix * yvx + viy * yvy, dy = viy * yvx - vix * yvy;
         const float ax = Ix + yvx, ay = Iy + yvy;
         const float ex = uix * ax + uiy * ay, ey = uiy * ax - uix * ay;
-        const float2 sp = __ldcg(w.spec32 + b);  // (P load, Q load)
-        const float dshape = fmaf(2.f * S.zip32[3 * i + 2], qi.z, S.zip32[3 * i + 1]);
+        const float dshape = fmaf(2.f * S.zip32[3 * i + 2], vm32, S.zip32[3 * i + 1]);
         j00 = -(scy - dy);
         j10 = scx - dx;
-        j01 = fmaf(sp.x, dshape, ex);
-        j11 = fmaf(sp.y, dshape, ey);
+        j01 = fmaf(pl32, dshape, ex);
+        j11 = fmaf(ql32, dshape, ey);
         if (t == PF_PV) {
           j01 = 0.f;
           j10 = 0.f;
@@ -350,6 +342,17 @@ __device__ void mismatch_jacobian_1ph(const DevSys& S, const DevWork& w, int i, 
       put(ed, j00, j01, j10, j11);
     }
   } else {
+#pragma unroll 4
+    for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
+      const int j = S.y_col[e];
+      const double2 y = Y[e], v = ldc(w.V + (size_t)j * B + gs);
+      I.x = fma(y.x, v.x, I.x);
+      I.x = fma(-y.y, v.y, I.x);
+      I.y = fma(y.x, v.y, I.y);
+      I.y = fma(y.y, v.x, I.y);
+    }
+    const double2 Sc = mismatch();
+    // U = V / |V| per bus (kept by the update in FP64 solves) avoids divisions
     const double2 Ui = ldc(w.U + b);
     const double dshape = fma(2.0 * zz, vmi, zi);
 #pragma unroll 2
@@ -456,7 +459,6 @@ __device__ void mismatch_jacobian_3ph(const DevSys& S, const DevWork& w, int i, 
   const double zp = S.zip[3 * i], zi = S.zip[3 * i + 1], zz = S.zip[3 * i + 2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    w.I[b * 3 + a] = I[a];
     const bool freea = ((mask >> a) & 1) && !src;
     double fim = 0.0, fre = 0.0;
     adj[a] = adj[3 + a] = adj[6 + a] = adj[9 + a] = 0.0;
@@ -1568,7 +1570,6 @@ __device__ __forceinline__ void setup_1ph(const DevSys& S, const DevWork& w, int
   w.spec[b * 3] = pl;
   w.spec[b * 3 + 1] = ql;
   w.spec[b * 3 + 2] = pg;
-  w.spec32[b] = make_float2(to_f32_trunc(pl), to_f32_trunc(ql));
   double vm, va;
   if (w.in_vm) {
     vm = w.in_vm[(size_t)gs * S.n + oi];
@@ -1584,9 +1585,8 @@ __device__ __forceinline__ void setup_1ph(const DevSys& S, const DevWork& w, int
   w.va[b] = va;
   double sn, cs;
   sincos_tab(S.trig, va, &sn, &cs);
-  w.U[b] = make_double2(cs, sn);
+  if (w.U) w.U[b] = make_double2(cs, sn);
   w.V[b] = make_double2(vm * cs, vm * sn);
-  w.uvm32[b] = make_float4(to_f32_trunc(cs), to_f32_trunc(sn), to_f32_trunc(vm), 0.0f);
 }
 
 // The accumulators of scenario gs (once per scenario, with bus 0).
@@ -1659,10 +1659,11 @@ __device__ __forceinline__ void dv_row(const DevSys& S, const DevWork& w, int i,
       w.dV[b * 3 + a] = make_double2(dr, di);
     }
   } else {
-    // dV = j d_delta V + d|V| U
-    const double2 V = ldc(w.V + b), U = ldc(w.U + b);
+    // dV = j d_delta V + d|V| U = V (d|V| / |V| + j d_delta)
+    const double2 V = ldc(w.V + b);
     const double dd = __ldcg(w.dx + b * 2), dm = __ldcg(w.dx + b * 2 + 1);
-    w.dV[b] = make_double2(-dd * V.y + dm * U.x, dd * V.x + dm * U.y);
+    const double sm = dm / __ldcg(w.vm + b);
+    w.dV[b] = make_double2(sm * V.x - dd * V.y, sm * V.y + dd * V.x);
   }
 }
 
@@ -1713,16 +1714,22 @@ __device__ __forceinline__ void resid_row(const DevSys& S, const DevWork& w, int
       y[b * 6 + 3 + a] = rre;
     }
   } else {
-    double2 YdV = make_double2(0.0, 0.0);
-#pragma unroll 4
+    // Y dV and the current I = Y V of the step's start point
+    double2 YdV = make_double2(0.0, 0.0), I = make_double2(0.0, 0.0);
+#pragma unroll 2
     for (int e = S.y_rowptr[i]; e < S.y_rowptr[i + 1]; ++e) {
-      const double2 y = Y[e], d = ldc(w.dV + (size_t)S.y_col[e] * B + gs);
+      const size_t bj = (size_t)S.y_col[e] * B + gs;
+      const double2 y = Y[e], d = ldc(w.dV + bj), v = ldc(w.V + bj);
       YdV.x = fma(y.x, d.x, YdV.x);
       YdV.x = fma(-y.y, d.y, YdV.x);
       YdV.y = fma(y.x, d.y, YdV.y);
       YdV.y = fma(y.y, d.x, YdV.y);
+      I.x = fma(y.x, v.x, I.x);
+      I.x = fma(-y.y, v.y, I.x);
+      I.y = fma(y.x, v.y, I.y);
+      I.y = fma(y.y, v.x, I.y);
     }
-    const double2 V = ldc(w.V + b), I = ldc(w.I + b), dV = ldc(w.dV + b);
+    const double2 V = ldc(w.V + b), dV = ldc(w.dV + b);
     // dS = dV conj(I) + V conj(Y dV), plus the load's slope on |V|
     const double2 dS = cadd(cmulc(dV, I), cmulc(V, YdV));
     const double vmi = __ldcg(w.vm + b);
@@ -1776,9 +1783,8 @@ __device__ __forceinline__ double update_row(const DevSys& S, const DevWork& w, 
     w.va[b] = va;
     double sn, cs;
     sincos_tab(S.trig, va, &sn, &cs);
-    w.U[b] = make_double2(cs, sn);
+    if (w.U) w.U[b] = make_double2(cs, sn);
     w.V[b] = make_double2(vm * cs, vm * sn);
-    w.uvm32[b] = make_float4(to_f32_trunc(cs), to_f32_trunc(sn), to_f32_trunc(vm), 0.0f);
   }
   return stp;
 }

@@ -142,6 +142,7 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   if (rc != PF_OK) return rc;
   DevWork w = ws->w;
   w.B = B;
+  if (fp32) w.U = nullptr;  // the mixed-precision Jacobian reads V alone
   w.in_p_load = d_p_load;
   w.in_q_load = d_q_load;
   w.in_p_gen = d_p_gen;
@@ -360,41 +361,38 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   const int nsl = kind == PF_SINGLE_PHASE ? 1 : 3;
   const bool fp32 = o.precision == PF_MIXED;
   const size_t tf = fp32 ? 4 : 8;
-  const SysBuf& sb = c->nr;
-  const Symbolic& sy = sb.sym;
-  const int threads = bs == 2 ? 512 : 256;
+  const Symbolic& sy = c->nr.sym;
+  const int threads = noalloc_threads(bs);
   int cluster = o.cluster_size;
   if (!cluster) cluster = max_cluster(bs, fp32, false, threads);
-  const int nflev = (int)sy.flev_ptr.size() - 1, nblev = (int)sy.blev_ptr.size() - 1;
+  // the lane tables of this launch shape, uploaded when the case was created
+  DevSys sys;
+  rc = c->nr.lanes_cached(threads, 1, sys);
+  if (rc != PF_OK) return rc;
   // carve the workspace (256-byte aligned pieces)
   const size_t nb = (size_t)n;
-  size_t off = 0;
-  size_t sizes[24];
-  int k = 0;
-  sizes[k++] = nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8;  // spec
-  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;         // vm
-  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;         // va
-  sizes[k++] = nb * nsl * 16;                                // V
-  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 16 : 0;        // U
-  sizes[k++] = nb * nsl * 16;                                // I
-  sizes[k++] = nb * nsl * 16;                                // dV
-  sizes[k++] = kind == PF_THREE_PHASE ? nb * 12 * 8 : 0;     // abcd
-  sizes[k++] = nb * bs * 8;                                  // F
-  sizes[k++] = nb * bs * 8;                                  // dx
-  sizes[k++] = nb * bs * 8;                                  // r
-  sizes[k++] = (size_t)sy.nnz_lu() * bs * bs * tf;           // lu
-  sizes[k++] = nb * bs * bs * tf;                            // uinv
-  sizes[k++] = nb * bs * tf;                                 // y
-  sizes[k++] = 2 * 8;                                        // norm
-  sizes[k++] = 2 * 8;                                        // step
-  sizes[k++] = 8;                                            // flag
-  sizes[k++] = (size_t)nflev;                                // forward lanes
-  sizes[k++] = (size_t)nblev;                                // backward lanes
-  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 16 : 0;        // FP32 (U, |V|)
-  sizes[k++] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;         // FP32 loads
-  sizes[k++] = kind == PF_THREE_PHASE ? nb * 3 * 8 : 0;      // PV reactive injection
-  size_t offs[24];
-  for (int q = 0; q < k; ++q) {
+  enum { kSpec, kVm, kVa, kV, kU, kDV, kAbcd, kF, kDx, kR, kLu, kUinv, kY, kNorm, kStep, kFlag,
+         kQg, kPieces };
+  size_t sizes[kPieces];
+  sizes[kSpec] = nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8;
+  sizes[kVm] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;
+  sizes[kVa] = kind == PF_SINGLE_PHASE ? nb * 8 : 0;
+  sizes[kV] = nb * nsl * 16;
+  sizes[kU] = kind == PF_SINGLE_PHASE && !fp32 ? nb * 16 : 0;  // FP64 solves only
+  sizes[kDV] = nb * nsl * 16;
+  sizes[kAbcd] = kind == PF_THREE_PHASE ? nb * 12 * 8 : 0;
+  sizes[kF] = nb * bs * 8;
+  sizes[kDx] = nb * bs * 8;
+  sizes[kR] = nb * bs * 8;
+  sizes[kLu] = (size_t)sy.nnz_lu() * bs * bs * tf;
+  sizes[kUinv] = nb * bs * bs * tf;
+  sizes[kY] = nb * bs * tf;
+  sizes[kNorm] = 2 * 8;
+  sizes[kStep] = 2 * 8;
+  sizes[kFlag] = 8;
+  sizes[kQg] = kind == PF_THREE_PHASE ? nb * 3 * 8 : 0;  // PV reactive injections
+  size_t offs[kPieces], off = 0;
+  for (int q = 0; q < kPieces; ++q) {
     offs[q] = off;
     off += (sizes[q] + 255) & ~size_t(255);
   }
@@ -424,61 +422,23 @@ int solve_noalloc(pf_case c, const pf_opts& o, const double* d_p_load, const dou
   w.warm_V = c->warm_V;
   w.warm_in = (o.warm_start && c->warm_valid) ? 1 : 0;
   w.warm_out = 1;
-  w.spec = (double*)at(0);
-  w.vm = (double*)at(1);
-  w.va = (double*)at(2);
-  w.V = (double2*)at(3);
-  w.U = (double2*)at(4);
-  w.I = (double2*)at(5);
-  w.dV = (double2*)at(6);
-  w.abcd = (double*)at(7);
-  w.F = (double*)at(8);
-  w.dx = (double*)at(9);
-  w.r = (double*)at(10);
-  w.lu = at(11);
-  w.uinv = at(12);
-  w.y = at(13);
-  w.norm = (unsigned long long*)at(14);
-  w.step = (unsigned long long*)at(15);
-  w.flag = (int*)at(16);
-  // lanes per level, written through a small stack buffer (no heap)
-  DevSys sys = sb.view;
-  int8_t* g_fwd = (int8_t*)at(17);
-  int8_t* g_bwd = (int8_t*)at(18);
-  w.uvm32 = (float4*)at(19);
-  w.spec32 = (float2*)at(20);
-  w.qg = (double*)at(21);
-  auto put_lanes = [&](const std::vector<int>& ptr, const std::vector<int>& longest, int8_t* dst) {
-    int8_t chunk[512];
-    const int nl = (int)ptr.size() - 1;
-    for (int l0 = 0; l0 < nl; l0 += 512) {
-      const int cnt = std::min(512, nl - l0);
-      for (int t = 0; t < cnt; ++t) {
-        const int l = l0 + t, width = ptr[l + 1] - ptr[l];
-        int want = 1;
-        while (want < 32 && want < longest[l]) want <<= 1;
-        while (want > 1 && (long long)want * width > threads) want >>= 1;
-        chunk[t] = (int8_t)want;
-      }
-      // a pageable source is staged before the call returns
-      cudaError_t e2 = cudaMemcpyAsync(dst + l0, chunk, cnt, cudaMemcpyHostToDevice, st);
-      if (e2 != cudaSuccess) return e2;
-    }
-    return cudaSuccess;
-  };
-  e = put_lanes(sy.flev_ptr, sy.flev_llen, g_fwd);
-  if (e == cudaSuccess) e = put_lanes(sy.blev_ptr, sy.blev_ulen, g_bwd);
-  if (e != cudaSuccess) return cuda_error(e, "writing the lane tables");
-  sys.g_fwd = g_fwd;
-  sys.g_bwd = g_bwd;
-  int solo = nflev;
-  while (solo > 0) {
-    const int l = solo - 1;
-    const int items = std::max(sy.fac_ptr[l + 1] - sy.fac_ptr[l], sy.tgt_ptr[l + 1] - sy.tgt_ptr[l]);
-    if (items > threads) break;
-    --solo;
-  }
-  sys.fac_solo_from = solo;
+  w.spec = (double*)at(kSpec);
+  w.vm = (double*)at(kVm);
+  w.va = (double*)at(kVa);
+  w.V = (double2*)at(kV);
+  w.U = (double2*)at(kU);
+  w.dV = (double2*)at(kDV);
+  w.abcd = (double*)at(kAbcd);
+  w.F = (double*)at(kF);
+  w.dx = (double*)at(kDx);
+  w.r = (double*)at(kR);
+  w.lu = at(kLu);
+  w.uinv = at(kUinv);
+  w.y = at(kY);
+  w.norm = (unsigned long long*)at(kNorm);
+  w.step = (unsigned long long*)at(kStep);
+  w.flag = (int*)at(kFlag);
+  w.qg = (double*)at(kQg);
   DevOpts d{};
   d.tol = o.tol;
   d.max_iter = o.max_iter;

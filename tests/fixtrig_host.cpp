@@ -1,5 +1,6 @@
 // Host build of the fixed-point sine / cosine of the voltage update
-// (csrc/fixtrig.h) with its table, for the CPU tests.
+// (csrc/fixtrig.h) with its table, and of its FP64 -> FP32 truncation, for
+// the CPU tests.
 #include <cmath>
 #include <vector>
 
@@ -32,4 +33,8 @@ int fx_to_q60(double a, long long* q) {
 }
 
 double fx_from_q60(long long q) { return pf::fx::from_q60(q); }
+
+void fx_to_f32(int n, const double* v, float* out) {
+  for (int k = 0; k < n; ++k) out[k] = pf::fx::to_f32_trunc(v[k]);
+}
 }

@@ -25,6 +25,7 @@ def fx():
     lib.fx_to_q60.argtypes = [C.c_double, C.POINTER(C.c_longlong)]
     lib.fx_from_q60.argtypes = [C.c_longlong]
     lib.fx_from_q60.restype = C.c_double
+    lib.fx_to_f32.argtypes = [C.c_int, dp, C.POINTER(C.c_float)]
     return lib
 
 
@@ -80,3 +81,37 @@ def test_fixed_point_conversions(fx):
         got = fx.fx_from_q60(k)
         exact = Fraction(k, 2 ** 60)
         assert abs(Fraction(got) - exact) <= Fraction(math.ulp(got)) / 2
+
+
+def _to_f32(fx, v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.empty(v.size, dtype=np.float32)
+    fx.fx_to_f32(v.size, v.ctypes.data_as(C.POINTER(C.c_double)),
+                 out.ctypes.data_as(C.POINTER(C.c_float)))
+    return out
+
+
+def test_fp32_truncation_rounds_toward_zero(fx):
+    """The integer-only FP64 -> FP32 cut of the Jacobian's operands equals
+    round-toward-zero (the nearest float32 stepped toward zero when it is
+    larger in magnitude) across the FP32 normal range and both signs."""
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(20000) * 10.0 ** rng.uniform(-37, 38, 20000)
+    r = r[(np.abs(r) >= 2.0 ** -126) & (np.abs(r) < 3.4e38)]  # the FP32 normal range
+    v = np.concatenate([r, [1.0, -1.0, 2.0 ** -126, -(2.0 ** -126), 3.4e38, 1.0 + 2.0 ** -30]])
+    got = _to_f32(fx, v)
+    near = v.astype(np.float32)
+    want = np.where(np.abs(near.astype(np.float64)) > np.abs(v),
+                    np.nextafter(near, np.float32(0.0)), near)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    assert np.all(np.abs(got.astype(np.float64) - v) < np.abs(v) * 2.0 ** -23)
+
+
+def test_fp32_truncation_edge_values(fx):
+    got = _to_f32(fx, [0.0, -0.0, 1e-40, -1e-45, 2.0 ** -127, 1e39, -1e300, np.inf, -np.inf,
+                       np.nan])
+    bits = got.view(np.uint32)
+    assert bits[0] == 0 and bits[1] == 0x80000000  # signed zeros
+    assert bits[2] == 0 and bits[3] == 0x80000000 and bits[4] == 0  # below 2^-126
+    assert got[5] == np.inf and got[6] == -np.inf and got[7] == np.inf and got[8] == -np.inf
+    assert np.isnan(got[9])

@@ -925,6 +925,37 @@ def test_three_phase_q_limit_two_node_closed_form(pf, ctx):
         pf.pf_destroy_case(c)
 
 
+def test_heavy_loading_mixed_precision(pf, ctx):
+    """The 10,000-bus grid loaded 5.3 times as heavily as the benchmark grid
+    (DC angle target 1.6 rad: lowest |V| about 0.36 pu, near the nose of the
+    loading curve; load spread lognormal(0, 0.1)).  Mixed precision (FP32
+    factors) needs exactly as many Newton steps as FP64 and matches the oracle;
+    its steps still cut the mismatch by more than tenfold, so the on-demand
+    FP64 refinement is not taken, while refinement of every step below
+    refine_below (refine_stall = 0) is taken and also matches the oracle."""
+    case = cases.transmission_case(10_000, 13_500, 2_000, 0, max_angle=1.6)
+    B = 64
+    pl, ql, pg = cases.scenario_loads(case, B, seed=31, sigma=0.1)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm, va, info = pf.pf_solve_batch(c, pl, ql, pg)
+        _, _, i64 = pf.pf_solve_batch(c, pl, ql, pg, pf.make_opts(precision=pf.PF_FP64))
+        vr, ar, ir = pf.pf_solve_batch(c, pl, ql, pg, pf.make_opts(refine_stall=0.0))
+        for inf in (info, i64, ir):
+            assert np.all(inf["status"] == 0) and np.all(inf["mismatch"] <= 1e-8)
+        assert np.array_equal(info["iterations"], i64["iterations"])
+        assert np.array_equal(info["linear_iterations"], info["iterations"])
+        assert np.all(ir["linear_iterations"] > ir["iterations"])
+        for b in (0, B // 2, B - 1):
+            ref = O.newton_polar(case.with_loads(pl[b], ql[b], pg[b]))
+            assert ref["converged"]
+            for v, a in ((vm, va), (vr, ar)):
+                assert np.max(np.abs(v[b] - ref["vm"])) <= V_TOL
+                assert np.max(np.abs(a[b] - ref["va"])) <= A_TOL
+    finally:
+        pf.pf_destroy_case(c)
+
+
 # ----------------------------------------------------------------------------
 # the benchmark's own workload at full size
 # ----------------------------------------------------------------------------
