@@ -549,78 +549,159 @@ def variants(pf, ctx, torch, dev, flush, pool):
     return out
 
 
-def serving_stream(pf, ctx, rate=2000.0, duration=1.0, seed=9, pool=None):
-    """Poisson arrivals, 70% transmission (500-70,000 buses) / 30% feeders
-    (1,000-20,000 nodes) from pools of resident cases, mixed precision with
-    warm starts.  The offered rate runs first (its sustained rate and
-    latencies); a second stream at 70% of the sustained rate gives the
-    latency percentiles below saturation."""
+def _pool_case(job):
+    """One seeded topology of the serving pool (run in a worker process):
+    the first of seeds seed, seed + 100,000, ... whose base case the FP64
+    oracle solves from a flat start (some large generated meshes have no
+    flat-start solution)."""
+    from paper_1711_10579_gb300 import cases
+
+    O = _W["O"]
+    kind, n, seed = job
+    for k in range(8):
+        s = seed + 100_000 * k
+        if kind == "transmission":
+            c = cases.transmission_case(n, int(round(1.35 * n)), n // 5, s)
+            ok = O.newton_polar(c)["converged"]
+        else:
+            c = cases.feeder_case(n, s)
+            ok = O.newton_cim(c)["converged"]
+        if ok:
+            return c
+    raise RuntimeError(f"no solvable {kind} topology of size {n} near seed {seed}")
+
+
+def serving_pool(pool, count, seed):
+    """`count` transmission grids (500-70,000 buses) and `count` feeders
+    (1,000-20,000 nodes), sizes log-uniform, generated (and their base cases
+    checked by the oracle) in the worker processes; returns
+    {kind: [case, ...]}."""
+    rng = np.random.default_rng(seed)
+    jobs = [("transmission", int(s), seed * 1000 + i)
+            for i, s in enumerate(np.exp(rng.uniform(np.log(500), np.log(70_000), count)))]
+    jobs += [("feeder", int(s), seed * 1000 + 500 + i)
+             for i, s in enumerate(np.exp(rng.uniform(np.log(1_000), np.log(20_000), count)))]
+    made = pool.map(_pool_case, jobs, chunksize=1)
+    return {"transmission": made[:count], "feeder": made[count:]}
+
+
+def serving_stream(pf, ctx, pool, rate=2000.0, duration=60.0, seed=9, topologies=32,
+                   check=8, warmup=2.0):
+    """Poisson arrivals at `rate` for `duration` seconds, 70% transmission
+    grids / 30% feeders drawn from resident pools of `topologies` each, every
+    request with a fresh per-bus lognormal(0, 0.2) load multiplier (PV
+    generation rescaled to 1.05 x the request's load), mixed precision, warm
+    starts.  Latency = completion seen by the client - arrival time.  A
+    `warmup`-second stream first (not reported) lets the runtime allocate
+    its job slots."""
     from paper_1711_10579_gb300 import cases
 
     t_setup = time.perf_counter()
-    pools = {"transmission": cases.topology_pool("transmission", 6, seed, 500, 70_000),
-             "feeder": cases.topology_pool("feeder", 3, seed + 1, 1_000, 20_000)}
-    handles, loads = {}, {}
-    for kind, pool in pools.items():
-        for i, case in enumerate(pool):
-            handles[(kind, i)] = pf.pf_create_case(ctx, case)
-            if kind == "transmission":
-                pl, ql, pg = cases.scenario_loads(case, 4, seed=i, sigma=0.2)
-                loads[(kind, i)] = [(pl[k], ql[k], pg[k]) for k in range(4)]
-            else:
-                pl, ql = cases.feeder_scenario_loads(case, 4, seed=i, sigma=0.2)
-                loads[(kind, i)] = [(pl[k].reshape(-1), ql[k].reshape(-1), None) for k in range(4)]
+    pools = serving_pool(pool, topologies, seed)
+    handles = {k: [pf.pf_create_case(ctx, c) for c in v] for k, v in pools.items()}
+    pv_w = {}
+    for i, c in enumerate(pools["transmission"]):
+        pvm = c.bus_type == cases.PV
+        w = np.where(pvm, c.p_gen, 0.0)
+        pv_w[i] = (pvm, w / w.sum())
     setup_s = time.perf_counter() - t_setup
     opts = pf.make_opts(warm_start=1)
+    rng = np.random.default_rng(seed + 1)
+    # lognormal(0, 0.2) drawn by inverse-CDF lookup over 65,536 quantiles
+    # (a uint16 draw per bus: the client keeps pace with the offered rate)
+    from scipy.stats import norm
 
-    def run(rate_, seed_):
-        reqs = cases.serving_stream(seed_, rate=rate_, duration=duration, pool_size=1)
-        rng = np.random.default_rng(seed_)
-        pending, lat, statuses, done_t = [], [], [], []
+    quant = np.exp(0.2 * norm.ppf((np.arange(65536) + 0.5) / 65536))
+
+    def loads(r):
+        c = pools[r.kind][r.topo]
+        n = c.n_bus if r.kind == "transmission" else c.n_node
+        mult = quant[rng.integers(0, 65536, n, dtype=np.uint16)]
+        if r.kind == "feeder":
+            mult = mult[:, None]
+        if r.kind == "feeder":
+            return (c.p_load * mult).reshape(-1), (c.q_load * mult).reshape(-1), None
+        pl, ql = c.p_load * mult, c.q_load * mult
+        pvm, w = pv_w[r.topo]
+        pg = np.where(pvm, 1.05 * pl.sum() * w, c.p_gen)
+        return pl, ql, pg
+
+    def run(reqs, dur, check):
+        pending, lat, statuses, sample = [], [], [], []
+        solve_us = {"transmission": [], "feeder": []}
+        client_s, backlog = 0.0, 0
         t0 = time.perf_counter()
         k = 0
         while k < len(reqs) or pending:
             now = time.perf_counter() - t0
             while k < len(reqs) and reqs[k].t_arrive <= now:
                 r = reqs[k]
-                key = (r.kind, int(rng.integers(0, len(pools[r.kind]))))
-                pl, ql, pg = loads[key][r.load_seed % 4]
-                t = pf.pf_submit(ctx, handles[key], pl, ql, pg, opts)
-                pending.append((t, r.t_arrive, handles[key].slots))
+                tc = time.perf_counter()
+                pl, ql, pg = loads(r)
+                h = handles[r.kind][r.topo]
+                t = pf.pf_submit(ctx, h, pl, ql, pg, opts)
+                client_s += time.perf_counter() - tc
+                keep = check and k % max(1, len(reqs) // check) == 0
+                pending.append((t, r.t_arrive, h.slots, r, (pl, ql, pg) if keep else None))
                 k += 1
+            backlog = max(backlog, len(pending))
             still = []
-            for j, (t, ta, sl) in enumerate(pending):
-                if j >= 64:  # completions come roughly in submission order
+            for j, item in enumerate(pending):
+                if j >= 128:  # completions come roughly in arrival order
                     still.extend(pending[j:])
                     break
-                res = pf.pf_poll(ctx, t, sl)
+                res = pf.pf_poll(ctx, item[0], item[2], values=item[4] is not None)
                 if res is None:
-                    still.append((t, ta, sl))
-                else:
-                    tn = time.perf_counter() - t0
-                    lat.append(tn - ta)
-                    done_t.append(tn)
-                    statuses.append(res[2]["status"])
+                    still.append(item)
+                    continue
+                lat.append(time.perf_counter() - t0 - item[1])
+                statuses.append(res[2]["status"])
+                solve_us[item[3].kind].append(res[2]["solve_us"])
+                if item[4] is not None and len(sample) < check:
+                    r = item[3]
+                    sample.append((pools[r.kind][r.topo], item[4], res[0], res[1]))
             pending = still
             if k < len(reqs) and not pending:
                 time.sleep(max(0.0, min(0.0005, reqs[k].t_arrive - (time.perf_counter() - t0))))
         span = time.perf_counter() - t0
         lat_ms = np.array(lat) * 1e3
         ok = sum(1 for s_ in statuses if s_ == 0)
-        return {"offered_req_per_s": rate_, "requests": len(reqs), "seconds": span,
-                "solves_per_s": ok / span, "converged": ok,
-                "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
-                               "p99": float(np.percentile(lat_ms, 99))}}
+        stats = pf.pf_serve_get_stats(ctx)
+        out = {"offered_req_per_s": rate, "duration_s": dur, "requests": len(reqs),
+               "seconds": span, "solves_per_s": ok / span, "converged": ok,
+               "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                              "p99": float(np.percentile(lat_ms, 99)),
+                              "max": float(lat_ms.max())},
+               "status_counts": {str(k): int(v) for k, v in zip(*np.unique(statuses,
+                                                                             return_counts=True))},
+               "device_ms_per_solve": {k: {"mean": float(np.mean(v)) * 1e-3,
+                                           "p99": float(np.percentile(v, 99)) * 1e-3}
+                                       for k, v in solve_us.items() if v},
+               "max_pending": backlog, "client_ms_per_request": 1e3 * client_s / max(1, len(reqs)),
+               "runtime": stats,
+               "pool": {"transmission_buses": [c.n_bus for c in pools["transmission"]],
+                        "feeder_nodes": [c.n_node for c in pools["feeder"]]},
+               "setup_s": setup_s,
+               "loads": "fresh per request: per-bus lognormal(0, 0.2) multipliers (inverse-CDF "
+                        "lookup over 65,536 quantiles)"}
+        return out, sample
 
-    first = run(rate, seed)
-    out = {"offered": first}
-    # latency below saturation: a second stream at 70% of the sustained rate
-    out["at_70pct_of_sustained"] = run(0.7 * first["solves_per_s"], seed + 100)
-    for h in handles.values():
-        pf.pf_destroy_case(h)
-    out["pool"] = {"transmission_buses": [p.n_bus for p in pools["transmission"]],
-                   "feeder_nodes": [p.n_node for p in pools["feeder"]]}
-    out["setup_s"] = setup_s
+    if warmup > 0:
+        run(cases.serving_stream(seed + 7, rate=rate, duration=warmup, pool_size=topologies),
+            warmup, 0)
+    stats0 = pf.pf_serve_get_stats(ctx)
+    reqs = cases.serving_stream(seed, rate=rate, duration=duration, pool_size=topologies)
+    out, sample = run(reqs, duration, check)
+    # counters of the timed stream (the largest group and peak include the warm-up)
+    for key in ("requests", "group_launches"):
+        out["runtime"][key] -= stats0[key]
+    out["warmup_s"] = warmup
+    jobs = [(c, ld, False) for c, ld, _, _ in sample]
+    out["oracle_err"] = dict(oracle_errors(pool, jobs, [(vm, va) for _, _, vm, va in sample]),
+                             sample=f"{len(sample)} served requests spread over the stream")
+    for v in handles.values():
+        for h in v:
+            pf.pf_destroy_case(h)
     return out
 
 

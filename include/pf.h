@@ -296,10 +296,13 @@ int pf_solve_batch_device(pf_case c, int B, const double* d_p_load,
 /*
  * Serving: queue one solve of case c with its own loads (host arrays as in
  * pf_solve_batch with B = 1; NULL = the case's own).  The runtime admits
- * queued requests onto the GPU as slots and device memory (the context's
- * budget) allow, so requests overlap on the device.  Warm start from the
- * case's last result if opts->warm_start.  PF_ERR_BUSY if the queue is full.
- * Thread safe.
+ * queued requests onto the GPU as job slots and device memory (the context's
+ * budget) allow, so requests overlap on the device (several cases of
+ * different sizes in one group launch; see pf_serve_get_stats).  Warm start
+ * from the case's last result if opts->warm_start: a served solve reads the
+ * case's warm-start voltages only while no other served solve of the case
+ * writes them, and writes them only when it is the case's only served solve
+ * on the GPU.  PF_ERR_BUSY if the queue is full.  Thread safe.
  */
 int pf_submit(pf_ctx ctx, pf_case c, const double* p_load, const double* q_load,
               const double* p_gen, const pf_opts* opts, pf_ticket* out);
@@ -311,6 +314,21 @@ int pf_submit(pf_ctx ctx, pf_case c, const double* p_load, const double* q_load,
 int pf_poll(pf_ctx ctx, pf_ticket t, double* vmag, double* vang, pf_info* info);
 /* Block until every submitted request has finished (bounded by timeout_ms). */
 int pf_drain(pf_ctx ctx, int timeout_ms);
+/*
+ * Counters of the context's serving runtime since it started (all zero before
+ * the first pf_submit).  Newton-Raphson requests (no reactive limits, default
+ * launch shape) run as group launches: one launch solves several queued
+ * requests of any cases and sizes, one CTA each, and each request retires
+ * when its own solve ends.  Newton-Krylov requests and requests with reactive
+ * limits run as one launch each.
+ */
+typedef struct {
+  uint64_t requests;        /* requests finished on the GPU */
+  uint64_t group_launches;  /* group launches issued */
+  int max_group;            /* most requests in one group launch */
+  int peak_running;         /* most requests on the GPU at the same time */
+} pf_serve_stats;
+int pf_serve_get_stats(pf_ctx ctx, pf_serve_stats* out);
 
 /*
  * Inspection entry points: single steps of the iteration on the GPU, for

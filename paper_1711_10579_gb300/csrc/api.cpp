@@ -515,10 +515,21 @@ int pf_create_case(pf_ctx ctx, const pf_case_desc* desc, pf_case* out) {
   rc = c->nr.build(c->data, c->y, Ordering::MinDegree, true);
   if (rc != PF_OK) return rc;
   {
-    // the lane tables of the entry point without allocation, uploaded now
+    // the lane tables of the entry point without allocation (and of served
+    // single-CTA solves), uploaded now
     DevSys unused;
     rc = c->nr.lanes_for(pf::noalloc_threads(c->bs), 1, unused);
     if (rc != PF_OK) return rc;
+  }
+  {
+    const int ki = c->data.kind == PF_SINGLE_PHASE ? 0 : 1;
+    const long long nnz = std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu());
+    int cur = ctx->max_n[ki].load();
+    while (cur < c->data.n && !ctx->max_n[ki].compare_exchange_weak(cur, c->data.n)) {
+    }
+    long long curz = ctx->max_nnz[ki].load();
+    while (curz < nnz && !ctx->max_nnz[ki].compare_exchange_weak(curz, nnz)) {
+    }
   }
   rc = c->nk.build(c->data, c->y, Ordering::RCM, false);
   if (rc != PF_OK) return rc;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <array>
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -97,6 +98,10 @@ struct pf_ctx_s {
   int device = 0;
   int num_sms = 0;
   size_t budget = 0;
+  // largest case created in this context per kind (single phase, three
+  // phase): rows and factor block entries (serving sizes its job slots once)
+  std::atomic<int> max_n[2] = {0, 0};
+  std::atomic<long long> max_nnz[2] = {0, 0};
   cudaStream_t stream = nullptr;
   pf::Server* server = nullptr;  // owned; released by serve_shutdown
   std::mutex server_mu;
@@ -135,13 +140,15 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load,
               const double* d_q_load, const double* d_p_gen, Workspace* ws,
               cudaStream_t st, RunMode mode, double* out_vm, double* out_va,
               pf_info* out_info = nullptr, unsigned long long* prof = nullptr,
-              const double* d_vm0 = nullptr, const double* d_va0 = nullptr, bool qlim = false);
+              const double* d_vm0 = nullptr, const double* d_va0 = nullptr, bool qlim = false,
+              bool warm_write = true);
 // run_solve of a Solve with the reactive limits of PV buses enforced when
 // o.q_limits is set and the case has them (rounds of solves, waiting for the
-// device between rounds); otherwise run_solve.
+// device between rounds); otherwise run_solve.  warm_write false: a single
+// solve leaves the case's warm-start voltages alone.
 int run_solve_q(pf_case c, const pf_opts& o, int B, const double* d_p_load,
                 const double* d_q_load, const double* d_p_gen, Workspace* ws, cudaStream_t st,
-                double* out_vm, double* out_va, pf_info* out_info);
+                double* out_vm, double* out_va, pf_info* out_info, bool warm_write = true);
 // Reactive-limit checks (qlim.cu).
 cudaError_t launch_qlim_init(const DevSys& S, const DevWork& w, bool three, cudaStream_t st);
 cudaError_t launch_qlim_check(const DevSys& S, const DevWork& w, const pf_info* info, int round,
@@ -163,6 +170,10 @@ cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const Dev
                           const DevOpts& o, int grid, int cluster, int threads,
                           cudaStream_t st);
 int max_cluster(int bs, bool fp32, bool nk, int threads);
+// Group launch (newton.cu): list.n CTAs, CTA b solving desc[list.job[b]]
+// with smem bytes of dynamic shared memory.
+cudaError_t launch_newton_group(int bs, bool fp32, const GroupJob* desc, const GroupList& list,
+                                size_t smem, cudaStream_t st);
 // Branch flows and losses (flows.cu); device arrays, ph = 1 or 3.
 cudaError_t launch_branch_flows(int ph, const int2* ft, const double* yb, const double* sh, int n,
                                 int m, int B, const double* vm, const double* va, double* pf_,

@@ -182,6 +182,22 @@ struct DevOpts {
 
 size_t dynamic_smem_bytes(int bs, size_t tf, bool nk, int n, const DevOpts& o, int threads);
 
+// One single-CTA solve of a group launch (several cases of different sizes
+// in one launch): its case, workspace and options, and the flag the CTA
+// raises (1) once its results are written.
+struct GroupJob {
+  DevSys S;
+  DevWork w;
+  DevOpts o;
+  int* done;
+};
+constexpr int kGroupMax = 160;  // jobs of one group launch
+// The jobs of a launch: CTA b runs desc[job[b]].
+struct GroupList {
+  int n;
+  int job[kGroupMax];
+};
+
 // Phases timed by the optional profile (cluster 0, CTA 0, between barriers).
 enum ProfPhase { kProfSetup = 0, kProfMismatch, kProfStop, kProfFactor, kProfSolve,
                  kProfResidual, kProfUpdate, kProfOutput, kProfPhases };

@@ -31,13 +31,14 @@ namespace pf {
 // the persistent kernel
 // ---------------------------------------------------------------------------
 
+// The solves of cluster (or, with CL false, CTA) number cid.
 template <int BS, typename TF, bool CL, bool NK>
-__global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, DevWork w, DevOpts o) {
+__device__ __forceinline__ void newton_solve(const DevSys& S, const DevWork& w, const DevOpts& o,
+                                             int cid) {
   constexpr bool THREE = (BS == 6);
   constexpr int NSL = THREE ? 3 : 1;  // complex voltages per row
   const int csize = CL ? (int)cg::this_cluster().num_blocks() : 1;
   const int crank = CL ? (int)cg::this_cluster().block_rank() : 0;
-  const int cid = blockIdx.x / csize;
   Team tm;
   // consecutive items go to different CTAs of the cluster (all SMs busy on
   // short loops); scenario slots stay in the low bits
@@ -714,6 +715,38 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
   }
 }
 
+template <int BS, typename TF, bool CL, bool NK>
+__global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, DevWork w, DevOpts o) {
+  const int csize = CL ? (int)cg::this_cluster().num_blocks() : 1;
+  newton_solve<BS, TF, CL, NK>(S, w, o, blockIdx.x / csize);
+}
+
+// Several cases of different sizes in one launch: CTA b solves the job
+// list.job[b] of the descriptor array (its own case, workspace, inputs and
+// outputs) as a single-CTA Newton-Raphson solve.  Descriptors, inputs and
+// outputs may live in pinned host memory.  When its results are written the
+// CTA raises the job's done flag, so every job can be retired on its own
+// while the other CTAs of the launch still run.
+template <int BS, typename TF>
+__global__ void __launch_bounds__(BS == 2 ? 512 : 256)
+    newton_group_kernel(const GroupJob* desc, GroupList list) {
+  __shared__ GroupJob job;
+  {
+    const unsigned* src = reinterpret_cast<const unsigned*>(desc + list.job[blockIdx.x]);
+    unsigned* dst = reinterpret_cast<unsigned*>(&job);
+    for (int k = threadIdx.x; k < (int)(sizeof(GroupJob) / 4); k += blockDim.x) dst[k] = src[k];
+  }
+  __syncthreads();
+  newton_solve<BS, TF, false, false>(job.S, job.w, job.o, 0);
+  // the results (every thread's writes) reach the host before the flag
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    *reinterpret_cast<volatile int*>(job.done) = 1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launcher
 // ---------------------------------------------------------------------------
@@ -829,6 +862,28 @@ cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const Dev
   if (fp32) { PF_LAUNCH(6, float) }
   PF_LAUNCH(6, double)
 #undef PF_LAUNCH
+}
+
+template <int BS, typename TF>
+static cudaError_t launch_group_t(const GroupJob* desc, const GroupList& list, size_t smem,
+                                  cudaStream_t st) {
+  auto kern = newton_group_kernel<BS, TF>;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<list.n, BS == 2 ? 512 : 256, smem, st>>>(desc, list);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_newton_group(int bs, bool fp32, const GroupJob* desc, const GroupList& list,
+                                size_t smem, cudaStream_t st) {
+  if (list.n <= 0 || list.n > kGroupMax) return cudaErrorInvalidValue;
+  if (bs == 2) return fp32 ? launch_group_t<2, float>(desc, list, smem, st)
+                           : launch_group_t<2, double>(desc, list, smem, st);
+  return fp32 ? launch_group_t<6, float>(desc, list, smem, st)
+              : launch_group_t<6, double>(desc, list, smem, st);
 }
 
 int max_cluster(int bs, bool fp32, bool nk, int threads) {

@@ -1,15 +1,26 @@
 // Serving runtime: continuous admission of queued solves onto the GPU.
 //
-// Each context owns one dispatcher thread and a set of slots.  A slot is a
-// CUDA stream with its own solve workspace and pinned host staging.  Requests
-// wait in a FIFO queue; the dispatcher admits the head of the queue whenever a
-// slot is free and the request's device footprint fits the context's HBM
-// budget, launches its persistent Newton kernel on the slot's stream, and
-// retires it when the stream's event completes.  Requests of different cases
-// and sizes therefore run concurrently on different SMs, and a request that
-// arrives while others are on the GPU starts as soon as a slot frees up.
+// Each context owns one dispatcher thread.  Requests wait in a FIFO queue.
+// Newton-Raphson requests run as group launches: one launch takes every
+// queued request that fits (free job slots and the context's HBM budget),
+// of any cases and sizes, and each of its CTAs solves one request on its own
+// (newton.cu: newton_group_kernel).  A job's descriptor, inputs and outputs
+// live in pinned host memory; the CTA raises the job's done flag when its
+// results are written, so every request retires as soon as its own solve
+// ends, while the other CTAs of its launch still run.  New requests form the
+// next group at once, on the next of several streams, so requests that
+// arrive while others are on the GPU start as job slots free up and their
+// work overlaps on the device.  Newton-Krylov requests and requests with
+// reactive limits (rounds that wait for the device between solves) run as
+// per-request launches on a few stream slots of their own.
+//
+// Warm starts: the case's warm-start voltages are read by a job only while
+// no job of that case that writes them is in flight, and written only by a
+// job that is the case's only one in flight, so no job starts from a mix of
+// two solutions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -26,13 +37,11 @@ namespace pf {
 
 namespace {
 
-constexpr int kSlots = 16;
+constexpr int kJobs = kGroupMax;  // single-CTA solves on the GPU at once (about one per SM)
+constexpr int kGroupStreams = 64;  // group launches in flight at once (each on its own stream)
+constexpr int kSlots = 8;         // per-request launches (Newton-Krylov, reactive limits)
 constexpr size_t kMaxQueue = 1 << 20;
-
-double now_us() {
-  using namespace std::chrono;
-  return duration<double, std::micro>(steady_clock::now().time_since_epoch()).count();
-}
+constexpr size_t kGroupSmemMax = 200 * 1024;  // a job's solve vector in shared memory up to this
 
 struct Request {
   pf_ticket id = 0;
@@ -45,17 +54,60 @@ struct Request {
   size_t footprint = 0;
 };
 
+bool grouped(const Request& r) {
+  return r.o.method == PF_NR && !(r.o.q_limits && !r.c->data.q_max.empty()) &&
+         !r.o.block_threads && !r.o.scen_per_cta && !r.o.cluster_size;
+}
+
+size_t slots_of(const Request& r) {
+  return (size_t)r.c->data.n * (r.c->data.kind == PF_SINGLE_PHASE ? 1 : 3);
+}
+
+// Pinned host staging of one request: inputs (3 vectors) and results (2).
+struct Staging {
+  double* h_in = nullptr;
+  double* h_out = nullptr;
+  size_t cap = 0;  // doubles per vector
+  int ensure(size_t per) {
+    if (per <= cap) return PF_OK;
+    if (h_in) cudaFreeHost(h_in);
+    if (h_out) cudaFreeHost(h_out);
+    h_in = h_out = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMallocHost(&h_in, 3 * per * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_out, 2 * per * sizeof(double));
+    if (e != cudaSuccess) return cuda_error(e, "allocating pinned staging");
+    cap = per;
+    return PF_OK;
+  }
+  ~Staging() {
+    if (h_in) cudaFreeHost(h_in);
+    if (h_out) cudaFreeHost(h_out);
+  }
+};
+
+// One single-CTA solve slot of the group launches.  One workspace per case
+// kind, grown to the largest request they have run (cudaFree would
+// synchronise the device, so they are never shrunk).
+struct Job {
+  Workspace ws1ph, ws3ph;
+  Staging io;
+  Request* req = nullptr;
+  int stream = -1;
+  bool warm_in = false, warm_out = false;
+  int want_n = 0;  // sizes to grow the buffers to (largest case of the kind seen)
+  long long want_nnz = 0;
+  size_t want_per = 0;
+};
+
+// One per-request launch slot: a stream with its own workspaces.
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
-  // one workspace per case kind, so alternating single- and three-phase
-  // requests do not reallocate (cudaFree would synchronise the device)
   Workspace ws1ph, ws3ph;
-  Request* req = nullptr;
-  double* h_in = nullptr;  // pinned: p_load, q_load, p_gen (3 * cap)
-  double* h_out = nullptr; // pinned: vm, va (2 * cap)
+  Staging io;
   pf_info* h_info = nullptr;
-  size_t cap = 0;          // doubles per staged vector
+  Request* req = nullptr;
 };
 
 }  // namespace
@@ -67,12 +119,26 @@ struct Server {
   std::condition_variable cv, done_cv;
   std::deque<Request*> queue;
   std::unordered_map<pf_ticket, std::unique_ptr<Request>> all;
+  Job jobs[kJobs];
+  GroupJob* h_desc = nullptr;  // pinned: the jobs' descriptors
+  pf_info* h_info = nullptr;   // pinned: the jobs' result records
+  int* h_done = nullptr;       // pinned: the jobs' done flags
+  cudaStream_t gst[kGroupStreams] = {};
+  int gnext = 0;
+  int ginflight[kGroupStreams] = {};
   Slot slots[kSlots];
+  std::unordered_map<pf_case, int> warm_readers, warm_writers;
+  // largest case seen per kind (single phase, three phase): rows, factor
+  // entries and staged doubles per vector
+  int max_n[2] = {0, 0};
+  long long max_nnz[2] = {0, 0};
+  size_t max_per[2] = {0, 0};
   size_t used = 0;  // device bytes of running requests
   int running = 0;
   bool stop = false;
   pf_ticket next = 1;
   std::string fatal;  // a CUDA failure that stopped the dispatcher
+  pf_serve_stats stats{};
 
   size_t footprint(const Request& r) const {
     const pf_case c = r.c;
@@ -81,73 +147,18 @@ struct Server {
                                 r.o.method == PF_NK ? r.o.gmres_restart : 0);
   }
 
-  // Launch r on slot s (dispatcher thread, lock held).
-  int start(Request* r, Slot& s) {
-    pf_case c = r->c;
-    const size_t per = (size_t)c->data.n * (c->data.kind == PF_SINGLE_PHASE ? 1 : 3);
-    if (per > s.cap) {
-      if (s.h_in) cudaFreeHost(s.h_in);
-      if (s.h_out) cudaFreeHost(s.h_out);
-      s.h_in = s.h_out = nullptr;
-      s.cap = 0;
-      cudaError_t e = cudaMallocHost(&s.h_in, 3 * per * sizeof(double));
-      if (e == cudaSuccess) e = cudaMallocHost(&s.h_out, 2 * per * sizeof(double));
-      if (e != cudaSuccess) return cuda_error(e, "allocating pinned staging");
-      s.cap = per;
-    }
-    if (!s.h_info) {
-      cudaError_t e = cudaMallocHost(&s.h_info, sizeof(pf_info));
-      if (e != cudaSuccess) return cuda_error(e, "allocating pinned staging");
-    }
-    Workspace& ws = (c->data.kind == PF_SINGLE_PHASE) ? s.ws1ph : s.ws3ph;
-    int rc = ws.ensure(c->data.kind, c->data.n,
-                       std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), 1,
-                       r->o.method == PF_NK ? r->o.gmres_restart : 0);
-    if (rc != PF_OK) return rc;
-    const double* d_in[3] = {nullptr, nullptr, nullptr};
-    double* dst[3] = {ws.st_p_load, ws.st_q_load, ws.st_p_gen};
-    const std::vector<double>* src[3] = {&r->p_load, &r->q_load, &r->p_gen};
-    for (int k = 0; k < 3; ++k) {
-      if (src[k]->empty()) continue;
-      std::memcpy(s.h_in + k * per, src[k]->data(), per * sizeof(double));
-      cudaError_t e = cudaMemcpyAsync(dst[k], s.h_in + k * per, per * sizeof(double),
-                                      cudaMemcpyHostToDevice, s.st);
-      if (e != cudaSuccess) return cuda_error(e, "staging request inputs");
-      d_in[k] = dst[k];
-    }
-    pf_opts o = r->o;
-    if (!c->warm_valid) o.warm_start = 0;
-    // served solves run on 8-CTA clusters so that every slot fits on the GPU
-    if (!o.cluster_size) o.cluster_size = 8;
-    rc = run_solve_q(c, o, 1, d_in[0], d_in[1], d_in[2], &ws, s.st, nullptr, nullptr, nullptr);
-    if (rc != PF_OK) return rc;
-    cudaError_t e = cudaMemcpyAsync(s.h_out, ws.st_vm, per * sizeof(double),
-                                    cudaMemcpyDeviceToHost, s.st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s.h_out + per, ws.st_va, per * sizeof(double),
-                          cudaMemcpyDeviceToHost, s.st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s.h_info, ws.st_info, sizeof(pf_info), cudaMemcpyDeviceToHost, s.st);
-    if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
-    if (e != cudaSuccess) return cuda_error(e, "launching a served solve");
+  void begin(Request* r) {
     r->state = 1;
-    s.req = r;
     used += r->footprint;
     ++running;
-    return PF_OK;
+    stats.peak_running = std::max(stats.peak_running, running);
   }
 
-  void finish(Slot& s) {
-    Request* r = s.req;
-    const size_t per = (size_t)r->c->data.n * (r->c->data.kind == PF_SINGLE_PHASE ? 1 : 3);
-    r->vm.assign(s.h_out, s.h_out + per);
-    r->va.assign(s.h_out + per, s.h_out + 2 * per);
-    r->info = *s.h_info;
-    if (r->info.status == PF_OK) r->c->warm_valid = true;
+  void end(Request* r) {
     r->state = 2;
     used -= r->footprint;
     --running;
-    s.req = nullptr;
+    ++stats.requests;
   }
 
   void fail(Request* r, int code) {
@@ -156,11 +167,325 @@ struct Server {
     r->state = 2;
   }
 
+  // ---- group launches ----
+
+  // Claims job k for request r (lock held): the warm-start roles.
+  void claim(int k, Request* r) {
+    Job& J = jobs[k];
+    pf_case c = r->c;
+    // warm start: read while no writer of the case is in flight; written by
+    // the case's only job in flight
+    const bool writer = warm_writers[c] > 0;
+    J.warm_in = r->o.warm_start && c->warm_valid && !writer;
+    J.warm_out = !writer && warm_readers[c] == 0;
+    if (J.warm_in) ++warm_readers[c];
+    if (J.warm_out) ++warm_writers[c];
+    // the slot's buffers are grown to the largest case of the kind created
+    // in the context (so that a slot is allocated once)
+    const int ki = c->data.kind == PF_SINGLE_PHASE ? 0 : 1;
+    J.want_n = std::max(max_n[ki], ctx->max_n[ki].load());
+    J.want_nnz = std::max(max_nnz[ki], ctx->max_nnz[ki].load());
+    J.want_per = std::max(max_per[ki], (size_t)J.want_n * (ki == 0 ? 1 : 3));
+    h_done[k] = 0;
+    J.req = r;
+    begin(r);
+  }
+
+  // Undoes claim() for a job that never ran (lock held).
+  void unclaim(int k, int code) {
+    Job& J = jobs[k];
+    Request* r = J.req;
+    if (J.warm_in) --warm_readers[r->c];
+    if (J.warm_out) --warm_writers[r->c];
+    J.req = nullptr;
+    J.stream = -1;
+    end(r);
+    fail(r, code);
+  }
+
+  // Stages job k (dispatcher thread, lock not held: it may allocate): its
+  // workspace, pinned inputs and descriptor; returns the dynamic shared
+  // memory its solve needs.
+  int stage(int k, size_t* smem) {
+    Job& J = jobs[k];
+    Request* r = J.req;
+    pf_case c = r->c;
+    const int kind = c->data.kind, n = c->data.n, bs = c->bs;
+    const bool fp32 = r->o.precision == PF_MIXED;
+    const size_t per = slots_of(*r), tf = fp32 ? 4 : 8;
+    Workspace& ws = kind == PF_SINGLE_PHASE ? J.ws1ph : J.ws3ph;
+    // grown at once to the largest case of the kind seen so far (claim), so
+    // that job slots are rarely reallocated (cudaFree synchronises the device)
+    const long long nnz = std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu());
+    int rc = ws.ensure(kind, std::max(n, J.want_n), std::max(nnz, J.want_nnz), 1, 0);
+    if (rc == PF_OK) rc = J.io.ensure(std::max(per, J.want_per));
+    GroupJob& g = h_desc[k];
+    if (rc == PF_OK) rc = c->nr.lanes_cached(noalloc_threads(bs), 1, g.S);
+    if (rc != PF_OK) return rc;
+    const std::vector<double>* src[3] = {&r->p_load, &r->q_load, &r->p_gen};
+    const double* in[3] = {nullptr, nullptr, nullptr};
+    for (int q = 0; q < 3; ++q) {
+      if (src[q]->empty()) continue;
+      std::memcpy(J.io.h_in + q * per, src[q]->data(), per * sizeof(double));
+      in[q] = J.io.h_in + q * per;
+    }
+    DevWork w = ws.w;
+    w.B = 1;
+    if (fp32) w.U = nullptr;
+    w.in_p_load = in[0];
+    w.in_q_load = in[1];
+    w.in_p_gen = in[2];
+    w.in_vm = w.in_va = nullptr;
+    w.out_vm = J.io.h_out;
+    w.out_va = J.io.h_out + per;
+    w.out_info = h_info + k;
+    w.warm_vm = c->warm_vm;
+    w.warm_va = c->warm_va;
+    w.warm_V = c->warm_V;
+    w.warm_in = J.warm_in ? 1 : 0;
+    w.warm_out = J.warm_out ? 1 : 0;
+    w.bt = nullptr;
+    DevOpts d{};
+    d.tol = r->o.tol;
+    d.max_iter = r->o.max_iter;
+    d.refine = fp32 ? r->o.refine_steps : 0;
+    d.refine_below = r->o.refine_below;
+    d.refine_stall = r->o.refine_stall;
+    d.S = 1;
+    d.mode = 0;
+    d.prof = nullptr;
+    d.y_in_smem = ((size_t)n * bs * tf <= kGroupSmemMax) ? 1 : 0;
+    d.max_lin = r->o.gmres_max_iter;
+    d.rtol = r->o.gmres_rtol;
+    g.w = w;
+    g.o = d;
+    g.done = h_done + k;
+    h_done[k] = 0;
+    *smem = d.y_in_smem ? (size_t)n * bs * tf : 0;
+    return PF_OK;
+  }
+
+  void retire(int k) {
+    Job& J = jobs[k];
+    Request* r = J.req;
+    const size_t per = slots_of(*r);
+    r->vm.assign(J.io.h_out, J.io.h_out + per);
+    r->va.assign(J.io.h_out + per, J.io.h_out + 2 * per);
+    r->info = h_info[k];
+    if (J.warm_in) --warm_readers[r->c];
+    if (J.warm_out) {
+      --warm_writers[r->c];
+      if (r->info.status == PF_OK) r->c->warm_valid = true;
+    }
+    --ginflight[J.stream];
+    J.req = nullptr;
+    J.stream = -1;
+    end(r);
+  }
+
+  // Admits queued Newton-Raphson requests into one group launch per (case
+  // kind, precision): the jobs are claimed with the lock held, staged and
+  // launched without it (staging may allocate), and failures are settled
+  // with the lock held again.  Returns whether anything was admitted.
+  bool admit_groups(std::unique_lock<std::mutex>& lk) {
+    // a new group goes to a stream with nothing in flight; with none free,
+    // arrivals wait in the queue and form a larger group when one frees up
+    int idle = 0;
+    for (int q = 0; q < kGroupStreams; ++q) idle += ginflight[q] == 0;
+    if (idle == 0) return false;
+    std::vector<int> claimed;
+    int free_job = 0;
+    bool any = false;
+    for (auto it = queue.begin(); it != queue.end();) {
+      Request* r = *it;
+      if (!grouped(*r)) {
+        ++it;
+        continue;
+      }
+      while (free_job < kJobs && jobs[free_job].req) ++free_job;
+      if (free_job >= kJobs) break;
+      if (used + r->footprint > ctx->budget) {
+        if (running > 0) break;  // wait for memory to free up (FIFO order)
+        it = queue.erase(it);    // can never fit, even alone
+        fail(r, PF_ERR_NOMEM);
+        any = true;
+        continue;
+      }
+      it = queue.erase(it);
+      claim(free_job, r);
+      claimed.push_back(free_job);
+      any = true;
+    }
+    if (claimed.empty()) return any;
+    struct Group {
+      GroupList list;
+      size_t smem = 0;
+      int bs = 2;
+      bool fp32 = true;
+    };
+    Group grp[4];
+    for (Group& g : grp) g.list.n = 0;
+    std::vector<std::pair<int, int>> failed;  // (job, status)
+    lk.unlock();
+    for (int k : claimed) {
+      Request* r = jobs[k].req;
+      size_t smem = 0;
+      const int rc = stage(k, &smem);
+      if (rc != PF_OK) {
+        failed.push_back({k, rc});
+        continue;
+      }
+      Group& g = grp[(r->c->bs == 2 ? 0 : 2) + (r->o.precision == PF_MIXED ? 0 : 1)];
+      g.bs = r->c->bs;
+      g.fp32 = r->o.precision == PF_MIXED;
+      g.smem = std::max(g.smem, smem);
+      g.list.job[g.list.n++] = k;
+    }
+    std::string err;
+    for (Group& g : grp) {
+      if (g.list.n == 0) continue;
+      // the next idle stream (round robin), else the next one
+      int sidx = gnext;
+      for (int q = 0; q < kGroupStreams; ++q) {
+        const int c = (gnext + q) % kGroupStreams;
+        if (ginflight[c] == 0) {
+          sidx = c;
+          break;
+        }
+      }
+      gnext = (sidx + 1) % kGroupStreams;
+      const cudaError_t e = launch_newton_group(g.bs, g.fp32, h_desc, g.list, g.smem, gst[sidx]);
+      for (int q = 0; q < g.list.n; ++q) {
+        if (e == cudaSuccess) jobs[g.list.job[q]].stream = sidx;
+        else failed.push_back({g.list.job[q], PF_ERR_CUDA});
+      }
+      if (e != cudaSuccess) {
+        err = cudaGetErrorString(e);
+        continue;
+      }
+      ginflight[sidx] += g.list.n;
+      ++stats.group_launches;
+      stats.max_group = std::max(stats.max_group, g.list.n);
+    }
+    lk.lock();
+    if (!err.empty()) fatal = err;
+    for (auto& f : failed) unclaim(f.first, f.second);
+    return any;
+  }
+
+  // ---- per-request launches ----
+
+  int start(Request* r, Slot& s) {
+    pf_case c = r->c;
+    const size_t per = slots_of(*r);
+    int rc = s.io.ensure(per);
+    if (rc != PF_OK) return rc;
+    if (!s.h_info) {
+      cudaError_t e = cudaMallocHost(&s.h_info, sizeof(pf_info));
+      if (e != cudaSuccess) return cuda_error(e, "allocating pinned staging");
+    }
+    Workspace& ws = (c->data.kind == PF_SINGLE_PHASE) ? s.ws1ph : s.ws3ph;
+    rc = ws.ensure(c->data.kind, c->data.n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()), 1,
+                   r->o.method == PF_NK ? r->o.gmres_restart : 0);
+    if (rc != PF_OK) return rc;
+    const double* d_in[3] = {nullptr, nullptr, nullptr};
+    double* dst[3] = {ws.st_p_load, ws.st_q_load, ws.st_p_gen};
+    const std::vector<double>* src[3] = {&r->p_load, &r->q_load, &r->p_gen};
+    for (int k = 0; k < 3; ++k) {
+      if (src[k]->empty()) continue;
+      std::memcpy(s.io.h_in + k * per, src[k]->data(), per * sizeof(double));
+      cudaError_t e = cudaMemcpyAsync(dst[k], s.io.h_in + k * per, per * sizeof(double),
+                                      cudaMemcpyHostToDevice, s.st);
+      if (e != cudaSuccess) return cuda_error(e, "staging request inputs");
+      d_in[k] = dst[k];
+    }
+    pf_opts o = r->o;
+    // these solves read the warm start only while no job of the case writes
+    // it, and never write it
+    if (!c->warm_valid || warm_writers[c] > 0) o.warm_start = 0;
+    // per-request solves run on 8-CTA clusters so that every slot fits
+    if (!o.cluster_size) o.cluster_size = 8;
+    rc = run_solve_q(c, o, 1, d_in[0], d_in[1], d_in[2], &ws, s.st, nullptr, nullptr, nullptr,
+                     /*warm_out=*/false);
+    if (rc != PF_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(s.io.h_out, ws.st_vm, per * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s.st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s.io.h_out + per, ws.st_va, per * sizeof(double),
+                          cudaMemcpyDeviceToHost, s.st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s.h_info, ws.st_info, sizeof(pf_info), cudaMemcpyDeviceToHost, s.st);
+    if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
+    if (e != cudaSuccess) return cuda_error(e, "launching a served solve");
+    s.req = r;
+    begin(r);
+    return PF_OK;
+  }
+
+  void finish(Slot& s) {
+    Request* r = s.req;
+    const size_t per = slots_of(*r);
+    r->vm.assign(s.io.h_out, s.io.h_out + per);
+    r->va.assign(s.io.h_out + per, s.io.h_out + 2 * per);
+    r->info = *s.h_info;
+    s.req = nullptr;
+    end(r);
+  }
+
+  bool admit_slots() {
+    bool any = false;
+    for (auto it = queue.begin(); it != queue.end();) {
+      Request* r = *it;
+      if (grouped(*r)) {
+        ++it;
+        continue;
+      }
+      Slot* free_slot = nullptr;
+      for (Slot& s : slots)
+        if (!s.req) {
+          free_slot = &s;
+          break;
+        }
+      if (!free_slot) break;
+      if (used + r->footprint > ctx->budget) {
+        if (running > 0) break;
+        it = queue.erase(it);
+        fail(r, PF_ERR_NOMEM);
+        any = true;
+        continue;
+      }
+      it = queue.erase(it);
+      int rc = start(r, *free_slot);
+      if (rc != PF_OK) fail(r, rc);
+      any = true;
+    }
+    return any;
+  }
+
   void loop() {
     cudaSetDevice(ctx->device);
     std::unique_lock<std::mutex> lk(mu);
     while (true) {
       bool progressed = false;
+      for (int k = 0; k < kJobs; ++k) {
+        if (jobs[k].req && __atomic_load_n(h_done + k, __ATOMIC_ACQUIRE) != 0) {
+          retire(k);
+          progressed = true;
+        }
+      }
+      // a failed group launch: its jobs never raise their flags
+      for (int q = 0; q < kGroupStreams; ++q) {
+        if (ginflight[q] == 0) continue;
+        const cudaError_t e = cudaStreamQuery(gst[q]);
+        if (e == cudaSuccess || e == cudaErrorNotReady) continue;
+        fatal = cudaGetErrorString(e);
+        for (int k = 0; k < kJobs; ++k) {
+          if (!jobs[k].req || jobs[k].stream != q) continue;
+          --ginflight[q];
+          unclaim(k, PF_ERR_CUDA);
+        }
+        progressed = true;
+      }
       for (Slot& s : slots) {
         if (!s.req) continue;
         cudaError_t q = cudaEventQuery(s.ev);
@@ -169,33 +494,16 @@ struct Server {
           progressed = true;
         } else if (q != cudaErrorNotReady) {
           fatal = cudaGetErrorString(q);
-          fail(s.req, PF_ERR_CUDA);
-          used -= s.req->footprint;
-          --running;
+          Request* r = s.req;
           s.req = nullptr;
+          end(r);
+          fail(r, PF_ERR_CUDA);
           progressed = true;
         }
       }
-      while (!queue.empty()) {
-        Request* r = queue.front();
-        Slot* free_slot = nullptr;
-        for (Slot& s : slots)
-          if (!s.req) {
-            free_slot = &s;
-            break;
-          }
-        if (!free_slot) break;
-        if (used + r->footprint > ctx->budget) {
-          if (running > 0) break;  // wait for memory to free up
-          queue.pop_front();       // can never fit, even alone
-          fail(r, PF_ERR_NOMEM);
-          progressed = true;
-          continue;
-        }
-        queue.pop_front();
-        int rc = start(r, *free_slot);
-        if (rc != PF_OK) fail(r, rc);
-        progressed = true;
+      if (!queue.empty()) {
+        if (admit_slots()) progressed = true;
+        if (admit_groups(lk)) progressed = true;
       }
       if (progressed) done_cv.notify_all();
       if (stop && queue.empty() && running == 0) break;
@@ -212,8 +520,17 @@ struct Server {
 
   int init(pf_ctx c) {
     ctx = c;
+    cudaError_t e = cudaMallocHost(&h_desc, kJobs * sizeof(GroupJob));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_info, kJobs * sizeof(pf_info));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_done, kJobs * sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "allocating the serving descriptors");
+    std::memset(h_done, 0, kJobs * sizeof(int));
+    for (cudaStream_t& st : gst) {
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_error(e, "creating serving streams");
+    }
     for (Slot& s : slots) {
-      cudaError_t e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
+      e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
       if (e != cudaSuccess) return cuda_error(e, "creating serving streams");
     }
@@ -228,13 +545,18 @@ struct Server {
     }
     cv.notify_all();
     if (th.joinable()) th.join();
+    for (cudaStream_t st : gst)
+      if (st) cudaStreamSynchronize(st);
+    for (cudaStream_t st : gst)
+      if (st) cudaStreamDestroy(st);
     for (Slot& s : slots) {
       if (s.st) cudaStreamDestroy(s.st);
       if (s.ev) cudaEventDestroy(s.ev);
-      if (s.h_in) cudaFreeHost(s.h_in);
-      if (s.h_out) cudaFreeHost(s.h_out);
       if (s.h_info) cudaFreeHost(s.h_info);
     }
+    if (h_desc) cudaFreeHost(h_desc);
+    if (h_info) cudaFreeHost(h_info);
+    if (h_done) cudaFreeHost(h_done);
   }
 };
 
@@ -276,8 +598,12 @@ void serve_forget_case(pf_ctx ctx, pf_case c) {
   sv->done_cv.wait(lk, [&] {
     for (Slot& s : sv->slots)
       if (s.req && s.req->c == c) return false;
+    for (Job& j : sv->jobs)
+      if (j.req && j.req->c == c) return false;
     return true;
   });
+  sv->warm_readers.erase(c);
+  sv->warm_writers.erase(c);
   for (auto& kv : sv->all)
     if (kv.second->c == c) kv.second->c = nullptr;
 }
@@ -308,6 +634,12 @@ int pf_submit(pf_ctx ctx, pf_case c, const double* p_load, const double* q_load,
   if (!sv->fatal.empty()) return set_error(PF_ERR_CUDA, "serving stopped: " + sv->fatal);
   if (sv->queue.size() >= kMaxQueue) return set_error(PF_ERR_BUSY, "serving queue is full");
   r->footprint = sv->footprint(*r);
+  {
+    const int ki = c->data.kind == PF_SINGLE_PHASE ? 0 : 1;
+    sv->max_n[ki] = std::max(sv->max_n[ki], c->data.n);
+    sv->max_nnz[ki] = std::max(sv->max_nnz[ki], (long long)std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()));
+    sv->max_per[ki] = std::max(sv->max_per[ki], per);
+  }
   r->id = sv->next++;
   *out = r->id;
   sv->queue.push_back(r.get());
@@ -330,6 +662,20 @@ int pf_poll(pf_ctx ctx, pf_ticket t, double* vmag, double* vang, pf_info* info) 
   if (vang && !r->va.empty()) std::copy(r->va.begin(), r->va.end(), vang);
   if (info) *info = r->info;
   sv->all.erase(it);
+  return PF_OK;
+}
+
+int pf_serve_get_stats(pf_ctx ctx, pf_serve_stats* out) {
+  if (!ctx || !out) return set_error(PF_ERR_INVALID, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  Server* sv;
+  {
+    std::lock_guard<std::mutex> lk(ctx->server_mu);
+    sv = ctx->server;
+  }
+  if (!sv) return PF_OK;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *out = sv->stats;
   return PF_OK;
 }
 

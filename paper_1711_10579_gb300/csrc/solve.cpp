@@ -113,7 +113,7 @@ void launch_shape(pf_case c, const pf_opts& o, int B, bool fp32, int* grid, int*
 int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const double* d_q_load,
               const double* d_p_gen, Workspace* ws, cudaStream_t st, RunMode mode, double* out_vm,
               double* out_va, pf_info* out_info, unsigned long long* prof, const double* d_vm0,
-              const double* d_va0, bool qlim) {
+              const double* d_va0, bool qlim, bool warm_write) {
   int rc = check_opts(o);
   if (rc != PF_OK) return rc;
   const bool nk = o.method == PF_NK;
@@ -155,7 +155,7 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
   w.warm_va = c->warm_va;
   w.warm_V = c->warm_V;
   w.warm_in = (o.warm_start && c->warm_valid && B == 1 && mode == RunMode::Solve) ? 1 : 0;
-  w.warm_out = (B == 1 && mode == RunMode::Solve) ? 1 : 0;
+  w.warm_out = (B == 1 && mode == RunMode::Solve && warm_write) ? 1 : 0;
   if (mode != RunMode::Solve) {
     w.in_vm = ws->st_p_load;  // staged start voltage of an inspection call
     w.in_va = ws->st_q_load;
@@ -225,11 +225,11 @@ int run_solve(pf_case c, const pf_opts& o, int B, const double* d_p_load, const 
 // are needed (capped at 64).
 int run_solve_q(pf_case c, const pf_opts& o, int B, const double* d_p_load, const double* d_q_load,
                 const double* d_p_gen, Workspace* ws, cudaStream_t st, double* out_vm,
-                double* out_va, pf_info* out_info) {
+                double* out_va, pf_info* out_info, bool warm_write) {
   const CaseData& cd = c->data;
   if (!o.q_limits || cd.q_max.empty())
     return run_solve(c, o, B, d_p_load, d_q_load, d_p_gen, ws, st, RunMode::Solve, out_vm,
-                     out_va, out_info);
+                     out_va, out_info, nullptr, nullptr, nullptr, false, warm_write);
   int rc = check_opts(o);
   if (rc != PF_OK) return rc;
   const bool nk = o.method == PF_NK;
@@ -255,7 +255,7 @@ int run_solve_q(pf_case c, const pf_opts& o, int B, const double* d_p_load, cons
   for (;;) {
     ++round;
     rc = run_solve(c, o, B, d_p_load, d_q_load, d_p_gen, ws, st, RunMode::Solve, vm, va, info,
-                   nullptr, round > 1 ? vm : nullptr, round > 1 ? va : nullptr, true);
+                   nullptr, round > 1 ? vm : nullptr, round > 1 ? va : nullptr, true, warm_write);
     if (rc != PF_OK) return rc;
     e = cudaMemsetAsync(w.nsw, 0, sizeof(int), st);
     if (e == cudaSuccess) e = launch_qlim_check(sys, w, info, round, three, st);

@@ -77,6 +77,14 @@ class pf_case_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pf_serve_stats(C.Structure):
+    _fields_ = [("requests", C.c_uint64), ("group_launches", C.c_uint64),
+                ("max_group", C.c_int), ("peak_running", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 INFO_DTYPE = np.dtype([("status", np.int32), ("iterations", np.int32),
                        ("linear_iterations", np.int32), ("fallback", np.int32),
                        ("mismatch", np.float64), ("max_step", np.float64),
@@ -118,6 +126,7 @@ def lib():
                                     C.POINTER(C.c_uint64)]),
             "pf_poll": (C.c_int, [vp, C.c_uint64, _dp, _dp, C.POINTER(pf_info)]),
             "pf_drain": (C.c_int, [vp, C.c_int]),
+            "pf_serve_get_stats": (C.c_int, [vp, C.POINTER(pf_serve_stats)]),
             "pf_case_pattern": (C.c_int, [vp, _ip, _ip]),
             "pf_eval_mismatch": (C.c_int, [vp, _dp, _dp, _dp]),
             "pf_eval_jacobian": (C.c_int, [vp, _dp, _dp, _dp]),
@@ -402,10 +411,11 @@ def pf_submit(ctx, c: CaseHandle, p_load=None, q_load=None, p_gen=None,
     return t.value
 
 
-def pf_poll(ctx, ticket: int, slots: int):
-    """None while pending, else (vmag, vang, info)."""
-    vm = np.zeros(slots)
-    va = np.zeros(slots)
+def pf_poll(ctx, ticket: int, slots: int, values: bool = True):
+    """None while pending, else (vmag, vang, info); with values False only
+    info is copied out (vmag, vang are None)."""
+    vm = np.zeros(slots) if values else None
+    va = np.zeros(slots) if values else None
     info = pf_info()
     rc = _check(lib().pf_poll(ctx, ticket, _ptr(vm, C.c_double), _ptr(va, C.c_double),
                               C.byref(info)))
@@ -416,6 +426,14 @@ def pf_poll(ctx, ticket: int, slots: int):
 
 def pf_drain(ctx, timeout_ms=60_000):
     _check(lib().pf_drain(ctx, timeout_ms))
+
+
+def pf_serve_get_stats(ctx) -> dict:
+    """Counters of the context's serving runtime (requests, group launches,
+    largest group, most requests on the GPU at once)."""
+    st = pf_serve_stats()
+    _check(lib().pf_serve_get_stats(ctx, C.byref(st)))
+    return st.as_dict()
 
 
 def pf_case_pattern(c: CaseHandle, nnz: int):

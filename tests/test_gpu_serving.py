@@ -67,6 +67,12 @@ def test_served_results_equal_standalone_solves(pf):
             tickets.append(t)
             slots[t] = pool[ci][1].slots
         res = _wait(pf, ctx, tickets, slots)
+        # the requests overlapped on the GPU: several of them in one launch
+        # of cases of different sizes, and several on the GPU at once
+        st = pf.pf_serve_get_stats(ctx)
+        assert st["requests"] == len(reqs)
+        assert st["max_group"] > 1 and st["peak_running"] > 1
+        assert st["group_launches"] < len(reqs)
         for k, (ci, pl, ql, pg) in enumerate(reqs):
             vm, va, info = res[tickets[k]]
             assert info["status"] == 0 and info["mismatch"] <= 1e-8, info

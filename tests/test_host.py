@@ -248,7 +248,8 @@ def _c_struct_fields(header, name):
 
 @pytest.mark.parametrize("cname,pyname", [("pf_opts", "pf_opts"), ("pf_info", "pf_info"),
                                           ("pf_case_desc", "pf_case_desc"),
-                                          ("pf_case_stats", "pf_case_stats")])
+                                          ("pf_case_stats", "pf_case_stats"),
+                                          ("pf_serve_stats", "pf_serve_stats")])
 def test_binding_structs_mirror_the_header(pf, cname, pyname):
     """The ctypes mirrors list the header's fields in the header's order (a
     field added to one side only, or reordered, shifts every later field)."""
