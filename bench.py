@@ -705,10 +705,11 @@ def serving_stream(pf, ctx, pool, rate=2000.0, duration=60.0, seed=9, topologies
     return out
 
 
-def profile_launches(count, B=608, S=4, threads=512):
-    """``count`` batched solves of B scenarios of the main step's grid with a
-    fixed launch shape, kernel by kernel (ncu does not look inside the CUDA
-    graph of a batch)."""
+def profile_launches(count, B=608, S=32, threads=512, grid="mesh10000"):
+    """``count`` batched solves of B scenarios of a grid (default: the main
+    step's) in a fixed launch shape (default: the one the autotuner picks for
+    the main step's factorisation), kernel by kernel (ncu does not look inside
+    the CUDA graph of a batch)."""
     import torch
 
     import __graft_entry__
@@ -718,7 +719,7 @@ def profile_launches(count, B=608, S=4, threads=512):
 
     dev = torch.device("cuda:0")
     ctx = pf.pf_ctx_create(0)
-    case = _case()
+    case = named_case((grid, 0))
     c = pf.pf_create_case(ctx, case)
     pl, ql, pg = _batch(case, B, seed=1)
     d = [torch.tensor(a, device=dev) for a in (pl, ql, pg)]
@@ -734,6 +735,48 @@ def profile_launches(count, B=608, S=4, threads=512):
     print(json.dumps({"solves": count, "B": B, "launch": pf.pf_launch_config(c, o, B),
                       "all_converged": bool((inf["status"] == 0).all())}))
     pf.pf_destroy_case(c)
+    pf.pf_ctx_destroy(ctx)
+
+
+def profile_single(count, precision="mixed", method="nr"):
+    """``count`` single solves of the main step's grid (the persistent
+    single-solve kernel), for ncu."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1711_10579_gb300 import pf
+
+    ctx = pf.pf_ctx_create(0)
+    case = _case()
+    c = pf.pf_create_case(ctx, case)
+    o = pf.make_opts(precision=pf.PF_MIXED if precision == "mixed" else pf.PF_FP64,
+                     method=pf.PF_NK if method == "nk" else pf.PF_NR)
+    infos = [pf.pf_solve(c, o)[2] for _ in range(count)]
+    print(json.dumps({"solves": count, "status": [i["status"] for i in infos],
+                      "iterations": [i["iterations"] for i in infos],
+                      "solve_us": [i["solve_us"] for i in infos]}))
+    pf.pf_destroy_case(c)
+    pf.pf_ctx_destroy(ctx)
+
+
+def profile_serve(count):
+    """``count`` served requests submitted at once, over a 500-, a 2,000-, a
+    10,000-bus grid and a 2,000-node feeder (group launches), for ncu."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1711_10579_gb300 import cases, pf
+
+    ctx = pf.pf_ctx_create(0)
+    pool = [cases.transmission_case(500, 675, 100, 3), cases.case_2000bus(0), _case(),
+            cases.feeder_case(2000, 4)]
+    hs = [pf.pf_create_case(ctx, c) for c in pool]
+    tickets = [(pf.pf_submit(ctx, hs[k % 4]), hs[k % 4].slots) for k in range(count)]
+    pf.pf_drain(ctx, 120_000)
+    st = [pf.pf_poll(ctx, t, n, values=False)[2]["status"] for t, n in tickets]
+    print(json.dumps({"requests": count, "status": st, "runtime": pf.pf_serve_get_stats(ctx)}))
+    for h in hs:
+        pf.pf_destroy_case(h)
     pf.pf_ctx_destroy(ctx)
 
 
@@ -753,6 +796,16 @@ def main():
                     help="only run the batched solve this many times (for ncu)")
     ap.add_argument("--profile-batch", type=int, default=608,
                     help="scenarios of the --profile-launches batch")
+    ap.add_argument("--profile-shape", default="32,512",
+                    help="scenarios per CTA and threads of the --profile-launches batch")
+    ap.add_argument("--profile-grid", default="mesh10000",
+                    help="grid of the --profile-launches batch (mesh10000, mesh2000, ...)")
+    ap.add_argument("--profile-single", type=int, default=0,
+                    help="only run this many single solves of the main grid (for ncu)")
+    ap.add_argument("--profile-precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--profile-method", default="nr", choices=["nr", "nk"])
+    ap.add_argument("--profile-serve", type=int, default=0,
+                    help="only submit this many served requests at once (for ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -762,8 +815,15 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.profile_single:
+        profile_single(args.profile_single, args.profile_precision, args.profile_method)
+        return
+    if args.profile_serve:
+        profile_serve(args.profile_serve)
+        return
     if args.profile_launches:
-        profile_launches(args.profile_launches, args.profile_batch)
+        S, T = (int(x) for x in args.profile_shape.split(","))
+        profile_launches(args.profile_launches, args.profile_batch, S, T, args.profile_grid)
         return
 
     # the oracle's worker processes (spawned), for the error check of the

@@ -596,6 +596,18 @@ int pf_solve(pf_case c, const pf_opts* opts, double* vmag, double* vang, pf_info
   return rc;
 }
 
+// The device address of a host buffer the GPU can reach directly (pinned
+// memory), or null (pageable memory, or no buffer).
+static void* device_view(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
                    const double* p_gen, const pf_opts* opts, double* vmag, double* vang,
                    pf_info* info) {
@@ -612,6 +624,25 @@ int pf_solve_batch(pf_case c, int B, const double* p_load, const double* q_load,
                       o.method == PF_NK ? o.gmres_restart : 0);
   if (rc != PF_OK) return rc;
   const size_t per = (size_t)c->data.n * (c->data.kind == PF_SINGLE_PHASE ? 1 : 3);
+  // A Newton-Raphson batch whose host buffers are all pinned: the set-up
+  // kernel reads the inputs and the result kernels write the outputs over the
+  // host link directly, with no staging copies around the solve.
+  if (B > 1 && o.method == PF_NR && !(o.q_limits && !c->data.q_max.empty())) {
+    const void* hp[6] = {p_load, q_load, p_gen, vmag, vang, info};
+    void* dp[6];
+    bool direct = true;
+    for (int k = 0; k < 6; ++k) {
+      dp[k] = device_view(hp[k]);
+      if (hp[k] && !dp[k]) direct = false;
+    }
+    if (direct) {
+      rc = run_solve(c, o, B, (const double*)dp[0], (const double*)dp[1], (const double*)dp[2],
+                     ws, st, RunMode::Solve, (double*)dp[3], (double*)dp[4], (pf_info*)dp[5]);
+      if (rc != PF_OK) return rc;
+      const cudaError_t e = cudaStreamSynchronize(st);
+      return e == cudaSuccess ? PF_OK : cuda_error(e, "running the solve");
+    }
+  }
   cudaError_t e = cudaSuccess;
   if (p_load) e = cudaMemcpyAsync(ws->st_p_load, p_load, per * B * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && q_load)

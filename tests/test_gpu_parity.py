@@ -267,6 +267,36 @@ def test_device_entry_point_matches_host_entry_point(pf, ctx):
         pf.pf_destroy_case(c)
 
 
+def test_pinned_host_buffers_are_read_and_written_in_place(pf, ctx):
+    """pf_solve_batch on pinned host buffers runs the batch reading the inputs
+    and writing the results in place over the host link (no staging copies):
+    on a ragged batch its results equal those of pageable buffers (staged
+    copies) bit for bit, with the same per-scenario records."""
+    torch = pytest.importorskip("torch")
+    case = cases.case_2000bus(3)
+    B = 37
+    p_load, q_load, p_gen = cases.scenario_loads(case, B, seed=6)
+    c = pf.pf_create_case(ctx, case)
+    try:
+        vm_p, va_p, info_p = pf.pf_solve_batch(c, p_load, q_load, p_gen)
+
+        def pinned(shape, dtype=torch.float64):
+            return torch.zeros(shape, dtype=dtype, pin_memory=True).numpy()
+
+        h = [pinned(a.shape) for a in (p_load, q_load, p_gen)]
+        for dst, src in zip(h, (p_load, q_load, p_gen)):
+            dst[...] = src
+        vm, va = pinned((B, case.n_bus)), pinned((B, case.n_bus))
+        info = pinned((B * pf.INFO_DTYPE.itemsize,), torch.uint8).view(pf.INFO_DTYPE)
+        pf.pf_solve_batch(c, h[0], h[1], h[2], out=(vm, va, info))
+        assert np.all(info["status"] == 0) and np.all(info["mismatch"] <= 1e-8)
+        assert np.array_equal(vm, vm_p) and np.array_equal(va, va_p)
+        for k in ("status", "iterations", "linear_iterations", "mismatch", "max_step"):
+            assert np.array_equal(info[k], info_p[k]), k
+    finally:
+        pf.pf_destroy_case(c)
+
+
 # ----------------------------------------------------------------------------
 # three phase (current injection)
 # ----------------------------------------------------------------------------
