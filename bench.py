@@ -36,13 +36,18 @@ sys.path.insert(0, ROOT)
 METRIC = "converged solves/sec at 1e-8 pu mismatch"
 B_MAIN = 4864
 ORACLE_SAMPLE = 16  # results of the timed step checked against the oracle
-# DRAM traffic per scenario-unit of each phase kernel, from ncu captures of
-# the 608-scenario batch (traffic scales with the scenarios of a launch).
-# Valid only for the kernel sources each was measured on (sha256 prefix of
-# csrc/batch.cu + csrc/kernels.cuh); otherwise the traffic is reported as null.
+# DRAM traffic per scenario-unit of each phase kernel: ncu dram__bytes_read +
+# dram__bytes_write of the first launch of each (every scenario running) in a
+# batch of 4,864 scenarios of the 10,000-bus grid in the tuned shapes (one-pass
+# capture at full size, profiles/batch_launches_mesh10000x4864.md), divided by
+# the 4,864 scenarios.  Valid only for the kernel sources it was measured on
+# (sha256 prefix of csrc/batch.cu + csrc/kernels.cuh); otherwise null.
+NCU_SOURCES = "5bac099f215f5e82"
 NCU_TRAFFIC = {
-    "k_solve": {"sources_sha256": "22df78494f6b7caa", "bytes_per_unit": 831.92e6 / 608},
-    "k_factor": {"sources_sha256": "22df78494f6b7caa", "bytes_per_unit": 1245.2e6 / 608},
+    "k_factor": 14_134_855_936 / 4864,
+    "k_solve": 7_858_597_632 / 4864,
+    "k_mismatch": 7_413_365_248 / 4864,
+    "k_update": 3_054_434_560 / 4864,
 }
 WORKLOAD = (f"mesh10000 x {B_MAIN} load scenarios per step, batched Newton-Raphson, "
             "FP32 LU + FP64 mismatch/refinement/update, one CUDA graph per batch")
@@ -158,10 +163,10 @@ def _sources_sha():
 def _ncu_traffic(kernel, units):
     """Measured DRAM bytes of a launch of `kernel` over `units` scenario-units,
     if the sources are the ones profiled (else None)."""
-    rec = NCU_TRAFFIC.get(kernel)
-    if rec is None or _sources_sha() != rec["sources_sha256"]:
+    per = NCU_TRAFFIC.get(kernel)
+    if per is None or _sources_sha() != NCU_SOURCES:
         return None
-    return rec["bytes_per_unit"] * units
+    return per * units
 
 
 # phase of pf_profile_solve -> (kernel, unit counted per scenario)
@@ -193,7 +198,10 @@ def kernel_rooflines(case, st, B, phase_us, pinfo, peak):
                                     "linear_iterations": "pass"}[u],
                      "units": units[u], "device_us": phase_us[ph],
                      "launch_us": phase_us[ph] / launches[u],
-                     "share_of_phases": phase_us[ph] / sum(phase_us.values())}
+                     "share_of_phases": phase_us[ph] / sum(phase_us.values()),
+                     "traffic": _ncu_traffic(kern, B),
+                     "traffic_over_algorithmic": (NCU_TRAFFIC[kern] / per[kern]
+                                                  if _ncu_traffic(kern, B) else None)}
     return out
 
 
@@ -705,11 +713,11 @@ def serving_stream(pf, ctx, pool, rate=2000.0, duration=60.0, seed=9, topologies
     return out
 
 
-def profile_launches(count, B=608, S=32, threads=512, grid="mesh10000"):
+def profile_launches(count, B=608, S=0, threads=0, grid="mesh10000"):
     """``count`` batched solves of B scenarios of a grid (default: the main
-    step's) in a fixed launch shape (default: the one the autotuner picks for
-    the main step's factorisation), kernel by kernel (ncu does not look inside
-    the CUDA graph of a batch)."""
+    step's), kernel by kernel (ncu does not look inside the CUDA graph of a
+    batch), in the autotuned shapes of the factorisation and the sweeps (the
+    timed step's), or in a fixed shape S scenarios per CTA x threads."""
     import torch
 
     import __graft_entry__
@@ -726,11 +734,17 @@ def profile_launches(count, B=608, S=32, threads=512, grid="mesh10000"):
     vm = torch.zeros((B, case.n_bus), dtype=torch.float64, device=dev)
     va = torch.zeros_like(vm)
     info = torch.zeros((B, pf.INFO_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    if S == 0:
+        pf.pf_autotune(c, B, pf.make_opts())
     o = pf.make_opts(scen_per_cta=S, block_threads=threads, kernel_by_kernel=1)
     s = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    # the profiled solves (ncu --nvtx --nvtx-include "pf_profiled/")
+    torch.cuda.nvtx.range_push("pf_profiled")
     for _ in range(count):
         pf.pf_solve_batch_device(c, B, d[0], d[1], d[2], o, vm, va, info, s.cuda_stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     inf = np.frombuffer(info.cpu().numpy().tobytes(), dtype=pf.INFO_DTYPE)
     print(json.dumps({"solves": count, "B": B, "launch": pf.pf_launch_config(c, o, B),
                       "all_converged": bool((inf["status"] == 0).all())}))
@@ -796,8 +810,9 @@ def main():
                     help="only run the batched solve this many times (for ncu)")
     ap.add_argument("--profile-batch", type=int, default=608,
                     help="scenarios of the --profile-launches batch")
-    ap.add_argument("--profile-shape", default="32,512",
-                    help="scenarios per CTA and threads of the --profile-launches batch")
+    ap.add_argument("--profile-shape", default="0,0",
+                    help="scenarios per CTA and threads of the --profile-launches batch "
+                         "(0,0: the autotuned shapes)")
     ap.add_argument("--profile-grid", default="mesh10000",
                     help="grid of the --profile-launches batch (mesh10000, mesh2000, ...)")
     ap.add_argument("--profile-single", type=int, default=0,
