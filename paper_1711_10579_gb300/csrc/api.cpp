@@ -280,8 +280,8 @@ size_t Workspace::bytes_for(int kind, int n, long long nnz_lu, int B, int m) {
   size_t t = 0;
   t += nb * (kind == PF_SINGLE_PHASE ? 3 : 6) * 8;      // spec
   t += (kind == PF_SINGLE_PHASE ? 2 : 0) * nb * 8;      // vm, va
-  t += 3 * nb * nsl * 16;                               // V, I, dV
-  t += (kind == PF_SINGLE_PHASE ? 40 : 0) * nb;         // U, FP32 (U, |V|), FP32 loads
+  t += 2 * nb * nsl * 16;                               // V, dV
+  t += (kind == PF_SINGLE_PHASE ? 16 : 0) * nb;         // U (FP64 solves)
   t += (kind == PF_SINGLE_PHASE ? 0 : 15) * nb * 8;     // abcd, PV reactive injection
   t += 3 * nb * bs * 8;                                 // F, dx, r
   t += (size_t)nnz_lu * B * bs * bs * 8;                // lu
