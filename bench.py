@@ -39,8 +39,8 @@ ORACLE_SAMPLE = 16  # results of the timed step checked against the oracle
 # DRAM traffic per scenario-unit of each phase kernel: ncu dram__bytes_read +
 # dram__bytes_write of the first launch of each (every scenario running) in a
 # batch of 4,864 scenarios of the 10,000-bus grid in the tuned shapes (one-pass
-# capture at full size, profiles/batch_launches_mesh10000x4864.md), divided by
-# the 4,864 scenarios.  Valid only for the kernel sources it was measured on
+# capture at full size of `--profile-launches 1 --profile-batch 4864`), divided
+# by the 4,864 scenarios.  Valid only for the kernel sources it was measured on
 # (sha256 prefix of csrc/batch.cu + csrc/kernels.cuh); otherwise null.
 NCU_SOURCES = "5bac099f215f5e82"
 NCU_TRAFFIC = {
