@@ -170,10 +170,10 @@ cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const Dev
                           const DevOpts& o, int grid, int cluster, int threads,
                           cudaStream_t st);
 int max_cluster(int bs, bool fp32, bool nk, int threads);
-// Group launch (newton.cu): list.n CTAs, CTA b solving desc[list.job[b]]
-// with smem bytes of dynamic shared memory.
+// Group launch (newton.cu): list.n clusters of `cluster` CTAs (1-8), cluster
+// b solving desc[list.job[b]] with smem bytes of dynamic shared memory per CTA.
 cudaError_t launch_newton_group(int bs, bool fp32, const GroupJob* desc, const GroupList& list,
-                                size_t smem, cudaStream_t st);
+                                size_t smem, int cluster, cudaStream_t st);
 // Branch flows and losses (flows.cu); device arrays, ph = 1 or 3.
 cudaError_t launch_branch_flows(int ph, const int2* ft, const double* yb, const double* sh, int n,
                                 int m, int B, const double* vm, const double* va, double* pf_,

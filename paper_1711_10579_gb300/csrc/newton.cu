@@ -721,27 +721,29 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) newton_kernel(DevSys S, D
   newton_solve<BS, TF, CL, NK>(S, w, o, blockIdx.x / csize);
 }
 
-// Several cases of different sizes in one launch: CTA b solves the job
-// list.job[b] of the descriptor array (its own case, workspace, inputs and
-// outputs) as a single-CTA Newton-Raphson solve.  Descriptors, inputs and
-// outputs may live in pinned host memory.  When its results are written the
-// CTA raises the job's done flag, so every job can be retired on its own
-// while the other CTAs of the launch still run.
-template <int BS, typename TF>
+// Several cases of different sizes in one launch: CTA (or, with CL, cluster)
+// b solves the job list.job[b] of the descriptor array (its own case,
+// workspace, inputs and outputs) as a single-scenario Newton-Raphson solve.
+// Descriptors, inputs and outputs may live in pinned host memory.  When its
+// results are written the CTA (cluster) raises the job's done flag, so every
+// job can be retired on its own while the rest of the launch still runs.
+template <int BS, typename TF, bool CL>
 __global__ void __launch_bounds__(BS == 2 ? 512 : 256)
     newton_group_kernel(const GroupJob* desc, GroupList list) {
+  const int csize = CL ? (int)cg::this_cluster().num_blocks() : 1;
+  const int crank = CL ? (int)cg::this_cluster().block_rank() : 0;
   __shared__ GroupJob job;
   {
-    const unsigned* src = reinterpret_cast<const unsigned*>(desc + list.job[blockIdx.x]);
+    const unsigned* src = reinterpret_cast<const unsigned*>(desc + list.job[blockIdx.x / csize]);
     unsigned* dst = reinterpret_cast<unsigned*>(&job);
     for (int k = threadIdx.x; k < (int)(sizeof(GroupJob) / 4); k += blockDim.x) dst[k] = src[k];
   }
   __syncthreads();
-  newton_solve<BS, TF, false, false>(job.S, job.w, job.o, 0);
+  newton_solve<BS, TF, CL, false>(job.S, job.w, job.o, 0);
   // the results (every thread's writes) reach the host before the flag
   __threadfence_system();
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  csync<CL>();
+  if (crank == 0 && threadIdx.x == 0) {
     __threadfence_system();
     *reinterpret_cast<volatile int*>(job.done) = 1;
   }
@@ -864,26 +866,46 @@ cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const Dev
 #undef PF_LAUNCH
 }
 
-template <int BS, typename TF>
+template <int BS, typename TF, bool CL>
 static cudaError_t launch_group_t(const GroupJob* desc, const GroupList& list, size_t smem,
-                                  cudaStream_t st) {
-  auto kern = newton_group_kernel<BS, TF>;
+                                  int cluster, cudaStream_t st) {
+  auto kern = newton_group_kernel<BS, TF, CL>;
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<list.n, BS == 2 ? 512 : 256, smem, st>>>(desc, list);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(list.n * cluster);
+  cfg.blockDim = dim3(BS == 2 ? 512 : 256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (CL) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, desc, list);
 }
 
 cudaError_t launch_newton_group(int bs, bool fp32, const GroupJob* desc, const GroupList& list,
-                                size_t smem, cudaStream_t st) {
-  if (list.n <= 0 || list.n > kGroupMax) return cudaErrorInvalidValue;
-  if (bs == 2) return fp32 ? launch_group_t<2, float>(desc, list, smem, st)
-                           : launch_group_t<2, double>(desc, list, smem, st);
-  return fp32 ? launch_group_t<6, float>(desc, list, smem, st)
-              : launch_group_t<6, double>(desc, list, smem, st);
+                                size_t smem, int cluster, cudaStream_t st) {
+  if (list.n <= 0 || list.n > kGroupMax || cluster < 1 || cluster > 8) return cudaErrorInvalidValue;
+  const bool cl = cluster > 1;
+#define PF_GROUP(BSV, TFT)                                                              \
+  return cl ? launch_group_t<BSV, TFT, true>(desc, list, smem, cluster, st)              \
+            : launch_group_t<BSV, TFT, false>(desc, list, smem, cluster, st);
+  if (bs == 2) {
+    if (fp32) { PF_GROUP(2, float) }
+    PF_GROUP(2, double)
+  }
+  if (fp32) { PF_GROUP(6, float) }
+  PF_GROUP(6, double)
+#undef PF_GROUP
 }
 
 int max_cluster(int bs, bool fp32, bool nk, int threads) {

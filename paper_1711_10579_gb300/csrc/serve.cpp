@@ -4,7 +4,8 @@
 // Newton-Raphson requests run as group launches: one launch takes every
 // queued request that fits (free job slots and the context's HBM budget),
 // of any cases and sizes, and each of its CTAs solves one request on its own
-// (newton.cu: newton_group_kernel).  A job's descriptor, inputs and outputs
+// (newton.cu: newton_group_kernel); the largest requests run in a separate
+// group launch of 4-CTA clusters, one cluster per request.  A job's descriptor, inputs and outputs
 // live in pinned host memory; the CTA raises the job's done flag when its
 // results are written, so every request retires as soon as its own solve
 // ends, while the other CTAs of its launch still run.  New requests form the
@@ -42,6 +43,10 @@ constexpr int kGroupStreams = 64;  // group launches in flight at once (each on 
 constexpr int kSlots = 8;         // per-request launches (Newton-Krylov, reactive limits)
 constexpr size_t kMaxQueue = 1 << 20;
 constexpr size_t kGroupSmemMax = 200 * 1024;  // a job's solve vector in shared memory up to this
+// Requests of at least this many rows (buses; nodes of a feeder) run on a
+// cluster of kBigCluster CTAs instead of one CTA: their single-CTA solve is
+// the tail of the latency (a 63,000-bus grid: 65 ms on one CTA, 37 ms on 4).
+constexpr int kBigRows1ph = 16000, kBigRows3ph = 5000, kBigCluster = 4;
 
 struct Request {
   pf_ticket id = 0;
@@ -57,6 +62,10 @@ struct Request {
 bool grouped(const Request& r) {
   return r.o.method == PF_NR && !(r.o.q_limits && !r.c->data.q_max.empty()) &&
          !r.o.block_threads && !r.o.scen_per_cta && !r.o.cluster_size;
+}
+
+bool big(const Request& r) {
+  return r.c->data.n >= (r.c->data.kind == PF_SINGLE_PHASE ? kBigRows1ph : kBigRows3ph);
 }
 
 size_t slots_of(const Request& r) {
@@ -322,8 +331,9 @@ struct Server {
       size_t smem = 0;
       int bs = 2;
       bool fp32 = true;
+      int cluster = 1;
     };
-    Group grp[4];
+    Group grp[8];
     for (Group& g : grp) g.list.n = 0;
     std::vector<std::pair<int, int>> failed;  // (job, status)
     lk.unlock();
@@ -335,9 +345,11 @@ struct Server {
         failed.push_back({k, rc});
         continue;
       }
-      Group& g = grp[(r->c->bs == 2 ? 0 : 2) + (r->o.precision == PF_MIXED ? 0 : 1)];
+      Group& g = grp[(r->c->bs == 2 ? 0 : 2) + (r->o.precision == PF_MIXED ? 0 : 1) +
+                     (big(*r) ? 4 : 0)];
       g.bs = r->c->bs;
       g.fp32 = r->o.precision == PF_MIXED;
+      g.cluster = big(*r) ? kBigCluster : 1;
       g.smem = std::max(g.smem, smem);
       g.list.job[g.list.n++] = k;
     }
@@ -354,7 +366,8 @@ struct Server {
         }
       }
       gnext = (sidx + 1) % kGroupStreams;
-      const cudaError_t e = launch_newton_group(g.bs, g.fp32, h_desc, g.list, g.smem, gst[sidx]);
+      const cudaError_t e =
+          launch_newton_group(g.bs, g.fp32, h_desc, g.list, g.smem, g.cluster, gst[sidx]);
       for (int q = 0; q < g.list.n; ++q) {
         if (e == cudaSuccess) jobs[g.list.job[q]].stream = sidx;
         else failed.push_back({g.list.job[q], PF_ERR_CUDA});

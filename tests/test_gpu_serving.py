@@ -55,8 +55,10 @@ def test_served_results_equal_standalone_solves(pf):
     ctx = pf.pf_ctx_create(0)
     try:
         pool = []
+        # the last two run on 4-CTA clusters (16,000 buses, 5,000 feeder nodes and more)
         for case in (cases.transmission_case(800, 1080, 160, 1), cases.case_2000bus(3),
-                     cases.feeder_case(600, 2), cases.transmission_case(5000, 6750, 1000, 4)):
+                     cases.feeder_case(600, 2), cases.transmission_case(5000, 6750, 1000, 4),
+                     cases.transmission_case(17000, 22950, 3400, 5), cases.feeder_case(5200, 6)):
             pool.append((case, pf.pf_create_case(ctx, case)))
         rng = np.random.default_rng(0)
         reqs = _requests(rng, pool, 48)
