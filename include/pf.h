@@ -302,7 +302,9 @@ int pf_solve_batch_device(pf_case c, int B, const double* d_p_load,
  * from the case's last result if opts->warm_start: a served solve reads the
  * case's warm-start voltages only while no other served solve of the case
  * writes them, and writes them only when it is the case's only served solve
- * on the GPU.  PF_ERR_BUSY if the queue is full.  Thread safe.
+ * on the GPU.  A Newton-Krylov request that ends without convergence is
+ * solved again with Newton-Raphson when opts->nk_fallback (info.fallback = 1),
+ * as in pf_solve.  PF_ERR_BUSY if the queue is full.  Thread safe.
  */
 int pf_submit(pf_ctx ctx, pf_case c, const double* p_load, const double* q_load,
               const double* p_gen, const pf_opts* opts, pf_ticket* out);

@@ -57,6 +57,7 @@ struct Request {
   pf_info info{};
   int state = 0;  // 0 queued, 1 running, 2 done
   size_t footprint = 0;
+  int nk_lin = -1;  // Newton-Krylov inner iterations before a Newton-Raphson redo
 };
 
 bool grouped(const Request& r) {
@@ -281,6 +282,10 @@ struct Server {
     r->vm.assign(J.io.h_out, J.io.h_out + per);
     r->va.assign(J.io.h_out + per, J.io.h_out + 2 * per);
     r->info = h_info[k];
+    if (r->nk_lin >= 0) {  // a Newton-Krylov request solved again by Newton-Raphson
+      r->info.fallback = 1;
+      r->info.linear_iterations = r->nk_lin;
+    }
     if (J.warm_in) --warm_readers[r->c];
     if (J.warm_out) {
       --warm_writers[r->c];
@@ -438,10 +443,28 @@ struct Server {
   void finish(Slot& s) {
     Request* r = s.req;
     const size_t per = slots_of(*r);
+    s.req = nullptr;
+    if (s.h_info->status != PF_OK && r->o.method == PF_NK && r->o.nk_fallback) {
+      // Newton-Krylov ended without convergence: the request is solved again
+      // with Newton-Raphson from a flat start, as pf_solve does
+      r->nk_lin = s.h_info->linear_iterations;
+      used -= r->footprint;
+      --running;
+      r->o.method = PF_NR;
+      r->o.cluster_size = r->o.block_threads = r->o.scen_per_cta = 0;
+      r->o.warm_start = 0;
+      r->footprint = footprint(*r);
+      r->state = 0;
+      queue.push_front(r);
+      return;
+    }
     r->vm.assign(s.io.h_out, s.io.h_out + per);
     r->va.assign(s.io.h_out + per, s.io.h_out + 2 * per);
     r->info = *s.h_info;
-    s.req = nullptr;
+    if (r->nk_lin >= 0) {
+      r->info.fallback = 1;
+      r->info.linear_iterations = r->nk_lin;
+    }
     end(r);
   }
 

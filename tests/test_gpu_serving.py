@@ -206,3 +206,46 @@ def test_served_solves_enforce_reactive_limits(pf):
         pf.pf_destroy_case(h3)
     finally:
         pf.pf_ctx_destroy(ctx)
+
+
+def test_served_fp64_and_newton_krylov_requests(pf):
+    """FP64 Newton-Raphson requests (group launches in FP64, one CTA and a
+    4-CTA cluster) equal the same solves run alone; Newton-Krylov requests
+    (one launch each) match the oracle, and one that does not converge falls
+    back to Newton-Raphson; all kinds mixed in one stream."""
+    ctx = pf.pf_ctx_create(0)
+    try:
+        small = cases.case_2000bus(2)
+        large = cases.transmission_case(17000, 22950, 3400, 7)
+        hs, hl = pf.pf_create_case(ctx, small), pf.pf_create_case(ctx, large)
+        f64 = pf.make_opts(precision=pf.PF_FP64)
+        nk = pf.make_opts(method=pf.PF_NK)
+        jobs = []
+        for k in range(6):
+            case, h = (small, hs) if k % 2 == 0 else (large, hl)
+            pl, ql, pg = cases.scenario_loads(case, 1, seed=40 + k, sigma=0.1)
+            o = nk if k in (2, 4) else f64
+            jobs.append((case, h, pl, ql, pg, o, pf.pf_submit(ctx, h, pl[0], ql[0], pg[0], o)))
+        # a Newton-Krylov request that GMRES cannot finish (2 inner iterations
+        # per Newton step) is solved again with Newton-Raphson, as pf_solve does
+        starved = pf.make_opts(method=pf.PF_NK, gmres_max_iter=2)
+        pl, ql, pg = cases.scenario_loads(large, 1, seed=60, sigma=0.1)
+        jobs.append((large, hl, pl, ql, pg, starved, pf.pf_submit(ctx, hl, pl[0], ql[0], pg[0],
+                                                                  starved)))
+        res = _wait(pf, ctx, [j[-1] for j in jobs], {j[-1]: j[1].slots for j in jobs})
+        assert res[jobs[-1][-1]][2]["fallback"] == 1
+        for case, h, pl, ql, pg, o, t in jobs:
+            vm, va, info = res[t]
+            assert info["status"] == 0 and info["mismatch"] <= 1e-8, info
+            if o.method == pf.PF_NR:
+                vm1, va1, _ = pf.pf_solve_batch(h, pl, ql, pg, o)
+                assert np.max(np.abs(vm - vm1[0])) <= 1e-12
+                assert np.max(np.abs(va - va1[0])) <= 1e-12
+            else:
+                ref = O.newton_polar(case.with_loads(pl[0], ql[0], pg[0]))
+                assert np.max(np.abs(vm - ref["vm"])) <= 1e-6
+                assert np.max(np.abs(va - ref["va"])) <= 1e-6
+        pf.pf_destroy_case(hs)
+        pf.pf_destroy_case(hl)
+    finally:
+        pf.pf_ctx_destroy(ctx)
