@@ -42,12 +42,12 @@ ORACLE_SAMPLE = 16  # results of the timed step checked against the oracle
 # capture at full size of `--profile-launches 1 --profile-batch 4864`), divided
 # by the 4,864 scenarios.  Valid only for the kernel sources it was measured on
 # (sha256 prefix of csrc/batch.cu + csrc/kernels.cuh); otherwise null.
-NCU_SOURCES = "5bac099f215f5e82"
+NCU_SOURCES = "fd0a3dd178d0f4ab"
 NCU_TRAFFIC = {
-    "k_factor": 14_134_855_936 / 4864,
-    "k_solve": 7_858_597_632 / 4864,
-    "k_mismatch": 7_413_365_248 / 4864,
-    "k_update": 3_054_434_560 / 4864,
+    "k_factor": 14_056_934_144 / 4864,
+    "k_solve": 7_858_743_296 / 4864,
+    "k_mismatch": 7_567_003_648 / 4864,
+    "k_update": 3_054_577_920 / 4864,
 }
 WORKLOAD = (f"mesh10000 x {B_MAIN} load scenarios per step, batched Newton-Raphson, "
             "FP32 LU + FP64 mismatch/refinement/update, one CUDA graph per batch")
