@@ -752,16 +752,16 @@ def profile_launches(count, B=608, S=0, threads=0, grid="mesh10000"):
     pf.pf_ctx_destroy(ctx)
 
 
-def profile_single(count, precision="mixed", method="nr"):
-    """``count`` single solves of the main step's grid (the persistent
-    single-solve kernel), for ncu."""
+def profile_single(count, precision="mixed", method="nr", grid="mesh10000"):
+    """``count`` single solves of a grid (default: the main step's) in the
+    persistent single-solve kernel, for ncu."""
     import __graft_entry__
 
     __graft_entry__.build()
     from paper_1711_10579_gb300 import pf
 
     ctx = pf.pf_ctx_create(0)
-    case = _case()
+    case = named_case((grid, 0))
     c = pf.pf_create_case(ctx, case)
     o = pf.make_opts(precision=pf.PF_MIXED if precision == "mixed" else pf.PF_FP64,
                      method=pf.PF_NK if method == "nk" else pf.PF_NR)
@@ -814,7 +814,8 @@ def main():
                     help="scenarios per CTA and threads of the --profile-launches batch "
                          "(0,0: the autotuned shapes)")
     ap.add_argument("--profile-grid", default="mesh10000",
-                    help="grid of the --profile-launches batch (mesh10000, mesh2000, ...)")
+                    help="grid of --profile-launches / --profile-single (mesh10000, mesh2000, "
+                         "feeder8000, ...)")
     ap.add_argument("--profile-single", type=int, default=0,
                     help="only run this many single solves of the main grid (for ncu)")
     ap.add_argument("--profile-precision", default="mixed", choices=["mixed", "fp64"])
@@ -831,7 +832,8 @@ def main():
         run_reference(args, rank, world)
         return
     if args.profile_single:
-        profile_single(args.profile_single, args.profile_precision, args.profile_method)
+        profile_single(args.profile_single, args.profile_precision, args.profile_method,
+                       args.profile_grid)
         return
     if args.profile_serve:
         profile_serve(args.profile_serve)

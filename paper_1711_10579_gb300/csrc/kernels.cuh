@@ -1474,6 +1474,172 @@ __device__ __noinline__ void factor_warp(const FactorArgs<TF> S, const Team tm, 
   }
 }
 
+// One level of factor_run for one scenario (S = 1), a warp per item with the
+// lanes on the entries of the block: lane t computes entries t and t + 32 of
+// a product, and the rows of the augmented matrix [A | I] of blk_inv's
+// Gauss-Jordan elimination are updated by all lanes at once.  Every entry
+// goes through the same operations in the same order as in blk_inv /
+// blk_mul / blk_msub, so results are bit for bit those of factor_run.
+// This GPU's FP64 pipe takes a warp instruction per 64 cycles per SM
+// sub-partition however many lanes are active, so a 6x6 FP64 item of ~1,000
+// FP64 instructions in one thread holds a narrow level for ~30 us; spread
+// over the lanes an item is ~150 warp instructions (more per item than 32
+// items a warp, so wide levels stay a thread per item).  The warps of every
+// CTA of the team take items (CL: a cluster).
+template <int BS, typename TF>
+struct FactorCoop {
+  static constexpr int kWarps = 8;     // warps of a CTA that take items
+  static constexpr int kMaxItems = 32;  // levels of at most this many items
+  static constexpr int BB = BS * BS, AW = 2 * BS;
+  static constexpr int words = BS * AW + 2 * BB;  // [A | I] (step 2: the target), two blocks
+};
+
+template <int BS, typename TF, bool CL>
+__device__ __noinline__ void factor_coop_level(const FactorArgs<TF> S, const Team tm, int l) {
+  using P = FactorCoop<BS, TF>;
+  constexpr int BB = P::BB, AW = P::AW;
+  static_assert(BB <= 64 && (BS - 1) * AW <= 64 && AW <= 32, "two entries per lane at most");
+  __shared__ TF sh[P::kWarps][P::words];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = min(P::kWarps, (int)(blockDim.x >> 5));
+  // CTAs of the team (S = 1: tid = threadIdx.x * csize + crank)
+  const int csize = tm.nthr / (int)blockDim.x;
+  const int crank = tm.tid - (int)threadIdx.x * csize;
+  const int gw = wid * csize + crank, ngw = nw * csize;  // this warp, warps of the team
+  const bool on = tm.ns > 0 && (tm.act & 1u) && wid < nw;
+  const int gs = tm.s0;
+  TF* aug = sh[min(wid, P::kWarps - 1)];  // BS rows of AW: [A | A^-1 in progress]
+  TF* X = aug + BS * AW;
+  TF* Y = X + BB;
+  TF* Z = aug;  // step 2's target block
+  auto gblk = [&](int e) { return S.lu + ((size_t)e * S.B + gs) * BB; };
+  auto load = [&](TF* dst, const TF* src) {
+    for (int q = lane; q < BB; q += 32) dst[q] = __ldcg(src + q);
+  };
+  auto store = [&](TF* dst, const TF* src) {
+    for (int q = lane; q < BB; q += 32) dst[q] = src[q];
+  };
+  // C -= A B on the lanes' entries (blk_msub's order of the k terms)
+  auto msub = [&](TF* C, const TF* A, const TF* B) {
+    for (int q = lane; q < BB; q += 32) {
+      const int i = q / BS, j = q % BS;
+      TF s = C[q];
+#pragma unroll
+      for (int k = 0; k < BS; ++k) s -= A[i * BS + k] * B[k * BS + j];
+      C[q] = s;
+    }
+  };
+  // step 1: r = {e, k, diag(k)}: U_kk^-1 for the diagonal, else L_ik = A_ik U_kk^-1
+  const int f0 = S.fac_ptr[l], nf = S.fac_ptr[l + 1] - f0;
+  if (on) {
+    for (int t = gw; t < nf; t += ngw) {
+      const int4 r = __ldg(S.fac_rec + f0 + t);
+      const TF* d = gblk(r.z);
+      for (int q = lane; q < BS * AW; q += 32) {
+        const int i = q / AW, j = q % AW;
+        aug[q] = j < BS ? __ldcg(d + i * BS + j) : (j - BS == i ? TF(1) : TF(0));
+      }
+      if (r.x != r.z) load(X, gblk(r.x));
+      __syncwarp();
+      bool ok = true;
+      for (int c = 0; c < BS; ++c) {
+        // pivot row: the first largest |a_rc|, r >= c (every lane alike)
+        int piv = c;
+        TF best = aug[c * AW + c] < 0 ? -aug[c * AW + c] : aug[c * AW + c];
+        for (int rr = c + 1; rr < BS; ++rr) {
+          const TF v = aug[rr * AW + c] < 0 ? -aug[rr * AW + c] : aug[rr * AW + c];
+          if (v > best) {
+            best = v;
+            piv = rr;
+          }
+        }
+        if (!(best > TF(0)) || !isfinite(best)) ok = false;
+        if (piv != c && lane < AW) {
+          const TF t0 = aug[c * AW + lane];
+          aug[c * AW + lane] = aug[piv * AW + lane];
+          aug[piv * AW + lane] = t0;
+        }
+        __syncwarp();
+        const TF dv = TF(1) / aug[c * AW + c];
+        __syncwarp();
+        if (lane < AW) aug[c * AW + lane] *= dv;
+        __syncwarp();
+        // rows r != c: a_rj -= a_rc a_cj, with a_rc read before any write
+        TF nv[2];
+        int at[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int q = lane + 32 * h;
+          at[h] = -1;
+          if (q < (BS - 1) * AW) {
+            int rr = q / AW;
+            rr += rr >= c;
+            const int j = q % AW;
+            const TF f = aug[rr * AW + c];
+            TF v = aug[rr * AW + j];
+            v -= f * aug[c * AW + j];
+            nv[h] = v;
+            at[h] = rr * AW + j;
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          if (at[h] >= 0) aug[at[h]] = nv[h];
+        __syncwarp();
+      }
+      if (r.x == r.z) {
+        if (!ok && lane == 0) S.flag[gs] = 1;
+        TF* u = S.uinv + ((size_t)r.y * S.B + gs) * BB;
+        for (int q = lane; q < BB; q += 32) u[q] = aug[(q / BS) * AW + BS + q % BS];
+      } else {
+        TF* o = gblk(r.x);
+        for (int q = lane; q < BB; q += 32) {
+          const int i = q / BS, j = q % BS;
+          TF s = 0;
+#pragma unroll
+          for (int k = 0; k < BS; ++k) s += X[i * BS + k] * aug[k * AW + BS + j];
+          o[q] = s;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  csync<CL>();
+  // step 2: r = {e, L entry, U entry, rest}: A_e -= L U, then the rest
+  const int t0 = S.tgt_ptr[l], nt = S.tgt_ptr[l + 1] - t0;
+  if (nt == 0) return;
+  if (on) {
+    for (int t = gw; t < nt; t += ngw) {
+      const int4 r = __ldg(S.tgt_rec + t0 + t);
+      const int e = r.x & ~kFillFirst;
+      if (r.x & kFillFirst) {
+        for (int q = lane; q < BB; q += 32) Z[q] = TF(0);
+      } else {
+        load(Z, gblk(e));
+      }
+      load(X, gblk(r.y));
+      load(Y, gblk(r.z));
+      __syncwarp();
+      msub(Z, X, Y);
+      if (r.w >= 0) {
+        for (int q = r.w;; ++q) {
+          const int2 cq = __ldg(S.con + q);
+          if (cq.x < 0) break;
+          __syncwarp();
+          load(X, gblk(cq.x));
+          load(Y, gblk(cq.y));
+          __syncwarp();
+          msub(Z, X, Y);
+        }
+      }
+      store(gblk(e), Z);
+      __syncwarp();
+    }
+  }
+  csync<CL>();
+}
+
 template <int BS, typename TF, bool CL>
 __device__ __forceinline__ void factor_levels(const DevSys& S, const DevWork& w, const Team& tm,
                                               int l0, int l1, unsigned char* ring) {
@@ -1488,6 +1654,27 @@ __device__ __forceinline__ void factor_levels(const DevSys& S, const DevWork& w,
   f.tgt_rec = S.tgt_rec;
   f.con = S.con;
   f.ring = ring;
+  // a single solve of 6x6 FP64 blocks: the levels of few items a warp per
+  // item, the others a thread per item
+  if constexpr (BS == 6 && sizeof(TF) == 8) {
+    if (tm.S == 1) {
+      for (int l = l0; l < l1;) {
+        auto items = [&](int q) {
+          return max(S.fac_ptr[q + 1] - S.fac_ptr[q], S.tgt_ptr[q + 1] - S.tgt_ptr[q]);
+        };
+        if (items(l) <= FactorCoop<BS, TF>::kMaxItems) {
+          factor_coop_level<BS, TF, CL>(f, tm, l);
+          ++l;
+        } else {
+          int l2 = l + 1;
+          while (l2 < l1 && items(l2) > FactorCoop<BS, TF>::kMaxItems) ++l2;
+          factor_run<BS, TF, CL>(f, tm, l, l2);
+          l = l2;
+        }
+      }
+      return;
+    }
+  }
   if constexpr (BS == 2 && !CL) {
     if (tm.S == 32 && ring) {
       factor_warp<TF>(f, tm, l0, l1);

@@ -761,7 +761,8 @@ static cudaError_t launch_t(const DevSys& S, const DevWork& w, const DevOpts& o,
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = dynamic_smem_bytes(BS, sizeof(TF), NK, S.n, o, threads);
-  if (cfg.dynamicSmemBytes > 48 * 1024) {
+  // (static + dynamic shared memory above 48 KB needs the opt-in)
+  if (cfg.dynamicSmemBytes > 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.dynamicSmemBytes);
     if (e != cudaSuccess) return e;
@@ -870,7 +871,7 @@ template <int BS, typename TF, bool CL>
 static cudaError_t launch_group_t(const GroupJob* desc, const GroupList& list, size_t smem,
                                   int cluster, cudaStream_t st) {
   auto kern = newton_group_kernel<BS, TF, CL>;
-  if (smem > 48 * 1024) {
+  if (smem > 0) {  // (static + dynamic shared memory above 48 KB needs the opt-in)
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
