@@ -1494,12 +1494,18 @@ struct FactorCoop {
   static constexpr int words = BS * AW + 2 * BB;  // [A | I] (step 2: the target), two blocks
 };
 
+// The warps' scratch, one array for both team kinds of a kernel.
+template <int BS, typename TF>
+__device__ __forceinline__ TF* factor_coop_scratch() {
+  __shared__ TF sh[FactorCoop<BS, TF>::kWarps * FactorCoop<BS, TF>::words];
+  return sh;
+}
+
 template <int BS, typename TF, bool CL>
 __device__ __noinline__ void factor_coop_level(const FactorArgs<TF> S, const Team tm, int l) {
   using P = FactorCoop<BS, TF>;
   constexpr int BB = P::BB, AW = P::AW;
   static_assert(BB <= 64 && (BS - 1) * AW <= 64 && AW <= 32, "two entries per lane at most");
-  __shared__ TF sh[P::kWarps][P::words];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nw = min(P::kWarps, (int)(blockDim.x >> 5));
   // CTAs of the team (S = 1: tid = threadIdx.x * csize + crank)
@@ -1508,7 +1514,8 @@ __device__ __noinline__ void factor_coop_level(const FactorArgs<TF> S, const Tea
   const int gw = wid * csize + crank, ngw = nw * csize;  // this warp, warps of the team
   const bool on = tm.ns > 0 && (tm.act & 1u) && wid < nw;
   const int gs = tm.s0;
-  TF* aug = sh[min(wid, P::kWarps - 1)];  // BS rows of AW: [A | A^-1 in progress]
+  // BS rows of AW: [A | A^-1 in progress]
+  TF* aug = factor_coop_scratch<BS, TF>() + (size_t)min(wid, P::kWarps - 1) * P::words;
   TF* X = aug + BS * AW;
   TF* Y = X + BB;
   TF* Z = aug;  // step 2's target block
