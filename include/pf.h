@@ -397,8 +397,8 @@ int pf_newton_step(pf_case c, const pf_opts* opts, const double* vmag,
  * solves of one case that overlap on the GPU may start from a mix of two
  * solutions, so a caller that warm-starts must not let them overlap.
  *
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Every call shares the array and the
+ * The first call on a device also looks up the array's device address (a
+ * host-side query, cached for later calls).  Every call shares the array and the
  * kernel writes all it later reads, so a call does not depend on what an
  * earlier call left there; calls that overlap on the GPU (other streams, or
  * other host threads) race on it and must be serialised by the caller.
