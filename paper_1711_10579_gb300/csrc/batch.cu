@@ -289,12 +289,16 @@ __global__ void __launch_bounds__(BS == 2 ? 512 : 256) k_solve(DevSys S, DevWork
   a.nlev = S.nflev;
   a.gsz = S.g_fwd;
   a.red = reinterpret_cast<TF*>(dsm);
+  a.refine = nullptr;
   // the staged records after the lanes' partial sums (16-byte aligned)
   a.srec = reinterpret_cast<int4*>(dsm + (((size_t)blockDim.x * BS * sizeof(TF) + 15) & ~(size_t)15));
   sweep_batch<BS, TF, true>(a, tm);
   a.rhs = nullptr;
   a.dx = w.dx;
   a.accumulate = (pass == 0) ? 0 : 1;
+  // single phase, first pass: the step of a scenario that takes no
+  // refinement stays in y (k_update reads it there)
+  a.refine = (BS == 2 && pass == 0) ? w.refine : nullptr;
   a.lev_ptr = S.blev_ptr;
   a.rec = S.bwd_rec;
   a.nlev = S.nblev;
@@ -317,8 +321,10 @@ __global__ void __launch_bounds__(kRowThreads) k_resid(DevSys S, DevWork w, int 
   for (int i = t.i; i < t.iend; i += t.di) resid_row<BS == 6>(S, w, i, t.gs);
 }
 
-// Step E: voltage update and the norm of the step.
-template <int BS>
+// Step E: voltage update and the norm of the step.  Single phase: the step
+// of a scenario that refined is in dx, of the others in y (FP32 in mixed
+// precision: 8 bytes per bus read instead of 16, and 16 not written).
+template <int BS, typename TF>
 __global__ void __launch_bounds__(kRowThreads) k_update(DevSys S, DevWork w, int sb) {
   RowTile t;
   const bool on = row_tile(w.B, S.n, sb, t) && w.status[t.gs] == kRunning;
@@ -326,7 +332,9 @@ __global__ void __launch_bounds__(kRowThreads) k_update(DevSys S, DevWork w, int
   int it = 0;
   if (on) {
     it = w.iter[t.gs] - 1;  // the stop test advanced it
-    for (int i = t.i; i < t.iend; i += t.di) m = max(m, abs_bits(update_row<BS == 6>(S, w, i, t.gs)));
+    const TF* y = (BS == 2 && !(w.refine[t.gs] & 1)) ? reinterpret_cast<const TF*>(w.y) : nullptr;
+    for (int i = t.i; i < t.iend; i += t.di)
+      m = max(m, abs_bits(update_row<BS == 6, TF>(S, w, i, t.gs, y)));
   }
   commit_max(m, sb, on, w.step + (size_t)(it & 1) * w.B + t.gs);
 }
@@ -434,7 +442,7 @@ struct Plan {
       ref.push_back(
           Launch{(const void*)k_solve<BS, TF>, gsv, dim3(threads_s), red, {&S, &w, &os, &pass1}});
     }
-    post = {rowk((const void*)k_update<BS>), rowk((const void*)k_mismatch<BS, TF>), stop};
+    post = {rowk((const void*)k_update<BS, TF>), rowk((const void*)k_mismatch<BS, TF>), stop};
     body = pre;
     body.insert(body.end(), ref.begin(), ref.end());
     body.insert(body.end(), post.begin(), post.end());
@@ -505,7 +513,7 @@ cudaError_t run_direct(Plan<BS, TF>& p, cudaStream_t st, unsigned long long* pro
     if (l.fn == ffac) return (int)kProfFactor;
     if (l.fn == fmis) return (int)kProfMismatch;
     if (l.fn == (const void*)k_stop) return (int)kProfStop;
-    if (l.fn == (const void*)k_update<BS>) return (int)kProfUpdate;
+    if (l.fn == (const void*)k_update<BS, TF>) return (int)kProfUpdate;
     if (l.fn == (const void*)k_setup<BS> || l.fn == (const void*)k_setup_tile)
       return (int)kProfSetup;
     if (l.fn == (const void*)k_output<BS> || l.fn == (const void*)k_output_tile)

@@ -748,6 +748,9 @@ struct BSweep {
   const int8_t* gsz;   // lanes per row for each level
   TF* red;             // shared memory for the partial sums of lanes
   int4* srec;          // shared memory for kSweepStage row records, or null
+  const int* refine;   // backward, dx not accumulated: dx only for the
+                       // scenarios with bit 0 set (the others' step stays
+                       // in y, where the update reads it), or null = all
 };
 
 // Rows of a wide level whose records one batched sweep stages in shared
@@ -796,10 +799,11 @@ __device__ __forceinline__ void brow_entry(const BRow<BS, TF>& P, const BSweep<T
   }
 }
 
-// Forward: y_i = b_i - acc.  Backward: y_i = U_ii^-1 (y_i - acc), and dx.
+// Forward: y_i = b_i - acc.  Backward: y_i = U_ii^-1 (y_i - acc), and dx
+// unless nodx.
 template <int BS, typename TF, bool FWD>
 __device__ __forceinline__ void brow_finish(const BRow<BS, TF>& P, const BSweep<TF>& a, int gs,
-                                            const TF (&acc)[BS]) {
+                                            const TF (&acc)[BS], bool nodx) {
   constexpr int BB = BS * BS;
   const size_t bi = ((size_t)P.i * a.B + gs) * BS;
   TF t[BS];
@@ -825,7 +829,7 @@ __device__ __forceinline__ void brow_finish(const BRow<BS, TF>& P, const BSweep<
   }
 #pragma unroll
   for (int c = 0; c < BS; ++c) a.y[bi + c] = t[c];
-  if (!FWD && a.dx) {
+  if (!FWD && a.dx && !nodx) {
 #pragma unroll
     for (int c = 0; c < BS; ++c)
       a.dx[bi + c] = a.accumulate ? __ldcg(a.dx + bi + c) + (double)t[c] : (double)t[c];
@@ -851,6 +855,7 @@ __device__ __noinline__ void sweep_batch(const BSweep<TF> a, const Team tm) {
   const bool on = slot < tm.ns && ((tm.act >> slot) & 1u);
   const int gs = tm.s0 + slot;
   const int q = tm.tid / NS, nq = tm.nthr / NS;
+  const bool nodx = !FWD && a.refine != nullptr && on && !(a.refine[gs] & 1);
   auto pref = [&](int l, BRow<BS, TF>& P) {
     const int G = a.gsz[l], base = a.lev_ptr[l], width = a.lev_ptr[l + 1] - base;
     const int group = q / G;
@@ -877,7 +882,7 @@ __device__ __noinline__ void sweep_batch(const BSweep<TF> a, const Team tm) {
 #pragma unroll
             for (int c = 0; c < BS; ++c) acc[rr] += L[rr * BS + c] * a.y[bk + c];
         }
-        if (P.i >= 0) brow_finish<BS, TF, FWD>(P, a, gs, acc);
+        if (P.i >= 0) brow_finish<BS, TF, FWD>(P, a, gs, acc, nodx);
       };
       if (on && q < width) row(cur);  // its record came during the last level
       if (a.srec && width > nq) {
@@ -941,7 +946,7 @@ __device__ __noinline__ void sweep_batch(const BSweep<TF> a, const Team tm) {
           }
         }
       }
-      if (row && lane == 0) brow_finish<BS, TF, FWD>(cur, a, gs, acc);
+      if (row && lane == 0) brow_finish<BS, TF, FWD>(cur, a, gs, acc, nodx);
     }
     __syncthreads();
     cur = nxt;
@@ -1955,8 +1960,12 @@ __device__ __forceinline__ void resid_row(const DevSys& S, const DevWork& w, int
 
 // Voltage update of row i (Sec. II.A box: delta += Delta delta, |V| +=
 // Delta|V|; Sec. II.B box: V^c += Delta V^c).  Returns the largest step.
-template <bool THREE>
-__device__ __forceinline__ double update_row(const DevSys& S, const DevWork& w, int i, int gs) {
+// Single phase: the step from dx, or (y non-null) from the solve vector y of
+// the sweeps, which holds it when no refinement followed (the same values:
+// dx = (double) y there).
+template <bool THREE, typename TY = double>
+__device__ __forceinline__ double update_row(const DevSys& S, const DevWork& w, int i, int gs,
+                                             const TY* y = nullptr) {
   const int B = w.B;
   constexpr int NSL = THREE ? 3 : 1;
   const size_t b = (size_t)i * B + gs;
@@ -1982,7 +1991,17 @@ __device__ __forceinline__ double update_row(const DevSys& S, const DevWork& w, 
       }
     }
   } else {
-    const double dd = __ldcg(w.dx + b * 2), dm = __ldcg(w.dx + b * 2 + 1);
+    // (d angle, d|V|) with one vector load
+    double dd, dm;
+    if (y && sizeof(TY) == 4) {
+      const float2 q = __ldcg(reinterpret_cast<const float2*>(y) + b);
+      dd = (double)q.x;
+      dm = (double)q.y;
+    } else {
+      const double2 q = __ldcg(reinterpret_cast<const double2*>(y ? (const void*)y : (const void*)w.dx) + b);
+      dd = q.x;
+      dm = q.y;
+    }
     stp = __longlong_as_double((long long)max(abs_bits(dd), abs_bits(dm)));
     const double vm = __ldcg(w.vm + b) + dm, va = __ldcg(w.va + b) + dd;
     w.vm[b] = vm;
