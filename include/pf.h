@@ -321,8 +321,9 @@ int pf_drain(pf_ctx ctx, int timeout_ms);
  * the first pf_submit).  Newton-Raphson requests (no reactive limits, default
  * launch shape) run as group launches: one launch solves several queued
  * requests of any cases and sizes, one CTA each (a cluster of 4 CTAs for
- * grids of 16,000 buses or feeders of 5,000 nodes and more), and each request
- * retires when its own solve ends.  Newton-Krylov requests and requests with reactive
+ * grids of 16,000 buses or feeders of 5,000 nodes and more, of 8 CTAs from
+ * 40,000 buses or 12,000 nodes), and each request retires when its own solve
+ * ends.  Newton-Krylov requests and requests with reactive
  * limits run as one launch each.
  */
 typedef struct {

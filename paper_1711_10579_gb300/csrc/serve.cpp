@@ -4,8 +4,9 @@
 // Newton-Raphson requests run as group launches: one launch takes every
 // queued request that fits (free job slots and the context's HBM budget),
 // of any cases and sizes, and each of its CTAs solves one request on its own
-// (newton.cu: newton_group_kernel); the largest requests run in a separate
-// group launch of 4-CTA clusters, one cluster per request.  A job's descriptor, inputs and outputs
+// (newton.cu: newton_group_kernel); the largest requests run in separate
+// group launches of 4- and 8-CTA clusters, one cluster per request.  A job's
+// descriptor, inputs and outputs
 // live in pinned host memory; the CTA raises the job's done flag when its
 // results are written, so every request retires as soon as its own solve
 // ends, while the other CTAs of its launch still run.  New requests form the
@@ -44,9 +45,11 @@ constexpr int kSlots = 8;         // per-request launches (Newton-Krylov, reacti
 constexpr size_t kMaxQueue = 1 << 20;
 constexpr size_t kGroupSmemMax = 200 * 1024;  // a job's solve vector in shared memory up to this
 // Requests of at least this many rows (buses; nodes of a feeder) run on a
-// cluster of kBigCluster CTAs instead of one CTA: their single-CTA solve is
-// the tail of the latency (a 63,000-bus grid: 65 ms on one CTA, 37 ms on 4).
+// cluster of CTAs instead of one CTA: their single-CTA solve is the tail of
+// the latency (a 63,000-bus grid: 65 ms on one CTA, 37 ms on 4).  Two tiers:
+// kBigCluster CTAs from kBigRows*, kHugeCluster from kHugeRows*.
 constexpr int kBigRows1ph = 16000, kBigRows3ph = 5000, kBigCluster = 4;
+constexpr int kHugeRows1ph = 40000, kHugeRows3ph = 12000, kHugeCluster = 8;
 
 struct Request {
   pf_ticket id = 0;
@@ -65,8 +68,12 @@ bool grouped(const Request& r) {
          !r.o.block_threads && !r.o.scen_per_cta && !r.o.cluster_size;
 }
 
-bool big(const Request& r) {
-  return r.c->data.n >= (r.c->data.kind == PF_SINGLE_PHASE ? kBigRows1ph : kBigRows3ph);
+// 0: one CTA; 1: kBigCluster CTAs; 2: kHugeCluster CTAs
+int size_tier(const Request& r) {
+  const bool one = r.c->data.kind == PF_SINGLE_PHASE;
+  const int n = r.c->data.n;
+  if (n >= (one ? kHugeRows1ph : kHugeRows3ph)) return 2;
+  return n >= (one ? kBigRows1ph : kBigRows3ph) ? 1 : 0;
 }
 
 size_t slots_of(const Request& r) {
@@ -338,7 +345,7 @@ struct Server {
       bool fp32 = true;
       int cluster = 1;
     };
-    Group grp[8];
+    Group grp[12];
     for (Group& g : grp) g.list.n = 0;
     std::vector<std::pair<int, int>> failed;  // (job, status)
     lk.unlock();
@@ -350,11 +357,11 @@ struct Server {
         failed.push_back({k, rc});
         continue;
       }
-      Group& g = grp[(r->c->bs == 2 ? 0 : 2) + (r->o.precision == PF_MIXED ? 0 : 1) +
-                     (big(*r) ? 4 : 0)];
+      const int tier = size_tier(*r);
+      Group& g = grp[(r->c->bs == 2 ? 0 : 2) + (r->o.precision == PF_MIXED ? 0 : 1) + 4 * tier];
       g.bs = r->c->bs;
       g.fp32 = r->o.precision == PF_MIXED;
-      g.cluster = big(*r) ? kBigCluster : 1;
+      g.cluster = tier == 2 ? kHugeCluster : (tier == 1 ? kBigCluster : 1);
       g.smem = std::max(g.smem, smem);
       g.list.job[g.list.n++] = k;
     }
