@@ -42,12 +42,12 @@ ORACLE_SAMPLE = 16  # results of the timed step checked against the oracle
 # capture at full size of `--profile-launches 1 --profile-batch 4864`), divided
 # by the 4,864 scenarios.  Valid only for the kernel sources it was measured on
 # (sha256 prefix of csrc/batch.cu + csrc/kernels.cuh); otherwise null.
-NCU_SOURCES = "fd0a3dd178d0f4ab"
+NCU_SOURCES = "a6c0d90eac7da3ed"
 NCU_TRAFFIC = {
-    "k_factor": 14_056_934_144 / 4864,
-    "k_solve": 7_858_743_296 / 4864,
-    "k_mismatch": 7_567_003_648 / 4864,
-    "k_update": 3_054_577_920 / 4864,
+    "k_factor": (8_101_610_496 + 5_945_336_320) / 4864,
+    "k_solve": (6_198_040_832 + 843_860_224) / 4864,
+    "k_mismatch": (3_846_259_968 + 3_717_613_824) / 4864,
+    "k_update": (1_167_779_328 + 1_493_288_960) / 4864,
 }
 WORKLOAD = (f"mesh10000 x {B_MAIN} load scenarios per step, batched Newton-Raphson, "
             "FP32 LU + FP64 mismatch/refinement/update, one CUDA graph per batch")
