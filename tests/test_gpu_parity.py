@@ -383,6 +383,31 @@ def test_solve_three_phase_matches_oracle(pf, ctx, n, prec):
         pf.pf_destroy_case(c)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
+def test_newton_step_three_phase_matches_oracle_solve(pf, ctx, prec, tol):
+    """One Newton step of the 8,000-node feeder (6x6 blocks; 66 of its 100
+    factor levels hold at most 32 items, which a single FP64 solve factors a
+    warp per item) against the oracle's sparse direct solve of Eq. 22-23 on
+    the free unknowns; absent phases take no step."""
+    case = cases.case_feeder8000(0)
+    Y = O.ybus_three_phase(case)
+    vm, va, _ = _rand_v3(case, 5)
+    V = vm * np.exp(1j * va)  # same rounding as the GPU input
+    c = pf.pf_create_case(ctx, case)
+    try:
+        p = pf.PF_FP64 if prec == "fp64" else pf.PF_MIXED
+        dx, _ = pf.pf_newton_step(c, vm, va, pf.make_opts(precision=p, refine_steps=2))
+        idx = O.cim_unknowns(case)
+        F = O.cim_mismatch(case, Y, V)[idx]
+        J = O.cim_jacobian(case, Y, V)[idx][:, idx].tocsr()
+        full = np.zeros(6 * case.n_node)
+        full[idx] = O.solve_linear(J, F, "splu")
+        ref = full.reshape(case.n_node, 6)
+        assert np.max(np.abs(dx - ref)) <= tol * max(1.0, np.max(np.abs(ref)))
+    finally:
+        pf.pf_destroy_case(c)
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_batch_graph_matches_kernel_by_kernel(pf, ctx, prec):
     """The batch as one CUDA graph (device-driven loop) and launched kernel by
