@@ -304,10 +304,24 @@ int pf_solve_batch_device(pf_case c, int B, const double* d_p_load,
  * writes them, and writes them only when it is the case's only served solve
  * on the GPU.  A Newton-Krylov request that ends without convergence is
  * solved again with Newton-Raphson when opts->nk_fallback (info.fallback = 1),
- * as in pf_solve.  PF_ERR_BUSY if the queue is full.  Thread safe.
+ * as in pf_solve.  Sixteen or more queued Newton-Raphson requests of one case
+ * with the same tol, max_iter, precision and refinement options and their own
+ * p_load and q_load (and all or none p_gen) are coalesced into one batched
+ * solve of up to 4,864 scenarios (the pf_solve_batch kernels; a flat start,
+ * warm_start ignored).  PF_ERR_BUSY if the queue is full.  Thread safe.
  */
 int pf_submit(pf_ctx ctx, pf_case c, const double* p_load, const double* q_load,
               const double* p_gen, const pf_opts* opts, pf_ticket* out);
+/*
+ * B requests of case c at once, queued together (so that they can be
+ * coalesced into one batched solve): request k has the loads
+ * p_load[k][...], q_load[k][...], p_gen[k][...] (host arrays laid out as in
+ * pf_solve_batch; NULL = the case's own) and the ticket out[k].  Either all
+ * B are queued or none (PF_ERR_BUSY when the queue cannot take them).
+ * Thread safe.
+ */
+int pf_submit_batch(pf_ctx ctx, pf_case c, int B, const double* p_load, const double* q_load,
+                    const double* p_gen, const pf_opts* opts, pf_ticket* out);
 /*
  * PF_PENDING while the request is queued or running; otherwise copies the
  * result into vmag/vang/info (host, may be NULL), releases the ticket and
@@ -323,7 +337,8 @@ int pf_drain(pf_ctx ctx, int timeout_ms);
  * requests of any cases and sizes, one CTA each (a cluster of 4 CTAs for
  * grids of 16,000 buses or feeders of 5,000 nodes and more, of 8 CTAs from
  * 40,000 buses or 12,000 nodes), and each request retires when its own solve
- * ends.  Newton-Krylov requests and requests with reactive
+ * ends.  Runs of queued requests of one case are coalesced into batched
+ * solves (pf_submit).  Newton-Krylov requests and requests with reactive
  * limits run as one launch each.
  */
 typedef struct {
@@ -331,6 +346,8 @@ typedef struct {
   uint64_t group_launches;  /* group launches issued */
   int max_group;            /* most requests in one group launch */
   int peak_running;         /* most requests on the GPU at the same time */
+  uint64_t batch_launches;  /* coalesced batched solves issued */
+  int max_batch;            /* most requests in one coalesced batch */
 } pf_serve_stats;
 int pf_serve_get_stats(pf_ctx ctx, pf_serve_stats* out);
 

@@ -51,6 +51,14 @@ constexpr size_t kGroupSmemMax = 200 * 1024;  // a job's solve vector in shared 
 constexpr int kBigRows1ph = 16000, kBigRows3ph = 5000, kBigCluster = 4;
 constexpr int kHugeRows1ph = 40000, kHugeRows3ph = 12000, kHugeCluster = 8;
 
+// Coalesced batches: kBatchMin or more queued Newton-Raphson requests of one
+// case with the same solve options and their own loads run as one batched
+// solve (the phase kernels of batch.cu in one CUDA graph, flat start) of at
+// most kBatchMax scenarios (and kBatchDoubles staged doubles per vector),
+// on one of kBatchSlots streams.
+constexpr int kBatchMin = 16, kBatchMax = 4864, kBatchSlots = 2;
+constexpr size_t kBatchDoubles = size_t(1) << 26;
+
 struct Request {
   pf_ticket id = 0;
   pf_case c = nullptr;
@@ -117,6 +125,61 @@ struct Job {
   size_t want_per = 0;
 };
 
+// One coalesced batch in flight: its stream, workspace and pinned staging
+// ([3][B][per] inputs, [2][B][per] results, [B] records), grown as needed.
+struct BatchSlot {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  Workspace ws;
+  double* h_in = nullptr;
+  double* h_out = nullptr;
+  pf_info* h_info = nullptr;
+  size_t cap = 0;  // doubles per [B][per] vector
+  int cap_B = 0;
+  std::vector<Request*> reqs;
+  size_t per = 0;
+  int ensure(size_t need, int B) {
+    if (need <= cap && B <= cap_B) return PF_OK;
+    release();
+    const size_t c = std::max(need, 2 * cap);
+    const int b = std::max(B, 2 * cap_B);
+    cudaError_t e = cudaMallocHost(&h_in, 3 * c * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_out, 2 * c * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_info, (size_t)b * sizeof(pf_info));
+    if (e != cudaSuccess) {
+      release();
+      return cuda_error(e, "allocating pinned batch staging");
+    }
+    cap = c;
+    cap_B = b;
+    return PF_OK;
+  }
+  void release() {
+    if (h_in) cudaFreeHost(h_in);
+    if (h_out) cudaFreeHost(h_out);
+    if (h_info) cudaFreeHost(h_info);
+    h_in = h_out = nullptr;
+    h_info = nullptr;
+    cap = 0;
+    cap_B = 0;
+  }
+  ~BatchSlot() { release(); }
+};
+
+// Requests that one coalesced batch can hold together: same case, options
+// that change the solve, and the same inputs given.
+bool batchable(const Request& r) {
+  return grouped(r) && !r.p_load.empty() && !r.q_load.empty() &&
+         (r.c->data.kind == PF_SINGLE_PHASE || r.p_gen.empty());
+}
+
+bool same_batch(const Request& a, const Request& b) {
+  return a.c == b.c && a.o.precision == b.o.precision && a.o.tol == b.o.tol &&
+         a.o.max_iter == b.o.max_iter && a.o.refine_steps == b.o.refine_steps &&
+         a.o.refine_below == b.o.refine_below && a.o.refine_stall == b.o.refine_stall &&
+         a.p_gen.empty() == b.p_gen.empty();
+}
+
 // One per-request launch slot: a stream with its own workspaces.
 struct Slot {
   cudaStream_t st = nullptr;
@@ -144,6 +207,7 @@ struct Server {
   int gnext = 0;
   int ginflight[kGroupStreams] = {};
   Slot slots[kSlots];
+  BatchSlot batches[kBatchSlots];
   std::unordered_map<pf_case, int> warm_readers, warm_writers;
   // largest case seen per kind (single phase, three phase): rows, factor
   // entries and staged doubles per vector
@@ -398,6 +462,126 @@ struct Server {
     return any;
   }
 
+  // ---- coalesced batches ----
+
+  // Takes the oldest run of kBatchMin or more batchable queued requests of
+  // one case and options into a free batch slot (lock held), stages and
+  // launches it without the lock.  Returns whether anything was admitted.
+  bool admit_batches(std::unique_lock<std::mutex>& lk) {
+    BatchSlot* bs = nullptr;
+    for (BatchSlot& b : batches)
+      if (b.reqs.empty()) {
+        bs = &b;
+        break;
+      }
+    if (!bs) return false;
+    Request* head = nullptr;
+    std::vector<Request*> pick;
+    for (Request* r : queue) {
+      if (!batchable(*r)) continue;
+      int cnt = 0;
+      for (Request* q : queue)
+        if (batchable(*q) && same_batch(*r, *q) && ++cnt >= kBatchMin) break;
+      if (cnt >= kBatchMin) {
+        head = r;
+        break;
+      }
+    }
+    if (!head) return false;
+    const size_t per = slots_of(*head);
+    const int cap = (int)std::min<size_t>(kBatchMax, std::max<size_t>(1, kBatchDoubles / per));
+    size_t need = 0;
+    for (Request* q : queue) {
+      if ((int)pick.size() >= cap) break;
+      if (!batchable(*q) || !same_batch(*head, *q)) continue;
+      if (used + need + q->footprint > ctx->budget) break;
+      pick.push_back(q);
+      need += q->footprint;
+    }
+    if ((int)pick.size() < kBatchMin) return false;  // wait for memory
+    for (Request* q : pick) {
+      queue.erase(std::find(queue.begin(), queue.end(), q));
+      begin(q);
+    }
+    bs->reqs = pick;
+    bs->per = per;
+    const int B = (int)pick.size();
+    ++stats.batch_launches;
+    stats.max_batch = std::max(stats.max_batch, B);
+    lk.unlock();
+    const int rc = launch_batch(*bs, B);
+    lk.lock();
+    if (rc != PF_OK) {
+      for (Request* q : bs->reqs) {
+        end(q);
+        fail(q, rc);
+      }
+      bs->reqs.clear();
+    }
+    return true;
+  }
+
+  // Stages the batch's inputs, runs the batched solve and queues the copies
+  // of its results (dispatcher thread, lock not held).
+  int launch_batch(BatchSlot& bs, int B) {
+    Request* r0 = bs.reqs[0];
+    pf_case c = r0->c;
+    const size_t per = bs.per, nb = per * (size_t)B;
+    int rc = bs.ensure(nb, B);
+    if (rc != PF_OK) return rc;
+    rc = bs.ws.ensure(c->data.kind, c->data.n, std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()),
+                      B, 0);
+    if (rc != PF_OK) return rc;
+    const bool gen = !r0->p_gen.empty();
+    for (int k = 0; k < B; ++k) {
+      const Request* r = bs.reqs[k];
+      std::memcpy(bs.h_in + k * per, r->p_load.data(), per * sizeof(double));
+      std::memcpy(bs.h_in + nb + k * per, r->q_load.data(), per * sizeof(double));
+      if (gen) std::memcpy(bs.h_in + 2 * nb + k * per, r->p_gen.data(), per * sizeof(double));
+    }
+    cudaError_t e = cudaMemcpyAsync(bs.ws.st_p_load, bs.h_in, nb * sizeof(double),
+                                    cudaMemcpyHostToDevice, bs.st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bs.ws.st_q_load, bs.h_in + nb, nb * sizeof(double),
+                          cudaMemcpyHostToDevice, bs.st);
+    if (e == cudaSuccess && gen)
+      e = cudaMemcpyAsync(bs.ws.st_p_gen, bs.h_in + 2 * nb, nb * sizeof(double),
+                          cudaMemcpyHostToDevice, bs.st);
+    if (e != cudaSuccess) return cuda_error(e, "staging batch inputs");
+    pf_opts o = r0->o;
+    o.warm_start = 0;
+    rc = run_solve(c, o, B, bs.ws.st_p_load, bs.ws.st_q_load, gen ? bs.ws.st_p_gen : nullptr,
+                   &bs.ws, bs.st, RunMode::Solve, nullptr, nullptr, nullptr);
+    if (rc != PF_OK) return rc;
+    e = cudaMemcpyAsync(bs.h_out, bs.ws.st_vm, nb * sizeof(double), cudaMemcpyDeviceToHost, bs.st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bs.h_out + nb, bs.ws.st_va, nb * sizeof(double),
+                          cudaMemcpyDeviceToHost, bs.st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bs.h_info, bs.ws.st_info, (size_t)B * sizeof(pf_info),
+                          cudaMemcpyDeviceToHost, bs.st);
+    if (e == cudaSuccess) e = cudaEventRecord(bs.ev, bs.st);
+    return e == cudaSuccess ? PF_OK : cuda_error(e, "launching a coalesced batch");
+  }
+
+  // Hands each request of a finished batch its results: copied without the
+  // lock (the requests are running, so nothing else touches their results),
+  // retired with it.
+  void finish_batch(BatchSlot& bs, std::unique_lock<std::mutex>& lk) {
+    const int B = (int)bs.reqs.size();
+    const size_t per = bs.per, nb = per * (size_t)B;
+    lk.unlock();
+    for (int k = 0; k < B; ++k) {
+      Request* r = bs.reqs[k];
+      r->vm.assign(bs.h_out + k * per, bs.h_out + (k + 1) * per);
+      r->va.assign(bs.h_out + nb + k * per, bs.h_out + nb + (k + 1) * per);
+      r->info = bs.h_info[k];
+    }
+    lk.lock();
+    for (Request* r : bs.reqs) end(r);
+    bs.reqs.clear();
+  }
+
   // ---- per-request launches ----
 
   int start(Request* r, Slot& s) {
@@ -529,6 +713,22 @@ struct Server {
         }
         progressed = true;
       }
+      for (BatchSlot& b : batches) {
+        if (b.reqs.empty()) continue;
+        const cudaError_t q = cudaEventQuery(b.ev);
+        if (q == cudaSuccess) {
+          finish_batch(b, lk);
+          progressed = true;
+        } else if (q != cudaErrorNotReady) {
+          fatal = cudaGetErrorString(q);
+          for (Request* r : b.reqs) {
+            end(r);
+            fail(r, PF_ERR_CUDA);
+          }
+          b.reqs.clear();
+          progressed = true;
+        }
+      }
       for (Slot& s : slots) {
         if (!s.req) continue;
         cudaError_t q = cudaEventQuery(s.ev);
@@ -546,7 +746,8 @@ struct Server {
       }
       if (!queue.empty()) {
         if (admit_slots()) progressed = true;
-        if (admit_groups(lk)) progressed = true;
+        if (admit_batches(lk)) progressed = true;
+        if (!queue.empty() && admit_groups(lk)) progressed = true;
       }
       if (progressed) done_cv.notify_all();
       if (stop && queue.empty() && running == 0) break;
@@ -577,6 +778,11 @@ struct Server {
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
       if (e != cudaSuccess) return cuda_error(e, "creating serving streams");
     }
+    for (BatchSlot& b : batches) {
+      e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_error(e, "creating serving streams");
+    }
     th = std::thread([this] { loop(); });
     return PF_OK;
   }
@@ -596,6 +802,11 @@ struct Server {
       if (s.st) cudaStreamDestroy(s.st);
       if (s.ev) cudaEventDestroy(s.ev);
       if (s.h_info) cudaFreeHost(s.h_info);
+    }
+    for (BatchSlot& b : batches) {
+      if (b.st) cudaStreamSynchronize(b.st);
+      if (b.st) cudaStreamDestroy(b.st);
+      if (b.ev) cudaEventDestroy(b.ev);
     }
     if (h_desc) cudaFreeHost(h_desc);
     if (h_info) cudaFreeHost(h_info);
@@ -641,6 +852,8 @@ void serve_forget_case(pf_ctx ctx, pf_case c) {
   sv->done_cv.wait(lk, [&] {
     for (Slot& s : sv->slots)
       if (s.req && s.req->c == c) return false;
+    for (BatchSlot& b : sv->batches)
+      if (!b.reqs.empty() && b.reqs[0]->c == c) return false;
     for (Job& j : sv->jobs)
       if (j.req && j.req->c == c) return false;
     return true;
@@ -657,38 +870,51 @@ using namespace pf;
 
 extern "C" {
 
-int pf_submit(pf_ctx ctx, pf_case c, const double* p_load, const double* q_load,
-              const double* p_gen, const pf_opts* opts, pf_ticket* out) {
-  if (!ctx || !c || !out) return set_error(PF_ERR_INVALID, "null argument");
+int pf_submit_batch(pf_ctx ctx, pf_case c, int B, const double* p_load, const double* q_load,
+                    const double* p_gen, const pf_opts* opts, pf_ticket* out) {
+  if (!ctx || !c || !out || B < 1) return set_error(PF_ERR_INVALID, "null argument or B < 1");
   if (c->ctx != ctx) return set_error(PF_ERR_INVALID, "the case belongs to another context");
   if (p_gen && c->data.kind != PF_SINGLE_PHASE)
     return set_error(PF_ERR_INVALID, "p_gen is for single-phase cases only");
   int rc;
   Server* sv = server_of(ctx, &rc);
   if (!sv) return rc;
-  auto r = std::make_unique<Request>();
-  r->c = c;
-  if (opts) r->o = *opts; else pf_opts_default(&r->o);
   const size_t per = (size_t)c->data.n * (c->data.kind == PF_SINGLE_PHASE ? 1 : 3);
-  if (p_load) r->p_load.assign(p_load, p_load + per);
-  if (q_load) r->q_load.assign(q_load, q_load + per);
-  if (p_gen) r->p_gen.assign(p_gen, p_gen + per);
+  std::vector<std::unique_ptr<Request>> rs(B);
+  for (int k = 0; k < B; ++k) {
+    auto& r = rs[k];
+    r = std::make_unique<Request>();
+    r->c = c;
+    if (opts) r->o = *opts; else pf_opts_default(&r->o);
+    if (p_load) r->p_load.assign(p_load + k * per, p_load + (k + 1) * per);
+    if (q_load) r->q_load.assign(q_load + k * per, q_load + (k + 1) * per);
+    if (p_gen) r->p_gen.assign(p_gen + k * per, p_gen + (k + 1) * per);
+  }
   std::lock_guard<std::mutex> lk(sv->mu);
   if (!sv->fatal.empty()) return set_error(PF_ERR_CUDA, "serving stopped: " + sv->fatal);
-  if (sv->queue.size() >= kMaxQueue) return set_error(PF_ERR_BUSY, "serving queue is full");
-  r->footprint = sv->footprint(*r);
+  if (sv->queue.size() + B > kMaxQueue) return set_error(PF_ERR_BUSY, "serving queue is full");
   {
     const int ki = c->data.kind == PF_SINGLE_PHASE ? 0 : 1;
     sv->max_n[ki] = std::max(sv->max_n[ki], c->data.n);
     sv->max_nnz[ki] = std::max(sv->max_nnz[ki], (long long)std::max(c->nr.sym.nnz_lu(), c->nk.sym.nnz_lu()));
     sv->max_per[ki] = std::max(sv->max_per[ki], per);
   }
-  r->id = sv->next++;
-  *out = r->id;
-  sv->queue.push_back(r.get());
-  sv->all.emplace(r->id, std::move(r));
+  // all B queued under one lock: the dispatcher sees them together
+  for (int k = 0; k < B; ++k) {
+    auto& r = rs[k];
+    r->footprint = sv->footprint(*r);
+    r->id = sv->next++;
+    out[k] = r->id;
+    sv->queue.push_back(r.get());
+    sv->all.emplace(r->id, std::move(r));
+  }
   sv->cv.notify_all();
   return PF_OK;
+}
+
+int pf_submit(pf_ctx ctx, pf_case c, const double* p_load, const double* q_load,
+              const double* p_gen, const pf_opts* opts, pf_ticket* out) {
+  return pf_submit_batch(ctx, c, 1, p_load, q_load, p_gen, opts, out);
 }
 
 int pf_poll(pf_ctx ctx, pf_ticket t, double* vmag, double* vang, pf_info* info) {

@@ -79,7 +79,8 @@ class pf_case_stats(C.Structure):
 
 class pf_serve_stats(C.Structure):
     _fields_ = [("requests", C.c_uint64), ("group_launches", C.c_uint64),
-                ("max_group", C.c_int), ("peak_running", C.c_int)]
+                ("max_group", C.c_int), ("peak_running", C.c_int),
+                ("batch_launches", C.c_uint64), ("max_batch", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -124,6 +125,8 @@ def lib():
                                                 vp, vp, vp]),
             "pf_submit": (C.c_int, [vp, vp, _dp, _dp, _dp, C.POINTER(pf_opts),
                                     C.POINTER(C.c_uint64)]),
+            "pf_submit_batch": (C.c_int, [vp, vp, C.c_int, _dp, _dp, _dp, C.POINTER(pf_opts),
+                                          C.POINTER(C.c_uint64)]),
             "pf_poll": (C.c_int, [vp, C.c_uint64, _dp, _dp, C.POINTER(pf_info)]),
             "pf_drain": (C.c_int, [vp, C.c_int]),
             "pf_serve_get_stats": (C.c_int, [vp, C.POINTER(pf_serve_stats)]),
@@ -409,6 +412,19 @@ def pf_submit(ctx, c: CaseHandle, p_load=None, q_load=None, p_gen=None,
     _check(lib().pf_submit(ctx, c.handle, *[_ptr(a, C.c_double) for a in arrs],
                            C.byref(opts) if opts else None, C.byref(t)))
     return t.value
+
+
+def pf_submit_batch(ctx, c: CaseHandle, p_load=None, q_load=None, p_gen=None,
+                    opts: pf_opts | None = None) -> list:
+    """B requests queued at once (arrays [B][...]); their tickets."""
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in
+            (p_load, q_load, p_gen)]
+    B = next(a.shape[0] for a in arrs if a is not None)
+    arrs = [None if a is None else a.reshape(B, -1) for a in arrs]
+    t = (C.c_uint64 * B)()
+    _check(lib().pf_submit_batch(ctx, c.handle, B, *[_ptr(a, C.c_double) for a in arrs],
+                                 C.byref(opts) if opts else None, t))
+    return list(t)
 
 
 def pf_poll(ctx, ticket: int, slots: int, values: bool = True):

@@ -249,3 +249,43 @@ def test_served_fp64_and_newton_krylov_requests(pf):
         pf.pf_destroy_case(hl)
     finally:
         pf.pf_ctx_destroy(ctx)
+
+
+def test_queued_requests_of_one_case_coalesce_into_a_batch(pf):
+    """Requests of one case queued together (pf_submit_batch) run as one
+    batched solve instead of one CTA each: every result equals pf_solve_batch
+    of the same loads (the same kernels and launch), a request of the case
+    with other options in the same burst runs on its own, and a sample
+    matches the oracle."""
+    ctx = pf.pf_ctx_create(0)
+    try:
+        case = cases.case_2000bus(2)
+        h = pf.pf_create_case(ctx, case)
+        B = 40
+        pl, ql, pg = cases.scenario_loads(case, B, seed=17)
+        opts = pf.make_opts()
+        tickets = pf.pf_submit_batch(ctx, h, pl, ql, pg, opts)
+        other = pf.make_opts(tol=1e-10)
+        t_other = pf.pf_submit(ctx, h, pl[0], ql[0], pg[0], other)
+        slots = {t: h.slots for t in tickets + [t_other]}
+        res = _wait(pf, ctx, tickets + [t_other], slots)
+        st = pf.pf_serve_get_stats(ctx)
+        assert st["batch_launches"] == 1 and st["max_batch"] == B
+        assert st["requests"] == B + 1
+        vm_b, va_b, inf_b = pf.pf_solve_batch(h, pl, ql, pg, opts)
+        for k, t in enumerate(tickets):
+            vm, va, info = res[t]
+            assert info["status"] == 0 and info["mismatch"] <= 1e-8, info
+            assert info["iterations"] == inf_b["iterations"][k]
+            assert np.max(np.abs(vm - vm_b[k])) <= 1e-12
+            assert np.max(np.abs(va - va_b[k])) <= 1e-12
+        vm, va, info = res[t_other]
+        assert info["status"] == 0 and info["mismatch"] <= 1e-10, info
+        for k in (0, B - 1):
+            ref = O.newton_polar(case.with_loads(pl[k], ql[k], pg[k]))
+            vm, va, _ = res[tickets[k]]
+            assert np.max(np.abs(vm - ref["vm"])) <= 1e-6
+            assert np.max(np.abs(va - ref["va"])) <= 1e-6
+        pf.pf_destroy_case(h)
+    finally:
+        pf.pf_ctx_destroy(ctx)
