@@ -554,7 +554,38 @@ def variants(pf, ctx, torch, dev, flush, pool):
             check=(pool, ("feeder8000", 0), False))
     pf.pf_destroy_case(c)
     out["serving"] = serving_stream(pf, ctx, pool=pool)
+    for grid, B in (("mesh2000", 512), ("mesh10000", 4864)):
+        out[f"serving_burst_{grid}_x{B}"] = serving_burst(pf, ctx, pool, grid, B)
     return out
+
+
+def serving_burst(pf, ctx, pool, grid, B, reps=2):
+    """B requests of one grid queued together (pf_submit_batch), coalesced by
+    the serving runtime into one batched solve: solves/s from the submit to
+    the last result polled (host copies of every request's inputs and
+    results included); the last of `reps` bursts is reported."""
+    from paper_1711_10579_gb300 import cases
+
+    case = named_case((grid, 0))
+    h = pf.pf_create_case(ctx, case)
+    pl, ql, pg = cases.scenario_loads(case, B, seed=23, sigma=0.2)
+    st0 = pf.pf_serve_get_stats(ctx)
+    res = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ts = pf.pf_submit_batch(ctx, h, pl, ql, pg, pf.make_opts())
+        pf.pf_drain(ctx, 600_000)
+        res = [pf.pf_poll(ctx, t, h.slots) for t in ts]
+        dt = time.perf_counter() - t0
+    st = pf.pf_serve_get_stats(ctx)
+    jobs = [((grid, 0), (pl[k], ql[k], pg[k]), False) for k in (0, B - 1)]
+    err = oracle_errors(pool, jobs, [(res[k][0], res[k][1]) for k in (0, B - 1)])
+    pf.pf_destroy_case(h)
+    return {"B": B, "seconds": dt, "solves_per_s": B / dt,
+            "converged": int(sum(r[2]["status"] == 0 for r in res)),
+            "batch_launches": st["batch_launches"] - st0["batch_launches"],
+            "max_batch": st["max_batch"], "oracle_err": err,
+            "note": "end to end through pf_submit_batch / pf_poll; host copies included"}
 
 
 def _pool_case(job):
