@@ -166,6 +166,23 @@ struct BatchSlot {
   ~BatchSlot() { release(); }
 };
 
+// Runs fn(k) for k in [0, B) on up to 8 host threads when the work is large
+// (copies of a coalesced batch's inputs and results), else on this thread.
+template <class Fn>
+void parallel_for(int B, size_t bytes, Fn fn) {
+  const int T = bytes >= (size_t(64) << 20) ? std::min(8, B) : 1;
+  if (T <= 1) {
+    for (int k = 0; k < B; ++k) fn(k);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < T; ++t)
+    th.emplace_back([&, t] {
+      for (int k = t; k < B; k += T) fn(k);
+    });
+  for (auto& x : th) x.join();
+}
+
 // Requests that one coalesced batch can hold together: same case, options
 // that change the solve, and the same inputs given.
 bool batchable(const Request& r) {
@@ -475,19 +492,19 @@ struct Server {
         break;
       }
     if (!bs) return false;
+    // the oldest request whose case has kBatchMin batchable requests queued
+    std::unordered_map<pf_case, int> per_case;
+    for (Request* r : queue)
+      if (batchable(*r)) ++per_case[r->c];
     Request* head = nullptr;
-    std::vector<Request*> pick;
     for (Request* r : queue) {
-      if (!batchable(*r)) continue;
-      int cnt = 0;
-      for (Request* q : queue)
-        if (batchable(*q) && same_batch(*r, *q) && ++cnt >= kBatchMin) break;
-      if (cnt >= kBatchMin) {
+      if (batchable(*r) && per_case[r->c] >= kBatchMin) {
         head = r;
         break;
       }
     }
     if (!head) return false;
+    std::vector<Request*> pick;
     const size_t per = slots_of(*head);
     const int cap = (int)std::min<size_t>(kBatchMax, std::max<size_t>(1, kBatchDoubles / per));
     size_t need = 0;
@@ -498,11 +515,10 @@ struct Server {
       pick.push_back(q);
       need += q->footprint;
     }
-    if ((int)pick.size() < kBatchMin) return false;  // wait for memory
-    for (Request* q : pick) {
-      queue.erase(std::find(queue.begin(), queue.end(), q));
-      begin(q);
-    }
+    if ((int)pick.size() < kBatchMin) return false;  // other options, or wait for memory
+    for (Request* q : pick) begin(q);  // state 1: running
+    queue.erase(std::remove_if(queue.begin(), queue.end(), [](const Request* q) { return q->state == 1; }),
+                queue.end());
     bs->reqs = pick;
     bs->per = per;
     const int B = (int)pick.size();
@@ -533,12 +549,12 @@ struct Server {
                       B, 0);
     if (rc != PF_OK) return rc;
     const bool gen = !r0->p_gen.empty();
-    for (int k = 0; k < B; ++k) {
+    parallel_for(B, nb * (gen ? 3 : 2) * sizeof(double), [&](int k) {
       const Request* r = bs.reqs[k];
       std::memcpy(bs.h_in + k * per, r->p_load.data(), per * sizeof(double));
       std::memcpy(bs.h_in + nb + k * per, r->q_load.data(), per * sizeof(double));
       if (gen) std::memcpy(bs.h_in + 2 * nb + k * per, r->p_gen.data(), per * sizeof(double));
-    }
+    });
     cudaError_t e = cudaMemcpyAsync(bs.ws.st_p_load, bs.h_in, nb * sizeof(double),
                                     cudaMemcpyHostToDevice, bs.st);
     if (e == cudaSuccess)
@@ -571,12 +587,12 @@ struct Server {
     const int B = (int)bs.reqs.size();
     const size_t per = bs.per, nb = per * (size_t)B;
     lk.unlock();
-    for (int k = 0; k < B; ++k) {
+    parallel_for(B, 2 * nb * sizeof(double), [&](int k) {
       Request* r = bs.reqs[k];
       r->vm.assign(bs.h_out + k * per, bs.h_out + (k + 1) * per);
       r->va.assign(bs.h_out + nb + k * per, bs.h_out + nb + (k + 1) * per);
       r->info = bs.h_info[k];
-    }
+    });
     lk.lock();
     for (Request* r : bs.reqs) end(r);
     bs.reqs.clear();
@@ -881,15 +897,16 @@ int pf_submit_batch(pf_ctx ctx, pf_case c, int B, const double* p_load, const do
   if (!sv) return rc;
   const size_t per = (size_t)c->data.n * (c->data.kind == PF_SINGLE_PHASE ? 1 : 3);
   std::vector<std::unique_ptr<Request>> rs(B);
-  for (int k = 0; k < B; ++k) {
-    auto& r = rs[k];
-    r = std::make_unique<Request>();
+  for (auto& r : rs) r = std::make_unique<Request>();
+  const int given = (p_load != nullptr) + (q_load != nullptr) + (p_gen != nullptr);
+  parallel_for(B, (size_t)given * per * B * sizeof(double), [&](int k) {
+    Request* r = rs[k].get();
     r->c = c;
     if (opts) r->o = *opts; else pf_opts_default(&r->o);
     if (p_load) r->p_load.assign(p_load + k * per, p_load + (k + 1) * per);
     if (q_load) r->q_load.assign(q_load + k * per, q_load + (k + 1) * per);
     if (p_gen) r->p_gen.assign(p_gen + k * per, p_gen + (k + 1) * per);
-  }
+  });
   std::lock_guard<std::mutex> lk(sv->mu);
   if (!sv->fatal.empty()) return set_error(PF_ERR_CUDA, "serving stopped: " + sv->fatal);
   if (sv->queue.size() + B > kMaxQueue) return set_error(PF_ERR_BUSY, "serving queue is full");
