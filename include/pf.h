@@ -334,10 +334,10 @@ int pf_drain(pf_ctx ctx, int timeout_ms);
  * Counters of the context's serving runtime since it started (all zero before
  * the first pf_submit).  Newton-Raphson requests (no reactive limits, default
  * launch shape) run as group launches: one launch solves several queued
- * requests of any cases and sizes, one CTA each (a cluster of 4 CTAs for
- * grids of 16,000 buses or feeders of 5,000 nodes and more, of 8 CTAs from
- * 40,000 buses or 12,000 nodes), and each request retires when its own solve
- * ends.  Runs of queued requests of one case are coalesced into batched
+ * requests of any cases and sizes, one CTA each (a cluster of 2 CTAs for
+ * grids of 4,000 buses or feeders of 2,000 nodes and more, of 4 CTAs from
+ * 16,000 buses or 5,000 nodes, of 8 CTAs from 40,000 buses or 12,000 nodes),
+ * and each request retires when its own solve ends.  Runs of queued requests of one case are coalesced into batched
  * solves (pf_submit).  Newton-Krylov requests and requests with reactive
  * limits run as one launch each.
  */

@@ -5,7 +5,7 @@
 // queued request that fits (free job slots and the context's HBM budget),
 // of any cases and sizes, and each of its CTAs solves one request on its own
 // (newton.cu: newton_group_kernel); the largest requests run in separate
-// group launches of 4- and 8-CTA clusters, one cluster per request.  A job's
+// group launches of 2-, 4- and 8-CTA clusters, one cluster per request.  A job's
 // descriptor, inputs and outputs
 // live in pinned host memory; the CTA raises the job's done flag when its
 // results are written, so every request retires as soon as its own solve
@@ -46,10 +46,13 @@ constexpr size_t kMaxQueue = 1 << 20;
 constexpr size_t kGroupSmemMax = 200 * 1024;  // a job's solve vector in shared memory up to this
 // Requests of at least this many rows (buses; nodes of a feeder) run on a
 // cluster of CTAs instead of one CTA: their single-CTA solve is the tail of
-// the latency (a 63,000-bus grid: 65 ms on one CTA, 37 ms on 4).  Two tiers:
-// kBigCluster CTAs from kBigRows*, kHugeCluster from kHugeRows*.
+// the latency (a 63,000-bus grid: 65 ms on one CTA, 37 ms on 4).  Tiers:
+// kMidCluster CTAs from kMidRows*, kBigCluster from kBigRows*, kHugeCluster
+// from kHugeRows*.
+constexpr int kMidRows1ph = 4000, kMidRows3ph = 2000, kMidCluster = 2;
 constexpr int kBigRows1ph = 16000, kBigRows3ph = 5000, kBigCluster = 4;
 constexpr int kHugeRows1ph = 40000, kHugeRows3ph = 12000, kHugeCluster = 8;
+constexpr int kTierCluster[4] = {1, kMidCluster, kBigCluster, kHugeCluster};
 
 // Coalesced batches: kBatchMin or more queued Newton-Raphson requests of one
 // case with the same solve options and their own loads run as one batched
@@ -76,12 +79,13 @@ bool grouped(const Request& r) {
          !r.o.block_threads && !r.o.scen_per_cta && !r.o.cluster_size;
 }
 
-// 0: one CTA; 1: kBigCluster CTAs; 2: kHugeCluster CTAs
+// The cluster size of a request is kTierCluster[size_tier].
 int size_tier(const Request& r) {
   const bool one = r.c->data.kind == PF_SINGLE_PHASE;
   const int n = r.c->data.n;
-  if (n >= (one ? kHugeRows1ph : kHugeRows3ph)) return 2;
-  return n >= (one ? kBigRows1ph : kBigRows3ph) ? 1 : 0;
+  if (n >= (one ? kHugeRows1ph : kHugeRows3ph)) return 3;
+  if (n >= (one ? kBigRows1ph : kBigRows3ph)) return 2;
+  return n >= (one ? kMidRows1ph : kMidRows3ph) ? 1 : 0;
 }
 
 size_t slots_of(const Request& r) {
@@ -426,7 +430,7 @@ struct Server {
       bool fp32 = true;
       int cluster = 1;
     };
-    Group grp[12];
+    Group grp[16];
     for (Group& g : grp) g.list.n = 0;
     std::vector<std::pair<int, int>> failed;  // (job, status)
     lk.unlock();
@@ -442,7 +446,7 @@ struct Server {
       Group& g = grp[(r->c->bs == 2 ? 0 : 2) + (r->o.precision == PF_MIXED ? 0 : 1) + 4 * tier];
       g.bs = r->c->bs;
       g.fp32 = r->o.precision == PF_MIXED;
-      g.cluster = tier == 2 ? kHugeCluster : (tier == 1 ? kBigCluster : 1);
+      g.cluster = kTierCluster[tier];
       g.smem = std::max(g.smem, smem);
       g.list.job[g.list.n++] = k;
     }
