@@ -1,6 +1,6 @@
 """Benchmark of the Newton power-flow hot path on one GB300 (or N replicas).
 
-A step solves one batch of B = 4,864 seeded load scenarios (32 per SM) of the
+A step solves one batch of B = 9,728 seeded load scenarios (64 per SM) of the
 10,000-bus synthetic transmission grid (average degree 2.7, 20% PV buses;
 every bus load x lognormal(0, 0.2), PV generation rescaled to match) to a
 power mismatch of 1e-8 pu with Newton-Raphson: FP32 sparse-LU
@@ -8,7 +8,7 @@ refactorisation and sweeps, FP64 mismatch, refinement and update.  The batch
 runs as phase kernels over the shared symbolic pattern inside one CUDA graph
 whose loop the device ends (launch shapes autotuned).  Inputs are resident
 in HBM before the timed region; each step has its own scenarios and L2 is
-flushed between timed steps.  Batches of 608 and 2,432 scenarios, single-
+flushed between timed steps.  Batches of 608, 2,432 and 4,864 scenarios, single-
 solve latency, the plain FP64 single-case solve, the Newton-Krylov solver,
 the three-phase feeder, the 2,000-bus x 512 batch and a serving stream are
 reported as variants.
@@ -34,13 +34,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "converged solves/sec at 1e-8 pu mismatch"
-B_MAIN = 4864
+B_MAIN = 9728
 ORACLE_SAMPLE = 16  # results of the timed step checked against the oracle
 # DRAM traffic per scenario-unit of each phase kernel: ncu dram__bytes_read +
 # dram__bytes_write of the first launch of each (every scenario running) in a
 # batch of 4,864 scenarios of the 10,000-bus grid in the tuned shapes (one-pass
 # capture at full size of `--profile-launches 1 --profile-batch 4864`), divided
-# by the 4,864 scenarios.  Valid only for the kernel sources it was measured on
+# by the 4,864 scenarios (a launch's traffic is taken as these bytes per
+# scenario times its scenarios).  Valid only for the kernel sources it was measured on
 # (sha256 prefix of csrc/batch.cu + csrc/kernels.cuh); otherwise null.
 NCU_SOURCES = "a6c0d90eac7da3ed"
 NCU_TRAFFIC = {
@@ -443,7 +444,7 @@ def variants(pf, ctx, torch, dev, flush, pool):
     from paper_1711_10579_gb300 import cases
 
     out = {}
-    # the 14-bus mesh: one batch of 4,864 load scenarios, and single solves
+    # the 14-bus mesh: one batch of B_MAIN load scenarios, and single solves
     case = named_case(("mesh14", 0))
     c = pf.pf_create_case(ctx, case)
     pl, ql, pg = _batch(case, B_MAIN, seed=5)
@@ -480,7 +481,7 @@ def variants(pf, ctx, torch, dev, flush, pool):
         pf, c, torch, dev, 1, pl, ql, pg, pf.make_opts(precision=pf.PF_FP64), reps=20, flush=flush,
         check=(pool, key, False))
     for Bv, prec, nm in ((608, pf.PF_MIXED, "mixed"), (2432, pf.PF_MIXED, "mixed"),
-                         (B_MAIN, pf.PF_FP64, "fp64")):
+                         (4864, pf.PF_MIXED, "mixed"), (B_MAIN, pf.PF_FP64, "fp64")):
         plb, qlb, pgb = _batch(case, Bv, seed=21)
         pf.pf_autotune(c, Bv, pf.make_opts(precision=prec))
         out[f"mesh10000_x{Bv}_batched_{nm}"] = _device_solves(

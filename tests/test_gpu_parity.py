@@ -1016,13 +1016,13 @@ def test_heavy_loading_mixed_precision(pf, ctx):
 # ----------------------------------------------------------------------------
 
 def test_full_size_batch_in_the_benchmark_launch_shape(pf, ctx):
-    """The 10,000-bus grid x 4,864 scenarios, autotuned as the benchmark runs
+    """The 10,000-bus grid x 9,728 scenarios, autotuned as the benchmark runs
     it (mixed NR, graph): every scenario converges with its PV magnitudes and
     the slack untouched; sampled scenarios match the oracle; and a random
     scenario's power mismatch, recomputed by the oracle from the GPU's
     voltages, is below the tolerance."""
     case = cases.case_10000bus(0)
-    B = 4864
+    B = 9728
     pl, ql, pg = cases.scenario_loads(case, B, seed=21, sigma=0.2)
     c = pf.pf_create_case(ctx, case)
     try:
