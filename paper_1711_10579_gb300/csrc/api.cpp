@@ -1,6 +1,7 @@
 // C ABI of the power-flow library: contexts, cases, solves and inspection
 // calls.  Host code only; every numeric step runs in the CUDA kernels of
-// newton.cu (and krylov.cu for the Newton-Krylov variant).
+// newton.cuh (single solves, Newton-Krylov, served requests), batch.cu
+// (batched Newton-Raphson), flows.cu and qlim.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -165,12 +165,12 @@ int fetch_results(pf_case c, Workspace* ws, int B, double* vmag, double* vang,
 int inspect(pf_case c, InspectKind k, const pf_opts* o, const double* vmag,
             const double* vang, double* out, pf_info* info);
 
-// Launchers in newton.cu and batch.cu.
+// Launchers in newton.cu (kernels in newton.cuh) and batch.cu.
 cudaError_t launch_newton(int bs, bool fp32, bool nk, const DevSys& S, const DevWork& w,
                           const DevOpts& o, int grid, int cluster, int threads,
                           cudaStream_t st);
 int max_cluster(int bs, bool fp32, bool nk, int threads);
-// Group launch (newton.cu): list.n clusters of `cluster` CTAs (1-8), cluster
+// Group launch (newton.cu, kernel in newton.cuh): list.n clusters of `cluster` CTAs (1-8), cluster
 // b solving desc[list.job[b]] with smem bytes of dynamic shared memory per CTA.
 cudaError_t launch_newton_group(int bs, bool fp32, const GroupJob* desc, const GroupList& list,
                                 size_t smem, int cluster, cudaStream_t st);

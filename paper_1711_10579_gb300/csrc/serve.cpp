@@ -4,7 +4,7 @@
 // Newton-Raphson requests run as group launches: one launch takes every
 // queued request that fits (free job slots and the context's HBM budget),
 // of any cases and sizes, and each of its CTAs solves one request on its own
-// (newton.cu: newton_group_kernel); the largest requests run in separate
+// (newton.cuh: newton_group_kernel); the largest requests run in separate
 // group launches of 2-, 4- and 8-CTA clusters, one cluster per request.  A job's
 // descriptor, inputs and outputs
 // live in pinned host memory; the CTA raises the job's done flag when its
