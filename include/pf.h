@@ -233,6 +233,25 @@ int pf_ybus(const pf_case_desc* desc, int64_t* nnz, int32_t* rowptr, int32_t* co
 int pf_symbolic(const pf_case_desc* desc, int method, int32_t* perm, int32_t* rowptr,
                 int32_t* col, int32_t* flevel, int32_t* blevel);
 
+/*
+ * Host-only: the packed schedule the kernels run for a method's symbolic
+ * pattern (in the new numbering of pf_symbolic; entries index its col[]),
+ * for tests and diagnostics.  sizes[6] = {n, factor levels L, backward
+ * levels, factor items F, targets T, con pairs C}; with any array NULL only
+ * what is given is written.  fac_ptr[L+1] / tgt_ptr[L+1]: items and targets
+ * of level l; fac_rec[F][4] = {entry, pivot k, diagonal entry of k, 0}
+ * (Sec. III.A fan-out step 1: U_kk^-1, or L_ik = A_ik U_kk^-1);
+ * tgt_rec[T][4] = {entry | 2^30 when a fill entry starts from zero, first L
+ * entry, first U entry, start of its other (L, U) pairs in con or -1}
+ * (step 2: A -= sum L U); con[C][2], lists ended by (-1, -1);
+ * flev_ptr[L+1] / fwd_rec[n][4] = {row, first entry, diagonal entry, 0} of
+ * the forward sweep by level; blev_ptr / bwd_rec[n][4] = {row, first U entry,
+ * end, 0} of the backward sweep.
+ */
+int pf_schedule(const pf_case_desc* desc, int method, int64_t* sizes, int32_t* fac_ptr,
+                int32_t* fac_rec, int32_t* tgt_ptr, int32_t* tgt_rec, int32_t* con,
+                int32_t* flev_ptr, int32_t* fwd_rec, int32_t* blev_ptr, int32_t* bwd_rec);
+
 /* Fill *opts with the defaults listed in pf_opts. */
 void pf_opts_default(pf_opts* opts);
 /* Message of the last failing call on this thread ("" if none). */

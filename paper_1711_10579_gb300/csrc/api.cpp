@@ -69,6 +69,47 @@ static cudaError_t upload(DevBuffer& buf, const std::vector<T>& v, const T** out
 // system upload
 // ---------------------------------------------------------------------------
 
+// The kernels' packed records of a symbolic analysis, one 16-byte load per
+// item: forward / backward sweep rows {row, first entry, end, 0} in level
+// order; factor items {entry, pivot k, diagonal entry of k, 0}; targets
+// {entry (| kFillFirst when a fill entry gets its first update, which then
+// starts from zero), first L entry, first U entry, start of the rest in
+// `con` or -1}; `con` holds the other (L, U) pairs of a target, each list
+// ended by (-1, -1) (most targets receive one update per level).
+static void pack_records(const Symbolic& s, std::vector<int4>& fwd, std::vector<int4>& bwd,
+                         std::vector<int4>& fac, std::vector<int4>& tgt, std::vector<int2>& con) {
+  const int n = s.n;
+  fwd.assign(n, make_int4(0, 0, 0, 0));
+  bwd.assign(n, make_int4(0, 0, 0, 0));
+  fac.assign(s.fac_items.size(), make_int4(0, 0, 0, 0));
+  tgt.assign(s.tgt_entry.size(), make_int4(0, 0, 0, 0));
+  for (int t = 0; t < n; ++t) {
+    const int i = s.flev_rows[t], j = s.blev_rows[t];
+    fwd[t] = make_int4(i, s.lu_rowptr[i], s.lu_diag[i], 0);
+    bwd[t] = make_int4(j, s.lu_diag[j] + 1, s.lu_rowptr[j + 1], 0);
+  }
+  for (size_t t = 0; t < fac.size(); ++t) {
+    const int e = s.fac_items[t], k = s.lu_col[e];
+    fac[t] = make_int4(e, k, s.lu_diag[k], 0);
+  }
+  con.clear();
+  std::vector<char> touched(s.nnz_lu(), 0);
+  for (size_t t = 0; t < tgt.size(); ++t) {
+    const int c0 = s.tgt_cptr[t], c1 = s.tgt_cptr[t + 1];
+    const int te = s.tgt_entry[t];
+    const bool fill_first = s.lu2y[te] < 0 && !touched[te];
+    touched[te] = 1;
+    int rest = -1;
+    if (c1 - c0 > 1) {
+      rest = (int)con.size();
+      for (int c = c0 + 1; c < c1; ++c) con.push_back(make_int2(s.con_l[c], s.con_u[c]));
+      con.push_back(make_int2(-1, -1));
+    }
+    tgt[t] = make_int4(te | (fill_first ? kFillFirst : 0), s.con_l[c0], s.con_u[c0], rest);
+  }
+  if (con.empty()) con.push_back(make_int2(-1, -1));
+}
+
 int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   analyze(y, ord, fill, sym);
   const int n = c.n;
@@ -180,36 +221,9 @@ int SysBuf::build(const CaseData& c, const Ybus& y, Ordering ord, bool fill) {
   for (size_t k = 0; k < s.perm.size(); ++k) iperm[s.perm[k]] = (int)k;
   UP(iperm, iperm);
   // packed per-item records (one 16-byte load each) for the kernels' prefetch
-  std::vector<int4> fwd(n), bwd(n), fac(s.fac_items.size()), tgt(s.tgt_entry.size());
+  std::vector<int4> fwd, bwd, fac, tgt;
   std::vector<int2> con;
-  for (int t = 0; t < n; ++t) {
-    const int i = s.flev_rows[t], j = s.blev_rows[t];
-    fwd[t] = make_int4(i, s.lu_rowptr[i], s.lu_diag[i], 0);
-    bwd[t] = make_int4(j, s.lu_diag[j] + 1, s.lu_rowptr[j + 1], 0);
-  }
-  for (size_t t = 0; t < fac.size(); ++t) {
-    const int e = s.fac_items[t], k = s.lu_col[e];
-    fac[t] = make_int4(e, k, s.lu_diag[k], 0);
-  }
-  // a target carries its first contribution; the others (rare: most targets
-  // receive one per level) follow in `con`, each list ended by (-1, -1)
-  // the first update of a fill entry (levels in order) starts from zero
-  con.clear();
-  std::vector<char> touched(s.nnz_lu(), 0);
-  for (size_t t = 0; t < tgt.size(); ++t) {
-    const int c0 = s.tgt_cptr[t], c1 = s.tgt_cptr[t + 1];
-    const int te = s.tgt_entry[t];
-    const bool fill_first = s.lu2y[te] < 0 && !touched[te];
-    touched[te] = 1;
-    int rest = -1;
-    if (c1 - c0 > 1) {
-      rest = (int)con.size();
-      for (int c = c0 + 1; c < c1; ++c) con.push_back(make_int2(s.con_l[c], s.con_u[c]));
-      con.push_back(make_int2(-1, -1));
-    }
-    tgt[t] = make_int4(te | (fill_first ? kFillFirst : 0), s.con_l[c0], s.con_u[c0], rest);
-  }
-  if (con.empty()) con.push_back(make_int2(-1, -1));
+  pack_records(s, fwd, bwd, fac, tgt, con);
   UP(fwd, fwd_rec);
   UP(bwd, bwd_rec);
   UP(fac, fac_rec);
@@ -787,6 +801,57 @@ int pf_symbolic(const pf_case_desc* desc, int method, int32_t* perm, int32_t* ro
   for (int l = 0; l + 1 < (int)s.blev_ptr.size(); ++l)
     for (int t = s.blev_ptr[l]; t < s.blev_ptr[l + 1]; ++t)
       if (blevel) blevel[s.blev_rows[t]] = l;
+  return PF_OK;
+}
+
+int pf_schedule(const pf_case_desc* desc, int method, int64_t* sizes, int32_t* fac_ptr,
+                int32_t* fac_rec, int32_t* tgt_ptr, int32_t* tgt_rec, int32_t* con,
+                int32_t* flev_ptr, int32_t* fwd_rec, int32_t* blev_ptr, int32_t* bwd_rec) {
+  if (!sizes) return set_error(PF_ERR_INVALID, "null sizes");
+  if (method != PF_NR && method != PF_NK)
+    return set_error(PF_ERR_INVALID, "method must be PF_NR or PF_NK");
+  CaseData d;
+  Ybus y;
+  std::string err;
+  int rc = copy_case(desc, d, err);
+  if (rc == PF_OK) rc = build_ybus(d, y, err);
+  if (rc != PF_OK) return set_error(rc, err);
+  Symbolic s;
+  if (method == PF_NR) analyze(y, Ordering::MinDegree, true, s);
+  else analyze(y, Ordering::RCM, false, s);
+  std::vector<int4> fwd, bwd, fac, tgt;
+  std::vector<int2> cn;
+  pack_records(s, fwd, bwd, fac, tgt, cn);
+  if (s.fac_ptr.size() != s.flev_ptr.size() || s.tgt_ptr.size() != s.flev_ptr.size())
+    return set_error(PF_ERR_INVALID, "factor and forward schedules differ in levels");
+  sizes[0] = s.n;
+  sizes[1] = (int64_t)s.flev_ptr.size() - 1;
+  sizes[2] = (int64_t)s.blev_ptr.size() - 1;
+  sizes[3] = (int64_t)fac.size();
+  sizes[4] = (int64_t)tgt.size();
+  sizes[5] = (int64_t)cn.size();
+  auto put4 = [](const std::vector<int4>& v, int32_t* out) {
+    if (!out) return;
+    for (size_t k = 0; k < v.size(); ++k) {
+      out[4 * k] = v[k].x;
+      out[4 * k + 1] = v[k].y;
+      out[4 * k + 2] = v[k].z;
+      out[4 * k + 3] = v[k].w;
+    }
+  };
+  if (fac_ptr) std::copy(s.fac_ptr.begin(), s.fac_ptr.end(), fac_ptr);
+  if (tgt_ptr) std::copy(s.tgt_ptr.begin(), s.tgt_ptr.end(), tgt_ptr);
+  if (flev_ptr) std::copy(s.flev_ptr.begin(), s.flev_ptr.end(), flev_ptr);
+  if (blev_ptr) std::copy(s.blev_ptr.begin(), s.blev_ptr.end(), blev_ptr);
+  put4(fac, fac_rec);
+  put4(tgt, tgt_rec);
+  put4(fwd, fwd_rec);
+  put4(bwd, bwd_rec);
+  if (con)
+    for (size_t k = 0; k < cn.size(); ++k) {
+      con[2 * k] = cn[k].x;
+      con[2 * k + 1] = cn[k].y;
+    }
   return PF_OK;
 }
 

@@ -113,6 +113,8 @@ def lib():
             "pf_analyze": (C.c_int, [C.POINTER(pf_case_desc), C.POINTER(pf_case_stats)]),
             "pf_ybus": (C.c_int, [C.POINTER(pf_case_desc), C.POINTER(C.c_int64), _ip, _ip, _dp]),
             "pf_symbolic": (C.c_int, [C.POINTER(pf_case_desc), C.c_int, _ip, _ip, _ip, _ip, _ip]),
+            "pf_schedule": (C.c_int, [C.POINTER(pf_case_desc), C.c_int, C.POINTER(C.c_int64),
+                                      _ip, _ip, _ip, _ip, _ip, _ip, _ip, _ip, _ip]),
             "pf_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(vp)]),
             "pf_ctx_destroy": (C.c_int, [vp]),
             "pf_create_case": (C.c_int, [vp, C.POINTER(pf_case_desc), C.POINTER(vp)]),
@@ -291,6 +293,23 @@ def pf_symbolic(case, method=PF_NR):
     _check(lib().pf_symbolic(C.byref(d.desc), method, *[_ptr(a, C.c_int32)
                                                         for a in (perm, rowptr, col, fl, bl)]))
     return perm, rowptr, col, fl, bl
+
+
+def pf_schedule(case, method=PF_NR) -> dict:
+    """The packed factor and sweep records the kernels run (pf.h)."""
+    d = make_desc(case)
+    sz = (C.c_int64 * 6)()
+    _check(lib().pf_schedule(C.byref(d.desc), method, sz, *([None] * 9)))
+    n, L, Lb, F, T, Cn = list(sz)
+    out = {"fac_ptr": np.zeros(L + 1, np.int32), "fac_rec": np.zeros((F, 4), np.int32),
+           "tgt_ptr": np.zeros(L + 1, np.int32), "tgt_rec": np.zeros((T, 4), np.int32),
+           "con": np.zeros((Cn, 2), np.int32), "flev_ptr": np.zeros(L + 1, np.int32),
+           "fwd_rec": np.zeros((n, 4), np.int32), "blev_ptr": np.zeros(Lb + 1, np.int32),
+           "bwd_rec": np.zeros((n, 4), np.int32)}
+    keys = ("fac_ptr", "fac_rec", "tgt_ptr", "tgt_rec", "con", "flev_ptr", "fwd_rec",
+            "blev_ptr", "bwd_rec")
+    _check(lib().pf_schedule(C.byref(d.desc), method, sz, *[_ptr(out[k], C.c_int32) for k in keys]))
+    return out
 
 
 # ----------------------------------------------------------------------------

@@ -257,3 +257,113 @@ def test_binding_structs_mirror_the_header(pf, cname, pyname):
 
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "pf.h")).read()
     assert [f for f, _ in getattr(pf, pyname)._fields_] == _c_struct_fields(hdr, cname)
+
+
+def _run_schedule(sch, col, rowptr, A):
+    """Executes the packed factor records level by level the way the kernels
+    do, every step reading the state before the step (so an item that reads
+    what another item of its own step writes gives a wrong factor), and
+    returns (factor blocks, inverse diagonal blocks)."""
+    FF = 1 << 30
+    LU = A.copy()
+    n, bs = rowptr.size - 1, A.shape[1]
+    uinv = np.zeros((n, bs, bs))
+    for l in range(sch["fac_ptr"].size - 1):
+        before = LU.copy()
+        for e, k, dg, _ in sch["fac_rec"][sch["fac_ptr"][l]:sch["fac_ptr"][l + 1]]:
+            inv = np.linalg.inv(before[dg])
+            if e == dg:
+                uinv[k] = inv
+            else:
+                LU[e] = before[e] @ inv
+        before = LU.copy()
+        for x, le, ue, rest in sch["tgt_rec"][sch["tgt_ptr"][l]:sch["tgt_ptr"][l + 1]]:
+            e = x & ~FF
+            if x & FF:
+                assert np.all(before[e] == 0.0)  # a fill entry's first update
+            c = np.zeros((bs, bs)) if x & FF else before[e].copy()
+            c -= before[le] @ before[ue]
+            q = rest
+            while q >= 0 and sch["con"][q][0] >= 0:
+                c -= before[sch["con"][q][0]] @ before[sch["con"][q][1]]
+                q += 1
+            LU[e] = c
+    return LU, uinv
+
+
+@pytest.mark.parametrize("name,method", [("14", 0), ("300", 0), ("feeder", 0), ("300", 1)])
+def test_packed_schedule_factors_and_solves(pf, name, method):
+    """The fan-out records the kernels run (pf_schedule), executed level by
+    level on the CPU with every step reading the state before it: Newton-
+    Raphson's records give the exact block LU of a random matrix on the
+    factor pattern (L U = A, fill entries starting from zero), Newton-
+    Krylov's the ILU(0) factor ((L U)_ij = A_ij on the pattern); the sweep
+    records, level by level, solve L U x = b."""
+    meth = pf.PF_NR if method == 0 else pf.PF_NK
+    case = {"14": cases.case_14bus(0), "300": cases.transmission_case(300, 405, 60, 2),
+            "feeder": cases.feeder_case(60, 3)}[name]
+    bs = 2 if isinstance(case, cases.SinglePhaseCase) else 6
+    perm, rowptr, col, _, _ = pf.pf_symbolic(case, meth)
+    sch = pf.pf_schedule(case, meth)
+    n = rowptr.size - 1
+    # the Ybus pattern in the new numbering: the entries that are not fill
+    import ctypes as C
+
+    st = pf.pf_analyze(case)
+    yrp = np.zeros(n + 1, np.int32)
+    ycol = np.zeros(st["nnz_y"], np.int32)
+    d = pf.make_desc(case)
+    nz = C.c_int64()
+    vals = np.zeros(st["nnz_y"] * (2 if bs == 2 else 18))
+    pf.lib().pf_ybus(C.byref(d.desc), C.byref(nz), yrp.ctypes.data_as(C.POINTER(C.c_int32)),
+                     ycol.ctypes.data_as(C.POINTER(C.c_int32)),
+                     vals.ctypes.data_as(C.POINTER(C.c_double)))
+    inv = np.empty(n, int)
+    inv[perm] = np.arange(n)
+    ypat = {(inv[i], inv[j]) for i in range(n) for j in ycol[yrp[i]:yrp[i + 1]]}
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    rng = np.random.default_rng(3)
+    A = rng.uniform(-1, 1, (col.size, bs, bs))
+    for e in range(col.size):
+        if (rows[e], col[e]) not in ypat:
+            A[e] = 0.0  # fill
+        elif rows[e] == col[e]:
+            A[e] += 4.0 * bs * np.eye(bs)
+    LU, uinv = _run_schedule(sch, col, rowptr, A)
+    Ad = np.zeros((n * bs, n * bs))
+    Ld = np.eye(n * bs)
+    Ud = np.zeros((n * bs, n * bs))
+    for e in range(col.size):
+        i, j = rows[e], col[e]
+        blk = (slice(i * bs, i * bs + bs), slice(j * bs, j * bs + bs))
+        Ad[blk] = A[e]
+        if j < i:
+            Ld[blk] = LU[e]
+        else:
+            Ud[blk] = LU[e]
+    for k in range(n):
+        dk = rowptr[k] + np.flatnonzero(col[rowptr[k]:rowptr[k + 1]] == k)[0]
+        assert np.allclose(uinv[k] @ LU[dk], np.eye(bs), atol=1e-12)
+    P = Ld @ Ud
+    if meth == pf.PF_NR:
+        assert np.max(np.abs(P - Ad)) <= 1e-11 * np.max(np.abs(Ad))
+    else:
+        mask = np.zeros_like(Ad, dtype=bool)
+        for e in range(col.size):
+            i, j = rows[e], col[e]
+            mask[i * bs:i * bs + bs, j * bs:j * bs + bs] = True
+        assert np.max(np.abs((P - Ad)[mask])) <= 1e-11 * np.max(np.abs(Ad))
+    # the sweeps, level by level, each level reading the vector before it
+    b = rng.uniform(-1, 1, (n, bs))
+    y = b.copy()
+    for l in range(sch["flev_ptr"].size - 1):
+        before = y.copy()
+        for i, p0, p1, _ in sch["fwd_rec"][sch["flev_ptr"][l]:sch["flev_ptr"][l + 1]]:
+            y[i] = before[i] - sum((LU[p] @ before[col[p]] for p in range(p0, p1)), np.zeros(bs))
+    for l in range(sch["blev_ptr"].size - 1):
+        before = y.copy()
+        for i, p0, p1, _ in sch["bwd_rec"][sch["blev_ptr"][l]:sch["blev_ptr"][l + 1]]:
+            acc = before[i] - sum((LU[p] @ before[col[p]] for p in range(p0, p1)), np.zeros(bs))
+            y[i] = uinv[i] @ acc
+    x = y.reshape(-1)
+    assert np.max(np.abs(P @ x - b.reshape(-1))) <= 1e-10
