@@ -29,3 +29,27 @@ def test_scope_bytes_per_unit():
     assert b["k_solve"] == 60 * 4 * 4 + 3 * 22 * 4
     assert b["k_update"] == 14 * 40
     assert b["k_mismatch"] == 54 * 20 + 4 * 15 + 14 * 48 + bench.jacobian_nnz(case) * 4
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores, one
+    bounded sample per step) prints one JSON line with the keys the driver
+    reads, on the workload and metric of the GPU arm."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "solves/s" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] >= 3
+    assert f"x {bench.B_MAIN} load scenarios" in line["config"]["workload"]
+    for k in ("cpu_baseline", "e2e"):
+        assert k in line
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
